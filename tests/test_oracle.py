@@ -1,0 +1,347 @@
+"""Pins for the CPU oracle against facts fixed by the paper and by mathematics.
+
+Nothing here compares the oracle with itself: every check is a worked example
+(Fig. 1), a closed form, a textbook special case, an independent brute-force
+algorithm that recomputes distances from the points, or an invariant the
+paper proves.  ``test_pins_catch_mutants`` shows the pins are sensitive by
+planting plausible mistakes in a copy of the oracle source.
+"""
+import itertools
+import json
+import math
+import os
+import subprocess
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2106_04727_gb300 import inputs
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+LKS = ["complete", "average", "ward"]
+
+
+def _fig1():
+    with open(os.path.join(GOLDEN, "fig1_six_points.json")) as f:
+        return json.load(f)
+
+
+# ---------------------------------------------------------------------------
+# Worked example: Fig. 1 / Section 1
+# ---------------------------------------------------------------------------
+
+def test_fig1_round_structure():
+    g = _fig1()
+    X = np.array(g["points"], dtype=np.float64)
+    r = oracle.rounds(X, g["linkage"], log_terminals=True)
+    assert r["n_rounds"] == g["n_rounds"]
+    got = {}
+    for a, b, rr in zip(r["a"], r["b"], r["round"]):
+        got.setdefault(int(rr), set()).add((int(a), int(b)))
+    want = {i: {tuple(p) for p in ms} for i, ms in enumerate(g["round_merges"])}
+    assert got == want
+    terms = {}
+    for rr, c in r["terminals"]:
+        terms.setdefault(int(rr), set()).add(int(c))
+    assert terms == {i: set(t) for i, t in enumerate(g["round_terminals"])}
+    # f (index 5) does no search in round 2 (index 1)
+    assert 5 not in terms[1]
+
+
+def test_fig1_heights_and_chain():
+    g = _fig1()
+    X = np.array(g["points"], dtype=np.float64)
+    for fn in (oracle.nnchain, oracle.rounds, oracle.greedy):
+        d = fn(X, g["linkage"])
+        m = oracle.as_map(d)
+        assert set(m) == {tuple(map(int, k.split(","))) for k in g["squared_heights"]}
+        for k, h2 in g["squared_heights"].items():
+            key = tuple(map(int, k.split(",")))
+            assert m[key][0] == math.sqrt(h2)  # exact: integer coordinates
+    # first-round successors from brute-force point NN with the (d, cid) key
+    D = ((X[:, None, :] - X[None, :, :]) ** 2).sum(-1)
+    np.fill_diagonal(D, np.inf)
+    for i, j in g["first_round_successor"].items():
+        i = int(i)
+        best = min(range(6), key=lambda t: (D[i, t], t))
+        assert best == j
+
+
+# ---------------------------------------------------------------------------
+# Closed forms and special cases
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("lk", LKS)
+def test_two_points(lk):
+    X = np.array([[0.5, -1.0, 2.0], [3.5, 3.0, 2.0]])
+    for fn in (oracle.nnchain, oracle.rounds, oracle.greedy):
+        d = fn(X, lk)
+        assert list(d["a"]) == [0] and list(d["b"]) == [1] and list(d["size"]) == [2]
+        assert d["h"][0] == pytest.approx(5.0, rel=1e-15)
+
+
+@pytest.mark.parametrize("lk", LKS)
+def test_single_point(lk):
+    d = oracle.nnchain(np.zeros((1, 2)), lk)
+    assert len(d["a"]) == 0
+
+
+@pytest.mark.parametrize("lk", LKS)
+def test_collinear_equally_spaced(lk):
+    """16 points 0, h, 2h, ...: ties everywhere; the (D, cid) key merges
+    neighbours pairwise, then pairs of pairs, ... (a balanced tree).  Merging
+    two blocks of s points at centroid spacing s*h gives complete (2s-1)h,
+    average s*h and Ward sqrt(2 s^2/(2s) (s h)^2) = s^1.5 h."""
+    m, hsp = 16, 0.5
+    X = np.zeros((m, 3))
+    X[:, 1] = hsp * np.arange(m)
+    want = {}
+    s = 1
+    while s < m:
+        for start in range(0, m, 2 * s):
+            if lk == "complete":
+                h = (2 * s - 1) * hsp
+            elif lk == "average":
+                h = s * hsp
+            else:
+                h = s ** 1.5 * hsp
+            want[(start, start + s)] = (h, 2 * s)
+        s *= 2
+    for fn in (oracle.nnchain, oracle.rounds, oracle.greedy):
+        got = oracle.as_map(fn(X, lk))
+        assert set(got) == set(want), fn.__name__
+        for k in want:
+            assert got[k][1] == want[k][1]
+            assert got[k][0] == pytest.approx(want[k][0], rel=1e-13)
+
+
+@pytest.mark.parametrize("lk", LKS)
+def test_all_duplicates(lk):
+    """All points equal: every height is 0 and the key (0, min cid, max cid)
+    always picks cluster 0 with the next index."""
+    n = 9
+    X = np.tile([[1.25, -3.0]], (n, 1))
+    for fn in (oracle.nnchain, oracle.rounds, oracle.greedy):
+        d = oracle.canonical(fn(X, lk))
+        assert list(d["a"]) == [0] * (n - 1)
+        assert list(d["b"]) == list(range(1, n))
+        assert list(d["size"]) == list(range(2, n + 1))
+        assert np.all(d["h"] == 0.0)
+    r = oracle.rounds(X, lk)
+    assert r["n_rounds"] == n - 1   # one merge per round on a full tie
+
+
+def test_ward_singletons_are_euclidean():
+    rng = np.random.default_rng(5)
+    A, B = rng.normal(size=(1, 4)), rng.normal(size=(1, 4))
+    assert oracle.cluster_dist("ward", A, B) == pytest.approx(np.linalg.norm(A - B), rel=1e-15)
+
+
+def test_ward_closed_form_variance_increase():
+    """Table 1: Ward = sqrt(2 (Var(A u B) - Var(A) - Var(B)))."""
+    rng = np.random.default_rng(6)
+    for _ in range(20):
+        A = rng.normal(size=(rng.integers(1, 9), 3))
+        B = rng.normal(size=(rng.integers(1, 9), 3)) + 2.0
+        var = lambda P: ((P - P.mean(0)) ** 2).sum()
+        want = math.sqrt(2 * (var(np.vstack([A, B])) - var(A) - var(B)))
+        assert oracle.cluster_dist("ward", A, B) == pytest.approx(want, rel=1e-11)
+
+
+@pytest.mark.parametrize("lk", LKS)
+def test_lance_williams_matches_definition(lk):
+    """Table 2 update of D(A u B, C) equals the Table 1 definition recomputed
+    from the points (squared distances for Ward)."""
+    rng = np.random.default_rng(7)
+    for _ in range(50):
+        A, B, C = (rng.normal(size=(rng.integers(1, 7), 2)) * rng.uniform(0.1, 3)
+                   + rng.normal(size=2) * 3 for _ in range(3))
+        f = (lambda P, Q: oracle.cluster_dist(lk, P, Q) ** 2) if lk == "ward" else \
+            (lambda P, Q: oracle.cluster_dist(lk, P, Q))
+        got = oracle.lw(lk, f(A, C), f(B, C), f(A, B), len(A), len(B), len(C))
+        want = f(np.vstack([A, B]), C)
+        assert got == pytest.approx(want, rel=1e-11, abs=1e-12)
+
+
+def test_lance_williams_complete_coefficients():
+    """a1 = a2 = c = 1/2, b = 0 reproduces the max."""
+    for x, y in [(1.0, 2.0), (3.0, 0.5), (2.0, 2.0)]:
+        lw = 0.5 * x + 0.5 * y + 0.5 * abs(x - y)
+        assert oracle.lw("complete", x, y, 7.0, 3, 4, 5) == lw == max(x, y)
+
+
+def test_centroid_lower_bound():
+    """Section 4.2 proof: ||c_A - c_B|| <= D_avg(A,B) <= D_comp(A,B)."""
+    rng = np.random.default_rng(8)
+    for _ in range(100):
+        A = rng.normal(size=(rng.integers(1, 12), 3))
+        B = rng.normal(size=(rng.integers(1, 12), 3)) + rng.normal(size=3)
+        c = np.linalg.norm(A.mean(0) - B.mean(0))
+        avg = oracle.cluster_dist("average", A, B)
+        comp = oracle.cluster_dist("complete", A, B)
+        assert c <= avg * (1 + 1e-12) and avg <= comp * (1 + 1e-12)
+
+
+def test_ward_radius_soundness():
+    """Section 4.1: if Ward(Ci, B) <= beta then ||c_i - c_B|| <= beta *
+    sqrt((|Ci| + n_min) / (2 n_min |Ci|)) for any |B| >= n_min."""
+    rng = np.random.default_rng(9)
+    for _ in range(200):
+        A = rng.normal(size=(rng.integers(1, 10), 2))
+        B = rng.normal(size=(rng.integers(1, 10), 2)) * 0.5 + rng.normal(size=2)
+        nmin = rng.integers(1, len(B) + 1)
+        beta = oracle.cluster_dist("ward", A, B) * rng.uniform(1.0, 1.5)
+        r = beta * math.sqrt((len(A) + nmin) / (2.0 * nmin * len(A)))
+        assert np.linalg.norm(A.mean(0) - B.mean(0)) <= r * (1 + 1e-12)
+
+
+# ---------------------------------------------------------------------------
+# Independent brute force and invariants
+# ---------------------------------------------------------------------------
+
+def _random_sets():
+    for seed in range(6):
+        n = [2, 3, 7, 23, 64, 97][seed]
+        yield f"uniform{n}", inputs.uniform_cube(n, 2, seed=100 + seed)
+        yield f"gmm{n}", inputs.gaussian_mixture(n, 3, 4, seed=200 + seed).astype(np.float64)
+
+
+@pytest.mark.parametrize("lk", LKS)
+def test_nnchain_equals_bruteforce(lk):
+    for name, X in _random_sets():
+        want = oracle.greedy(X, lk)
+        for fn in (oracle.nnchain, oracle.rounds):
+            got = fn(X, lk)
+            c = oracle.compare(got, want, rtol=1e-12)
+            assert c["ok"], (name, fn.__name__, c)
+            assert oracle.check_tree(got, len(X)) == []
+
+
+@pytest.mark.parametrize("lk", LKS)
+def test_start_independence(lk):
+    X = inputs.gaussian_mixture(150, 2, 5, seed=11).astype(np.float64)
+    base = oracle.nnchain(X, lk, start=0)
+    for st in (1, 37, 149):
+        c = oracle.compare(oracle.nnchain(X, lk, start=st), base, rtol=1e-12)
+        assert c["same_tree"], (st, c)
+
+
+def test_lattice_complete_exact_ties():
+    """On a coarse lattice every complete-linkage value is sqrt of an exact
+    FP64 integer multiple of the step^2, so ties are exact and the Lance-
+    Williams matrix and the brute force must agree merge for merge."""
+    for seed in range(4):
+        X = inputs.lattice(60, 3, seed=seed, levels=6).astype(np.float64)
+        want = oracle.greedy(X, "complete")
+        for fn in (oracle.nnchain, oracle.rounds):
+            c = oracle.compare(fn(X, "complete"), want, rtol=0.0)
+            assert c["ok"], (seed, fn.__name__, c)
+
+
+@pytest.mark.parametrize("lk", ["average", "ward"])
+def test_lattice_ties_validate(lk):
+    """With exact real ties, average/Ward values from different rounding
+    orders may break ties differently (and a different early choice changes
+    later heights); both trees must still be valid greedy dendrograms."""
+    for seed in range(3):
+        X = inputs.lattice(50, 3, seed=seed, levels=5).astype(np.float64)
+        a, b = oracle.nnchain(X, lk), oracle.greedy(X, lk)
+        for d in (a, b):
+            bad, stats = oracle.validate(X, lk, d, rtol=1e-9)
+            assert bad == 0, (seed, stats)
+
+
+@pytest.mark.parametrize("lk", LKS)
+def test_validate_detects_planted_errors(lk):
+    X = inputs.uniform_cube(40, 2, seed=3)
+    d = oracle.nnchain(X, lk)
+    assert oracle.validate(X, lk, d)[0] == 0
+    bad = {k: v.copy() for k, v in d.items()}
+    i = int(np.argmax(bad["h"] > np.median(bad["h"])))
+    bad["h"][i] *= 1.01
+    assert oracle.validate(X, lk, bad)[0] != 0
+    # a tree built for another linkage is (generically) not valid for this one
+    other = oracle.nnchain(X, {"complete": "ward", "average": "complete", "ward": "average"}[lk])
+    assert oracle.validate(X, lk, other)[0] != 0
+
+
+@pytest.mark.parametrize("lk", LKS)
+def test_rounds_monotone_and_tree(lk):
+    X = inputs.gaussian_mixture(300, 2, 6, seed=21).astype(np.float64)
+    r = oracle.rounds(X, lk)
+    assert oracle.check_tree(r, len(X)) == []
+    assert r["round"].max() == r["n_rounds"] - 1
+    # per round, merged clusters are disjoint (each cid appears at most once)
+    for rr in range(r["n_rounds"]):
+        sel = r["round"] == rr
+        ids = np.concatenate([r["a"][sel], r["b"][sel]])
+        assert len(ids) == len(set(ids.tolist())) and sel.sum() >= 1
+
+
+def test_scipy_crosscheck():
+    """scipy's NN-chain / generic implementations (run, not copied) as a
+    third-party check on heights and tree for all three linkages."""
+    sch = pytest.importorskip("scipy.cluster.hierarchy")
+    X = inputs.gaussian_mixture(200, 3, 5, seed=31).astype(np.float64)
+    n = len(X)
+    for lk in LKS:
+        Z = sch.linkage(X, method=lk)
+        cid = list(range(n))
+        m = {}
+        for i, (p, q, h, cnt) in enumerate(Z):
+            a, b = cid[int(p)], cid[int(q)]
+            m[(min(a, b), max(a, b))] = (float(h), int(cnt))
+            cid.append(min(a, b))
+        got = oracle.as_map(oracle.nnchain(X, lk))
+        assert set(got) == set(m), lk
+        for k in m:
+            assert got[k][1] == m[k][1]
+            assert got[k][0] == pytest.approx(m[k][0], rel=1e-10)
+
+
+# ---------------------------------------------------------------------------
+# Mutation check: plausible oracle mistakes are caught by the pins above
+# ---------------------------------------------------------------------------
+
+MUTANTS = {
+    "ward_b_sign": ("- nc * dab) / (na + nb + nc)", "+ nc * dab) / (na + nb + nc)"),
+    "ward_a1_uses_nb": ("return ((na + nc) * dac", "return ((nb + nc) * dac"),
+    "avg_weights_swapped": ("return (na * dac + nb * dbc) / (na + nb);",
+                            "return (nb * dac + na * dbc) / (na + nb);"),
+    "complete_min": ("return fmax(dac, dbc);", "return fmin(dac, dbc);"),
+    "tie_prefers_larger_cid": ("if (best < 0 || v < bd) {", "if (best < 0 || v <= bd) {"),
+    "ward_not_squared": ("if (linkage == LK_WARD) return point_dist2(",
+                         "if (linkage == LK_WARD) return point_dist("),
+}
+
+
+@pytest.mark.parametrize("mut", sorted(MUTANTS))
+def test_pins_catch_mutants(mut, tmp_path):
+    import ctypes
+    src = open(os.path.join(os.path.dirname(oracle.__file__), "hac_oracle.c")).read()
+    old, new = MUTANTS[mut]
+    assert src.count(old) == 1
+    path = tmp_path / "m.c"
+    path.write_text(src.replace(old, new))
+    so = tmp_path / "m.so"
+    subprocess.check_call(["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-shared", "-fPIC",
+                           "-o", str(so), str(path), "-lm"])
+    lib = ctypes.CDLL(str(so))
+    P, i64 = ctypes.c_void_p, ctypes.c_int64
+    lib.oracle_nnchain.argtypes = [P, i64, ctypes.c_int, ctypes.c_int, i64, P, P, P, P]
+    caught = False
+    cases = list(_random_sets()) + [("dups", np.tile([[0.0, 1.0]], (5, 1))),
+                                    ("collinear", np.c_[np.arange(8.0), np.zeros(8)])]
+    for lk, (name, X) in itertools.product(range(3), cases):
+        X = np.ascontiguousarray(X, dtype=np.float64)
+        n = len(X)
+        a, b, h, s = (np.zeros(n - 1, np.int64), np.zeros(n - 1, np.int64),
+                      np.zeros(n - 1), np.zeros(n - 1, np.int64))
+        p = lambda v: v.ctypes.data_as(P)
+        lib.oracle_nnchain(p(X), n, X.shape[1], lk, 0, p(a), p(b), p(h), p(s))
+        got = dict(a=a, b=b, h=h, size=s)
+        if not oracle.compare(got, oracle.greedy(X, lk), rtol=1e-9)["ok"]:
+            caught = True
+            break
+    assert caught, mut
