@@ -1,0 +1,147 @@
+/*
+ * hac.h -- C ABI of the GB300 nearest-neighbor-chain HAC library.
+ *
+ * The library computes the exact hierarchical agglomerative clustering
+ * dendrogram of n points in d <= 16 dimensions under complete, average
+ * (Euclidean, "avg-1") or Ward linkage (ParChain, arXiv 2106.04727, Table 1),
+ * with the parallel nearest-neighbor-chain rounds of Algorithm 1: every round,
+ * each terminal cluster finds its nearest active cluster (Algorithms 2-4,
+ * range-pruned), all reciprocal-nearest-neighbor pairs merge at once, and the
+ * cluster state is refreshed.  All compute runs in the library's own sm_103a
+ * CUDA kernels on the current CUDA device; there is no CPU fallback.
+ *
+ * Conventions (fixed by the paper, Section 1 footnote and Fig. 1 caption):
+ *   - a cluster's id (cid) is the smallest input index among its points;
+ *     a merged cluster keeps min(cid_a, cid_b);
+ *   - ties are broken lexicographically: a cluster's nearest neighbour is the
+ *     candidate of least (distance, cid).
+ *
+ * Errors: every int-returning call returns HAC_OK (0) or a negative HAC_E*
+ * code; hac_strerror() names it.  No call aborts the process.  A call that
+ * fails leaves the handle usable unless it returns HAC_EDEVICE (then only
+ * hac_destroy is valid).
+ *
+ * Threading: one handle must not be used by two host threads at once;
+ * distinct handles are independent.
+ */
+#ifndef HAC_H_
+#define HAC_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* status codes */
+#define HAC_OK 0
+#define HAC_EINVAL (-1)    /* bad argument: null pointer, n < 1, d outside 1..16,
+                              non-finite coordinate, unknown enum value */
+#define HAC_ENOMEM (-2)    /* device or host allocation failed */
+#define HAC_EDEVICE (-3)   /* a CUDA call failed; the handle is unusable */
+#define HAC_ETIMEOUT (-4)  /* opts->timeout_s or opts->max_rounds reached */
+#define HAC_EPENDING (-5)  /* no dendrogram yet: hac_run has not completed */
+#define HAC_ECAP (-6)      /* output buffer smaller than n - 1 records */
+#define HAC_EINTERNAL (-7) /* an internal consistency check failed */
+
+typedef struct hac_ctx *hac_t; /* opaque; owns all device memory of one instance */
+
+typedef enum { HAC_COMPLETE = 0, HAC_AVERAGE = 1, HAC_WARD = 2 } hac_linkage;
+typedef enum { HAC_F32 = 0, HAC_F64 = 1 } hac_dtype;
+typedef enum {
+  HAC_PREC_F64 = 0,         /* every distance in FP64 */
+  HAC_PREC_F32_RECHECK = 1  /* bulk distances in FP32; candidates within the
+                               stated FP32 error bound of the minimum are
+                               re-scored in FP64, so nearest neighbours (and
+                               hence the tree) are the FP64 ones */
+} hac_precision;
+
+/* One dendrogram node: clusters cid_a < cid_b merged at `height` into a
+ * cluster of `size` points (Algorithm 1, merge step). */
+typedef struct {
+  int64_t cid_a;
+  int64_t cid_b;
+  double height;
+  int64_t size;
+} hac_merge;
+
+typedef struct {
+  int precision;      /* hac_precision; default HAC_PREC_F64 */
+  int cache_slots;    /* per-cluster pair-distance cache slots (Section 5); 0 = off */
+  int64_t max_rounds; /* 0 = unlimited; else HAC_ETIMEOUT after this many rounds */
+  double timeout_s;   /* 0 = none; else HAC_ETIMEOUT once exceeded (checked per round) */
+  void *stream;       /* cudaStream_t to run on; NULL = the handle's own stream */
+} hac_opts;
+
+typedef struct {
+  int64_t rounds;            /* rounds of Algorithm 1 executed */
+  int64_t merges;            /* merges made (n - 1 when complete) */
+  int64_t nn_searches;       /* terminal nearest-neighbour searches, summed over rounds */
+  int64_t cluster_pairs;     /* cluster-pair distance evaluations */
+  int64_t point_pairs;       /* point-pair distance evaluations (the paper's D) */
+  int64_t nodes_visited;     /* range-query tree nodes tested */
+  int64_t rechecks;          /* FP64 re-scores made in HAC_PREC_F32_RECHECK mode */
+  double ms_init;            /* layout + index build (Algorithm 1 initialisation) */
+  double ms_nn;              /* nearest-neighbour search + chain update */
+  double ms_merge;           /* reciprocal-pair filter + merges */
+  double ms_update;          /* active/terminal refresh, point re-layout, index rebuild */
+  double ms_total;           /* whole hac_run */
+  int64_t device_bytes;      /* device memory held by the handle */
+  double ms_query;           /* device time of the nearest-neighbour search kernel
+                                alone (CUDA events around each launch) */
+  int64_t query_launches;    /* launches of that kernel */
+  int64_t query_bytes;       /* algorithmic bytes that kernel had to read: tree nodes
+                                tested, leaf slots scanned, cluster records and point
+                                rows of evaluated pairs (each counted once per use) */
+  int64_t leaf_tests;        /* candidate clusters tested against the search ball */
+  int64_t kernel_launches;   /* all kernels the library launched in the run */
+} hac_stats_t;
+
+/* Default options (FP64, no cache, no limits, own stream). */
+void hac_default_opts(hac_opts *opts);
+
+/* Create an instance from HOST points: `points` is row-major n x d of type
+ * `dt` (float or double), read during the call and not retained.  Allocates
+ * all device memory the instance needs; the points are copied to the device.
+ * HAC_EINVAL: points/out NULL, n < 1, d < 1 or d > 16, unknown dt/lk, or a
+ * non-finite coordinate.  HAC_ENOMEM: device allocation failed. */
+int hac_create(const void *points, int64_t n, int d, hac_dtype dt, hac_linkage lk, hac_t *out);
+
+/* As hac_create, but `dev_points` is a DEVICE pointer (row-major n x d of
+ * `dt`, on the current device) that the caller keeps owning; it is copied
+ * device-to-device during the call.  Non-finite coordinates are reported by
+ * hac_run as HAC_EINVAL. */
+int hac_create_device(const void *dev_points, int64_t n, int d, hac_dtype dt, hac_linkage lk,
+                      hac_t *out);
+
+/* Run the whole clustering (initial layout, then rounds until one cluster is
+ * left).  opts may be NULL (defaults).  Blocks until done.  May be called
+ * again on the same handle: each call recomputes from the stored points.
+ * HAC_ETIMEOUT if a limit in opts is hit (the handle stays usable). */
+int hac_run(hac_t h, const hac_opts *opts);
+
+/* Copy the n-1 merges of the last completed hac_run to host array `out`
+ * (capacity `cap` records), sorted by (height, size, cid_a).  *n_written
+ * receives the count.  HAC_EPENDING before a completed run, HAC_ECAP if
+ * cap < n - 1. */
+int hac_dendrogram(hac_t h, hac_merge *out, int64_t cap, int64_t *n_written);
+
+/* The round (0-based) in which each merge of hac_dendrogram's output was
+ * made, in the same order.  Same errors as hac_dendrogram. */
+int hac_merge_rounds(hac_t h, int32_t *out, int64_t cap, int64_t *n_written);
+
+/* Counters and phase times of the last hac_run. */
+int hac_stats(hac_t h, hac_stats_t *out);
+
+/* Free the instance and all its device memory.  NULL is a no-op. */
+void hac_destroy(hac_t h);
+
+/* Static description of a status code. */
+const char *hac_strerror(int code);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HAC_H_ */

@@ -1,0 +1,1085 @@
+// GB300 nearest-neighbor-chain HAC: initial layout, the per-round kernels of
+// ParChain Algorithm 1 around the nearest-neighbour search, and the C ABI.
+//
+// Round r (Algorithm 1):
+//   find_nearest_neighbors      k_query (hac_query.cu), one warp per terminal
+//   succ / WriteMin(pred)       k_chain: packed (f32 key, cid) 64-bit atomicMin
+//   R-NN parallel filter        k_rnn: terminal i with succ(succ(i)) == i
+//   merge                       k_merge: size, FP64 coordinate sums, box union
+//   D.update / active / terms   k_cmp_*: chain repair, stable compaction of the
+//                               active order, new terminal list, new segment
+//                               offsets; k_relayout moves points so every
+//                               cluster stays one contiguous segment;
+//                               k_tree_*: rebuild the range-query tree
+#include "hac.h"
+#include "hac_internal.cuh"
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <vector>
+
+using namespace hacg;
+
+namespace {
+
+constexpr int TPB = 256;
+
+enum { LK_COMPLETE = 0, LK_AVERAGE = 1, LK_WARD = 2 };
+
+__host__ __device__ inline int cdiv(long long a, long long b) { return (int)((a + b - 1) / b); }
+
+// ---------------------------------------------------------------------------
+// block-wide helpers (256 threads)
+// ---------------------------------------------------------------------------
+
+// exclusive scan of one int per thread; returns the block total in *total
+__device__ int block_excl_scan(int v, int *total) {
+  __shared__ int ws[TPB / 32];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  int x = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    int y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) ws[w] = x;
+  __syncthreads();
+  if (w == 0) {
+    int t = lane < TPB / 32 ? ws[lane] : 0;
+#pragma unroll
+    for (int o = 1; o < TPB / 32; o <<= 1) {
+      int y = __shfl_up_sync(0xffffffffu, t, o);
+      if (lane >= o) t += y;
+    }
+    if (lane < TPB / 32) ws[lane] = t;
+  }
+  __syncthreads();
+  const int pre = w ? ws[w - 1] : 0;
+  *total = ws[TPB / 32 - 1];
+  __syncthreads();
+  return pre + x - v;
+}
+
+__device__ int block_sum(int v) {
+  int t;
+  block_excl_scan(v, &t);
+  return t;
+}
+
+// ---------------------------------------------------------------------------
+// generic exclusive scan of an int array (3 phases)
+// ---------------------------------------------------------------------------
+constexpr int SC_ITEMS = 8, SC_TILE = TPB * SC_ITEMS;
+
+__global__ void k_scan_reduce(const int32_t *in, int m, int32_t *bs) {
+  int s = 0;
+  const int base = blockIdx.x * SC_TILE;
+  for (int i = threadIdx.x; i < SC_TILE; i += TPB)
+    if (base + i < m) s += in[base + i];
+  s = block_sum(s);
+  if (threadIdx.x == 0) bs[blockIdx.x] = s;
+}
+
+// one block: exclusive scan of `nb` values in place; total to *tot
+__global__ void k_scan_top(int32_t *bs, int nb, int32_t *tot) {
+  const int per = cdiv(nb, TPB);
+  const int b0 = threadIdx.x * per;
+  int s = 0;
+  for (int i = 0; i < per; ++i)
+    if (b0 + i < nb) s += bs[b0 + i];
+  int t;
+  int pre = block_excl_scan(s, &t);
+  for (int i = 0; i < per; ++i)
+    if (b0 + i < nb) {
+      int v = bs[b0 + i];
+      bs[b0 + i] = pre;
+      pre += v;
+    }
+  if (threadIdx.x == 0 && tot) *tot = t;
+}
+
+__global__ void k_scan_down(const int32_t *in, int32_t *out, int m, const int32_t *bs) {
+  const int base = blockIdx.x * SC_TILE + threadIdx.x * SC_ITEMS;
+  int v[SC_ITEMS];
+  int s = 0;
+#pragma unroll
+  for (int i = 0; i < SC_ITEMS; ++i) {
+    v[i] = base + i < m ? in[base + i] : 0;
+    s += v[i];
+  }
+  int t;
+  int pre = block_excl_scan(s, &t) + bs[blockIdx.x];
+#pragma unroll
+  for (int i = 0; i < SC_ITEMS; ++i) {
+    if (base + i < m) out[base + i] = pre;
+    pre += v[i];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// LSD radix sort of (u64 key, i32 value), 8-bit digits, stable
+// ---------------------------------------------------------------------------
+constexpr int RS_ITEMS = 8, RS_TILE = TPB * RS_ITEMS;
+
+__global__ void k_rs_hist(const uint64_t *keys, int n, int shift, int32_t *hist, int ntiles) {
+  __shared__ int h[256];
+  h[threadIdx.x] = 0;
+  __syncthreads();
+  const int base = blockIdx.x * RS_TILE;
+  for (int i = threadIdx.x; i < RS_TILE; i += TPB)
+    if (base + i < n) atomicAdd(&h[(keys[base + i] >> shift) & 255], 1);
+  __syncthreads();
+  hist[threadIdx.x * ntiles + blockIdx.x] = h[threadIdx.x];
+}
+
+__global__ void k_rs_scatter(const uint64_t *kin, const int32_t *vin, uint64_t *kout,
+                             int32_t *vout, int n, int shift, const int32_t *hscan, int ntiles) {
+  __shared__ int run[256];
+  __shared__ int wcnt[TPB / 32][257];
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  run[tid] = hscan[tid * ntiles + blockIdx.x];
+  const int base = blockIdx.x * RS_TILE;
+  for (int c = 0; c < RS_ITEMS; ++c) {
+    for (int i = tid; i < (TPB / 32) * 257; i += TPB) (&wcnt[0][0])[i] = 0;
+    __syncthreads();
+    const int p = base + c * TPB + tid;
+    const bool v = p < n;
+    const uint64_t k = v ? kin[p] : 0;
+    const int val = v ? vin[p] : 0;
+    const int dig = v ? (int)((k >> shift) & 255) : 256;
+    const unsigned peers = __match_any_sync(0xffffffffu, dig);
+    const int rank = __popc(peers & ((1u << lane) - 1u));
+    if (rank == 0) wcnt[w][dig] = __popc(peers);
+    __syncthreads();
+    if (v) {
+      int off = run[dig];
+      for (int ww = 0; ww < w; ++ww) off += wcnt[ww][dig];
+      kout[off + rank] = k;
+      vout[off + rank] = val;
+    }
+    __syncthreads();
+    int s = 0;
+    for (int ww = 0; ww < TPB / 32; ++ww) s += wcnt[ww][tid];
+    run[tid] += s;
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------------------
+// init: bounding box, Morton keys, layout
+// ---------------------------------------------------------------------------
+
+// order-preserving map of doubles to u64 (for atomicMin/Max)
+__device__ __forceinline__ unsigned long long ord_enc(double x) {
+  unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  return (b >> 63) ? ~b : (b | 0x8000000000000000ull);
+}
+
+template <typename T>
+__global__ void k_bbox(const T *X, int64_t n, int d, unsigned long long *mn,
+                       unsigned long long *mx, Counters *ctr) {
+  double lo[MAXD], hi[MAXD];
+  for (int k = 0; k < d; ++k) {
+    lo[k] = INFINITY;
+    hi[k] = -INFINITY;
+  }
+  bool bad = false;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    for (int k = 0; k < d; ++k) {
+      double x = (double)X[i * d + k];
+      if (!isfinite(x)) bad = true;
+      lo[k] = fmin(lo[k], x);
+      hi[k] = fmax(hi[k], x);
+    }
+  if (bad) atomicOr(&ctr->err, ERR_NONFINITE);
+  for (int k = 0; k < d; ++k) {
+    double a = lo[k], b = hi[k];
+    for (int o = 16; o; o >>= 1) {
+      a = fmin(a, __shfl_xor_sync(0xffffffffu, a, o));
+      b = fmax(b, __shfl_xor_sync(0xffffffffu, b, o));
+    }
+    if ((threadIdx.x & 31) == 0) {
+      atomicMin(mn + k, ord_enc(a));
+      atomicMax(mx + k, ord_enc(b));
+    }
+  }
+}
+
+struct MortonParams {
+  double lo[MAXD], inv[MAXD];
+  int bits;
+};
+
+template <typename T>
+__global__ void k_morton(const T *X, int64_t n, int d, MortonParams mp, uint64_t *keys,
+                         int32_t *vals) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    uint32_t q[MAXD];
+    const double top = (double)((1u << mp.bits) - 1u);
+    for (int k = 0; k < d; ++k) {
+      double t = ((double)X[i * d + k] - mp.lo[k]) * mp.inv[k];
+      t = fmin(fmax(t, 0.0), 1.0) * top;
+      q[k] = (uint32_t)t;
+    }
+    uint64_t code = 0;
+    for (int b = mp.bits - 1; b >= 0; --b)
+      for (int k = 0; k < d; ++k) code = (code << 1) | ((q[k] >> b) & 1u);
+    keys[i] = code;
+    vals[i] = (int32_t)i;
+  }
+}
+
+template <typename T>
+__global__ void k_layout(State s, const T *X, const int32_t *perm, MortonParams ctr_) {
+  // ctr_.lo holds the recentring offset
+  const int64_t n = s.n;
+  const int d = s.d, dp = s.dp;
+  for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n;
+       p += (int64_t)gridDim.x * blockDim.x) {
+    const int i = perm[p];
+    for (int k = 0; k < dp; ++k) {
+      double x = k < d ? (double)X[(int64_t)i * d + k] - ctr_.lo[k] : 0.0;
+      s.p64[0][p * dp + k] = x;
+      s.p32[0][p * dp + k] = (float)x;
+      s.csum[(int64_t)i * dp + k] = x;
+      s.cent[(int64_t)i * dp + k] = x;
+      s.cent32[(int64_t)i * dp + k] = (float)x;
+      s.blo[(int64_t)i * dp + k] = __double2float_rd(x);
+      s.bhi[(int64_t)i * dp + k] = __double2float_ru(x);
+    }
+    s.plab[0][p] = i;
+    s.seg[0][i] = (int32_t)p;
+    s.csize[i] = 1;
+    s.succ[i] = -1;
+    s.pred[i] = PRED_EMPTY;
+    s.mround[i] = -1;
+    s.isterm[i] = 0;
+    s.alive[i] = 1;
+    s.rootof[i] = i;
+    s.reloff[i] = 0;
+    s.order[0][p] = i;
+    s.pos[i] = (int32_t)p;
+    s.term[p] = i;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// range-query tree
+// ---------------------------------------------------------------------------
+template <int DP>
+__global__ void k_tree_leaf(State s, const int32_t *order, int K) {
+  const int lane = threadIdx.x & 31;
+  const int cnt = level_count(K, 0);
+  for (int j = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; j < cnt;
+       j += (gridDim.x * blockDim.x) >> 5) {
+    const int idx = j * FAN + lane;
+    const bool v = idx < K;
+    const int c = v ? order[idx] : 0;
+    int nm = v ? s.csize[c] : INT_MAX;
+    for (int o = 16; o; o >>= 1) nm = min(nm, __shfl_xor_sync(0xffffffffu, nm, o));
+    const int node = s.lvl_base[0] + j;
+#pragma unroll
+    for (int k = 0; k < DP; ++k) {
+      float lo = v ? s.cent32[(size_t)c * DP + k] : INFINITY;
+      float hi = v ? s.cent32[(size_t)c * DP + k] : -INFINITY;
+      float hm = v ? s.bhi[(size_t)c * DP + k] : INFINITY;
+      float lm = v ? s.blo[(size_t)c * DP + k] : -INFINITY;
+      for (int o = 16; o; o >>= 1) {
+        lo = fminf(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+        hi = fmaxf(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+        hm = fminf(hm, __shfl_xor_sync(0xffffffffu, hm, o));
+        lm = fmaxf(lm, __shfl_xor_sync(0xffffffffu, lm, o));
+      }
+      if (lane == k) {
+        s.nclo[(size_t)node * DP + k] = lo;
+        s.nchi[(size_t)node * DP + k] = hi;
+        s.nhmin[(size_t)node * DP + k] = hm;
+        s.nlmax[(size_t)node * DP + k] = lm;
+      }
+    }
+    if (lane == 0) s.nnmin[node] = nm;
+  }
+}
+
+template <int DP>
+__global__ void k_tree_up(State s, int K, int L) {
+  const int lane = threadIdx.x & 31;
+  const int cnt = level_count(K, L), ccnt = level_count(K, L - 1);
+  for (int j = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; j < cnt;
+       j += (gridDim.x * blockDim.x) >> 5) {
+    const int ch = j * FAN + lane;
+    const bool v = ch < ccnt;
+    const int cn = s.lvl_base[L - 1] + (v ? ch : 0);
+    int nm = v ? s.nnmin[cn] : INT_MAX;
+    for (int o = 16; o; o >>= 1) nm = min(nm, __shfl_xor_sync(0xffffffffu, nm, o));
+    const int node = s.lvl_base[L] + j;
+#pragma unroll
+    for (int k = 0; k < DP; ++k) {
+      float lo = v ? s.nclo[(size_t)cn * DP + k] : INFINITY;
+      float hi = v ? s.nchi[(size_t)cn * DP + k] : -INFINITY;
+      float hm = v ? s.nhmin[(size_t)cn * DP + k] : INFINITY;
+      float lm = v ? s.nlmax[(size_t)cn * DP + k] : -INFINITY;
+      for (int o = 16; o; o >>= 1) {
+        lo = fminf(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+        hi = fmaxf(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+        hm = fminf(hm, __shfl_xor_sync(0xffffffffu, hm, o));
+        lm = fmaxf(lm, __shfl_xor_sync(0xffffffffu, lm, o));
+      }
+      if (lane == k) {
+        s.nclo[(size_t)node * DP + k] = lo;
+        s.nchi[(size_t)node * DP + k] = hi;
+        s.nhmin[(size_t)node * DP + k] = hm;
+        s.nlmax[(size_t)node * DP + k] = lm;
+      }
+    }
+    if (lane == 0) s.nnmin[node] = nm;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// per-round kernels
+// ---------------------------------------------------------------------------
+
+// succ(i) = nearest neighbour; WriteMin(pred(succ), (key, i)) (Algorithm 1)
+__global__ void k_chain(State s, int nterm) {
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < nterm; t += gridDim.x * blockDim.x) {
+    const int i = s.term[t];
+    const int j = s.Ecid[i];
+    if (j < 0) continue;
+    s.succ[i] = j;
+    const float kf = __double2float_ru(s.Ekey[i]);
+    const unsigned long long v =
+        ((unsigned long long)__float_as_uint(kf) << 32) | (unsigned long long)(unsigned)i;
+    atomicMin(&s.pred[j], v);
+  }
+}
+
+// parallel filter for reciprocal nearest neighbours: each pair once
+__global__ void k_rnn(State s, int nterm, int round) {
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < nterm; t += gridDim.x * blockDim.x) {
+    const int i = s.term[t];
+    const int j = s.succ[i];
+    if (j < 0) continue;
+    if (s.succ[j] == i && (i < j || s.isterm[j] != round)) {
+      const int p = atomicAdd(&s.ctr->npairs, 1);
+      s.pair_lo[p] = min(i, j);
+      s.pair_hi[p] = max(i, j);
+      s.pair_key[p] = s.Ekey[i];
+    }
+  }
+}
+
+// merge every reciprocal pair: the cluster keeps the smaller cid
+__global__ void k_merge(State s, int round, int npairs) {
+  const int dp = s.dp;
+  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < npairs; p += gridDim.x * blockDim.x) {
+    const int lo = s.pair_lo[p], hi = s.pair_hi[p];
+    const double key = s.pair_key[p];
+    const int na = s.csize[lo], nb = s.csize[hi];
+    const int m = atomicAdd(&s.ctr->nmerges, 1);
+    s.m_a[m] = lo;
+    s.m_b[m] = hi;
+    s.m_h[m] = s.linkage == LK_WARD ? sqrt(key) : key;
+    s.m_size[m] = na + nb;
+    s.m_round[m] = round;
+    const double inv = 1.0 / (double)(na + nb);
+    for (int k = 0; k < dp; ++k) {
+      const double sum = s.csum[(size_t)lo * dp + k] + s.csum[(size_t)hi * dp + k];
+      s.csum[(size_t)lo * dp + k] = sum;
+      const double c = sum * inv;
+      s.cent[(size_t)lo * dp + k] = c;
+      s.cent32[(size_t)lo * dp + k] = (float)c;
+      s.blo[(size_t)lo * dp + k] = fminf(s.blo[(size_t)lo * dp + k], s.blo[(size_t)hi * dp + k]);
+      s.bhi[(size_t)lo * dp + k] = fmaxf(s.bhi[(size_t)lo * dp + k], s.bhi[(size_t)hi * dp + k]);
+    }
+    s.csize[lo] = na + nb;
+    s.succ[lo] = -1;
+    s.pred[lo] = PRED_EMPTY;
+    s.mround[lo] = round;
+    s.mround[hi] = round;
+    s.alive[hi] = 0;
+    s.rootof[hi] = lo;
+    s.reloff[hi] = na;
+  }
+}
+
+// compaction phase 1: chain repair (succ merged this round -> terminal) and
+// per-block counts of (active, terminal, points)
+__global__ void k_cmp_count(State s, const int32_t *order, int K, int round) {
+  const int p = blockIdx.x * TPB + threadIdx.x;
+  int keep = 0, ist = 0, sz = 0;
+  if (p < K) {
+    const int c = order[p];
+    if (s.alive[c]) {
+      keep = 1;
+      int sc = s.succ[c];
+      if (sc >= 0 && s.mround[sc] == round) {
+        s.succ[c] = -1;
+        sc = -1;
+      }
+      ist = sc < 0;
+      sz = s.csize[c];
+    }
+  }
+  keep = block_sum(keep);
+  ist = block_sum(ist);
+  sz = block_sum(sz);
+  if (threadIdx.x == 0) {
+    s.bsum[blockIdx.x] = keep;
+    s.bsum[gridDim.x + blockIdx.x] = ist;
+    s.bsum[2 * gridDim.x + blockIdx.x] = sz;
+  }
+}
+
+__global__ void k_cmp_top(State s, int nb) {
+  // three independent exclusive scans of nb block sums, one per warp-group pass
+  for (int f = 0; f < 3; ++f) {
+    int32_t *bs = s.bsum + (size_t)f * nb;
+    const int per = cdiv(nb, TPB);
+    const int b0 = threadIdx.x * per;
+    int sum = 0;
+    for (int i = 0; i < per; ++i)
+      if (b0 + i < nb) sum += bs[b0 + i];
+    int t;
+    int pre = block_excl_scan(sum, &t);
+    for (int i = 0; i < per; ++i)
+      if (b0 + i < nb) {
+        int v = bs[b0 + i];
+        bs[b0 + i] = pre;
+        pre += v;
+      }
+    if (threadIdx.x == 0) {
+      if (f == 0) s.ctr->nactive = t;
+      if (f == 1) s.ctr->nterm = t;
+    }
+    __syncthreads();
+  }
+}
+
+__global__ void k_cmp_write(State s, const int32_t *order, int32_t *order_out, int32_t *seg_out,
+                            int K, int round) {
+  const int p = blockIdx.x * TPB + threadIdx.x;
+  const int nb = gridDim.x;
+  int keep = 0, ist = 0, sz = 0, c = -1;
+  if (p < K) {
+    c = order[p];
+    if (s.alive[c]) {
+      keep = 1;
+      ist = s.succ[c] < 0;
+      sz = s.csize[c];
+    }
+  }
+  int t;
+  const int ok = block_excl_scan(keep, &t) + s.bsum[blockIdx.x];
+  const int ot = block_excl_scan(ist, &t) + s.bsum[nb + blockIdx.x];
+  const int os = block_excl_scan(sz, &t) + s.bsum[2 * nb + blockIdx.x];
+  if (keep) {
+    order_out[ok] = c;
+    s.pos[c] = ok;
+    if (seg_out) seg_out[c] = os;
+    if (ist) {
+      s.term[ot] = c;
+      s.isterm[c] = round + 1;
+    }
+  }
+}
+
+// move points so that each merged cluster is one segment
+__global__ void k_relayout(State s, int pc) {
+  const int64_t n = s.n;
+  const int dp = s.dp, nx = pc ^ 1;
+  for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n;
+       p += (int64_t)gridDim.x * blockDim.x) {
+    const int c = s.plab[pc][p];
+    int r = c;
+    int off = (int)p - s.seg[pc][c];
+    if (!s.alive[c]) {
+      r = s.rootof[c];
+      off += s.reloff[c];
+    }
+    const int64_t q = (int64_t)s.seg[nx][r] + off;
+    for (int k = 0; k < dp; ++k) {
+      s.p64[nx][q * dp + k] = s.p64[pc][p * dp + k];
+      s.p32[nx][q * dp + k] = s.p32[pc][p * dp + k];
+    }
+    s.plab[nx][q] = r;
+  }
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// instance
+// ---------------------------------------------------------------------------
+struct hac_ctx {
+  State s{};
+  int64_t n = 0;
+  int d = 0;
+  hac_dtype dt = HAC_F64;
+  hac_linkage lk = HAC_WARD;
+  void *raw = nullptr;          // device copy of the input points (input order)
+  cudaStream_t own = nullptr;
+  std::vector<void *> allocs;
+  int64_t bytes = 0;
+  // sort scratch
+  uint64_t *keys[2] = {nullptr, nullptr};
+  int32_t *vals[2] = {nullptr, nullptr};
+  int32_t *hist = nullptr, *hbs = nullptr;
+  unsigned long long *bb = nullptr;  // 2 x MAXD bbox words
+  int nlev_max = 1;
+  int64_t launches = 0;  // kernels launched in the current run
+  int ocur = 0, pcur = 0;
+  bool done = false;
+  int64_t n_merges = 0;
+  hac_stats_t st{};
+  std::vector<hac_merge> out;       // canonical dendrogram
+  std::vector<int32_t> out_round;
+};
+
+namespace {
+
+template <typename T>
+int dalloc(hac_ctx *h, T **p, size_t count) {
+  if (count == 0) count = 1;
+  void *q = nullptr;
+  if (cudaMalloc(&q, count * sizeof(T)) != cudaSuccess) {
+    cudaGetLastError();
+    return HAC_ENOMEM;
+  }
+  h->allocs.push_back(q);
+  h->bytes += (int64_t)(count * sizeof(T));
+  *p = (T *)q;
+  return HAC_OK;
+}
+
+void free_all(hac_ctx *h) {
+  for (void *p : h->allocs) cudaFree(p);
+  h->allocs.clear();
+  if (h->own) cudaStreamDestroy(h->own);
+  h->own = nullptr;
+}
+
+int pad_dim(int d) { return d <= 2 ? 2 : d <= 4 ? 4 : d <= 8 ? 8 : 16; }
+
+int alloc_state(hac_ctx *h) {
+  State &s = h->s;
+  const int64_t n = h->n;
+  const int dp = s.dp;
+  int rc = 0;
+#define A(ptr, cnt)                          \
+  do {                                       \
+    if ((rc = dalloc(h, &(ptr), (size_t)(cnt)))) return rc; \
+  } while (0)
+  for (int b = 0; b < 2; ++b) {
+    A(s.p64[b], n * dp);
+    A(s.p32[b], n * dp);
+    A(s.plab[b], n);
+    A(s.seg[b], n);
+    A(s.order[b], n);
+  }
+  A(s.csize, n);
+  A(s.csum, n * dp);
+  A(s.cent, n * dp);
+  A(s.cent32, n * dp);
+  A(s.blo, n * dp);
+  A(s.bhi, n * dp);
+  A(s.succ, n);
+  A(s.pred, n);
+  A(s.mround, n);
+  A(s.isterm, n);
+  A(s.alive, n);
+  A(s.rootof, n);
+  A(s.reloff, n);
+  A(s.pos, n);
+  A(s.Ekey, n);
+  A(s.Ecid, n);
+  A(s.term, n);
+  A(s.pair_lo, n / 2 + 1);
+  A(s.pair_hi, n / 2 + 1);
+  A(s.pair_key, n / 2 + 1);
+  A(s.m_a, n);
+  A(s.m_b, n);
+  A(s.m_size, n);
+  A(s.m_round, n);
+  A(s.m_h, n);
+  // tree levels sized for K = n
+  int base = 0;
+  const int nlev = tree_levels((int)n);
+  for (int L = 0; L <= MAXLEV; ++L) {
+    s.lvl_base[L] = base;
+    if (L < nlev) base += level_count((int)n, L);
+  }
+  h->nlev_max = nlev;
+  A(s.nclo, (int64_t)base * dp);
+  A(s.nchi, (int64_t)base * dp);
+  A(s.nhmin, (int64_t)base * dp);
+  A(s.nlmax, (int64_t)base * dp);
+  A(s.nnmin, base);
+  A(s.bsum, 3 * (int64_t)cdiv(n, TPB) + 3);
+  A(s.ctr, 1);
+  for (int b = 0; b < 2; ++b) {
+    A(h->keys[b], n);
+    A(h->vals[b], n);
+  }
+  const int ntiles = cdiv(n, RS_TILE);
+  A(h->hist, (int64_t)256 * ntiles + 1);
+  A(h->hbs, cdiv((int64_t)256 * ntiles, SC_TILE) + 1);
+  A(h->bb, 2 * MAXD);
+#undef A
+  return HAC_OK;
+}
+
+#define CK(x)                                \
+  do {                                       \
+    cudaError_t e_ = (x);                    \
+    if (e_ != cudaSuccess) return HAC_EDEVICE; \
+  } while (0)
+
+int grid_for(int64_t work, int tpb) {
+  int64_t g = (work + tpb - 1) / tpb;
+  if (g < 1) g = 1;
+  if (g > 152 * 64) g = 152 * 64;
+  return (int)g;
+}
+
+template <int DP>
+int build_tree_dp(hac_ctx *h, const int32_t *order, int K, cudaStream_t st) {
+  const int nlev = tree_levels(K);
+  h->launches += nlev;
+  k_tree_leaf<DP><<<grid_for((int64_t)level_count(K, 0) * 32, TPB), TPB, 0, st>>>(h->s, order, K);
+  for (int L = 1; L < nlev; ++L)
+    k_tree_up<DP><<<grid_for((int64_t)level_count(K, L) * 32, TPB), TPB, 0, st>>>(h->s, K, L);
+  CK(cudaGetLastError());
+  return HAC_OK;
+}
+
+int build_tree(hac_ctx *h, const int32_t *order, int K, cudaStream_t st) {
+  switch (h->s.dp) {
+    case 2: return build_tree_dp<2>(h, order, K, st);
+    case 4: return build_tree_dp<4>(h, order, K, st);
+    case 8: return build_tree_dp<8>(h, order, K, st);
+    case 16: return build_tree_dp<16>(h, order, K, st);
+  }
+  return HAC_EINTERNAL;
+}
+
+int radix_sort(hac_ctx *h, int bits, cudaStream_t st) {
+  const int n = (int)h->n;
+  const int ntiles = cdiv(n, RS_TILE);
+  const int hm = 256 * ntiles;
+  const int hb = cdiv(hm, SC_TILE);
+  int cur = 0;
+  for (int shift = 0; shift < bits; shift += 8) {
+    h->launches += 5;
+    k_rs_hist<<<ntiles, TPB, 0, st>>>(h->keys[cur], n, shift, h->hist, ntiles);
+    k_scan_reduce<<<hb, TPB, 0, st>>>(h->hist, hm, h->hbs);
+    k_scan_top<<<1, TPB, 0, st>>>(h->hbs, hb, nullptr);
+    k_scan_down<<<hb, TPB, 0, st>>>(h->hist, h->hist, hm, h->hbs);
+    k_rs_scatter<<<ntiles, TPB, 0, st>>>(h->keys[cur], h->vals[cur], h->keys[cur ^ 1],
+                                         h->vals[cur ^ 1], n, shift, h->hist, ntiles);
+    cur ^= 1;
+  }
+  CK(cudaGetLastError());
+  return cur;  // buffer holding the sorted result
+}
+
+template <typename T>
+int init_layout(hac_ctx *h, cudaStream_t st) {
+  State &s = h->s;
+  const T *X = (const T *)h->raw;
+  const int64_t n = h->n;
+  const int d = h->d;
+  std::vector<unsigned long long> init(2 * MAXD);
+  for (int k = 0; k < MAXD; ++k) {
+    init[k] = ~0ull;
+    init[MAXD + k] = 0ull;
+  }
+  CK(cudaMemcpyAsync(h->bb, init.data(), 2 * MAXD * sizeof(unsigned long long),
+                     cudaMemcpyHostToDevice, st));
+  CK(cudaMemsetAsync(s.ctr, 0, sizeof(Counters), st));
+  k_bbox<T><<<grid_for(n, TPB), TPB, 0, st>>>(X, n, d, h->bb, h->bb + MAXD, s.ctr);
+  h->launches += 3;  // bbox, morton, layout
+  CK(cudaGetLastError());
+  std::vector<unsigned long long> bb(2 * MAXD);
+  Counters c0;
+  CK(cudaMemcpyAsync(bb.data(), h->bb, 2 * MAXD * sizeof(unsigned long long),
+                     cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(&c0, s.ctr, sizeof(Counters), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  if (c0.err & ERR_NONFINITE) return HAC_EINVAL;
+  auto dec = [](unsigned long long u) {
+    unsigned long long b = (u >> 63) ? (u & 0x7fffffffffffffffull) : ~u;
+    double x;
+    memcpy(&x, &b, 8);
+    return x;
+  };
+  MortonParams mp{}, ctrp{};
+  double scale = 0.0;
+  for (int k = 0; k < d; ++k) {
+    double lo = dec(bb[k]), hi = dec(bb[MAXD + k]);
+    mp.lo[k] = lo;
+    mp.inv[k] = hi > lo ? 1.0 / (hi - lo) : 0.0;
+    ctrp.lo[k] = 0.5 * (lo + hi);
+    scale = std::max(scale, std::max(std::fabs(lo - ctrp.lo[k]), std::fabs(hi - ctrp.lo[k])));
+  }
+  mp.bits = std::min(21, 64 / d);
+  s.abs_slack = std::max(scale, 1e-300) * std::ldexp(1.0, -18);
+  k_morton<T><<<grid_for(n, TPB), TPB, 0, st>>>(X, n, d, mp, h->keys[0], h->vals[0]);
+  CK(cudaGetLastError());
+  int sc = radix_sort(h, mp.bits * d, st);
+  if (sc < 0) return sc;
+  h->ocur = h->pcur = 0;
+  s.cur = 0;
+  k_layout<T><<<grid_for(n, TPB), TPB, 0, st>>>(s, X, h->vals[sc], ctrp);
+  CK(cudaGetLastError());
+  Counters c{};
+  c.nterm = (int)n;
+  c.nactive = (int)n;
+  CK(cudaMemcpyAsync(s.ctr, &c, sizeof(Counters), cudaMemcpyHostToDevice, st));
+  return build_tree(h, s.order[0], (int)n, st);
+}
+
+int create_common(const void *pts, bool dev, int64_t n, int d, hac_dtype dt, hac_linkage lk,
+                  hac_t *out) {
+  if (!out) return HAC_EINVAL;
+  *out = nullptr;
+  if (!pts || n < 1 || n > (int64_t)INT32_MAX / 2 || d < 1 || d > MAXD) return HAC_EINVAL;
+  if (dt != HAC_F32 && dt != HAC_F64) return HAC_EINVAL;
+  if (lk != HAC_COMPLETE && lk != HAC_AVERAGE && lk != HAC_WARD) return HAC_EINVAL;
+  const size_t esz = dt == HAC_F32 ? 4 : 8;
+  if (!dev) {
+    for (int64_t i = 0; i < n * d; ++i) {
+      double x = dt == HAC_F32 ? (double)((const float *)pts)[i] : ((const double *)pts)[i];
+      if (!std::isfinite(x)) return HAC_EINVAL;
+    }
+  }
+  hac_ctx *h = new (std::nothrow) hac_ctx();
+  if (!h) return HAC_ENOMEM;
+  h->n = n;
+  h->d = d;
+  h->dt = dt;
+  h->lk = lk;
+  h->s.n = n;
+  h->s.d = d;
+  h->s.dp = pad_dim(d);
+  h->s.linkage = (int)lk;
+  if (cudaStreamCreateWithFlags(&h->own, cudaStreamNonBlocking) != cudaSuccess) {
+    cudaGetLastError();
+    delete h;
+    return HAC_EDEVICE;
+  }
+  int rc = alloc_state(h);
+  if (!rc) {
+    void *raw = nullptr;
+    if (cudaMalloc(&raw, n * d * esz) != cudaSuccess) {
+      cudaGetLastError();
+      rc = HAC_ENOMEM;
+    } else {
+      h->allocs.push_back(raw);
+      h->bytes += n * d * esz;
+      h->raw = raw;
+      if (cudaMemcpyAsync(raw, pts, n * d * esz,
+                          dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                          h->own) != cudaSuccess ||
+          cudaStreamSynchronize(h->own) != cudaSuccess)
+        rc = HAC_EDEVICE;
+    }
+  }
+  if (rc) {
+    free_all(h);
+    delete h;
+    return rc;
+  }
+  *out = h;
+  return HAC_OK;
+}
+
+struct Ev {
+  cudaEvent_t e = nullptr;
+  Ev() { cudaEventCreate(&e); }
+  ~Ev() {
+    if (e) cudaEventDestroy(e);
+  }
+};
+
+int run_impl(hac_ctx *h, const hac_opts *o) {
+  hac_opts opt;
+  hac_default_opts(&opt);
+  if (o) opt = *o;
+  if (opt.precision != HAC_PREC_F64 && opt.precision != HAC_PREC_F32_RECHECK) return HAC_EINVAL;
+  if (opt.cache_slots < 0 || opt.max_rounds < 0 || opt.timeout_s < 0) return HAC_EINVAL;
+  cudaStream_t st = opt.stream ? (cudaStream_t)opt.stream : h->own;
+  State &s = h->s;
+  s.prec = opt.precision;
+  h->done = false;
+  h->st = hac_stats_t{};
+  h->st.device_bytes = h->bytes;
+  const auto t0 = std::chrono::steady_clock::now();
+  Ev e0, e1, e2, e3, eq0, eq1;
+  double ms_nn = 0, ms_merge = 0, ms_update = 0, ms_init = 0, ms_query = 0;
+  int64_t qlaunch = 0;
+  h->launches = 0;
+  cudaEventRecord(e0.e, st);
+  int rc = h->dt == HAC_F32 ? init_layout<float>(h, st) : init_layout<double>(h, st);
+  if (rc) return rc;
+  cudaEventRecord(e1.e, st);
+  CK(cudaEventSynchronize(e1.e));
+  {
+    float ms;
+    cudaEventElapsedTime(&ms, e0.e, e1.e);
+    ms_init = ms;
+  }
+  int K = (int)h->n, nterm = (int)h->n, round = 0;
+  const bool need_points = s.linkage != LK_WARD;
+  Counters c{};
+  while (K > 1) {
+    if (opt.max_rounds && round >= opt.max_rounds) return HAC_ETIMEOUT;
+    if (opt.timeout_s > 0 &&
+        std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count() >
+            opt.timeout_s)
+      return HAC_ETIMEOUT;
+    s.cur = h->pcur;
+    cudaEventRecord(e0.e, st);
+    QueryArgs qa{};
+    qa.d = s.d;
+    qa.linkage = s.linkage;
+    qa.round = round;
+    qa.K = K;
+    qa.nterm = nterm;
+    qa.abs_slack = s.abs_slack;
+    qa.term = s.term;
+    qa.order = s.order[h->ocur];
+    qa.pos = s.pos;
+    qa.csize = s.csize;
+    qa.seg = s.seg[h->pcur];
+    qa.cent = s.cent;
+    qa.p64 = s.p64[h->pcur];
+    qa.cent32 = s.cent32;
+    qa.blo = s.blo;
+    qa.bhi = s.bhi;
+    qa.p32 = s.p32[h->pcur];
+    qa.pred = s.pred;
+    qa.nclo = s.nclo;
+    qa.nchi = s.nchi;
+    qa.nhmin = s.nhmin;
+    qa.nlmax = s.nlmax;
+    qa.nnmin = s.nnmin;
+    for (int L = 0; L <= MAXLEV; ++L) qa.lvl_base[L] = s.lvl_base[L];
+    qa.Ekey = s.Ekey;
+    qa.Ecid = s.Ecid;
+    qa.ctr = s.ctr;
+    cudaEventRecord(eq0.e, st);
+    CK(launch_query(qa, s.dp, s.prec, st));
+    cudaEventRecord(eq1.e, st);
+    ++qlaunch;
+    k_chain<<<grid_for(nterm, TPB), TPB, 0, st>>>(s, nterm);
+    h->launches += 3;  // query, chain, rnn
+    cudaEventRecord(e1.e, st);
+    CK(cudaMemsetAsync(&s.ctr->npairs, 0, sizeof(int32_t), st));
+    k_rnn<<<grid_for(nterm, TPB), TPB, 0, st>>>(s, nterm, round);
+    CK(cudaGetLastError());
+    int npairs = 0;
+    CK(cudaMemcpyAsync(&npairs, &s.ctr->npairs, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    if (npairs <= 0) {
+      CK(cudaMemcpyAsync(&c, s.ctr, sizeof(Counters), cudaMemcpyDeviceToHost, st));
+      CK(cudaStreamSynchronize(st));
+      return HAC_EINTERNAL;
+    }
+    k_merge<<<grid_for(npairs, TPB), TPB, 0, st>>>(s, round, npairs);
+    h->launches += 4;  // merge, 3 compaction kernels
+    cudaEventRecord(e2.e, st);
+    const int nb = cdiv(K, TPB);
+    const int32_t *ord = s.order[h->ocur];
+    int32_t *ordn = s.order[h->ocur ^ 1];
+    k_cmp_count<<<nb, TPB, 0, st>>>(s, ord, K, round);
+    k_cmp_top<<<1, TPB, 0, st>>>(s, nb);
+    k_cmp_write<<<nb, TPB, 0, st>>>(s, ord, ordn, need_points ? s.seg[h->pcur ^ 1] : nullptr,
+                                    K, round);
+    CK(cudaGetLastError());
+    h->ocur ^= 1;
+    if (need_points) {
+      k_relayout<<<grid_for(h->n, TPB), TPB, 0, st>>>(s, h->pcur);
+      h->launches += 1;
+      h->pcur ^= 1;
+    }
+    K -= npairs;
+    if (K > 1) {
+      rc = build_tree(h, s.order[h->ocur], K, st);
+      if (rc) return rc;
+    }
+    cudaEventRecord(e3.e, st);
+    CK(cudaMemcpyAsync(&c, s.ctr, sizeof(Counters), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    if (c.err & ~ERR_NONFINITE) return HAC_EINTERNAL;
+    if (c.nactive != K) return HAC_EINTERNAL;
+    nterm = c.nterm;
+    h->st.nn_searches += 0;  // counted on device
+    {
+      float a, b, d3;
+      cudaEventElapsedTime(&a, e0.e, e1.e);
+      cudaEventElapsedTime(&b, e1.e, e2.e);
+      cudaEventElapsedTime(&d3, e2.e, e3.e);
+      float q;
+      cudaEventElapsedTime(&q, eq0.e, eq1.e);
+      ms_query += q;
+      ms_nn += a;
+      ms_merge += b;
+      ms_update += d3;
+    }
+    h->st.nn_searches += qa.nterm;
+    ++round;
+  }
+  CK(cudaMemcpyAsync(&c, s.ctr, sizeof(Counters), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  const int64_t m = h->n - 1;
+  if (c.nmerges != m) return HAC_EINTERNAL;
+  // gather and sort the dendrogram on the host (canonical order)
+  std::vector<int32_t> a(m), b(m), sz(m), rr(m);
+  std::vector<double> hh(m);
+  if (m > 0) {
+    CK(cudaMemcpyAsync(a.data(), s.m_a, m * 4, cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(b.data(), s.m_b, m * 4, cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(sz.data(), s.m_size, m * 4, cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(rr.data(), s.m_round, m * 4, cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(hh.data(), s.m_h, m * 8, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+  }
+  std::vector<int64_t> idx(m);
+  for (int64_t i = 0; i < m; ++i) idx[i] = i;
+  std::sort(idx.begin(), idx.end(), [&](int64_t x, int64_t y) {
+    if (hh[x] != hh[y]) return hh[x] < hh[y];
+    if (sz[x] != sz[y]) return sz[x] < sz[y];
+    if (a[x] != a[y]) return a[x] < a[y];
+    return b[x] < b[y];
+  });
+  h->out.resize(m);
+  h->out_round.resize(m);
+  for (int64_t i = 0; i < m; ++i) {
+    const int64_t j = idx[i];
+    h->out[i] = hac_merge{a[j], b[j], hh[j], sz[j]};
+    h->out_round[i] = rr[j];
+  }
+  h->n_merges = m;
+  h->st.rounds = round;
+  h->st.merges = c.nmerges;
+  h->st.cluster_pairs = (int64_t)c.cluster_pairs;
+  h->st.point_pairs = (int64_t)c.point_pairs;
+  h->st.nodes_visited = (int64_t)c.nodes;
+  h->st.rechecks = (int64_t)c.rechecks;
+  h->st.ms_init = ms_init;
+  h->st.ms_query = ms_query;
+  h->st.query_launches = qlaunch;
+  h->st.leaf_tests = (int64_t)c.ltests;
+  h->st.kernel_launches = h->launches;
+  {
+    // algorithmic bytes of the search kernel (true dimension d, not padded):
+    // node test = centroid box (+ complete's hi-min / lo-max) + min size;
+    // leaf slot = order entry + FP32 centroid + size (+ complete's box);
+    // evaluated pair = Ward FP64 centroid, or the point rows of both clusters;
+    // per terminal = its own centroid, box, size and pred word.
+    const int64_t d = h->d;
+    const int64_t ew = 8;  // FP64 path
+    const bool comp = s.linkage == LK_COMPLETE;
+    const int64_t node_b = 2 * d * 4 + 4 + (comp ? 2 * d * 4 : 0);
+    const int64_t leaf_b = 4 + d * 4 + 4 + (comp ? 2 * d * 4 : 0);
+    const int64_t term_b = d * 4 + 2 * d * 4 + 4 + 8 + 4 + 16;
+    int64_t qb = (int64_t)c.nodes * node_b + (int64_t)c.ltests * leaf_b +
+                 h->st.nn_searches * term_b;
+    if (s.linkage == LK_WARD)
+      qb += (int64_t)c.cluster_pairs * d * ew;
+    else
+      qb += (int64_t)c.prows * d * ew;
+    h->st.query_bytes = qb;
+  }
+  h->st.ms_nn = ms_nn;
+  h->st.ms_merge = ms_merge;
+  h->st.ms_update = ms_update;
+  h->st.ms_total =
+      std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  h->done = true;
+  return HAC_OK;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// C ABI
+// ---------------------------------------------------------------------------
+extern "C" {
+
+void hac_default_opts(hac_opts *o) {
+  if (!o) return;
+  o->precision = HAC_PREC_F64;
+  o->cache_slots = 0;
+  o->max_rounds = 0;
+  o->timeout_s = 0.0;
+  o->stream = nullptr;
+}
+
+int hac_create(const void *points, int64_t n, int d, hac_dtype dt, hac_linkage lk, hac_t *out) {
+  return create_common(points, false, n, d, dt, lk, out);
+}
+
+int hac_create_device(const void *dev_points, int64_t n, int d, hac_dtype dt, hac_linkage lk,
+                      hac_t *out) {
+  return create_common(dev_points, true, n, d, dt, lk, out);
+}
+
+int hac_run(hac_t h, const hac_opts *opts) {
+  if (!h) return HAC_EINVAL;
+  int rc = run_impl(h, opts);
+  if (rc == HAC_EDEVICE) cudaGetLastError();
+  return rc;
+}
+
+int hac_dendrogram(hac_t h, hac_merge *out, int64_t cap, int64_t *n_written) {
+  if (!h || !n_written || (!out && h->n > 1)) return HAC_EINVAL;
+  if (!h->done) return HAC_EPENDING;
+  if (cap < h->n_merges) return HAC_ECAP;
+  if (h->n_merges) memcpy(out, h->out.data(), h->n_merges * sizeof(hac_merge));
+  *n_written = h->n_merges;
+  return HAC_OK;
+}
+
+int hac_merge_rounds(hac_t h, int32_t *out, int64_t cap, int64_t *n_written) {
+  if (!h || !n_written || (!out && h->n > 1)) return HAC_EINVAL;
+  if (!h->done) return HAC_EPENDING;
+  if (cap < h->n_merges) return HAC_ECAP;
+  if (h->n_merges) memcpy(out, h->out_round.data(), h->n_merges * sizeof(int32_t));
+  *n_written = h->n_merges;
+  return HAC_OK;
+}
+
+int hac_stats(hac_t h, hac_stats_t *out) {
+  if (!h || !out) return HAC_EINVAL;
+  *out = h->st;
+  return HAC_OK;
+}
+
+void hac_destroy(hac_t h) {
+  if (!h) return;
+  free_all(h);
+  delete h;
+}
+
+const char *hac_strerror(int code) {
+  switch (code) {
+    case HAC_OK: return "ok";
+    case HAC_EINVAL: return "invalid argument";
+    case HAC_ENOMEM: return "out of memory";
+    case HAC_EDEVICE: return "CUDA device error";
+    case HAC_ETIMEOUT: return "round or time limit reached";
+    case HAC_EPENDING: return "no completed run";
+    case HAC_ECAP: return "output buffer too small";
+    case HAC_EINTERNAL: return "internal consistency check failed";
+  }
+  return "unknown status";
+}
+
+}  // extern "C"

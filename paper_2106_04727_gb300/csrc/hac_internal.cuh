@@ -1,0 +1,114 @@
+// Internal declarations of the GB300 HAC library (not part of the C ABI).
+//
+// Device state of one instance, laid out struct-of-arrays and indexed by
+// cluster id (cid).  A merged cluster keeps min(cid_a, cid_b) (ParChain,
+// Section 1 footnote), so every per-cluster array is sized n and a merge only
+// retires the larger cid: no ids are ever allocated.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace hacg {
+
+constexpr int MAXD = 16;     // largest supported dimension
+constexpr int FAN = 32;      // range-query tree fan-out (one warp lane per child)
+constexpr int MAXLEV = 8;    // 32^8 > 2^31 > any n
+constexpr unsigned long long PRED_EMPTY = ~0ull;
+
+// Device-side counters of one instance.
+struct Counters {
+  int32_t npairs;    // reciprocal pairs found this round
+  int32_t nterm;     // terminals for the next search
+  int32_t nactive;   // active clusters
+  int32_t nmerges;   // merges made so far
+  int32_t err;       // sticky error bits (ERR_*)
+  int32_t pad_;
+  unsigned long long cluster_pairs, point_pairs, nodes, rechecks, searches, ltests, prows;
+};
+
+enum : int32_t { ERR_NONFINITE = 1, ERR_NO_NN = 2, ERR_STACK = 4, ERR_WINDOW = 8 };
+
+// Everything a round's kernels read or write.  Arrays with [2] are double
+// buffered across the point re-layout; `cur` selects the live one.
+struct State {
+  int64_t n;
+  int d, dp;            // dimension and padded row stride (2, 4, 8 or 16)
+  int linkage, prec;
+  double abs_slack;     // absolute pruning slack (coordinate scale * 2^-18)
+  // points, permuted into cluster-contiguous segments
+  double *p64[2];
+  float *p32[2];
+  int32_t *plab[2];     // owning cid of each permuted point
+  int32_t *seg[2];      // segment start of each cid
+  // per-cid cluster state
+  int32_t *csize;
+  double *csum;         // coordinate sums (FP64), n x dp
+  double *cent;         // centroids (FP64), n x dp
+  float *cent32;        // centroid rounded to FP32, n x dp
+  float *blo, *bhi;     // point bounding box, rounded outward to FP32, n x dp
+  int32_t *succ;        // nearest-neighbour successor, -1 = terminal
+  unsigned long long *pred;  // (f32 key rounded up) << 32 | cid, by WriteMin
+  int32_t *mround;      // round in which the cid last took part in a merge
+  int32_t *isterm;      // round in which the cid is a terminal
+  uint8_t *alive;
+  int32_t *rootof;      // retired cid -> surviving cid of its merge
+  int32_t *reloff;      // retired cid -> offset of its points in the merged segment
+  int32_t *pos;         // position of each active cid in `order`
+  double *Ekey;         // nearest-neighbour key of each terminal (linkage key space)
+  int32_t *Ecid;
+  // lists
+  int32_t *order[2];    // active cids in spatial order
+  int32_t *term;        // terminal cids
+  int32_t *pair_lo, *pair_hi;
+  double *pair_key;
+  // dendrogram records
+  int32_t *m_a, *m_b, *m_size, *m_round;
+  double *m_h;
+  // range-query tree: level L node j lives at index lvl_base[L] + j
+  float *nclo, *nchi;   // box of the children's FP32 centroids, nodes x dp
+  float *nhmin, *nlmax; // min over children of box hi / max of box lo, nodes x dp
+  int32_t *nnmin;       // min child cluster size
+  int32_t lvl_base[MAXLEV + 1];
+  // scan scratch
+  int32_t *bsum;        // 3 x nblocks block partial sums
+  Counters *ctr;
+  int cur;
+};
+
+// Query kernel arguments (by value).
+struct QueryArgs {
+  int d, linkage, round, K, nterm;
+  double abs_slack;
+  const int32_t *term, *order, *pos, *csize, *seg;
+  const double *cent, *p64;
+  const float *cent32, *blo, *bhi, *p32;
+  const unsigned long long *pred;
+  const float *nclo, *nchi, *nhmin, *nlmax;
+  const int32_t *nnmin;
+  int32_t lvl_base[MAXLEV + 1];
+  double *Ekey;
+  int32_t *Ecid;
+  Counters *ctr;
+};
+
+// number of tree levels for K active clusters (>= 1)
+__host__ __device__ inline int tree_levels(int K) {
+  int lev = 1, c = (K + FAN - 1) / FAN;
+  while (c > 1) {
+    c = (c + FAN - 1) / FAN;
+    ++lev;
+  }
+  return lev;
+}
+
+__host__ __device__ inline int level_count(int K, int L) {
+  int c = (K + FAN - 1) / FAN;
+  for (int l = 0; l < L; ++l) c = (c + FAN - 1) / FAN;
+  return c < 1 ? 1 : c;
+}
+
+// launches the nearest-neighbour query of every terminal (hac_query.cu)
+cudaError_t launch_query(const QueryArgs &a, int dp, int prec, cudaStream_t s);
+
+}  // namespace hacg

@@ -1,0 +1,226 @@
+"""GPU parity: the CUDA path (through the C ABI) against the CPU oracle.
+
+Element by element on seeded inputs: every merge (cid_a, cid_b, size) must be
+identical to the oracle's and heights must agree within 1e-9 relative in FP64
+mode; the round in which each merge happens must match Algorithm 1 run on the
+CPU.  Inputs span several 32-cluster tree leaves and levels with ragged tails,
+plus the degenerate cases (n = 1, 2, duplicates, exact ties).
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2106_04727_gb300 import hac, inputs
+
+pytestmark = pytest.mark.gpu
+
+LKS = ["complete", "average", "ward"]
+RTOL64 = 1e-9
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _round_sets(d):
+    out = {}
+    for a, b, r in zip(d["a"], d["b"], d["round"]):
+        out.setdefault(int(r), set()).add((int(a), int(b)))
+    return out
+
+
+def _assert_same(got, want, rtol=RTOL64, rounds=True):
+    c = oracle.compare(got, want, rtol=rtol)
+    assert c["ok"], c
+    if rounds and "round" in want:
+        assert _round_sets(got) == _round_sets(want)
+
+
+def test_fig1_worked_example():
+    with open(os.path.join(GOLDEN, "fig1_six_points.json")) as f:
+        g = json.load(f)
+    X = np.array(g["points"], dtype=np.float64)
+    got = hac.cluster(X, g["linkage"])
+    want = {i: {tuple(p) for p in ms} for i, ms in enumerate(g["round_merges"])}
+    assert _round_sets(got) == want
+    assert got["stats"]["rounds"] == g["n_rounds"]
+    m = oracle.as_map(got)
+    for k, h2 in g["squared_heights"].items():
+        assert m[tuple(map(int, k.split(",")))][0] == math.sqrt(h2)
+    # nearest-neighbour searches: 6 + 3 + 3 + 2 (f skips round 2)
+    assert got["stats"]["nn_searches"] == sum(len(t) for t in g["round_terminals"])
+
+
+@pytest.mark.parametrize("lk", LKS)
+def test_uniform_1024_fp64(lk):
+    X = inputs.workload("uniform2d_1k_f64")
+    _assert_same(hac.cluster(X, lk), oracle.rounds(X, lk))
+
+
+SHAPES = [(2, 2, np.float64), (3, 1, np.float64), (33, 3, np.float32), (100, 5, np.float32),
+          (257, 2, np.float64), (1100, 2, np.float32), (600, 10, np.float32),
+          (300, 16, np.float32), (70, 7, np.float64)]
+
+
+@pytest.mark.parametrize("lk", LKS)
+@pytest.mark.parametrize("shape", SHAPES, ids=lambda s: f"n{s[0]}d{s[1]}{np.dtype(s[2]).name}")
+def test_shapes(lk, shape):
+    n, d, dt = shape
+    X = inputs.gaussian_mixture(n, d, 5, seed=n * 31 + d, dtype=dt)
+    _assert_same(hac.cluster(X, lk), oracle.rounds(X.astype(np.float64), lk))
+
+
+@pytest.mark.parametrize("lk", LKS)
+def test_single_point(lk):
+    got = hac.cluster(np.zeros((1, 3)), lk)
+    assert len(got["a"]) == 0 and got["stats"]["rounds"] == 0
+
+
+@pytest.mark.parametrize("lk", LKS)
+def test_duplicates(lk):
+    n = 40
+    X = np.tile(np.array([[2.5, -1.0, 0.25]]), (n, 1))
+    got = oracle.canonical(hac.cluster(X, lk))
+    assert list(got["a"]) == [0] * (n - 1)
+    assert list(got["b"]) == list(range(1, n))
+    assert np.all(got["h"] == 0.0)
+    assert got["stats"]["rounds"] == n - 1
+
+
+@pytest.mark.parametrize("lk", LKS)
+def test_collinear_closed_form(lk):
+    m, hsp = 64, 0.25
+    X = np.zeros((m, 2))
+    X[:, 0] = hsp * np.arange(m)
+    got = oracle.as_map(hac.cluster(X, lk))
+    s = 1
+    while s < m:
+        for start in range(0, m, 2 * s):
+            want = {"complete": (2 * s - 1) * hsp, "average": s * hsp, "ward": s ** 1.5 * hsp}[lk]
+            h, size = got[(start, start + s)]
+            assert size == 2 * s and h == pytest.approx(want, rel=1e-12)
+        s *= 2
+
+
+def test_lattice_complete_exact_ties():
+    for seed in range(3):
+        X = inputs.lattice(500, 3, seed=seed, levels=12)
+        got = hac.cluster(X, "complete")
+        want = oracle.rounds(X.astype(np.float64), "complete")
+        _assert_same(got, want, rtol=0.0)
+
+
+@pytest.mark.parametrize("lk", ["average", "ward"])
+def test_lattice_ties_valid(lk):
+    X = inputs.lattice(300, 4, seed=7, levels=10)
+    got = hac.cluster(X, lk)
+    bad, stats = oracle.validate(X.astype(np.float64), lk, got, rtol=1e-9)
+    assert bad == 0, stats
+    assert oracle.check_tree(got, len(X)) == []
+
+
+@pytest.mark.parametrize("lk", LKS)
+def test_multilevel_tree(lk):
+    """12,000 points: three tree levels, ragged last leaf and node."""
+    X = inputs.gaussian_mixture(12000, 2, 40, seed=77)
+    _assert_same(hac.cluster(X, lk), oracle.rounds(X.astype(np.float64), lk))
+
+
+@pytest.mark.parametrize("lk", LKS)
+def test_gmm5d_sample(lk):
+    """The 5-D Gaussian-mixture workload's recipe at a size the oracle runs."""
+    X = inputs.workload("gmm5d_1m_f32", n=5000)
+    _assert_same(hac.cluster(X, lk), oracle.rounds(X.astype(np.float64), lk))
+
+
+def test_spreaders_sample():
+    X = inputs.spreaders(6000, seed=3000)
+    for lk in ("ward", "complete"):
+        _assert_same(hac.cluster(X, lk), oracle.rounds(X.astype(np.float64), lk))
+
+
+@pytest.mark.parametrize("lk", LKS)
+def test_deterministic(lk):
+    X = inputs.gaussian_mixture(3000, 3, 8, seed=5)
+    a, b = hac.cluster(X, lk), hac.cluster(X, lk)
+    for k in ("a", "b", "size", "round"):
+        assert np.array_equal(a[k], b[k])
+    assert np.array_equal(a["h"].view(np.int64), b["h"].view(np.int64))
+
+
+def test_device_pointer_entry():
+    torch = pytest.importorskip("torch")
+    X = inputs.gaussian_mixture(2000, 4, 6, seed=9)
+    t = torch.from_numpy(X).cuda()
+    h = hac.hac_create_device(t.data_ptr(), X.shape[0], X.shape[1], np.float32, "ward")
+    try:
+        assert hac.hac_run(h) == 0
+        m = hac.hac_dendrogram(h, len(X))
+    finally:
+        hac.hac_destroy(h)
+    got = dict(a=m["cid_a"], b=m["cid_b"], h=m["height"], size=m["size"])
+    _assert_same(got, oracle.nnchain(X.astype(np.float64), "ward"), rounds=False)
+
+
+def test_nonfinite_device_input_rejected():
+    torch = pytest.importorskip("torch")
+    X = inputs.gaussian_mixture(100, 2, 3, seed=1)
+    X[17, 1] = np.nan
+    t = torch.from_numpy(X).cuda()
+    h = hac.hac_create_device(t.data_ptr(), 100, 2, np.float32, "average")
+    try:
+        assert hac.hac_run(h) == hac.HAC_EINVAL
+        with pytest.raises(hac.HacError):
+            hac.hac_dendrogram(h, 100)
+    finally:
+        hac.hac_destroy(h)
+
+
+def test_round_limit_and_rerun():
+    X = inputs.gaussian_mixture(500, 2, 4, seed=2)
+    h = hac.hac_create(X, "complete")
+    try:
+        assert hac.hac_run(h, max_rounds=2) == hac.HAC_ETIMEOUT
+        assert hac.hac_run(h) == 0
+        m = hac.hac_dendrogram(h, len(X))
+        assert len(m) == len(X) - 1
+    finally:
+        hac.hac_destroy(h)
+
+
+def _members_small(d, n, cap=64):
+    """Members of every merged cluster of size <= cap, by replaying merges in
+    size order (children before parents)."""
+    mem = {}
+    order = np.argsort(d["size"], kind="stable")
+    out = {}
+    for t in order:
+        s = int(d["size"][t])
+        if s > cap:
+            break
+        a, b = int(d["a"][t]), int(d["b"][t])
+        ma = mem.pop(a, [a])
+        mb = mem.pop(b, [b])
+        out[t] = (ma, mb)
+        mem[a] = ma + mb
+    return out
+
+
+@pytest.mark.parametrize("lk", ["ward"])
+def test_full_size_1m_properties(lk):
+    """The 10^6-point 5-D workload in the benchmark's launch configuration:
+    a valid tree with monotone heights, and sampled merge heights equal to the
+    oracle's linkage distance of the two merged point sets."""
+    X = inputs.workload("gmm5d_1m_f32")
+    got = hac.cluster(X, lk)
+    n = len(X)
+    assert oracle.check_tree(got, n, rtol=1e-12) == []
+    mem = _members_small(got, n)
+    rng = np.random.default_rng(0)
+    keys = list(mem)
+    X64 = X.astype(np.float64)
+    for t in rng.choice(len(keys), size=min(300, len(keys)), replace=False):
+        ma, mb = mem[keys[t]]
+        want = oracle.cluster_dist(lk, X64[ma], X64[mb])
+        assert got["h"][keys[t]] == pytest.approx(want, rel=RTOL64, abs=1e-12)
