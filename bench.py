@@ -251,7 +251,8 @@ def main():
                        "l2": "flushed between steps (256 MB write)"},
             "hac": {"wall_s_per_run": tot_ms / args.steps / 1e3, "rounds": st["rounds"],
                     "nn_searches": st["nn_searches"], "cluster_pairs": st["cluster_pairs"],
-                    "point_pairs": st["point_pairs"],
+                    "point_pairs": st["point_pairs"], "nodes_visited": st["nodes_visited"],
+                    "leaf_tests": st["leaf_tests"], "query_launches": st["query_launches"],
                     "cluster_pair_evals_per_s": st["cluster_pairs"] / (times[-1] / 1e3),
                     "point_pair_evals_per_s": st["point_pairs"] / (times[-1] / 1e3),
                     "ms_init": st["ms_init"], "ms_nn": st["ms_nn"], "ms_merge": st["ms_merge"],

@@ -251,7 +251,13 @@ __global__ void k_layout(State s, const T *X, const int32_t *perm, MortonParams 
       s.cent32[(int64_t)i * dp + k] = (float)x;
       s.blo[(int64_t)i * dp + k] = __double2float_rd(x);
       s.bhi[(int64_t)i * dp + k] = __double2float_ru(x);
+      s.q32[p * dp + k] = (float)x;
+      s.q64[p * dp + k] = x;
+      s.qblo[p * dp + k] = __double2float_rd(x);
+      s.qbhi[p * dp + k] = __double2float_ru(x);
     }
+    s.qsz[p] = 1;
+    s.qseg[p] = (int32_t)p;
     s.plab[0][p] = i;
     s.seg[0][i] = (int32_t)p;
     s.csize[i] = 1;
@@ -279,16 +285,16 @@ __global__ void k_tree_leaf(State s, const int32_t *order, int K) {
        j += (gridDim.x * blockDim.x) >> 5) {
     const int idx = j * FAN + lane;
     const bool v = idx < K;
-    const int c = v ? order[idx] : 0;
-    int nm = v ? s.csize[c] : INT_MAX;
+    const size_t c = v ? (size_t)idx : 0;  // position-ordered records
+    int nm = v ? s.qsz[c] : INT_MAX;
     for (int o = 16; o; o >>= 1) nm = min(nm, __shfl_xor_sync(0xffffffffu, nm, o));
     const int node = s.lvl_base[0] + j;
 #pragma unroll
     for (int k = 0; k < DP; ++k) {
-      float lo = v ? s.cent32[(size_t)c * DP + k] : INFINITY;
-      float hi = v ? s.cent32[(size_t)c * DP + k] : -INFINITY;
-      float hm = v ? s.bhi[(size_t)c * DP + k] : INFINITY;
-      float lm = v ? s.blo[(size_t)c * DP + k] : -INFINITY;
+      float lo = v ? s.q32[c * DP + k] : INFINITY;
+      float hi = v ? s.q32[c * DP + k] : -INFINITY;
+      float hm = v ? s.qbhi[c * DP + k] : INFINITY;
+      float lm = v ? s.qblo[c * DP + k] : -INFINITY;
       for (int o = 16; o; o >>= 1) {
         lo = fminf(lo, __shfl_xor_sync(0xffffffffu, lo, o));
         hi = fmaxf(hi, __shfl_xor_sync(0xffffffffu, hi, o));
@@ -482,6 +488,15 @@ __global__ void k_cmp_write(State s, const int32_t *order, int32_t *order_out, i
     order_out[ok] = c;
     s.pos[c] = ok;
     if (seg_out) seg_out[c] = os;
+    const int dp = s.dp;
+    for (int k = 0; k < dp; ++k) {
+      s.q32[(size_t)ok * dp + k] = s.cent32[(size_t)c * dp + k];
+      s.q64[(size_t)ok * dp + k] = s.cent[(size_t)c * dp + k];
+      s.qblo[(size_t)ok * dp + k] = s.blo[(size_t)c * dp + k];
+      s.qbhi[(size_t)ok * dp + k] = s.bhi[(size_t)c * dp + k];
+    }
+    s.qsz[ok] = sz;
+    s.qseg[ok] = os;
     if (ist) {
       s.term[ot] = c;
       s.isterm[c] = round + 1;
@@ -511,6 +526,38 @@ __global__ void k_relayout(State s, int pc) {
   }
 }
 
+// canonical order of the merge records: stable passes by cid_a, then size,
+// then height (non-negative doubles order like their bit patterns)
+__global__ void k_rec_key(const State s, int m, int field, const int32_t *perm, uint64_t *keys,
+                          int32_t *vals) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gridDim.x * blockDim.x) {
+    const int v = perm ? perm[i] : i;
+    uint64_t k;
+    if (field == 0)
+      k = (uint64_t)(uint32_t)s.m_a[v];
+    else if (field == 1)
+      k = (uint64_t)(uint32_t)s.m_size[v];
+    else
+      k = (uint64_t)__double_as_longlong(s.m_h[v]);
+    keys[i] = k;
+    vals[i] = v;
+  }
+}
+
+__global__ void k_rec_gather(const State s, int m, const int32_t *perm, hac_merge *out,
+                             int32_t *out_round) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gridDim.x * blockDim.x) {
+    const int v = perm[i];
+    hac_merge r;
+    r.cid_a = s.m_a[v];
+    r.cid_b = s.m_b[v];
+    r.height = s.m_h[v];
+    r.size = s.m_size[v];
+    out[i] = r;
+    out_round[i] = s.m_round[v];
+  }
+}
+
 }  // namespace
 
 // ---------------------------------------------------------------------------
@@ -537,8 +584,8 @@ struct hac_ctx {
   bool done = false;
   int64_t n_merges = 0;
   hac_stats_t st{};
-  std::vector<hac_merge> out;       // canonical dendrogram
-  std::vector<int32_t> out_round;
+  hac_merge *dout = nullptr;        // canonical dendrogram (device)
+  int32_t *dout_round = nullptr;
 };
 
 namespace {
@@ -583,6 +630,12 @@ int alloc_state(hac_ctx *h) {
     A(s.order[b], n);
   }
   A(s.csize, n);
+  A(s.q32, n * dp);
+  A(s.q64, n * dp);
+  A(s.qblo, n * dp);
+  A(s.qbhi, n * dp);
+  A(s.qsz, n);
+  A(s.qseg, n);
   A(s.csum, n * dp);
   A(s.cent, n * dp);
   A(s.cent32, n * dp);
@@ -630,6 +683,8 @@ int alloc_state(hac_ctx *h) {
   A(h->hist, (int64_t)256 * ntiles + 1);
   A(h->hbs, cdiv((int64_t)256 * ntiles, SC_TILE) + 1);
   A(h->bb, 2 * MAXD);
+  A(h->dout, n);
+  A(h->dout_round, n);
 #undef A
   return HAC_OK;
 }
@@ -668,24 +723,31 @@ int build_tree(hac_ctx *h, const int32_t *order, int K, cudaStream_t st) {
   return HAC_EINTERNAL;
 }
 
-int radix_sort(hac_ctx *h, int bits, cudaStream_t st) {
-  const int n = (int)h->n;
-  const int ntiles = cdiv(n, RS_TILE);
+// stable LSD sort of h->keys[0]/h->vals[0] (first m entries) by the low
+// `bits` bits of the key; returns the buffer index holding the result
+int radix_sort(hac_ctx *h, int m, int bits, cudaStream_t st) {
+  const int ntiles = cdiv(m, RS_TILE);
   const int hm = 256 * ntiles;
   const int hb = cdiv(hm, SC_TILE);
   int cur = 0;
   for (int shift = 0; shift < bits; shift += 8) {
     h->launches += 5;
-    k_rs_hist<<<ntiles, TPB, 0, st>>>(h->keys[cur], n, shift, h->hist, ntiles);
+    k_rs_hist<<<ntiles, TPB, 0, st>>>(h->keys[cur], m, shift, h->hist, ntiles);
     k_scan_reduce<<<hb, TPB, 0, st>>>(h->hist, hm, h->hbs);
     k_scan_top<<<1, TPB, 0, st>>>(h->hbs, hb, nullptr);
     k_scan_down<<<hb, TPB, 0, st>>>(h->hist, h->hist, hm, h->hbs);
     k_rs_scatter<<<ntiles, TPB, 0, st>>>(h->keys[cur], h->vals[cur], h->keys[cur ^ 1],
-                                         h->vals[cur ^ 1], n, shift, h->hist, ntiles);
+                                         h->vals[cur ^ 1], m, shift, h->hist, ntiles);
     cur ^= 1;
   }
   CK(cudaGetLastError());
-  return cur;  // buffer holding the sorted result
+  return cur;
+}
+
+int bits_for(int64_t maxval) {
+  int b = 1;
+  while (b < 63 && ((int64_t)1 << b) <= maxval) ++b;
+  return b;
 }
 
 template <typename T>
@@ -731,7 +793,7 @@ int init_layout(hac_ctx *h, cudaStream_t st) {
   s.abs_slack = std::max(scale, 1e-300) * std::ldexp(1.0, -18);
   k_morton<T><<<grid_for(n, TPB), TPB, 0, st>>>(X, n, d, mp, h->keys[0], h->vals[0]);
   CK(cudaGetLastError());
-  int sc = radix_sort(h, mp.bits * d, st);
+  int sc = radix_sort(h, (int)n, mp.bits * d, st);
   if (sc < 0) return sc;
   h->ocur = h->pcur = 0;
   s.cur = 0;
@@ -864,6 +926,12 @@ int run_impl(hac_ctx *h, const hac_opts *o) {
     qa.bhi = s.bhi;
     qa.p32 = s.p32[h->pcur];
     qa.pred = s.pred;
+    qa.q32 = s.q32;
+    qa.q64 = s.q64;
+    qa.qblo = s.qblo;
+    qa.qbhi = s.qbhi;
+    qa.qsz = s.qsz;
+    qa.qseg = s.qseg;
     qa.nclo = s.nclo;
     qa.nchi = s.nchi;
     qa.nhmin = s.nhmin;
@@ -939,31 +1007,26 @@ int run_impl(hac_ctx *h, const hac_opts *o) {
   CK(cudaStreamSynchronize(st));
   const int64_t m = h->n - 1;
   if (c.nmerges != m) return HAC_EINTERNAL;
-  // gather and sort the dendrogram on the host (canonical order)
-  std::vector<int32_t> a(m), b(m), sz(m), rr(m);
-  std::vector<double> hh(m);
+  // canonical order on the device: (height, size, cid_a); (cid_a, size)
+  // already identifies a merge, so the order is total
   if (m > 0) {
-    CK(cudaMemcpyAsync(a.data(), s.m_a, m * 4, cudaMemcpyDeviceToHost, st));
-    CK(cudaMemcpyAsync(b.data(), s.m_b, m * 4, cudaMemcpyDeviceToHost, st));
-    CK(cudaMemcpyAsync(sz.data(), s.m_size, m * 4, cudaMemcpyDeviceToHost, st));
-    CK(cudaMemcpyAsync(rr.data(), s.m_round, m * 4, cudaMemcpyDeviceToHost, st));
-    CK(cudaMemcpyAsync(hh.data(), s.m_h, m * 8, cudaMemcpyDeviceToHost, st));
+    const int mm = (int)m;
+    const int g = grid_for(mm, TPB);
+    int32_t *perm = nullptr;
+    const int fbits[3] = {bits_for(h->n), bits_for(h->n), 64};
+    for (int f = 0; f < 3; ++f) {
+      k_rec_key<<<g, TPB, 0, st>>>(s, mm, f, perm, h->keys[0], h->vals[0]);
+      const int r = radix_sort(h, mm, fbits[f], st);
+      if (r < 0) return r;
+      if (r == 1) {
+        CK(cudaMemcpyAsync(h->vals[0], h->vals[1], (size_t)mm * 4, cudaMemcpyDeviceToDevice, st));
+      }
+      perm = h->vals[0];
+    }
+    k_rec_gather<<<g, TPB, 0, st>>>(s, mm, perm, h->dout, h->dout_round);
+    h->launches += 4;
+    CK(cudaGetLastError());
     CK(cudaStreamSynchronize(st));
-  }
-  std::vector<int64_t> idx(m);
-  for (int64_t i = 0; i < m; ++i) idx[i] = i;
-  std::sort(idx.begin(), idx.end(), [&](int64_t x, int64_t y) {
-    if (hh[x] != hh[y]) return hh[x] < hh[y];
-    if (sz[x] != sz[y]) return sz[x] < sz[y];
-    if (a[x] != a[y]) return a[x] < a[y];
-    return b[x] < b[y];
-  });
-  h->out.resize(m);
-  h->out_round.resize(m);
-  for (int64_t i = 0; i < m; ++i) {
-    const int64_t j = idx[i];
-    h->out[i] = hac_merge{a[j], b[j], hh[j], sz[j]};
-    h->out_round[i] = rr[j];
   }
   h->n_merges = m;
   h->st.rounds = round;
@@ -1042,7 +1105,12 @@ int hac_dendrogram(hac_t h, hac_merge *out, int64_t cap, int64_t *n_written) {
   if (!h || !n_written || (!out && h->n > 1)) return HAC_EINVAL;
   if (!h->done) return HAC_EPENDING;
   if (cap < h->n_merges) return HAC_ECAP;
-  if (h->n_merges) memcpy(out, h->out.data(), h->n_merges * sizeof(hac_merge));
+  if (h->n_merges &&
+      cudaMemcpy(out, h->dout, h->n_merges * sizeof(hac_merge), cudaMemcpyDeviceToHost) !=
+          cudaSuccess) {
+    cudaGetLastError();
+    return HAC_EDEVICE;
+  }
   *n_written = h->n_merges;
   return HAC_OK;
 }
@@ -1051,7 +1119,12 @@ int hac_merge_rounds(hac_t h, int32_t *out, int64_t cap, int64_t *n_written) {
   if (!h || !n_written || (!out && h->n > 1)) return HAC_EINVAL;
   if (!h->done) return HAC_EPENDING;
   if (cap < h->n_merges) return HAC_ECAP;
-  if (h->n_merges) memcpy(out, h->out_round.data(), h->n_merges * sizeof(int32_t));
+  if (h->n_merges &&
+      cudaMemcpy(out, h->dout_round, h->n_merges * sizeof(int32_t), cudaMemcpyDeviceToHost) !=
+          cudaSuccess) {
+    cudaGetLastError();
+    return HAC_EDEVICE;
+  }
   *n_written = h->n_merges;
   return HAC_OK;
 }

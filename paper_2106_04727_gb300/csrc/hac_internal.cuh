@@ -57,6 +57,11 @@ struct State {
   int32_t *pos;         // position of each active cid in `order`
   double *Ekey;         // nearest-neighbour key of each terminal (linkage key space)
   int32_t *Ecid;
+  // position-ordered copies of the search record of every active cluster,
+  // rebuilt at each compaction so that a leaf scan reads 32 contiguous records
+  float *q32, *qblo, *qbhi;  // FP32 centroid and box, K x dp
+  double *q64;               // FP64 centroid, K x dp
+  int32_t *qsz, *qseg;       // size and segment start
   // lists
   int32_t *order[2];    // active cids in spatial order
   int32_t *term;        // terminal cids
@@ -84,6 +89,9 @@ struct QueryArgs {
   const double *cent, *p64;
   const float *cent32, *blo, *bhi, *p32;
   const unsigned long long *pred;
+  const float *q32, *qblo, *qbhi;
+  const double *q64;
+  const int32_t *qsz, *qseg;
   const float *nclo, *nchi, *nhmin, *nlmax;
   const int32_t *nnmin;
   int32_t lvl_base[MAXLEV + 1];

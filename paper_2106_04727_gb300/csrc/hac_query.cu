@@ -126,15 +126,15 @@ __device__ __forceinline__ float node_lb(const QueryArgs &a, int node, const flo
   return dc;
 }
 
-// Lower bound on D(C_i, B) for one cluster B, in D units.
+// Lower bound on D(C_i, B) for the cluster B at position q of the order.
 template <int LK, int DP>
-__device__ __forceinline__ float cluster_lb(const QueryArgs &a, int cb, const float *ci32,
+__device__ __forceinline__ float cluster_lb(const QueryArgs &a, int q, const float *ci32,
                                             const float *alo, const float *ahi, float na,
                                             float nb) {
   float s = 0.f;
 #pragma unroll
   for (int k = 0; k < DP; ++k) {
-    float t = ci32[k] - a.cent32[(size_t)cb * DP + k];
+    float t = ci32[k] - a.q32[(size_t)q * DP + k];
     s = fmaf(t, t, s);
   }
   float dc = sqrtf(s);
@@ -143,8 +143,8 @@ __device__ __forceinline__ float cluster_lb(const QueryArgs &a, int cb, const fl
     float lb = dc;
 #pragma unroll
     for (int k = 0; k < DP; ++k) {
-      lb = fmaxf(lb, a.bhi[(size_t)cb * DP + k] - alo[k]);
-      lb = fmaxf(lb, ahi[k] - a.blo[(size_t)cb * DP + k]);
+      lb = fmaxf(lb, a.qbhi[(size_t)q * DP + k] - alo[k]);
+      lb = fmaxf(lb, ahi[k] - a.qblo[(size_t)q * DP + k]);
     }
     return lb;
   }
@@ -299,10 +299,10 @@ struct Searcher {
     int cb = -1;
     if (idx < a.K) cb = a.order[idx];
     const bool valid = cb >= 0 && cb != ci;
-    int nb = valid ? a.csize[cb] : 1;
+    int nb = valid ? a.qsz[idx] : 1;
     float lb = INFINITY;
     if (valid) {
-      lb = cluster_lb<LK, DP>(a, cb, ci32, alo, ahi, fna, (float)nb);
+      lb = cluster_lb<LK, DP>(a, idx, ci32, alo, ahi, fna, (float)nb);
       ltests += 1;
     }
     bool ok = valid && pass(lb);
@@ -314,7 +314,7 @@ struct Searcher {
 #pragma unroll
         for (int k = 0; k < DP; ++k) {
           cA[k] = a.cent[(size_t)ci * DP + k];
-          cB[k] = a.cent[(size_t)cb * DP + k];
+          cB[k] = a.q64[(size_t)idx * DP + k];
         }
         key = ward_key<DP>(cA, cB, na, nb);
         c = cb;
@@ -330,7 +330,7 @@ struct Searcher {
       int c = INT_MAX;
       unsigned long long pp = 0;
       if (small) {
-        key = eval_pair_lane<LK, DP>(a.p64, sa, na, a.seg[cb], nb, bound_key(), pp);
+        key = eval_pair_lane<LK, DP>(a.p64, sa, na, a.qseg[idx], nb, bound_key(), pp);
         c = cb;
         prows += (unsigned long long)(na + nb);
       }
@@ -348,8 +348,9 @@ struct Searcher {
       if (!pass(v)) break;  // remaining candidates have lb >= v
       int cw = __shfl_sync(0xffffffffu, cb, who);
       int nw = __shfl_sync(0xffffffffu, nb, who);
+      int sw = __shfl_sync(0xffffffffu, valid ? a.qseg[idx] : 0, who);
       unsigned long long pp = 0;
-      double key = eval_pair_warp<LK, DP>(a.p64, sa, na, a.seg[cw], nw, bound_key(), lane, pp);
+      double key = eval_pair_warp<LK, DP>(a.p64, sa, na, sw, nw, bound_key(), lane, pp);
       ppairs += pp;
       cpairs += lane == 0;
       if (lane == 0) prows += (unsigned long long)(na + nw);
