@@ -16,6 +16,8 @@
 
 #include <algorithm>
 #include <chrono>
+#include <cstdio>
+#include <cstdlib>
 #include <cmath>
 #include <cstring>
 #include <new>
@@ -791,6 +793,7 @@ int init_layout(hac_ctx *h, cudaStream_t st) {
   }
   mp.bits = std::min(21, 64 / d);
   s.abs_slack = std::max(scale, 1e-300) * std::ldexp(1.0, -18);
+  s.coord_scale = (float)(scale * (1.0 + 1e-6));
   k_morton<T><<<grid_for(n, TPB), TPB, 0, st>>>(X, n, d, mp, h->keys[0], h->vals[0]);
   CK(cudaGetLastError());
   int sc = radix_sort(h, (int)n, mp.bits * d, st);
@@ -898,7 +901,9 @@ int run_impl(hac_ctx *h, const hac_opts *o) {
   }
   int K = (int)h->n, nterm = (int)h->n, round = 0;
   const bool need_points = s.linkage != LK_WARD;
-  Counters c{};
+  Counters c{}, cprev{};
+  const char *tr = getenv("HAC_TRACE");
+  const bool trace = tr && tr[0] && tr[0] != '0';
   while (K > 1) {
     if (opt.max_rounds && round >= opt.max_rounds) return HAC_ETIMEOUT;
     if (opt.timeout_s > 0 &&
@@ -914,6 +919,7 @@ int run_impl(hac_ctx *h, const hac_opts *o) {
     qa.K = K;
     qa.nterm = nterm;
     qa.abs_slack = s.abs_slack;
+    qa.coord_scale = s.coord_scale;
     qa.term = s.term;
     qa.order = s.order[h->ocur];
     qa.pos = s.pos;
@@ -986,8 +992,18 @@ int run_impl(hac_ctx *h, const hac_opts *o) {
     CK(cudaStreamSynchronize(st));
     if (c.err & ~ERR_NONFINITE) return HAC_EINTERNAL;
     if (c.nactive != K) return HAC_EINTERNAL;
+    if (trace) {
+      float qms;
+      cudaEventElapsedTime(&qms, eq0.e, eq1.e);
+      fprintf(stderr,
+              "hac round %d K %d terms %d pairs %d query_ms %.3f leaf_tests %llu nodes %llu "
+              "cpairs %llu ppairs %llu rechecks %llu\n",
+              round, K + npairs, nterm, npairs, qms, c.ltests - cprev.ltests,
+              c.nodes - cprev.nodes, c.cluster_pairs - cprev.cluster_pairs,
+              c.point_pairs - cprev.point_pairs, c.rechecks - cprev.rechecks);
+      cprev = c;
+    }
     nterm = c.nterm;
-    h->st.nn_searches += 0;  // counted on device
     {
       float a, b, d3;
       cudaEventElapsedTime(&a, e0.e, e1.e);

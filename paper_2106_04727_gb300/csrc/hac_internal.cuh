@@ -36,6 +36,7 @@ struct State {
   int d, dp;            // dimension and padded row stride (2, 4, 8 or 16)
   int linkage, prec;
   double abs_slack;     // absolute pruning slack (coordinate scale * 2^-18)
+  float coord_scale;    // largest |coordinate| after recentring
   // points, permuted into cluster-contiguous segments
   double *p64[2];
   float *p32[2];
@@ -85,6 +86,7 @@ struct State {
 struct QueryArgs {
   int d, linkage, round, K, nterm;
   double abs_slack;
+  float coord_scale;
   const int32_t *term, *order, *pos, *csize, *seg;
   const double *cent, *p64;
   const float *cent32, *blo, *bhi, *p32;

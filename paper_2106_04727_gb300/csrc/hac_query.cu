@@ -7,7 +7,9 @@
 // the paper's range query with the ball radius of Section 4 for each linkage,
 // run as branch-and-bound: the radius starts from beta = pred.d (Algorithm 2)
 // and shrinks to the best distance found so far, so every cluster that could
-// still beat the current best is evaluated and nothing else is.
+// still beat the current best is evaluated and nothing else is.  The first
+// candidate is the nearest-looking cluster of C_i's own leaf (a spatially
+// adjacent cluster: the "distance to a nearby cluster" of Algorithm 2).
 //
 //   Ward    (Sec. 4.1): ||c_i - c_B|| <= beta * sqrt((|C_i| + m) / (2 m |C_i|)),
 //                        m = smallest cluster size under the node (the paper
@@ -19,12 +21,27 @@
 //
 // Every lower bound is tested in FP32 with a relative slack EPS and an
 // absolute slack (coordinate scale * 2^-18), so a bound can only admit extra
-// candidates, never drop the true nearest neighbour.  Candidate distances are
-// evaluated exactly as defined (Table 1) in FP64; the nearest neighbour is the
-// candidate of least (key, cid) (ties broken lexicographically, Section 1).
+// candidates, never drop the true nearest neighbour.
 //
-// Key space: Ward compares D^2 = 2|A||B|/(|A|+|B|) ||c_A - c_B||^2, complete
-// compares sqrt(max ||x - y||^2), average compares the mean of ||x - y||.
+// Precision modes (the nearest neighbour is always the candidate of least
+// (FP64 key, cid): ties broken lexicographically, Section 1):
+//   F64     every candidate that survives the bound tests is evaluated in FP64
+//           (Table 1 definitions).
+//   F32     pass 1 evaluates candidates in FP32 with the error model
+//           |D32 - D| <= delta + rho * D  (D in distance units;
+//           delta = 2.01 u M sqrt(d) [* sqrt(2|A||B|/(|A|+|B|)) for Ward],
+//           u = 2^-24, M = largest |coordinate| after recentring,
+//           rho = (d + 16) u [+ 32 u for average: FP32 partial sums of at most
+//           32 terms]).  lo = (D32 - delta)(1 - rho) and
+//           up = (D32 + delta)(1 + rho) bracket the true D.  With U = min up,
+//           the FP64 winner is among the candidates with lo <= U.  If only one
+//           candidate has lo <= U it is the winner; otherwise a second
+//           traversal re-scores every candidate with lo <= U in FP64.
+//
+// Keys: Ward compares D^2 = 2|A||B|/(|A|+|B|) ||c_A - c_B||^2, complete
+// sqrt(max ||x - y||^2), average the mean of ||x - y||.  Exact keys are
+// compared as the bit patterns of non-negative doubles (integer compares), so
+// the bookkeeping issues no FP64 instructions.
 #include "hac_internal.cuh"
 
 #include <cfloat>
@@ -38,25 +55,34 @@ constexpr int QWARPS = 4;          // warps per block
 constexpr int STK = 256;           // per-warp stack, >= 1 + 31 * (MAXLEV - 1)
 constexpr float EPS = 1e-5f;       // relative slack of the FP32 bound tests
 constexpr long long SMALLP = 32;   // pairs of at most this many point pairs run per lane
+constexpr float U32 = 5.9604645e-8f;  // 2^-24
+constexpr unsigned long long KINF = 0x7ff0000000000000ull;  // bits of +inf
 
 enum { LK_COMPLETE = 0, LK_AVERAGE = 1, LK_WARD = 2 };
+enum { M_F64 = 0, M_F32 = 1, M_RECHECK = 2 };
 
-__device__ __forceinline__ bool key_less(double k1, int c1, double k2, int c2) {
+__device__ __forceinline__ unsigned long long kbits(double k) {
+  return (unsigned long long)__double_as_longlong(k);
+}
+
+__device__ __forceinline__ bool kless(unsigned long long k1, int c1, unsigned long long k2,
+                                      int c2) {
   return k1 < k2 || (k1 == k2 && c1 < c2);
 }
 
-__device__ __forceinline__ void warp_argmin(double &k, int &c) {
+__device__ __forceinline__ void warp_argmin_u(unsigned long long &k, int &c) {
 #pragma unroll
   for (int o = 16; o; o >>= 1) {
-    double k2 = __shfl_xor_sync(0xffffffffu, k, o);
+    unsigned long long k2 = __shfl_xor_sync(0xffffffffu, k, o);
     int c2 = __shfl_xor_sync(0xffffffffu, c, o);
-    if (key_less(k2, c2, k, c)) {
+    if (kless(k2, c2, k, c)) {
       k = k2;
       c = c2;
     }
   }
 }
 
+// (value, lane) argmin; ties go to the lower lane
 __device__ __forceinline__ void warp_argmin_f(float &v, int &l) {
 #pragma unroll
   for (int o = 16; o; o >>= 1) {
@@ -67,6 +93,18 @@ __device__ __forceinline__ void warp_argmin_f(float &v, int &l) {
       l = l2;
     }
   }
+}
+
+__device__ __forceinline__ float warp_minf(float v) {
+#pragma unroll
+  for (int o = 16; o; o >>= 1) v = fminf(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+
+__device__ __forceinline__ float warp_maxf(float v) {
+#pragma unroll
+  for (int o = 16; o; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
 }
 
 __device__ __forceinline__ double warp_sum(double v) {
@@ -81,10 +119,12 @@ __device__ __forceinline__ double warp_max(double v) {
   return v;
 }
 
-// key -> Euclidean-like distance D (Ward keys are D^2)
+// exact key -> distance (FP32, rounded up)
 template <int LK>
-__device__ __forceinline__ double key_to_dist(double k) {
-  return LK == LK_WARD ? sqrt(k) : k;
+__device__ __forceinline__ float key_dist_ru(unsigned long long kb) {
+  if (kb >= KINF) return INFINITY;
+  const float f = __double2float_ru(__longlong_as_double((long long)kb));
+  return LK == LK_WARD ? __fsqrt_ru(f) : f;
 }
 
 // Squared distance from point c to box [lo, hi] (0 inside).
@@ -99,6 +139,11 @@ __device__ __forceinline__ float box_d2(const float *c, const float *lo, const f
   return s;
 }
 
+// 2|A||B|/(|A|+|B|) in FP32 (relative error <= 3u)
+__device__ __forceinline__ float ward_w(float na, float nb) {
+  return 2.f * na * nb * __frcp_rn(na + nb);
+}
+
 // Lower bound on D(C_i, B) for every cluster B under a node, in D units.
 template <int LK, int DP>
 __device__ __forceinline__ float node_lb(const QueryArgs &a, int node, const float *ci32,
@@ -109,46 +154,17 @@ __device__ __forceinline__ float node_lb(const QueryArgs &a, int node, const flo
     lo[k] = a.nclo[(size_t)node * DP + k];
     hi[k] = a.nchi[(size_t)node * DP + k];
   }
-  float dc = sqrtf(box_d2<DP>(ci32, lo, hi));
-  if (LK == LK_WARD) {
-    float m = (float)a.nnmin[node];
-    return dc * sqrtf(2.f * na * m / (na + m));
-  }
+  const float dc2 = box_d2<DP>(ci32, lo, hi);
+  if (LK == LK_WARD) return sqrtf(ward_w(na, (float)a.nnmin[node]) * dc2);
+  float lb = sqrtf(dc2);
   if (LK == LK_COMPLETE) {
-    float lb = dc;
 #pragma unroll
     for (int k = 0; k < DP; ++k) {
       lb = fmaxf(lb, a.nhmin[(size_t)node * DP + k] - alo[k]);
       lb = fmaxf(lb, ahi[k] - a.nlmax[(size_t)node * DP + k]);
     }
-    return lb;
   }
-  return dc;
-}
-
-// Lower bound on D(C_i, B) for the cluster B at position q of the order.
-template <int LK, int DP>
-__device__ __forceinline__ float cluster_lb(const QueryArgs &a, int q, const float *ci32,
-                                            const float *alo, const float *ahi, float na,
-                                            float nb) {
-  float s = 0.f;
-#pragma unroll
-  for (int k = 0; k < DP; ++k) {
-    float t = ci32[k] - a.q32[(size_t)q * DP + k];
-    s = fmaf(t, t, s);
-  }
-  float dc = sqrtf(s);
-  if (LK == LK_WARD) return dc * sqrtf(2.f * na * nb / (na + nb));
-  if (LK == LK_COMPLETE) {
-    float lb = dc;
-#pragma unroll
-    for (int k = 0; k < DP; ++k) {
-      lb = fmaxf(lb, a.qbhi[(size_t)q * DP + k] - alo[k]);
-      lb = fmaxf(lb, ahi[k] - a.qblo[(size_t)q * DP + k]);
-    }
-    return lb;
-  }
-  return dc;
+  return lb;
 }
 
 // Ward key 2|A||B|/(|A|+|B|) ||c_A - c_B||^2 in FP64 (Table 1).
@@ -163,22 +179,22 @@ __device__ __forceinline__ double ward_key(const double *cA, const double *cB, i
   return (2.0 * (double)na * (double)nb) / (double)(na + nb) * s;
 }
 
-template <int DP>
-__device__ __forceinline__ double pt_d2(const double *x, const double *y) {
-  double s = 0.0;
+template <int DP, typename T>
+__device__ __forceinline__ T pt_d2(const T *x, const T *y) {
+  T s = 0;
 #pragma unroll
   for (int k = 0; k < DP; ++k) {
-    double t = x[k] - y[k];
-    s += t * t;
+    T t = x[k] - y[k];
+    s = s + t * t;
   }
   return s;
 }
 
-// One lane evaluates a whole (small) pair.  Returns the key, or +inf when a
-// partial result already exceeds `bound` (then B cannot be the nearest).
+// ---- FP64 pair evaluation (average / complete) -----------------------------
+
+// One lane evaluates a whole small pair in FP64.
 template <int LK, int DP>
-__device__ double eval_pair_lane(const double *P, int sa, int na, int sb, int nb, double bound,
-                                 unsigned long long &pp) {
+__device__ double eval64_lane(const double *P, int sa, int na, int sb, int nb) {
   double acc = 0.0;
   for (int i = 0; i < na; ++i) {
     double x[DP];
@@ -192,19 +208,16 @@ __device__ double eval_pair_lane(const double *P, int sa, int na, int sb, int nb
         acc += sqrt(d2);
     }
   }
-  pp += (unsigned long long)na * nb;
-  (void)bound;
   if (LK == LK_COMPLETE) return sqrt(acc);
   return acc / ((double)na * (double)nb);
 }
 
-// The whole warp evaluates one pair: lanes stride over the larger cluster's
-// points, each lane loops over the smaller cluster (broadcast loads).  Exits
-// early once the partial max (complete) or partial sum (average) proves the
-// key exceeds `bound`.
+// The whole warp evaluates one pair in FP64: lanes stride over the larger
+// cluster's points, each lane loops over the smaller one (broadcast loads).
+// Returns +inf once a partial result proves D > bound (D units).
 template <int LK, int DP>
-__device__ double eval_pair_warp(const double *P, int sa, int na, int sb, int nb, double bound,
-                                 int lane, unsigned long long &pp) {
+__device__ double eval64_warp(const double *P, int sa, int na, int sb, int nb, double bound,
+                              int lane, unsigned long long &pp) {
   int sL = sa, nL = na, sS = sb, nS = nb;
   if (nb > na) {
     sL = sb;
@@ -214,10 +227,11 @@ __device__ double eval_pair_warp(const double *P, int sa, int na, int sb, int nb
   }
   const double nn = (double)na * (double)nb;
   double thr = INFINITY;
-  if (bound < INFINITY) thr = LK == LK_COMPLETE ? bound * bound * (1.0 + 1e-9) : bound * nn * (1.0 + 1e-9);
+  if (bound < INFINITY)
+    thr = LK == LK_COMPLETE ? bound * bound * (1.0 + 1e-9) : bound * nn * (1.0 + 1e-9);
   double acc = 0.0;
   for (int base = 0; base < nL; base += 32) {
-    int l = base + lane;
+    const int l = base + lane;
     if (l < nL) {
       double x[DP];
 #pragma unroll
@@ -230,114 +244,306 @@ __device__ double eval_pair_warp(const double *P, int sa, int na, int sb, int nb
           acc += sqrt(d2);
       }
     }
-    double tot = LK == LK_COMPLETE ? warp_max(acc) : warp_sum(acc);
-    int done = min(nL, base + 32);
-    if (tot > thr) {
-      if (lane == 0) pp += (unsigned long long)done * nS;
-      return INFINITY;
+    if (thr < INFINITY) {
+      const double tot = LK == LK_COMPLETE ? warp_max(acc) : warp_sum(acc);
+      if (tot > thr) {
+        pp += (unsigned long long)min(nL, base + 32) * nS;
+        return INFINITY;
+      }
     }
   }
-  if (lane == 0) pp += (unsigned long long)nL * nS;
-  double tot = LK == LK_COMPLETE ? warp_max(acc) : warp_sum(acc);
+  pp += (unsigned long long)nL * nS;
+  const double tot = LK == LK_COMPLETE ? warp_max(acc) : warp_sum(acc);
   if (LK == LK_COMPLETE) return sqrt(tot);
   return tot / nn;
 }
 
+// ---- FP32 pair evaluation (average / complete) -----------------------------
+
+// One lane, FP32, at most SMALLP point pairs (one FP32 partial sum).
 template <int LK, int DP>
+__device__ float eval32_lane(const float *P, int sa, int na, int sb, int nb) {
+  float acc = 0.f;
+  for (int i = 0; i < na; ++i) {
+    float x[DP];
+#pragma unroll
+    for (int k = 0; k < DP; ++k) x[k] = P[(size_t)(sa + i) * DP + k];
+    for (int j = 0; j < nb; ++j) {
+      const float d2 = pt_d2<DP>(x, P + (size_t)(sb + j) * DP);
+      if (LK == LK_COMPLETE)
+        acc = fmaxf(acc, d2);
+      else
+        acc += sqrtf(d2);
+    }
+  }
+  if (LK == LK_COMPLETE) return sqrtf(acc);
+  return acc / ((float)na * (float)nb);
+}
+
+// Warp-cooperative FP32 evaluation; average flushes FP32 partial sums of at
+// most 32 terms into an FP64 accumulator.  Returns +inf once the partial
+// result's lower bound exceeds `bound` (D units).
+template <int LK, int DP>
+__device__ float eval32_warp(const float *P, int sa, int na, int sb, int nb, float bound,
+                             float delta, float rho, int lane, unsigned long long &pp) {
+  int sL = sa, nL = na, sS = sb, nS = nb;
+  if (nb > na) {
+    sL = sb;
+    nL = nb;
+    sS = sa;
+    nS = na;
+  }
+  const double nn = (double)na * (double)nb;
+  float macc = 0.f;
+  double sacc = 0.0;
+  for (int base = 0; base < nL; base += 32) {
+    const int l = base + lane;
+    if (l < nL) {
+      float x[DP];
+#pragma unroll
+      for (int k = 0; k < DP; ++k) x[k] = P[(size_t)(sL + l) * DP + k];
+      float part = 0.f;
+      int cnt = 0;
+      for (int j = 0; j < nS; ++j) {
+        const float d2 = pt_d2<DP>(x, P + (size_t)(sS + j) * DP);
+        if (LK == LK_COMPLETE) {
+          macc = fmaxf(macc, d2);
+        } else {
+          part += sqrtf(d2);
+          if (++cnt == 32) {
+            sacc += (double)part;
+            part = 0.f;
+            cnt = 0;
+          }
+        }
+      }
+      if (LK != LK_COMPLETE) sacc += (double)part;
+    }
+    if (bound < INFINITY) {
+      float est;
+      if (LK == LK_COMPLETE)
+        est = sqrtf(warp_maxf(macc));
+      else
+        est = (float)(warp_sum(sacc) / nn);
+      if ((est - delta) * (1.f - rho) > bound) {
+        pp += (unsigned long long)min(nL, base + 32) * nS;
+        return INFINITY;
+      }
+    }
+  }
+  pp += (unsigned long long)nL * nS;
+  if (LK == LK_COMPLETE) return sqrtf(warp_maxf(macc));
+  return (float)(warp_sum(sacc) / nn);
+}
+
+// ---------------------------------------------------------------------------
+
+template <int LK, int DP, int MODE>
 struct Searcher {
   const QueryArgs &a;
-  int lane, ci, na;
-  int sa;
+  int lane, ci, na, sa;
   float fna;
   float ci32[DP], alo[DP], ahi[DP];
-  double beta_key;     // pred's key (rounded up) or +inf
-  double best_key;
-  int best_cid;
-  float bd;            // current bound in D units (FP32, rounded up)
   float slack;
-  unsigned long long cpairs, ppairs, nodes, ltests, prows;
+  float beta_d;   // pred bound, D units
+  float bd;       // current upper bound on the NN distance, D units
+  float T;        // pruning threshold: bd * (1 + EPS) + slack
+  // exact (FP64) best, as key bits and cid
+  unsigned long long bk;
+  int bc;
+  // FP32 pass-1 state
+  float U;        // min over candidates of the FP32 upper bound
+  float L1, L2;   // two smallest FP32 lower bounds
+  int c1;         // cid holding L1
+  float delta0, rho;
+  unsigned long long cpairs, ppairs, nodes, ltests, prows, rechecks;
 
-  __device__ Searcher(const QueryArgs &args, int lane_, int ci_) : a(args), lane(lane_), ci(ci_) {
+  __device__ Searcher(const QueryArgs &args, int lane_, int ci_, float Ufix)
+      : a(args), lane(lane_), ci(ci_) {
     na = a.csize[ci];
     fna = (float)na;
-    sa = a.seg ? a.seg[ci] : 0;
+    sa = a.seg[ci];
 #pragma unroll
     for (int k = 0; k < DP; ++k) {
       ci32[k] = a.cent32[(size_t)ci * DP + k];
       alo[k] = a.blo[(size_t)ci * DP + k];
       ahi[k] = a.bhi[(size_t)ci * DP + k];
     }
-    unsigned long long pv = a.pred[ci];
-    beta_key = pv == PRED_EMPTY ? INFINITY : (double)__uint_as_float((unsigned)(pv >> 32));
-    best_key = INFINITY;
-    best_cid = INT_MAX;
+    const unsigned long long pv = a.pred[ci];
+    if (pv == PRED_EMPTY) {
+      beta_d = INFINITY;
+    } else {
+      const float bkey = __uint_as_float((unsigned)(pv >> 32));
+      beta_d = LK == LK_WARD ? __fsqrt_ru(bkey) : bkey;
+    }
     slack = (float)a.abs_slack * (LK == LK_WARD ? sqrtf(2.f * fna) : 2.f);
-    cpairs = ppairs = nodes = ltests = prows = 0;
+    delta0 = 2.01f * U32 * a.coord_scale * sqrtf((float)a.d);
+    rho = ((float)a.d + 16.f) * U32 + (LK == LK_AVERAGE ? 32.f * U32 : 0.f);
+    bk = KINF;
+    bc = INT_MAX;
+    U = Ufix;
+    L1 = L2 = INFINITY;
+    c1 = INT_MAX;
+    cpairs = ppairs = nodes = ltests = prows = rechecks = 0;
     refresh();
   }
 
-  __device__ double bound_key() const { return fmin(beta_key, best_key); }
-
   __device__ void refresh() {
-    double bk = bound_key();
-    bd = bk == INFINITY ? INFINITY : __double2float_ru(key_to_dist<LK>(bk));
+    if (MODE == M_F32)
+      bd = fminf(beta_d, U);
+    else if (MODE == M_RECHECK)
+      bd = fminf(U, key_dist_ru<LK>(bk));
+    else
+      bd = fminf(beta_d, key_dist_ru<LK>(bk));
+    T = bd * (1.f + EPS) + slack;
   }
 
-  __device__ bool pass(float lb) const { return lb <= bd * (1.f + EPS) + slack; }
+  __device__ bool pass(float lb) const { return lb <= T; }
 
-  __device__ void offer(double key, int cid) {
-    warp_argmin(key, cid);
-    if (key_less(key, cid, best_key, best_cid)) {
-      best_key = key;
-      best_cid = cid;
+  __device__ float lower(float d32, float dlt) const { return fmaxf(d32 - dlt, 0.f) * (1.f - rho); }
+
+  // exact candidates: every lane offers its own (k, c) (c = INT_MAX if none)
+  __device__ void offer_exact(unsigned long long k, int c) {
+    warp_argmin_u(k, c);
+    if (kless(k, c, bk, bc)) {
+      bk = k;
+      bc = c;
       refresh();
     }
   }
 
-  __device__ void leaf(int j) {
+  // FP32 candidates: every lane offers its own estimate (has = false if none)
+  __device__ void offer_f32(bool has, float d32, float dlt, int c) {
+    const float lo = has ? lower(d32, dlt) : INFINITY;
+    const float up = has ? (d32 + dlt) * (1.f + rho) : INFINITY;
+    const int cc = has ? c : INT_MAX;
+    const float umin = warp_minf(up);
+    float m1 = lo;
+    int ml = lane;
+    warp_argmin_f(m1, ml);
+    const float m2 = warp_minf(lane == ml ? INFINITY : lo);
+    const int cmin = __shfl_sync(0xffffffffu, cc, ml);
+    if (m1 < L1 || (m1 == L1 && cmin < c1)) {
+      L2 = fminf(L1, m2);
+      L1 = m1;
+      c1 = cmin;
+    } else {
+      L2 = fminf(L2, m1);
+    }
+    if (umin < U) {
+      U = umin;
+      refresh();
+    }
+  }
+
+  __device__ unsigned long long ward64(int q, int nb) const {
+    double cA[DP], cB[DP];
+#pragma unroll
+    for (int k = 0; k < DP; ++k) {
+      cA[k] = a.cent[(size_t)ci * DP + k];
+      cB[k] = a.q64[(size_t)q * DP + k];
+    }
+    return kbits(ward_key<DP>(cA, cB, na, nb));
+  }
+
+  __device__ void leaf(int j, bool seed) {
     const int idx = j * FAN + lane;
-    int cb = -1;
-    if (idx < a.K) cb = a.order[idx];
-    const bool valid = cb >= 0 && cb != ci;
-    int nb = valid ? a.qsz[idx] : 1;
-    float lb = INFINITY;
+    const bool in = idx < a.K;
+    const int cb = in ? a.order[idx] : -1;
+    const bool valid = in && cb != ci;
+    const int nb = valid ? a.qsz[idx] : 1;
+    float dc2 = INFINITY, bx = 0.f;
     if (valid) {
-      lb = cluster_lb<LK, DP>(a, idx, ci32, alo, ahi, fna, (float)nb);
+      dc2 = 0.f;
+#pragma unroll
+      for (int k = 0; k < DP; ++k) {
+        const float t = ci32[k] - a.q32[(size_t)idx * DP + k];
+        dc2 = fmaf(t, t, dc2);
+        if (LK == LK_COMPLETE) {
+          bx = fmaxf(bx, a.qbhi[(size_t)idx * DP + k] - alo[k]);
+          bx = fmaxf(bx, ahi[k] - a.qblo[(size_t)idx * DP + k]);
+        }
+      }
       ltests += 1;
     }
-    bool ok = valid && pass(lb);
     if (LK == LK_WARD) {
-      double key = INFINITY;
+      const float w = valid ? ward_w(fna, (float)nb) : 0.f;
+      const float d32 = valid ? sqrtf(w * dc2) : INFINITY;  // FP32 Ward distance
+      const float dlt = delta0 * sqrtf(w);
+      if (MODE == M_F32) {
+        const bool has = valid && lower(d32, dlt) <= T;
+        if (__any_sync(0xffffffffu, has)) {
+          cpairs += __popc(__ballot_sync(0xffffffffu, has));
+          offer_f32(has, d32, dlt, cb);
+        }
+        return;
+      }
+      bool ok = valid && pass(d32);
+      if (MODE == M_RECHECK) ok = ok && lower(d32, dlt) <= U;
+      unsigned m = __ballot_sync(0xffffffffu, ok);
+      if (!m) return;
+      if (seed && __popc(m) > 1) {
+        // nearest-looking candidate first: it usually settles the bound
+        float v = ok ? d32 : INFINITY;
+        int who = lane;
+        warp_argmin_f(v, who);
+        unsigned long long k = KINF;
+        int c = INT_MAX;
+        if (lane == who) {
+          k = ward64(idx, nb);
+          c = cb;
+        }
+        cpairs += 1;
+        if (MODE == M_RECHECK) rechecks += 1;
+        offer_exact(k, c);
+        ok = ok && lane != who && pass(d32);
+        m = __ballot_sync(0xffffffffu, ok);
+        if (!m) return;
+      }
+      unsigned long long k = KINF;
       int c = INT_MAX;
       if (ok) {
-        double cA[DP], cB[DP];
-#pragma unroll
-        for (int k = 0; k < DP; ++k) {
-          cA[k] = a.cent[(size_t)ci * DP + k];
-          cB[k] = a.q64[(size_t)idx * DP + k];
-        }
-        key = ward_key<DP>(cA, cB, na, nb);
+        k = ward64(idx, nb);
         c = cb;
       }
-      cpairs += __popc(__ballot_sync(0xffffffffu, ok));
-      offer(key, c);
+      cpairs += __popc(m);
+      if (MODE == M_RECHECK) rechecks += __popc(m);
+      offer_exact(k, c);
       return;
     }
-    // complete / average: small pairs one per lane, then the rest one warp each
+    // ---- complete / average ----
+    const float lb = valid ? fmaxf(sqrtf(dc2), bx) : INFINITY;
+    const bool ok = valid && pass(lb);
+    const int sb = valid ? a.qseg[idx] : 0;
+    const float dlt = delta0;
     const bool small = ok && (long long)na * nb <= SMALLP;
-    {
-      double key = INFINITY;
+    const unsigned sm = __ballot_sync(0xffffffffu, small);
+    if (sm) {
+      unsigned long long k = KINF;
       int c = INT_MAX;
-      unsigned long long pp = 0;
+      float d32 = INFINITY;
+      bool rec = false;
       if (small) {
-        key = eval_pair_lane<LK, DP>(a.p64, sa, na, a.qseg[idx], nb, bound_key(), pp);
+        if (MODE == M_F64) {
+          k = kbits(eval64_lane<LK, DP>(a.p64, sa, na, sb, nb));
+        } else {
+          d32 = eval32_lane<LK, DP>(a.p32, sa, na, sb, nb);
+          if (MODE == M_RECHECK && lower(d32, dlt) <= fminf(U, bd)) {
+            k = kbits(eval64_lane<LK, DP>(a.p64, sa, na, sb, nb));
+            rec = true;
+          }
+        }
         c = cb;
-        prows += (unsigned long long)(na + nb);
       }
-      ppairs += pp;
-      unsigned sm = __ballot_sync(0xffffffffu, small);
+      ppairs += __reduce_add_sync(0xffffffffu, small ? (unsigned)(na * nb) : 0u);
+      prows += __reduce_add_sync(0xffffffffu, small ? (unsigned)(na + nb) : 0u);
       cpairs += __popc(sm);
-      if (sm) offer(key, c);
+      if (MODE == M_F32) {
+        offer_f32(small, d32, dlt, cb);
+      } else {
+        if (MODE == M_RECHECK) rechecks += __popc(__ballot_sync(0xffffffffu, rec));
+        offer_exact(k, c);
+      }
     }
     unsigned big = __ballot_sync(0xffffffffu, ok && !small);
     while (big) {
@@ -346,26 +552,126 @@ struct Searcher {
       warp_argmin_f(v, who);
       big &= ~(1u << who);
       if (!pass(v)) break;  // remaining candidates have lb >= v
-      int cw = __shfl_sync(0xffffffffu, cb, who);
-      int nw = __shfl_sync(0xffffffffu, nb, who);
-      int sw = __shfl_sync(0xffffffffu, valid ? a.qseg[idx] : 0, who);
+      const int cw = __shfl_sync(0xffffffffu, cb, who);
+      const int nw = __shfl_sync(0xffffffffu, nb, who);
+      const int sw = __shfl_sync(0xffffffffu, sb, who);
       unsigned long long pp = 0;
-      double key = eval_pair_warp<LK, DP>(a.p64, sa, na, sw, nw, bound_key(), lane, pp);
-      ppairs += pp;
-      cpairs += lane == 0;
-      if (lane == 0) prows += (unsigned long long)(na + nw);
-      // all lanes hold the same key
-      if (key_less(key, cw, best_key, best_cid)) {
-        best_key = key;
-        best_cid = cw;
-        refresh();
+      cpairs += 1;
+      prows += (unsigned long long)(na + nw);
+      if (MODE == M_F64) {
+        const double key = eval64_warp<LK, DP>(a.p64, sa, na, sw, nw, (double)bd, lane, pp);
+        ppairs += pp;
+        const unsigned long long kb = kbits(key);
+        if (key < INFINITY && kless(kb, cw, bk, bc)) {
+          bk = kb;
+          bc = cw;
+          refresh();
+        }
+      } else {
+        const float bnd = MODE == M_F32 ? bd : fminf(U, bd);
+        const float d32 = eval32_warp<LK, DP>(a.p32, sa, na, sw, nw, bnd, dlt, rho, lane, pp);
+        ppairs += pp;
+        if (MODE == M_F32) {
+          offer_f32(lane == 0 && d32 < INFINITY, d32, dlt, cw);
+        } else if (d32 < INFINITY && lower(d32, dlt) <= fminf(U, bd)) {
+          unsigned long long pp2 = 0;
+          const double key = eval64_warp<LK, DP>(a.p64, sa, na, sw, nw, INFINITY, lane, pp2);
+          ppairs += pp2;
+          rechecks += 1;
+          const unsigned long long kb = kbits(key);
+          if (kless(kb, cw, bk, bc)) {
+            bk = kb;
+            bc = cw;
+            refresh();
+          }
+        }
       }
     }
   }
+
+  // FP64 key of (ci, the cluster at position q): the winner of an FP32 search
+  // whose window held a single candidate
+  __device__ unsigned long long exact_of(int q) {
+    const int nb = a.qsz[q];
+    if (LK == LK_WARD) return ward64(q, nb);
+    unsigned long long pp = 0;
+    const double key = eval64_warp<LK, DP>(a.p64, sa, na, a.qseg[q], nb, INFINITY, lane, pp);
+    ppairs += pp;
+    return kbits(key);
+  }
 };
 
-template <int LK, int DP>
-__global__ void __launch_bounds__(QWARPS * 32) k_query64(QueryArgs a) {
+// Branch-and-bound traversal of the tree for one Searcher.
+template <int LK, int DP, int MODE>
+__device__ void traverse(const QueryArgs &a, Searcher<LK, DP, MODE> &S, uint32_t *sn, float *sl,
+                         int own, int lane) {
+  const int nlev = tree_levels(a.K);
+  S.leaf(own, true);
+  if (lane == 0) {
+    sn[0] = (uint32_t)(nlev - 1) << 27;
+    sl[0] = 0.f;
+  }
+  int top = 1;
+  __syncwarp();
+  while (top > 0) {
+    --top;
+    const uint32_t e = sn[top];
+    const float lb = sl[top];
+    __syncwarp();
+    if (!S.pass(lb)) continue;
+    const int L = (int)(e >> 27), j = (int)(e & ((1u << 27) - 1));
+    if (L == 0) {
+      if (j != own) S.leaf(j, false);
+      continue;
+    }
+    const int cnt = level_count(a.K, L - 1);
+    const int child = j * FAN + lane;
+    float lbc = INFINITY;
+    bool ok = false;
+    if (child < cnt) {
+      lbc = node_lb<LK, DP>(a, a.lvl_base[L - 1] + child, S.ci32, S.alo, S.ahi, S.fna);
+      ok = S.pass(lbc);
+      S.nodes += 1;
+    }
+    const unsigned m = __ballot_sync(0xffffffffu, ok);
+    if (m) {
+      const int rank = __popc(m & ((1u << lane) - 1u));
+      if (ok) {
+        sn[top + rank] = ((uint32_t)(L - 1) << 27) | (uint32_t)child;
+        sl[top + rank] = lbc;
+      }
+      float mv = ok ? lbc : INFINITY;
+      int ml = lane;
+      warp_argmin_f(mv, ml);
+      __syncwarp();
+      if (lane == 0) {  // nearest child popped first
+        const int mp = top + __popc(m & ((1u << ml) - 1u));
+        const int last = top + __popc(m) - 1;
+        const uint32_t tn = sn[mp];
+        const float tl = sl[mp];
+        sn[mp] = sn[last];
+        sl[mp] = sl[last];
+        sn[last] = tn;
+        sl[last] = tl;
+      }
+      top += __popc(m);
+      __syncwarp();
+    }
+  }
+}
+
+template <int LK, int DP, int MODE>
+__device__ void tally(const Searcher<LK, DP, MODE> &S, unsigned long long *c) {
+  c[0] += S.cpairs;  // warp-uniform counts
+  c[1] += S.ppairs;
+  c[2] += S.nodes;   // per-lane counts below
+  c[3] += S.ltests;
+  c[4] += S.prows;
+  c[5] += S.rechecks;
+}
+
+template <int LK, int DP, int PREC>
+__global__ void __launch_bounds__(QWARPS * 32) k_query(QueryArgs a) {
   __shared__ uint32_t s_node[QWARPS][STK];
   __shared__ float s_lb[QWARPS][STK];
   const int lane = threadIdx.x & 31;
@@ -373,118 +679,86 @@ __global__ void __launch_bounds__(QWARPS * 32) k_query64(QueryArgs a) {
   const int nw = (gridDim.x * blockDim.x) >> 5;
   uint32_t *sn = s_node[wib];
   float *sl = s_lb[wib];
-  const int nlev = tree_levels(a.K);
-  unsigned long long cp = 0, pp = 0, nv = 0, lt = 0, pr = 0;
+  unsigned long long c[6] = {0, 0, 0, 0, 0, 0};
   for (int t = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; t < a.nterm; t += nw) {
     const int ci = a.term[t];
-    Searcher<LK, DP> S(a, lane, ci);
     const int own = a.pos[ci] / FAN;
-    S.leaf(own);  // seeds the bound with a spatially adjacent cluster (Alg. 2, "nearby cluster")
-    int top = 0;
-    if (lane == 0) {
-      sn[0] = (uint32_t)(nlev - 1) << 27;
-      sl[0] = 0.f;
-    }
-    top = 1;
-    __syncwarp();
-    while (top > 0) {
-      --top;
-      const uint32_t e = sn[top];
-      const float lb = sl[top];
-      __syncwarp();
-      if (!S.pass(lb)) continue;
-      const int L = (int)(e >> 27), j = (int)(e & ((1u << 27) - 1));
-      if (L == 0) {
-        if (j != own) S.leaf(j);
-        continue;
-      }
-      const int cnt = level_count(a.K, L - 1);
-      const int child = j * FAN + lane;
-      float lbc = INFINITY;
-      bool ok = false;
-      if (child < cnt) {
-        lbc = node_lb<LK, DP>(a, a.lvl_base[L - 1] + child, S.ci32, S.alo, S.ahi, S.fna);
-        ok = S.pass(lbc);
-        S.nodes += 1;
-      }
-      const unsigned m = __ballot_sync(0xffffffffu, ok);
-      if (m) {
-        const int rank = __popc(m & ((1u << lane) - 1u));
-        if (ok) {
-          sn[top + rank] = ((uint32_t)(L - 1) << 27) | (uint32_t)child;
-          sl[top + rank] = lbc;
-        }
-        float mv = ok ? lbc : INFINITY;
-        int ml = lane;
-        warp_argmin_f(mv, ml);
-        __syncwarp();
-        if (lane == 0) {  // nearest child popped first
-          const int mp = top + __popc(m & ((1u << ml) - 1u));
-          const int last = top + __popc(m) - 1;
-          uint32_t tn = sn[mp];
-          float tl = sl[mp];
-          sn[mp] = sn[last];
-          sl[mp] = sl[last];
-          sn[last] = tn;
-          sl[last] = tl;
-        }
-        top += __popc(m);
-        __syncwarp();
+    unsigned long long bk;
+    int bc;
+    if (PREC == 0) {
+      Searcher<LK, DP, M_F64> S(a, lane, ci, INFINITY);
+      traverse(a, S, sn, sl, own, lane);
+      bk = S.bk;
+      bc = S.bc;
+      tally(S, c);
+    } else {
+      Searcher<LK, DP, M_F32> S(a, lane, ci, INFINITY);
+      traverse(a, S, sn, sl, own, lane);
+      if (S.L2 > S.U && S.c1 != INT_MAX) {
+        // exactly one candidate can be the FP64 winner
+        bc = S.c1;
+        bk = S.exact_of(a.pos[bc]);
+        S.rechecks += 1;
+        tally(S, c);
+      } else {
+        tally(S, c);
+        Searcher<LK, DP, M_RECHECK> R(a, lane, ci, S.U);
+        traverse(a, R, sn, sl, own, lane);
+        bk = R.bk;
+        bc = R.bc;
+        tally(R, c);
       }
     }
     if (lane == 0) {
-      a.Ekey[ci] = S.best_key;
-      a.Ecid[ci] = S.best_cid == INT_MAX ? -1 : S.best_cid;
-      if (S.best_cid == INT_MAX) atomicOr(&a.ctr->err, ERR_NO_NN);
+      a.Ekey[ci] = __longlong_as_double((long long)bk);
+      a.Ecid[ci] = bc == INT_MAX ? -1 : bc;
+      if (bc == INT_MAX) atomicOr(&a.ctr->err, ERR_NO_NN);
     }
-    cp += S.cpairs;
-    pp += S.ppairs;
-    nv += S.nodes;
-    lt += S.ltests;
-    pr += S.prows;
   }
-  // per-warp counter totals (lane values differ for nodes; sum them)
+  // node / leaf-slot tests are counted per lane; everything else per warp
   for (int o = 16; o; o >>= 1) {
-    nv += __shfl_xor_sync(0xffffffffu, nv, o);
-    pp += __shfl_xor_sync(0xffffffffu, pp, o);
-    lt += __shfl_xor_sync(0xffffffffu, lt, o);
-    pr += __shfl_xor_sync(0xffffffffu, pr, o);
+    c[2] += __shfl_xor_sync(0xffffffffu, c[2], o);
+    c[3] += __shfl_xor_sync(0xffffffffu, c[3], o);
   }
   if (lane == 0) {
-    atomicAdd(&a.ctr->cluster_pairs, cp);
-    atomicAdd(&a.ctr->point_pairs, pp);
-    atomicAdd(&a.ctr->nodes, nv);
-    atomicAdd(&a.ctr->ltests, lt);
-    atomicAdd(&a.ctr->prows, pr);
+    atomicAdd(&a.ctr->cluster_pairs, c[0]);
+    atomicAdd(&a.ctr->point_pairs, c[1]);
+    atomicAdd(&a.ctr->nodes, c[2]);
+    atomicAdd(&a.ctr->ltests, c[3]);
+    atomicAdd(&a.ctr->prows, c[4]);
+    atomicAdd(&a.ctr->rechecks, c[5]);
   }
 }
 
-template <int LK>
+template <int LK, int PREC>
 cudaError_t launch_lk(const QueryArgs &a, int dp, cudaStream_t s) {
-  const int warps = a.nterm;
-  int blocks = (warps + QWARPS - 1) / QWARPS;
+  int blocks = (a.nterm + QWARPS - 1) / QWARPS;
   if (blocks < 1) blocks = 1;
   switch (dp) {
-    case 2: k_query64<LK, 2><<<blocks, QWARPS * 32, 0, s>>>(a); break;
-    case 4: k_query64<LK, 4><<<blocks, QWARPS * 32, 0, s>>>(a); break;
-    case 8: k_query64<LK, 8><<<blocks, QWARPS * 32, 0, s>>>(a); break;
-    case 16: k_query64<LK, 16><<<blocks, QWARPS * 32, 0, s>>>(a); break;
+    case 2: k_query<LK, 2, PREC><<<blocks, QWARPS * 32, 0, s>>>(a); break;
+    case 4: k_query<LK, 4, PREC><<<blocks, QWARPS * 32, 0, s>>>(a); break;
+    case 8: k_query<LK, 8, PREC><<<blocks, QWARPS * 32, 0, s>>>(a); break;
+    case 16: k_query<LK, 16, PREC><<<blocks, QWARPS * 32, 0, s>>>(a); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
 }
 
+template <int PREC>
+cudaError_t launch_prec(const QueryArgs &a, int dp, cudaStream_t s) {
+  switch (a.linkage) {
+    case LK_COMPLETE: return launch_lk<LK_COMPLETE, PREC>(a, dp, s);
+    case LK_AVERAGE: return launch_lk<LK_AVERAGE, PREC>(a, dp, s);
+    case LK_WARD: return launch_lk<LK_WARD, PREC>(a, dp, s);
+  }
+  return cudaErrorInvalidValue;
+}
+
 }  // namespace
 
 cudaError_t launch_query(const QueryArgs &a, int dp, int prec, cudaStream_t s) {
-  (void)prec;
   if (a.nterm <= 0) return cudaSuccess;
-  switch (a.linkage) {
-    case LK_COMPLETE: return launch_lk<LK_COMPLETE>(a, dp, s);
-    case LK_AVERAGE: return launch_lk<LK_AVERAGE>(a, dp, s);
-    case LK_WARD: return launch_lk<LK_WARD>(a, dp, s);
-  }
-  return cudaErrorInvalidValue;
+  return prec == 0 ? launch_prec<0>(a, dp, s) : launch_prec<1>(a, dp, s);
 }
 
 }  // namespace hacg

@@ -19,6 +19,8 @@ from paper_2106_04727_gb300 import hac, inputs
 pytestmark = pytest.mark.gpu
 
 LKS = ["complete", "average", "ward"]
+PRECS = [hac.PREC_F64, hac.PREC_F32_RECHECK]
+PREC_IDS = ["f64", "f32recheck"]
 RTOL64 = 1e-9
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
 
@@ -52,10 +54,11 @@ def test_fig1_worked_example():
     assert got["stats"]["nn_searches"] == sum(len(t) for t in g["round_terminals"])
 
 
+@pytest.mark.parametrize("prec", PRECS, ids=PREC_IDS)
 @pytest.mark.parametrize("lk", LKS)
-def test_uniform_1024_fp64(lk):
+def test_uniform_1024_fp64(lk, prec):
     X = inputs.workload("uniform2d_1k_f64")
-    _assert_same(hac.cluster(X, lk), oracle.rounds(X, lk))
+    _assert_same(hac.cluster(X, lk, precision=prec), oracle.rounds(X, lk))
 
 
 SHAPES = [(2, 2, np.float64), (3, 1, np.float64), (33, 3, np.float32), (100, 5, np.float32),
@@ -63,12 +66,13 @@ SHAPES = [(2, 2, np.float64), (3, 1, np.float64), (33, 3, np.float32), (100, 5, 
           (300, 16, np.float32), (70, 7, np.float64)]
 
 
+@pytest.mark.parametrize("prec", PRECS, ids=PREC_IDS)
 @pytest.mark.parametrize("lk", LKS)
 @pytest.mark.parametrize("shape", SHAPES, ids=lambda s: f"n{s[0]}d{s[1]}{np.dtype(s[2]).name}")
-def test_shapes(lk, shape):
+def test_shapes(lk, shape, prec):
     n, d, dt = shape
     X = inputs.gaussian_mixture(n, d, 5, seed=n * 31 + d, dtype=dt)
-    _assert_same(hac.cluster(X, lk), oracle.rounds(X.astype(np.float64), lk))
+    _assert_same(hac.cluster(X, lk, precision=prec), oracle.rounds(X.astype(np.float64), lk))
 
 
 @pytest.mark.parametrize("lk", LKS)
@@ -103,47 +107,69 @@ def test_collinear_closed_form(lk):
         s *= 2
 
 
-def test_lattice_complete_exact_ties():
+@pytest.mark.parametrize("prec", PRECS, ids=PREC_IDS)
+def test_lattice_complete_exact_ties(prec):
     for seed in range(3):
         X = inputs.lattice(500, 3, seed=seed, levels=12)
-        got = hac.cluster(X, "complete")
+        got = hac.cluster(X, "complete", precision=prec)
         want = oracle.rounds(X.astype(np.float64), "complete")
         _assert_same(got, want, rtol=0.0)
 
 
+@pytest.mark.parametrize("prec", PRECS, ids=PREC_IDS)
 @pytest.mark.parametrize("lk", ["average", "ward"])
-def test_lattice_ties_valid(lk):
+def test_lattice_ties_valid(lk, prec):
     X = inputs.lattice(300, 4, seed=7, levels=10)
-    got = hac.cluster(X, lk)
+    got = hac.cluster(X, lk, precision=prec)
     bad, stats = oracle.validate(X.astype(np.float64), lk, got, rtol=1e-9)
     assert bad == 0, stats
     assert oracle.check_tree(got, len(X)) == []
 
 
+@pytest.mark.parametrize("prec", PRECS, ids=PREC_IDS)
 @pytest.mark.parametrize("lk", LKS)
-def test_multilevel_tree(lk):
+def test_multilevel_tree(lk, prec):
     """12,000 points: three tree levels, ragged last leaf and node."""
     X = inputs.gaussian_mixture(12000, 2, 40, seed=77)
-    _assert_same(hac.cluster(X, lk), oracle.rounds(X.astype(np.float64), lk))
+    _assert_same(hac.cluster(X, lk, precision=prec), oracle.rounds(X.astype(np.float64), lk))
 
 
+@pytest.mark.parametrize("prec", PRECS, ids=PREC_IDS)
 @pytest.mark.parametrize("lk", LKS)
-def test_gmm5d_sample(lk):
+def test_gmm5d_sample(lk, prec):
     """The 5-D Gaussian-mixture workload's recipe at a size the oracle runs."""
     X = inputs.workload("gmm5d_1m_f32", n=5000)
-    _assert_same(hac.cluster(X, lk), oracle.rounds(X.astype(np.float64), lk))
+    _assert_same(hac.cluster(X, lk, precision=prec), oracle.rounds(X.astype(np.float64), lk))
 
 
-def test_spreaders_sample():
+@pytest.mark.parametrize("prec", PRECS, ids=PREC_IDS)
+@pytest.mark.parametrize("lk", ["average", "ward"])
+def test_lattice16d_sample(lk, prec):
+    """The 16-D lattice tie-stress recipe at oracle size: exact ties among
+    singletons break by cid identically; later near-ties are checked by the
+    greedy-validity replay."""
+    X = inputs.workload("lattice16d_1m_f32", n=2000)
+    got = hac.cluster(X, lk, precision=prec)
+    bad, stats = oracle.validate(X.astype(np.float64), lk, got, rtol=1e-9)
+    assert bad == 0, stats
+    want = oracle.rounds(X.astype(np.float64), lk)
+    # round-0 merges are between singletons at exactly representable distances
+    r0 = lambda d: {(int(a), int(b)) for a, b, r in zip(d["a"], d["b"], d["round"]) if r == 0}
+    assert r0(got) == r0(want)
+
+
+@pytest.mark.parametrize("prec", PRECS, ids=PREC_IDS)
+def test_spreaders_sample(prec):
     X = inputs.spreaders(6000, seed=3000)
     for lk in ("ward", "complete"):
-        _assert_same(hac.cluster(X, lk), oracle.rounds(X.astype(np.float64), lk))
+        _assert_same(hac.cluster(X, lk, precision=prec), oracle.rounds(X.astype(np.float64), lk))
 
 
+@pytest.mark.parametrize("prec", PRECS, ids=PREC_IDS)
 @pytest.mark.parametrize("lk", LKS)
-def test_deterministic(lk):
+def test_deterministic(lk, prec):
     X = inputs.gaussian_mixture(3000, 3, 8, seed=5)
-    a, b = hac.cluster(X, lk), hac.cluster(X, lk)
+    a, b = hac.cluster(X, lk, precision=prec), hac.cluster(X, lk, precision=prec)
     for k in ("a", "b", "size", "round"):
         assert np.array_equal(a[k], b[k])
     assert np.array_equal(a["h"].view(np.int64), b["h"].view(np.int64))
@@ -207,13 +233,14 @@ def _members_small(d, n, cap=64):
     return out
 
 
+@pytest.mark.parametrize("prec", PRECS, ids=PREC_IDS)
 @pytest.mark.parametrize("lk", ["ward"])
-def test_full_size_1m_properties(lk):
+def test_full_size_1m_properties(lk, prec):
     """The 10^6-point 5-D workload in the benchmark's launch configuration:
     a valid tree with monotone heights, and sampled merge heights equal to the
     oracle's linkage distance of the two merged point sets."""
     X = inputs.workload("gmm5d_1m_f32")
-    got = hac.cluster(X, lk)
+    got = hac.cluster(X, lk, precision=prec)
     n = len(X)
     assert oracle.check_tree(got, n, rtol=1e-12) == []
     mem = _members_small(got, n)
@@ -224,3 +251,13 @@ def test_full_size_1m_properties(lk):
         ma, mb = mem[keys[t]]
         want = oracle.cluster_dist(lk, X64[ma], X64[mb])
         assert got["h"][keys[t]] == pytest.approx(want, rel=RTOL64, abs=1e-12)
+    if prec == hac.PREC_F64:
+        _FULL[lk] = got
+    else:
+        # FP32 bulk + FP64 re-score must give the FP64 path's tree exactly
+        ref = _FULL.get(lk) or hac.cluster(X, lk, precision=hac.PREC_F64)
+        c = oracle.compare(got, ref, rtol=RTOL64)
+        assert c["ok"], c
+
+
+_FULL = {}
