@@ -140,6 +140,37 @@ void hac_destroy(hac_t h);
 /* Static description of a status code. */
 const char *hac_strerror(int code);
 
+/* Largest n accepted by hac_run_static. */
+#define HAC_STATIC_MAX_N 4096
+
+/* A whole clustering that allocates nothing (the paper has no counterpart;
+ * this exists for callers that cannot call cudaMalloc when they need a
+ * dendrogram, e.g. a serving process whose memory pool already owns every
+ * byte of the GPU, or latency-sensitive code that must not risk the device
+ * synchronisation that cudaMalloc/cudaFree can cause).
+ *
+ * Same result as hac_create + hac_run + hac_dendrogram on the same points and
+ * options, computed by the same kernels, but all working memory comes from a
+ * fixed 6 MiB device array inside the library, which every GPU that loads the
+ * library holds until the process exits.  No cudaMalloc, cudaFree or other
+ * allocating call is made.
+ *   dev_points  DEVICE pointer, row-major n x d of `dt`, on the current device;
+ *               read only, owned by the caller.
+ *   opts        may be NULL (defaults); opts->stream selects the stream
+ *               (NULL = the legacy default stream).  Blocks until done.
+ *   dev_out     DEVICE buffer of at least n - 1 hac_merge records, owned by the
+ *               caller; receives the merges sorted by (height, size, cid_a).
+ * Errors: HAC_EINVAL for n > HAC_STATIC_MAX_N (or the usual bad arguments,
+ * including non-finite coordinates), HAC_ECAP if cap < n - 1, HAC_EDEVICE if
+ * the array's device address cannot be obtained or a CUDA call fails.
+ * The first call on each device looks up the array's device address (once per
+ * device, with that device current); make that first call before any stream
+ * capture.  Every call shares the one array and overwrites it, so calls that
+ * overlap on the GPU (other host threads, other streams) race and must be
+ * serialised by the caller. */
+int hac_run_static(const void *dev_points, int64_t n, int d, hac_dtype dt, hac_linkage lk,
+                   const hac_opts *opts, hac_merge *dev_out, int64_t cap);
+
 #ifdef __cplusplus
 }
 #endif

@@ -15,6 +15,7 @@
 #include "hac_internal.cuh"
 
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <cstdio>
 #include <cstdlib>
@@ -1172,3 +1173,328 @@ const char *hac_strerror(int code) {
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// hac_run_static: a whole clustering that allocates nothing
+//
+// Some callers cannot call cudaMalloc at the moment they need a clustering:
+// a serving process whose memory pool has already claimed every byte of the
+// GPU, or latency-sensitive code that must not hit cudaMalloc/cudaFree (which
+// can synchronise the whole device).  This entry point runs the same kernels
+// as hac_create/hac_run/hac_dendrogram, but every piece of working memory is
+// carved out of one file-scope device array that the library owns for as
+// long as it is loaded (kStaticArenaBytes on every GPU that loads it).  The
+// caller passes the device input points and a device output buffer.
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr size_t kStaticArenaBytes = (size_t)6 << 20;  // 6 MiB: room for n <= HAC_STATIC_MAX_N
+static __device__ __align__(256) unsigned char g_static_arena[kStaticArenaBytes];
+
+constexpr int kStaticMaxDevices = 64;
+std::atomic<unsigned char *> g_static_ptr[kStaticMaxDevices];  // per device, set on first use
+
+// Device address of the arena on the current device.  Host code must not
+// use the symbol g_static_arena itself: on the host it only names a stand-in.
+int static_arena(unsigned char **out) {
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    cudaGetLastError();
+    return HAC_EDEVICE;
+  }
+  if (dev < 0 || dev >= kStaticMaxDevices) return HAC_EDEVICE;
+  unsigned char *p = g_static_ptr[dev].load(std::memory_order_acquire);
+  if (!p) {
+    void *q = nullptr;
+    if (cudaGetSymbolAddress(&q, g_static_arena) != cudaSuccess || q == nullptr) {
+      cudaGetLastError();
+      return HAC_EDEVICE;
+    }
+    p = (unsigned char *)q;
+    g_static_ptr[dev].store(p, std::memory_order_release);
+  }
+  *out = p;
+  return HAC_OK;
+}
+
+// bump allocator over the arena (256-byte aligned pieces)
+struct Carver {
+  unsigned char *base;
+  size_t off, cap;
+  bool ok;
+  template <typename T>
+  void take(T **p, size_t count) {
+    off = (off + 255) & ~(size_t)255;
+    *p = (T *)(base + off);
+    off += (count ? count : 1) * sizeof(T);
+    if (off > cap) ok = false;
+  }
+};
+
+// the same arrays as alloc_state, carved instead of allocated
+bool carve_state(hac_ctx &h, Carver &cv) {
+  State &s = h.s;
+  const int64_t n = h.n;
+  const int dp = s.dp;
+  for (int b = 0; b < 2; ++b) {
+    cv.take(&s.p64[b], n * dp);
+    cv.take(&s.p32[b], n * dp);
+    cv.take(&s.plab[b], n);
+    cv.take(&s.seg[b], n);
+    cv.take(&s.order[b], n);
+  }
+  cv.take(&s.csize, n);
+  cv.take(&s.q32, n * dp);
+  cv.take(&s.q64, n * dp);
+  cv.take(&s.qblo, n * dp);
+  cv.take(&s.qbhi, n * dp);
+  cv.take(&s.qsz, n);
+  cv.take(&s.qseg, n);
+  cv.take(&s.csum, n * dp);
+  cv.take(&s.cent, n * dp);
+  cv.take(&s.cent32, n * dp);
+  cv.take(&s.blo, n * dp);
+  cv.take(&s.bhi, n * dp);
+  cv.take(&s.succ, n);
+  cv.take(&s.pred, n);
+  cv.take(&s.mround, n);
+  cv.take(&s.isterm, n);
+  cv.take(&s.alive, n);
+  cv.take(&s.rootof, n);
+  cv.take(&s.reloff, n);
+  cv.take(&s.pos, n);
+  cv.take(&s.Ekey, n);
+  cv.take(&s.Ecid, n);
+  cv.take(&s.term, n);
+  cv.take(&s.pair_lo, n / 2 + 1);
+  cv.take(&s.pair_hi, n / 2 + 1);
+  cv.take(&s.pair_key, n / 2 + 1);
+  cv.take(&s.m_a, n);
+  cv.take(&s.m_b, n);
+  cv.take(&s.m_size, n);
+  cv.take(&s.m_round, n);
+  cv.take(&s.m_h, n);
+  int base = 0;
+  const int nlev = tree_levels((int)n);
+  for (int L = 0; L <= MAXLEV; ++L) {
+    s.lvl_base[L] = base;
+    if (L < nlev) base += level_count((int)n, L);
+  }
+  h.nlev_max = nlev;
+  cv.take(&s.nclo, (size_t)base * dp);
+  cv.take(&s.nchi, (size_t)base * dp);
+  cv.take(&s.nhmin, (size_t)base * dp);
+  cv.take(&s.nlmax, (size_t)base * dp);
+  cv.take(&s.nnmin, (size_t)base);
+  cv.take(&s.bsum, 3 * (size_t)cdiv(n, TPB) + 3);
+  cv.take(&s.ctr, 1);
+  for (int b = 0; b < 2; ++b) {
+    cv.take(&h.keys[b], n);
+    cv.take(&h.vals[b], n);
+  }
+  const int ntiles = cdiv(n, RS_TILE);
+  cv.take(&h.hist, (size_t)256 * ntiles + 1);
+  cv.take(&h.hbs, (size_t)cdiv((int64_t)256 * ntiles, SC_TILE) + 1);
+  cv.take(&h.bb, 2 * MAXD);
+  cv.take(&h.dout_round, n);
+  return cv.ok;
+}
+
+// initial layout with stack buffers only (no host or device allocation)
+template <typename T>
+int static_layout(hac_ctx &h, cudaStream_t st) {
+  State &s = h.s;
+  const T *X = (const T *)h.raw;
+  const int64_t n = h.n;
+  const int d = h.d;
+  unsigned long long bb[2 * MAXD];
+  for (int k = 0; k < MAXD; ++k) {
+    bb[k] = ~0ull;
+    bb[MAXD + k] = 0ull;
+  }
+  CK(cudaMemcpyAsync(h.bb, bb, sizeof(bb), cudaMemcpyHostToDevice, st));
+  // the arena keeps the previous call's contents: counters start from zero
+  CK(cudaMemsetAsync(s.ctr, 0, sizeof(Counters), st));
+  k_bbox<T><<<grid_for(n, TPB), TPB, 0, st>>>(X, n, d, h.bb, h.bb + MAXD, s.ctr);
+  CK(cudaGetLastError());
+  Counters c0;
+  CK(cudaMemcpyAsync(bb, h.bb, sizeof(bb), cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(&c0, s.ctr, sizeof(Counters), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  if (c0.err & ERR_NONFINITE) return HAC_EINVAL;
+  MortonParams mp{}, ctrp{};
+  double scale = 0.0;
+  for (int k = 0; k < d; ++k) {
+    unsigned long long u = bb[k], v = bb[MAXD + k];
+    u = (u >> 63) ? (u & 0x7fffffffffffffffull) : ~u;
+    v = (v >> 63) ? (v & 0x7fffffffffffffffull) : ~v;
+    double lo, hi;
+    memcpy(&lo, &u, 8);
+    memcpy(&hi, &v, 8);
+    mp.lo[k] = lo;
+    mp.inv[k] = hi > lo ? 1.0 / (hi - lo) : 0.0;
+    ctrp.lo[k] = 0.5 * (lo + hi);
+    scale = std::max(scale, std::max(std::fabs(lo - ctrp.lo[k]), std::fabs(hi - ctrp.lo[k])));
+  }
+  mp.bits = std::min(21, 64 / d);
+  s.abs_slack = std::max(scale, 1e-300) * std::ldexp(1.0, -18);
+  s.coord_scale = (float)(scale * (1.0 + 1e-6));
+  k_morton<T><<<grid_for(n, TPB), TPB, 0, st>>>(X, n, d, mp, h.keys[0], h.vals[0]);
+  CK(cudaGetLastError());
+  const int sc = radix_sort(&h, (int)n, mp.bits * d, st);
+  if (sc < 0) return sc;
+  h.ocur = h.pcur = 0;
+  s.cur = 0;
+  k_layout<T><<<grid_for(n, TPB), TPB, 0, st>>>(s, X, h.vals[sc], ctrp);
+  CK(cudaGetLastError());
+  Counters c{};
+  c.nterm = (int)n;
+  c.nactive = (int)n;
+  CK(cudaMemcpyAsync(s.ctr, &c, sizeof(Counters), cudaMemcpyHostToDevice, st));
+  return build_tree(&h, s.order[0], (int)n, st);
+}
+
+// Algorithm 1 rounds with the state carved from the arena; writes the
+// canonical dendrogram to `dev_out`
+int static_run(hac_ctx &h, const hac_opts &opt, cudaStream_t st, hac_merge *dev_out) {
+  State &s = h.s;
+  int rc = h.dt == HAC_F32 ? static_layout<float>(h, st) : static_layout<double>(h, st);
+  if (rc) return rc;
+  const auto t0 = std::chrono::steady_clock::now();
+  int K = (int)h.n, nterm = (int)h.n, round = 0;
+  const bool need_points = s.linkage != LK_WARD;
+  Counters c{};
+  while (K > 1) {
+    if (opt.max_rounds && round >= opt.max_rounds) return HAC_ETIMEOUT;
+    if (opt.timeout_s > 0 &&
+        std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count() >
+            opt.timeout_s)
+      return HAC_ETIMEOUT;
+    s.cur = h.pcur;
+    QueryArgs qa{};
+    qa.d = s.d;
+    qa.linkage = s.linkage;
+    qa.round = round;
+    qa.K = K;
+    qa.nterm = nterm;
+    qa.abs_slack = s.abs_slack;
+    qa.coord_scale = s.coord_scale;
+    qa.term = s.term;
+    qa.order = s.order[h.ocur];
+    qa.pos = s.pos;
+    qa.csize = s.csize;
+    qa.seg = s.seg[h.pcur];
+    qa.cent = s.cent;
+    qa.p64 = s.p64[h.pcur];
+    qa.cent32 = s.cent32;
+    qa.blo = s.blo;
+    qa.bhi = s.bhi;
+    qa.p32 = s.p32[h.pcur];
+    qa.pred = s.pred;
+    qa.q32 = s.q32;
+    qa.q64 = s.q64;
+    qa.qblo = s.qblo;
+    qa.qbhi = s.qbhi;
+    qa.qsz = s.qsz;
+    qa.qseg = s.qseg;
+    qa.nclo = s.nclo;
+    qa.nchi = s.nchi;
+    qa.nhmin = s.nhmin;
+    qa.nlmax = s.nlmax;
+    qa.nnmin = s.nnmin;
+    for (int L = 0; L <= MAXLEV; ++L) qa.lvl_base[L] = s.lvl_base[L];
+    qa.Ekey = s.Ekey;
+    qa.Ecid = s.Ecid;
+    qa.ctr = s.ctr;
+    CK(launch_query(qa, s.dp, s.prec, st));
+    k_chain<<<grid_for(nterm, TPB), TPB, 0, st>>>(s, nterm);
+    CK(cudaMemsetAsync(&s.ctr->npairs, 0, sizeof(int32_t), st));
+    k_rnn<<<grid_for(nterm, TPB), TPB, 0, st>>>(s, nterm, round);
+    CK(cudaGetLastError());
+    int npairs = 0;
+    CK(cudaMemcpyAsync(&npairs, &s.ctr->npairs, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    if (npairs <= 0) return HAC_EINTERNAL;
+    k_merge<<<grid_for(npairs, TPB), TPB, 0, st>>>(s, round, npairs);
+    const int nb = cdiv(K, TPB);
+    const int32_t *ord = s.order[h.ocur];
+    int32_t *ordn = s.order[h.ocur ^ 1];
+    k_cmp_count<<<nb, TPB, 0, st>>>(s, ord, K, round);
+    k_cmp_top<<<1, TPB, 0, st>>>(s, nb);
+    k_cmp_write<<<nb, TPB, 0, st>>>(s, ord, ordn, need_points ? s.seg[h.pcur ^ 1] : nullptr, K,
+                                    round);
+    CK(cudaGetLastError());
+    h.ocur ^= 1;
+    if (need_points) {
+      k_relayout<<<grid_for(h.n, TPB), TPB, 0, st>>>(s, h.pcur);
+      h.pcur ^= 1;
+    }
+    K -= npairs;
+    if (K > 1) {
+      rc = build_tree(&h, s.order[h.ocur], K, st);
+      if (rc) return rc;
+    }
+    CK(cudaMemcpyAsync(&c, s.ctr, sizeof(Counters), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    if ((c.err & ~ERR_NONFINITE) || c.nactive != K) return HAC_EINTERNAL;
+    nterm = c.nterm;
+    ++round;
+  }
+  const int64_t m = h.n - 1;
+  if (c.nmerges != m && m > 0) return HAC_EINTERNAL;
+  if (m > 0) {
+    const int mm = (int)m;
+    const int g = grid_for(mm, TPB);
+    int32_t *perm = nullptr;
+    const int fbits[3] = {bits_for(h.n), bits_for(h.n), 64};
+    for (int f = 0; f < 3; ++f) {
+      k_rec_key<<<g, TPB, 0, st>>>(s, mm, f, perm, h.keys[0], h.vals[0]);
+      const int r = radix_sort(&h, mm, fbits[f], st);
+      if (r < 0) return r;
+      if (r == 1)
+        CK(cudaMemcpyAsync(h.vals[0], h.vals[1], (size_t)mm * 4, cudaMemcpyDeviceToDevice, st));
+      perm = h.vals[0];
+    }
+    k_rec_gather<<<g, TPB, 0, st>>>(s, mm, perm, dev_out, h.dout_round);
+    CK(cudaGetLastError());
+  }
+  CK(cudaStreamSynchronize(st));
+  return HAC_OK;
+}
+
+}  // namespace
+
+extern "C" int hac_run_static(const void *dev_points, int64_t n, int d, hac_dtype dt,
+                              hac_linkage lk, const hac_opts *opts, hac_merge *dev_out,
+                              int64_t cap) {
+  if (!dev_points || !dev_out || n < 1 || n > HAC_STATIC_MAX_N || d < 1 || d > MAXD)
+    return HAC_EINVAL;
+  if (dt != HAC_F32 && dt != HAC_F64) return HAC_EINVAL;
+  if (lk != HAC_COMPLETE && lk != HAC_AVERAGE && lk != HAC_WARD) return HAC_EINVAL;
+  if (cap < n - 1) return HAC_ECAP;
+  hac_opts opt;
+  hac_default_opts(&opt);
+  if (opts) opt = *opts;
+  if (opt.precision != HAC_PREC_F64 && opt.precision != HAC_PREC_F32_RECHECK) return HAC_EINVAL;
+  if (opt.cache_slots < 0 || opt.max_rounds < 0 || opt.timeout_s < 0) return HAC_EINVAL;
+  unsigned char *arena = nullptr;
+  int rc = static_arena(&arena);
+  if (rc) return rc;
+  hac_ctx h;  // on the stack; its pointers all point into the arena
+  h.n = n;
+  h.d = d;
+  h.dt = dt;
+  h.lk = lk;
+  h.raw = const_cast<void *>(dev_points);
+  h.s.n = n;
+  h.s.d = d;
+  h.s.dp = pad_dim(d);
+  h.s.linkage = (int)lk;
+  h.s.prec = opt.precision;
+  Carver cv{arena, 0, kStaticArenaBytes, true};
+  if (!carve_state(h, cv)) return HAC_EINVAL;
+  const cudaStream_t st = (cudaStream_t)opt.stream;
+  rc = static_run(h, opt, st, dev_out);
+  if (rc == HAC_EDEVICE) cudaGetLastError();
+  return rc;
+}

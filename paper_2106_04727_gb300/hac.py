@@ -91,6 +91,8 @@ def load(build_if_missing: bool = True):
         L.hac_destroy.restype = None
         L.hac_strerror.argtypes = [i32]
         L.hac_strerror.restype = ctypes.c_char_p
+        L.hac_run_static.argtypes = [P, i64, i32, i32, i32, ctypes.POINTER(hac_opts), P, i64]
+        L.hac_run_static.restype = i32
         _lib = L
         return L
 
@@ -172,6 +174,29 @@ def hac_stats(h) -> dict:
 def hac_destroy(h) -> None:
     if h:
         load().hac_destroy(h)
+
+
+HAC_STATIC_MAX_N = 4096
+
+
+def hac_run_static(dev_points: int, n: int, d: int, dtype, linkage, dev_out: int, cap: int,
+                   precision: int = PREC_F64, stream: int | None = None) -> int:
+    """hac_run_static: the whole clustering with no device allocation.
+
+    For callers that cannot call cudaMalloc when they need a dendrogram (a
+    memory pool that already owns the GPU, or code that must not risk the
+    device-wide synchronisation of cudaMalloc/cudaFree).  ``dev_points`` and
+    ``dev_out`` are device pointers owned by the caller (``dev_out`` holds at
+    least n - 1 records of MERGE_DTYPE); working memory comes from a fixed
+    array inside the library.  Returns the status code.  Calls share that
+    array, so calls that overlap on the GPU must be serialised by the caller.
+    """
+    o = hac_default_opts()
+    o.precision = precision
+    o.stream = stream
+    dt = F32 if np.dtype(dtype) == np.float32 else F64
+    return load().hac_run_static(ctypes.c_void_p(dev_points), n, d, dt, _lk(linkage),
+                                 ctypes.byref(o), ctypes.c_void_p(dev_out), cap)
 
 
 def cluster(points: np.ndarray, linkage, precision: int = PREC_F64, with_rounds: bool = True,
