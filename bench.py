@@ -152,11 +152,15 @@ def main():
     ap.add_argument("--workload", default="gmm5d_1m_f32")
     ap.add_argument("--linkage", default="ward", choices=["ward", "average", "complete"])
     ap.add_argument("--precision", default="f64", choices=["f64", "f32"])
+    ap.add_argument("--cache-slots", type=int, default=-1,
+                    help="Section 5 cache slots per cluster (default 64 for complete/average)")
     ap.add_argument("--ref-sample", type=int, default=20000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
+    if args.cache_slots < 0:
+        args.cache_slots = 0 if args.linkage == "ward" else 64
     if args.impl == "reference":
         return run_reference(args)
 
@@ -181,7 +185,8 @@ def main():
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
 
     def step():
-        rc = hac.hac_run(h, precision=prec, stream=stream.cuda_stream)
+        rc = hac.hac_run(h, precision=prec, cache_slots=args.cache_slots,
+                         stream=stream.cuda_stream)
         if rc != 0:
             raise hac.HacError(rc, "hac_run")
 
@@ -231,7 +236,8 @@ def main():
         for _ in range(2):
             torch.cuda.synchronize()
             t0 = time.perf_counter()
-            res = hac.cluster(Xp, args.linkage, precision=prec, with_rounds=False)
+            res = hac.cluster(Xp, args.linkage, precision=prec, with_rounds=False,
+                              cache_slots=args.cache_slots)
             e2e_t.append(time.perf_counter() - t0)
             assert len(res["a"]) == n - 1
         e2e = {"value": n / min(e2e_t), "unit": UNIT, "h2d_bytes_per_step": int(X.nbytes),
@@ -247,7 +253,8 @@ def main():
             "dtype": "f64" if prec == hac.PREC_F64 else "f32+f64",
             "data": "synthetic",
             "config": {"workload": args.workload, "n": n, "d": d, "linkage": args.linkage,
-                       "precision": args.precision, "parallelism": f"replicas{ws}",
+                       "precision": args.precision, "cache_slots": args.cache_slots,
+                       "parallelism": f"replicas{ws}",
                        "l2": "flushed between steps (256 MB write)"},
             "hac": {"wall_s_per_run": tot_ms / args.steps / 1e3, "rounds": st["rounds"],
                     "nn_searches": st["nn_searches"], "cluster_pairs": st["cluster_pairs"],

@@ -68,7 +68,10 @@ typedef struct {
 
 typedef struct {
   int precision;      /* hac_precision; default HAC_PREC_F64 */
-  int cache_slots;    /* per-cluster pair-distance cache slots (Section 5); 0 = off */
+  int cache_slots;    /* per-cluster pair-distance cache slots (Section 5), complete and
+                         average only (at most 256); 0 = off.  The first run with a larger
+                         value allocates the tables (n * slots * 20 bytes) in the handle.
+                         hac_run_static ignores it. */
   int64_t max_rounds; /* 0 = unlimited; else HAC_ETIMEOUT after this many rounds */
   double timeout_s;   /* 0 = none; else HAC_ETIMEOUT once exceeded (checked per round) */
   void *stream;       /* cudaStream_t to run on; NULL = the handle's own stream */
@@ -96,6 +99,8 @@ typedef struct {
                                 rows of evaluated pairs (each counted once per use) */
   int64_t leaf_tests;        /* candidate clusters tested against the search ball */
   int64_t kernel_launches;   /* all kernels the library launched in the run */
+  int64_t cache_hits;        /* pair distances taken from the cache instead of evaluated */
+  int64_t cache_lw_entries;  /* cache entries derived by Lance-Williams after merges */
 } hac_stats_t;
 
 /* Default options (FP64, no cache, no limits, own stream). */

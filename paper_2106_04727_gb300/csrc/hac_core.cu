@@ -16,6 +16,7 @@
 
 #include <algorithm>
 #include <atomic>
+#include <type_traits>
 #include <chrono>
 #include <cstdio>
 #include <cstdlib>
@@ -248,7 +249,9 @@ __global__ void k_layout(State s, const T *X, const int32_t *perm, MortonParams 
     for (int k = 0; k < dp; ++k) {
       double x = k < d ? (double)X[(int64_t)i * d + k] - ctr_.lo[k] : 0.0;
       s.p64[0][p * dp + k] = x;
-      s.p32[0][p * dp + k] = (float)x;
+      // FP32 input stays unrounded (exact) in the FP32 copy; differences of
+      // FP32 numbers then carry only relative rounding error
+      s.p32[0][p * dp + k] = s.pts32_exact ? (k < d ? (float)X[(int64_t)i * d + k] : 0.f) : (float)x;
       s.csum[(int64_t)i * dp + k] = x;
       s.cent[(int64_t)i * dp + k] = x;
       s.cent32[(int64_t)i * dp + k] = (float)x;
@@ -271,6 +274,7 @@ __global__ void k_layout(State s, const T *X, const int32_t *perm, MortonParams 
     s.alive[i] = 1;
     s.rootof[i] = i;
     s.reloff[i] = 0;
+    s.gen[i] = 0;
     s.order[0][p] = i;
     s.pos[i] = (int32_t)p;
     s.term[p] = i;
@@ -414,6 +418,536 @@ __global__ void k_merge(State s, int round, int npairs) {
     s.alive[hi] = 0;
     s.rootof[hi] = lo;
     s.reloff[hi] = na;
+    s.osize[lo] = na;
+    s.osize[hi] = nb;
+    s.partner[lo] = hi;
+    s.partner[hi] = lo;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// pair-distance cache (Section 5)
+// ---------------------------------------------------------------------------
+
+constexpr unsigned long long CKEY_BUSY = ~1ull;  // a slot whose value is being written
+
+__device__ __forceinline__ unsigned long long slot_key(const State &s, size_t idx) {
+  return *(volatile unsigned long long *)&s.ckey[idx];
+}
+
+// an empty slot, or one whose neighbour has merged since (stale generation)
+__device__ __forceinline__ bool slot_free(const State &s, unsigned long long cur) {
+  if (cur == CKEY_EMPTY) return true;
+  if (cur == CKEY_BUSY) return false;
+  return (unsigned)cur != (unsigned)s.gen[(int)(cur >> 32)];
+}
+
+// Claim slot idx (holding `cur`) by CAS to BUSY, write the value, then
+// publish the key: concurrent writers skip BUSY slots, so a slot's key and
+// value always come from the same writer.  Readers run in later kernels.
+__device__ bool slot_put(const State &s, size_t idx, unsigned long long cur,
+                         unsigned long long want, double v, float e) {
+  if (atomicCAS(&s.ckey[idx], cur, CKEY_BUSY) != cur) return false;
+  s.cval[idx] = v;
+  s.cerr[idx] = e;
+  __threadfence();
+  atomicExch(&s.ckey[idx], want);
+  return true;
+}
+
+// Insert (nbr -> v, e) into the table of `owner` if there is a free slot;
+// an entry already present is kept.
+__device__ void cache_insert(const State &s, int owner, int nbr, int nbr_gen, double v, float e) {
+  const int S = s.cache_slots;
+  const unsigned long long want = ckey_of(nbr, nbr_gen);
+  const size_t base = (size_t)owner * S;
+  int t = (int)(((unsigned)nbr * 2654435761u) % (unsigned)S);
+  for (int q = 0; q < S; ++q, t = t + 1 == S ? 0 : t + 1) {
+    // a free slot only turns BUSY or live within a kernel, so this ends
+    for (;;) {
+      const unsigned long long cur = slot_key(s, base + t);
+      if (cur == want) return;
+      if (!slot_free(s, cur)) break;
+      if (slot_put(s, base + t, cur, want, v, e)) return;
+    }
+  }
+}
+
+// pairs evaluated by the search, into both clusters' tables
+__global__ void k_cache_insert(State s) {
+  const int m = min(s.ctr->nins, s.ins_cap);
+  for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < m; q += gridDim.x * blockDim.x) {
+    const int i = s.ins_i[q], j = s.ins_j[q];
+    cache_insert(s, i, j, s.gen[j], s.ins_v[q], s.ins_e[q]);
+    cache_insert(s, j, i, s.gen[i], s.ins_v[q], s.ins_e[q]);
+  }
+}
+
+struct CEntry {
+  int cid;
+  float err;
+  double val;
+};
+
+constexpr int CM_WARPS = 2;  // warps per block of k_cache_merge (4 * slots entries each)
+
+// look for neighbour `g` in a warp-local list
+__device__ __forceinline__ int clist_find(const CEntry *L, int n, int g) {
+  for (int t = 0; t < n; ++t)
+    if (L[t].cid == g) return t;
+  return -1;
+}
+
+// look for the entry of `nbr` (at its current generation) in a global table
+__device__ bool ctable_find(const State &s, int owner, int nbr, double &v, float &e) {
+  const int S = s.cache_slots;
+  const unsigned long long want = ckey_of(nbr, s.gen[nbr]);
+  for (int t = 0; t < S; ++t)
+    if (s.ckey[(size_t)owner * S + t] == want) {
+      v = s.cval[(size_t)owner * S + t];
+      e = s.cerr[(size_t)owner * S + t];
+      return true;
+    }
+  return false;
+}
+
+// Cache update after the merges of a round (Algorithm 5), one warp per merged
+// pair (lo, hi) -> k (cid lo).  From the tables of lo and hi, every neighbour g
+// whose distances to both lo and hi are known gets D(k, g) by Lance-Williams
+// (Table 2): complete = max, average = size-weighted mean; if g itself merged
+// this round with g2 (case 1), D(k, g u g2) combines the four distances
+// lo/hi x g/g2.  The new entries replace lo's table and are also inserted into
+// g's table (case 2).  Error bounds combine the same way (max / weighted mean).
+// Generations are bumped only afterwards (k_gen_bump), so every lookup here
+// sees the pre-merge generations.
+template <int LK>
+__global__ void k_cache_merge(State s, int npairs, int round) {
+  extern __shared__ unsigned char smem_raw[];
+  const int S = s.cache_slots;
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  CEntry *A = (CEntry *)smem_raw + (size_t)wib * 4 * S;
+  CEntry *B = A + S;
+  CEntry *N = B + S;  // up to 2S new entries (cid, err, val); gen kept in a parallel array
+  __shared__ int cnt[CM_WARPS][3];
+  __shared__ int ngen_s[CM_WARPS][2 * CACHE_MAX_SLOTS];
+  int *ngen = ngen_s[wib];
+  const int warps = (gridDim.x * blockDim.x) >> 5;
+  for (int p = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; p < npairs; p += warps) {
+    const int lo = s.pair_lo[p], hi = s.pair_hi[p];
+    const double na = (double)s.osize[lo], nb = (double)s.osize[hi];
+    if (lane == 0) cnt[wib][0] = cnt[wib][1] = cnt[wib][2] = 0;
+    __syncwarp();
+    // valid entries of the two old tables
+    for (int side = 0; side < 2; ++side) {
+      const int owner = side ? hi : lo;
+      CEntry *L = side ? B : A;
+      for (int base = 0; base < S; base += 32) {
+        const int t = base + lane;
+        bool v = false;
+        unsigned long long key = CKEY_EMPTY;
+        if (t < S) {
+          key = s.ckey[(size_t)owner * S + t];
+          v = key != CKEY_EMPTY && (unsigned)key == (unsigned)s.gen[(int)(key >> 32)];
+        }
+        const unsigned m = __ballot_sync(0xffffffffu, v);
+        if (v) {
+          const int at = cnt[wib][side] + __popc(m & ((1u << lane) - 1u));
+          L[at].cid = (int)(key >> 32);
+          L[at].val = s.cval[(size_t)owner * S + t];
+          L[at].err = s.cerr[(size_t)owner * S + t];
+        }
+        __syncwarp();
+        if (lane == 0) cnt[wib][side] += __popc(m);
+        __syncwarp();
+      }
+    }
+    const int nA = cnt[wib][0], nB = cnt[wib][1];
+    const double wa = na / (na + nb), wb = nb / (na + nb);
+    // neighbours known from lo's table
+    for (int t = lane; t < nA; t += 32) {
+      const int g = A[t].cid;
+      if (g == hi) continue;
+      double v = -1.0;
+      float e = 0.f;
+      int gg = 0;
+      if (s.mround[g] == round) {
+        if (!s.alive[g]) continue;  // the retired side: its survivor handles the pair
+        const int g2 = s.partner[g];
+        const int a2 = clist_find(A, nA, g2), b1 = clist_find(B, nB, g), b2 = clist_find(B, nB, g2);
+        if (a2 < 0 || b1 < 0 || b2 < 0) continue;
+        const double ng = (double)s.osize[g], ng2 = (double)s.osize[g2];
+        if (LK == 0) {
+          v = fmax(fmax(A[t].val, A[a2].val), fmax(B[b1].val, B[b2].val));
+          e = fmaxf(fmaxf(A[t].err, A[a2].err), fmaxf(B[b1].err, B[b2].err));
+        } else {
+          const double w = 1.0 / ((na + nb) * (ng + ng2));
+          v = (na * ng * A[t].val + na * ng2 * A[a2].val + nb * ng * B[b1].val +
+               nb * ng2 * B[b2].val) * w;
+          e = (float)((na * ng * A[t].err + na * ng2 * A[a2].err + nb * ng * B[b1].err +
+                       nb * ng2 * B[b2].err) * w);
+        }
+        gg = s.gen[g] + 1;
+      } else {
+        double vh;
+        float eh;
+        const int b1 = clist_find(B, nB, g);
+        if (b1 >= 0) {
+          vh = B[b1].val;
+          eh = B[b1].err;
+        } else if (!ctable_find(s, g, hi, vh, eh)) {
+          continue;
+        }
+        if (LK == 0) {
+          v = fmax(A[t].val, vh);
+          e = fmaxf(A[t].err, eh);
+        } else {
+          v = wa * A[t].val + wb * vh;
+          e = (float)(wa * A[t].err + wb * eh);
+        }
+        gg = s.gen[g];
+        cache_insert(s, g, lo, s.gen[lo] + 1, v, e);
+      }
+      const int at = atomicAdd(&cnt[wib][2], 1);
+      N[at].cid = g;
+      N[at].val = v;
+      N[at].err = e;
+      ngen[at] = gg;
+    }
+    __syncwarp();
+    // neighbours known only from hi's table (case 2 needs D(lo, g) from g's table)
+    for (int t = lane; t < nB; t += 32) {
+      const int g = B[t].cid;
+      if (g == lo || s.mround[g] == round || clist_find(A, nA, g) >= 0) continue;
+      double vl;
+      float el;
+      if (!ctable_find(s, g, lo, vl, el)) continue;
+      double v;
+      float e;
+      if (LK == 0) {
+        v = fmax(vl, B[t].val);
+        e = fmaxf(el, B[t].err);
+      } else {
+        v = wa * vl + wb * B[t].val;
+        e = (float)(wa * el + wb * B[t].err);
+      }
+      cache_insert(s, g, lo, s.gen[lo] + 1, v, e);
+      const int at = atomicAdd(&cnt[wib][2], 1);
+      N[at].cid = g;
+      N[at].val = v;
+      N[at].err = e;
+      ngen[at] = s.gen[g];
+    }
+    __syncwarp();
+    // the merged cluster's new table (first S entries), replacing lo's
+    const int nN = min(cnt[wib][2], S);
+    for (int t = lane; t < S; t += 32) {
+      const size_t slot = (size_t)lo * S + t;
+      if (t < nN) {
+        s.ckey[slot] = ckey_of(N[t].cid, ngen[t]);
+        s.cval[slot] = N[t].val;
+        s.cerr[slot] = N[t].err;
+      } else {
+        s.ckey[slot] = CKEY_EMPTY;
+      }
+    }
+    if (lane == 0) atomicAdd((unsigned long long *)&s.ctr->cache_lw, (unsigned long long)nN);
+    __syncwarp();
+  }
+}
+
+// ---------------------------------------------------------------------------
+// big pairs: evaluated by the whole GPU, then cached for the re-run search
+// ---------------------------------------------------------------------------
+constexpr int BIG_TPB = 256;       // threads per tile
+constexpr int BIG_PPT = 2;         // points of the larger cluster per thread
+constexpr int BIG_TILE = BIG_TPB * BIG_PPT;  // FP64 tiles
+constexpr int B32_PPT = 4;
+constexpr int B32_TILE = BIG_TPB * B32_PPT;  // FP32 tiles
+constexpr int BIG_BATCH = 512;     // requests per batch (one scan block)
+
+// tile prefix of the batch's requests: tiles = ceil(larger size / 256)
+__global__ void k_big_tiles(State s, int r0, int m) {
+  const int t = threadIdx.x;
+  int v = 0;
+  if (t < m) {
+    const int nL = max(s.breq_na[r0 + t], s.breq_nb[r0 + t]);
+    const int w = s.breq_exact[r0 + t] ? BIG_TILE : B32_TILE;
+    v = s.breq_na[r0 + t] > 0 ? (nL + w - 1) / w : 0;  // na = 0: dropped duplicate
+  }
+  __shared__ int ws[BIG_BATCH / 32];
+  const int lane = t & 31, w = t >> 5;
+  int x = v;
+  for (int o = 1; o < 32; o <<= 1) {
+    int y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) ws[w] = x;
+  __syncthreads();
+  if (w == 0) {
+    int z = lane < BIG_BATCH / 32 ? ws[lane] : 0;
+    for (int o = 1; o < 32; o <<= 1) {
+      int y = __shfl_up_sync(0xffffffffu, z, o);
+      if (lane >= o) z += y;
+    }
+    if (lane < BIG_BATCH / 32) ws[lane] = z;
+  }
+  __syncthreads();
+  const int incl = x + (w ? ws[w - 1] : 0);
+  if (t < m) s.btile[t + 1] = incl;
+  if (t == 0) s.btile[0] = 0;
+}
+
+// One CTA per tile: 512 points of the larger cluster (two per thread)
+// against every point of the smaller one, staged through shared memory, so
+// each staged point feeds two distances.  The tile's partial (sum of
+// distances, or max of squared distances) goes to bpart[tile].  FP32 partial
+// sums of at most 32 terms are flushed into FP64 accumulators.  Tiles whose
+// request wants the other precision are left to the other launch.
+template <int LK, int DP, typename T>
+__global__ void __launch_bounds__(BIG_TPB) k_big_eval(State s, int r0, int m) {
+  constexpr bool EXACT = sizeof(T) == 8;
+  __shared__ T sh[BIG_TPB * DP];
+  __shared__ double red[BIG_TPB / 32];
+  const T *P = EXACT ? (const T *)s.p64[s.cur] : (const T *)s.p32[s.cur];
+  const int total = s.btile[m];
+  for (int tile = blockIdx.x; tile < total; tile += gridDim.x) {
+    int lo = 0, hi = m;  // request with btile[lo] <= tile < btile[lo + 1]
+    while (hi - lo > 1) {
+      const int mid = (lo + hi) >> 1;
+      if (s.btile[mid] <= tile) lo = mid; else hi = mid;
+    }
+    const int r = r0 + lo;
+    if ((s.breq_exact[r] != 0) != EXACT) continue;  // uniform over the CTA
+    int sL = s.breq_sa[r], nL = s.breq_na[r], sS = s.breq_sb[r], nS = s.breq_nb[r];
+    if (nS > nL) {
+      int t0 = sL; sL = sS; sS = t0;
+      t0 = nL; nL = nS; nS = t0;
+    }
+    const int l0 = (tile - s.btile[lo]) * BIG_TILE + threadIdx.x, l1 = l0 + BIG_TPB;
+    const bool v0 = l0 < nL, v1 = l1 < nL;
+    T x0[DP], x1[DP];
+#pragma unroll
+    for (int k = 0; k < DP; ++k) {
+      x0[k] = v0 ? P[(size_t)(sL + l0) * DP + k] : (T)0;
+      x1[k] = v1 ? P[(size_t)(sL + l1) * DP + k] : (T)0;
+    }
+    double acc = 0.0;
+    T macc = 0;
+    for (int c0 = 0; c0 < nS; c0 += BIG_TPB) {
+      const int cn = min(BIG_TPB, nS - c0);
+      __syncthreads();
+      for (int i = threadIdx.x; i < cn * DP; i += BIG_TPB) sh[i] = P[(size_t)(sS + c0) * DP + i];
+      __syncthreads();
+      T part = 0;
+      int cnt = 0;
+      for (int j = 0; j < cn; ++j) {
+        T d0 = 0, d1 = 0;
+#pragma unroll
+        for (int k = 0; k < DP; ++k) {
+          const T y = sh[j * DP + k];
+          const T t0 = x0[k] - y, t1 = x1[k] - y;
+          d0 = d0 + t0 * t0;
+          d1 = d1 + t1 * t1;
+        }
+        if (LK == 0) {
+          if (v0) macc = d0 > macc ? d0 : macc;
+          if (v1) macc = d1 > macc ? d1 : macc;
+        } else {
+          const T s0 = v0 ? (EXACT ? (T)sqrt((double)d0) : (T)sqrtf((float)d0)) : (T)0;
+          const T s1 = v1 ? (EXACT ? (T)sqrt((double)d1) : (T)sqrtf((float)d1)) : (T)0;
+          part += s0 + s1;
+          if (!EXACT && ++cnt == 16) {  // at most 32 terms per FP32 partial
+            acc += (double)part;
+            part = 0;
+            cnt = 0;
+          }
+        }
+      }
+      if (LK != 0) acc += (double)part;
+    }
+    // block reduction in a fixed order (deterministic)
+    double v = LK == 0 ? (double)macc : acc;
+    for (int o = 16; o; o >>= 1) {
+      const double u = __shfl_xor_sync(0xffffffffu, v, o);
+      v = LK == 0 ? fmax(v, u) : v + u;
+    }
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double t = red[0];
+      for (int w = 1; w < BIG_TPB / 32; ++w) t = LK == 0 ? fmax(t, red[w]) : t + red[w];
+      s.bpart[tile] = t;
+    }
+  }
+}
+
+// FP32 tiles, specialised on the true dimension D (rows have stride DP):
+// 1024 points of the larger cluster per CTA (four per thread) against the
+// smaller cluster staged through shared memory 256 points at a time.  Square
+// roots use the hardware approximation (sqrt.approx.f32); with it a term's
+// relative error stays within ((D+1)/2 + 4)u <= (D+16)u, the bound the search
+// states for FP32 distances.  FP32 partials sum 32 terms (8 staged points x 4)
+// before an FP64 add.
+__device__ __forceinline__ float sqrt_approx(float x) {
+  float r;
+  asm("sqrt.approx.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+
+template <int LK, int D, int DP>
+__global__ void __launch_bounds__(BIG_TPB) k_big_eval32(State s, int r0, int m) {
+  __shared__ float sh[BIG_TPB * D];
+  __shared__ double red[BIG_TPB / 32];
+  const float *P = s.p32[s.cur];
+  const int total = s.btile[m];
+  for (int tile = blockIdx.x; tile < total; tile += gridDim.x) {
+    int lo = 0, hi = m;  // request with btile[lo] <= tile < btile[lo + 1]
+    while (hi - lo > 1) {
+      const int mid = (lo + hi) >> 1;
+      if (s.btile[mid] <= tile) lo = mid; else hi = mid;
+    }
+    const int r = r0 + lo;
+    if (s.breq_exact[r] != 0) continue;  // FP64 requests: k_big_eval<..., double>
+    int sL = s.breq_sa[r], nL = s.breq_na[r], sS = s.breq_sb[r], nS = s.breq_nb[r];
+    if (nS > nL) {
+      int t0 = sL; sL = sS; sS = t0;
+      t0 = nL; nL = nS; nS = t0;
+    }
+    const int q = tile - s.btile[lo];
+    float x[B32_PPT][D];
+    bool v[B32_PPT];
+#pragma unroll
+    for (int p = 0; p < B32_PPT; ++p) {
+      const int l = q * B32_TILE + p * BIG_TPB + threadIdx.x;
+      v[p] = l < nL;
+#pragma unroll
+      for (int k = 0; k < D; ++k) x[p][k] = v[p] ? P[(size_t)(sL + l) * DP + k] : 0.f;
+    }
+    double acc = 0.0;
+    float macc = 0.f;
+    for (int c0 = 0; c0 < nS; c0 += BIG_TPB) {
+      const int cn = min(BIG_TPB, nS - c0);
+      __syncthreads();
+      for (int i = threadIdx.x; i < cn * D; i += BIG_TPB) {
+        const int j = i / D, k = i - j * D;
+        sh[i] = P[(size_t)(sS + c0 + j) * DP + k];
+      }
+      __syncthreads();
+      for (int j0 = 0; j0 < cn; j0 += 8) {
+        float part = 0.f;
+        const int jn = min(8, cn - j0);
+#pragma unroll
+        for (int jj = 0; jj < 8; ++jj) {
+          if (jj < jn) {
+            const float *y = sh + (j0 + jj) * D;
+#pragma unroll
+            for (int p = 0; p < B32_PPT; ++p) {
+              float d2 = 0.f;
+#pragma unroll
+              for (int k = 0; k < D; ++k) {
+                const float t = x[p][k] - y[k];
+                d2 = fmaf(t, t, d2);
+              }
+              if (LK == 0)
+                macc = v[p] ? fmaxf(macc, d2) : macc;
+              else
+                part += v[p] ? sqrt_approx(d2) : 0.f;
+            }
+          }
+        }
+        if (LK != 0) acc += (double)part;
+      }
+    }
+    double val = LK == 0 ? (double)macc : acc;
+    for (int o = 16; o; o >>= 1) {
+      const double u = __shfl_xor_sync(0xffffffffu, val, o);
+      val = LK == 0 ? fmax(val, u) : val + u;
+    }
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = val;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double t = red[0];
+      for (int w = 1; w < BIG_TPB / 32; ++w) t = LK == 0 ? fmax(t, red[w]) : t + red[w];
+      s.bpart[tile] = t;
+    }
+  }
+}
+
+// Drop the second of two requests for the same unordered pair in a batch
+// (both terminals asked): one value fills both tables.  Quadratic in the
+// batch, one block of BIG_BATCH threads.
+__global__ void k_big_dedup(State s, int r0, int m) {
+  const int t = threadIdx.x;
+  if (t >= m) return;
+  const int r = r0 + t;
+  const int a = min(s.breq_i[r], s.breq_j[r]), b = max(s.breq_i[r], s.breq_j[r]);
+  const uint8_t ex = s.breq_exact[r];
+  for (int u = 0; u < t; ++u) {
+    const int q = r0 + u;
+    if (min(s.breq_i[q], s.breq_j[q]) == a && max(s.breq_i[q], s.breq_j[q]) == b &&
+        s.breq_exact[q] >= ex) {
+      s.breq_na[r] = 0;  // k_big_tiles gives it no tiles
+      return;
+    }
+  }
+}
+
+// insert that may evict: a big pair's value must land in both tables
+// (if a concurrent writer holds the home slot the value is dropped; the
+// re-run search then asks for it again or evaluates it itself)
+__device__ void cache_insert_evict(const State &s, int owner, int nbr, int nbr_gen, double v,
+                                   float e) {
+  const int S = s.cache_slots;
+  const unsigned long long want = ckey_of(nbr, nbr_gen);
+  const size_t base = (size_t)owner * S;
+  const int t0 = (int)(((unsigned)nbr * 2654435761u) % (unsigned)S);
+  for (int q = 0; q < S; ++q) {
+    const int t = (t0 + q) % S;
+    for (;;) {
+      const unsigned long long cur = slot_key(s, base + t);
+      if (cur == want) return;
+      if (!slot_free(s, cur)) break;
+      if (slot_put(s, base + t, cur, want, v, e)) return;
+    }
+  }
+  const unsigned long long cur = slot_key(s, base + t0);  // full of live entries
+  if (cur != CKEY_BUSY && cur != want) slot_put(s, base + t0, cur, want, v, e);
+}
+
+// one warp per request: fold its tiles in order, cache the distance
+__global__ void k_big_final(State s, int r0, int m) {
+  const int lane = threadIdx.x & 31;
+  const int warps = (gridDim.x * blockDim.x) >> 5;
+  for (int q = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; q < m; q += warps) {
+    const int r = r0 + q;
+    if (s.breq_na[r] == 0) continue;  // duplicate dropped by k_big_dedup
+    const int t0 = s.btile[q], t1 = s.btile[q + 1];
+    double v = 0.0;
+    for (int t = t0 + lane; t < t1; t += 32) v = s.linkage == 0 ? fmax(v, s.bpart[t]) : v + s.bpart[t];
+    for (int o = 16; o; o >>= 1) {
+      const double u = __shfl_xor_sync(0xffffffffu, v, o);
+      v = s.linkage == 0 ? fmax(v, u) : v + u;
+    }
+    if (lane == 0) {
+      const int i = s.breq_i[r], j = s.breq_j[r];
+      const double nn = (double)s.breq_na[r] * (double)s.breq_nb[r];
+      const double D = s.linkage == 0 ? sqrt(v) : v / nn;
+      const bool exact = s.breq_exact[r] != 0;
+      atomicAdd(&s.ctr->big_pp, (unsigned long long)s.breq_na[r] * (unsigned long long)s.breq_nb[r]);
+      if (exact) atomicAdd(&s.ctr->big_exact, 1ull);
+      const float e = exact ? 0.f
+: fmaxf(s.delta_pts, EST_MARK);
+      cache_insert_evict(s, i, j, s.gen[j], D, e);
+      cache_insert_evict(s, j, i, s.gen[i], D, e);
+    }
+  }
+}
+
+// merged cids change identity: entries that name them go stale
+__global__ void k_gen_bump(State s, int npairs) {
+  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < npairs; p += gridDim.x * blockDim.x) {
+    s.gen[s.pair_lo[p]] += 1;
+    s.gen[s.pair_hi[p]] += 1;
   }
 }
 
@@ -582,6 +1116,10 @@ struct hac_ctx {
   int32_t *hist = nullptr, *hbs = nullptr;
   unsigned long long *bb = nullptr;  // 2 x MAXD bbox words
   int nlev_max = 1;
+  int cache_alloc_slots = 0;  // slots per cluster the cache tables were allocated for
+  // pairs of at least this many point pairs go to the GPU-wide evaluation
+  // (FP32 / FP64 values); HAC_BIG_PAIRS / HAC_BIG_PAIRS_F64 override them
+  long long big_pairs = BIG_PAIRS, big_pairs64 = BIG_PAIRS_F64;
   int64_t launches = 0;  // kernels launched in the current run
   int ocur = 0, pcur = 0;
   bool done = false;
@@ -651,6 +1189,9 @@ int alloc_state(hac_ctx *h) {
   A(s.alive, n);
   A(s.rootof, n);
   A(s.reloff, n);
+  A(s.osize, n);
+  A(s.partner, n);
+  A(s.gen, n);
   A(s.pos, n);
   A(s.Ekey, n);
   A(s.Ecid, n);
@@ -703,6 +1244,49 @@ int grid_for(int64_t work, int tpb) {
   if (g < 1) g = 1;
   if (g > 152 * 64) g = 152 * 64;
   return (int)g;
+}
+
+template <int LK, int D>
+void launch_big32(const State &s, int r0, int m, cudaStream_t st) {
+  constexpr int DP = D <= 2 ? 2 : D <= 4 ? 4 : D <= 8 ? 8 : 16;
+  k_big_eval32<LK, D, DP><<<152 * 8, BIG_TPB, 0, st>>>(s, r0, m);
+}
+
+template <int LK>
+int launch_big_lk(const State &s, int r0, int m, cudaStream_t st) {
+  const int g = 152 * 8;
+  switch (s.d) {  // FP32 requests, specialised on the true dimension
+    case 1: launch_big32<LK, 1>(s, r0, m, st); break;
+    case 2: launch_big32<LK, 2>(s, r0, m, st); break;
+    case 3: launch_big32<LK, 3>(s, r0, m, st); break;
+    case 4: launch_big32<LK, 4>(s, r0, m, st); break;
+    case 5: launch_big32<LK, 5>(s, r0, m, st); break;
+    case 6: launch_big32<LK, 6>(s, r0, m, st); break;
+    case 7: launch_big32<LK, 7>(s, r0, m, st); break;
+    case 8: launch_big32<LK, 8>(s, r0, m, st); break;
+    case 9: launch_big32<LK, 9>(s, r0, m, st); break;
+    case 10: launch_big32<LK, 10>(s, r0, m, st); break;
+    case 11: launch_big32<LK, 11>(s, r0, m, st); break;
+    case 12: launch_big32<LK, 12>(s, r0, m, st); break;
+    case 13: launch_big32<LK, 13>(s, r0, m, st); break;
+    case 14: launch_big32<LK, 14>(s, r0, m, st); break;
+    case 15: launch_big32<LK, 15>(s, r0, m, st); break;
+    case 16: launch_big32<LK, 16>(s, r0, m, st); break;
+    default: return HAC_EINTERNAL;
+  }
+  switch (s.dp) {  // FP64 requests
+    case 2: k_big_eval<LK, 2, double><<<g, BIG_TPB, 0, st>>>(s, r0, m); break;
+    case 4: k_big_eval<LK, 4, double><<<g, BIG_TPB, 0, st>>>(s, r0, m); break;
+    case 8: k_big_eval<LK, 8, double><<<g, BIG_TPB, 0, st>>>(s, r0, m); break;
+    case 16: k_big_eval<LK, 16, double><<<g, BIG_TPB, 0, st>>>(s, r0, m); break;
+    default: return HAC_EINTERNAL;
+  }
+  CK(cudaGetLastError());
+  return HAC_OK;
+}
+
+int launch_big(const State &s, int r0, int m, cudaStream_t st) {
+  return s.linkage == 0 ? launch_big_lk<0>(s, r0, m, st) : launch_big_lk<1>(s, r0, m, st);
 }
 
 template <int DP>
@@ -795,6 +1379,7 @@ int init_layout(hac_ctx *h, cudaStream_t st) {
   mp.bits = std::min(21, 64 / d);
   s.abs_slack = std::max(scale, 1e-300) * std::ldexp(1.0, -18);
   s.coord_scale = (float)(scale * (1.0 + 1e-6));
+  s.delta_pts = s.pts32_exact ? 0.f : 2.01f * 5.9604645e-8f * s.coord_scale * std::sqrt((float)d);
   k_morton<T><<<grid_for(n, TPB), TPB, 0, st>>>(X, n, d, mp, h->keys[0], h->vals[0]);
   CK(cudaGetLastError());
   int sc = radix_sort(h, (int)n, mp.bits * d, st);
@@ -834,6 +1419,9 @@ int create_common(const void *pts, bool dev, int64_t n, int d, hac_dtype dt, hac
   h->s.d = d;
   h->s.dp = pad_dim(d);
   h->s.linkage = (int)lk;
+  h->s.pts32_exact = dt == HAC_F32;
+  if (const char *e = getenv("HAC_BIG_PAIRS")) h->big_pairs = std::max(1ll, atoll(e));
+  if (const char *e = getenv("HAC_BIG_PAIRS_F64")) h->big_pairs64 = std::max(1ll, atoll(e));
   if (cudaStreamCreateWithFlags(&h->own, cudaStreamNonBlocking) != cudaSuccess) {
     cudaGetLastError();
     delete h;
@@ -883,6 +1471,35 @@ int run_impl(hac_ctx *h, const hac_opts *o) {
   State &s = h->s;
   s.prec = opt.precision;
   h->done = false;
+  // Section 5 cache tables (complete / average only: Ward distances are O(1))
+  const int slots = s.linkage == LK_WARD ? 0 : std::min(opt.cache_slots, CACHE_MAX_SLOTS);
+  if (slots > h->cache_alloc_slots) {
+    int rc0 = 0;
+    const size_t cells = (size_t)h->n * slots;
+    const int64_t cap = std::max<int64_t>(4 * h->n, 1 << 16);
+    if ((rc0 = dalloc(h, &s.ckey, cells)) || (rc0 = dalloc(h, &s.cval, cells)) ||
+        (rc0 = dalloc(h, &s.cerr, cells)) || (rc0 = dalloc(h, &s.ins_i, cap)) ||
+        (rc0 = dalloc(h, &s.ins_j, cap)) || (rc0 = dalloc(h, &s.ins_v, cap)) ||
+        (rc0 = dalloc(h, &s.ins_e, cap)))
+      return rc0;
+    s.ins_cap = (int)cap;
+    if (!s.breq_i) {  // big-pair deferral buffers (sized once per handle)
+      const int bcap = 1 << 18;
+      const size_t tiles = (size_t)BIG_BATCH * (size_t)cdiv(h->n, BIG_TILE) + BIG_BATCH;
+      if ((rc0 = dalloc(h, &s.breq_i, bcap)) || (rc0 = dalloc(h, &s.breq_j, bcap)) ||
+          (rc0 = dalloc(h, &s.breq_sa, bcap)) || (rc0 = dalloc(h, &s.breq_na, bcap)) ||
+          (rc0 = dalloc(h, &s.breq_sb, bcap)) || (rc0 = dalloc(h, &s.breq_nb, bcap)) ||
+          (rc0 = dalloc(h, &s.breq_exact, bcap)) || (rc0 = dalloc(h, &s.btile, BIG_BATCH + 1)) ||
+          (rc0 = dalloc(h, &s.bpart, tiles)) || (rc0 = dalloc(h, &s.pend[0], h->n)) ||
+          (rc0 = dalloc(h, &s.pend[1], h->n)))
+        return rc0;
+      s.breq_cap = bcap;
+    }
+    h->cache_alloc_slots = slots;
+  }
+  s.cache_slots = slots;
+  if (slots > 0)
+    CK(cudaMemsetAsync(s.ckey, 0xff, (size_t)h->n * slots * sizeof(unsigned long long), st));
   h->st = hac_stats_t{};
   h->st.device_bytes = h->bytes;
   const auto t0 = std::chrono::steady_clock::now();
@@ -921,6 +1538,7 @@ int run_impl(hac_ctx *h, const hac_opts *o) {
     qa.nterm = nterm;
     qa.abs_slack = s.abs_slack;
     qa.coord_scale = s.coord_scale;
+    qa.delta_pts = s.delta_pts;
     qa.term = s.term;
     qa.order = s.order[h->ocur];
     qa.pos = s.pos;
@@ -948,10 +1566,78 @@ int run_impl(hac_ctx *h, const hac_opts *o) {
     qa.Ekey = s.Ekey;
     qa.Ecid = s.Ecid;
     qa.ctr = s.ctr;
+    qa.cache_slots = s.cache_slots;
+    qa.ins_cap = s.ins_cap;
+    qa.ckey = s.ckey;
+    qa.cval = s.cval;
+    qa.cerr = s.cerr;
+    qa.gen = s.gen;
+    qa.ins_i = s.ins_i;
+    qa.ins_j = s.ins_j;
+    qa.ins_v = s.ins_v;
+    qa.ins_e = s.ins_e;
+    const bool defer = s.cache_slots > 0 && need_points;
+    qa.defer = defer ? 1 : 0;
+    qa.big_pairs = h->big_pairs;
+    qa.big_pairs64 = h->big_pairs64;
+    qa.breq_cap = s.breq_cap;
+    qa.breq_i = s.breq_i;
+    qa.breq_j = s.breq_j;
+    qa.breq_sa = s.breq_sa;
+    qa.breq_na = s.breq_na;
+    qa.breq_sb = s.breq_sb;
+    qa.breq_nb = s.breq_nb;
+    qa.breq_exact = s.breq_exact;
+    qa.pend_out = s.pend[0];
     cudaEventRecord(eq0.e, st);
     CK(launch_query(qa, s.dp, s.prec, st));
     cudaEventRecord(eq1.e, st);
     ++qlaunch;
+    if (s.cache_slots > 0) {
+      k_cache_insert<<<grid_for((int64_t)152 * 8 * TPB, TPB), TPB, 0, st>>>(s);
+      CK(cudaMemsetAsync(&s.ctr->nins, 0, sizeof(int32_t), st));
+      h->launches += 1;
+    }
+    // searches that handed big pairs to the whole GPU: evaluate those pairs
+    // (results go to the cache), then search again; the last re-run
+    // evaluates any remaining big pair itself, so the loop ends
+    int big_iters = 0, big_reqs = 0;
+    for (int it = 0; defer; ++it) {
+      int cnt[2];
+      CK(cudaMemcpyAsync(cnt, &s.ctr->nbreq, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
+      CK(cudaStreamSynchronize(st));
+      const int nreq = std::min(cnt[0], s.breq_cap), npend = cnt[1];
+      if (npend == 0) break;
+      ++big_iters;
+      big_reqs += nreq;
+      {
+        float q;
+        cudaEventElapsedTime(&q, eq0.e, eq1.e);
+        ms_query += q;
+      }
+      for (int r0 = 0; r0 < nreq; r0 += BIG_BATCH) {
+        const int m = std::min(BIG_BATCH, nreq - r0);
+        k_big_dedup<<<1, BIG_BATCH, 0, st>>>(s, r0, m);
+        k_big_tiles<<<1, BIG_BATCH, 0, st>>>(s, r0, m);
+        rc = launch_big(s, r0, m, st);
+        if (rc) return rc;
+        k_big_final<<<cdiv(m, 8), 256, 0, st>>>(s, r0, m);
+        h->launches += 5;
+      }
+      CK(cudaMemsetAsync(&s.ctr->nbreq, 0, 2 * sizeof(int32_t), st));
+      h->st.nn_searches += npend;
+      qa.term = s.pend[it & 1];
+      qa.nterm = npend;
+      qa.pend_out = s.pend[(it & 1) ^ 1];
+      qa.defer = it < 4 ? 1 : 0;
+      cudaEventRecord(eq0.e, st);
+      CK(launch_query(qa, s.dp, s.prec, st));
+      cudaEventRecord(eq1.e, st);
+      ++qlaunch;
+      k_cache_insert<<<grid_for((int64_t)152 * 8 * TPB, TPB), TPB, 0, st>>>(s);
+      CK(cudaMemsetAsync(&s.ctr->nins, 0, sizeof(int32_t), st));
+      h->launches += 2;
+    }
     k_chain<<<grid_for(nterm, TPB), TPB, 0, st>>>(s, nterm);
     h->launches += 3;  // query, chain, rnn
     cudaEventRecord(e1.e, st);
@@ -964,10 +1650,22 @@ int run_impl(hac_ctx *h, const hac_opts *o) {
     if (npairs <= 0) {
       CK(cudaMemcpyAsync(&c, s.ctr, sizeof(Counters), cudaMemcpyDeviceToHost, st));
       CK(cudaStreamSynchronize(st));
+      if (trace) fprintf(stderr, "hac round %d: no reciprocal pair (err %d)\n", round, c.err);
       return HAC_EINTERNAL;
     }
     k_merge<<<grid_for(npairs, TPB), TPB, 0, st>>>(s, round, npairs);
     h->launches += 4;  // merge, 3 compaction kernels
+    if (s.cache_slots > 0) {
+      const int S = s.cache_slots;
+      const size_t smem = (size_t)CM_WARPS * 4 * S * sizeof(CEntry);
+      const int blocks = std::max(1, std::min(cdiv(npairs, CM_WARPS), 152 * 32));
+      if (s.linkage == LK_COMPLETE)
+        k_cache_merge<0><<<blocks, CM_WARPS * 32, smem, st>>>(s, npairs, round);
+      else
+        k_cache_merge<1><<<blocks, CM_WARPS * 32, smem, st>>>(s, npairs, round);
+      k_gen_bump<<<grid_for(npairs, TPB), TPB, 0, st>>>(s, npairs);
+      h->launches += 2;
+    }
     cudaEventRecord(e2.e, st);
     const int nb = cdiv(K, TPB);
     const int32_t *ord = s.order[h->ocur];
@@ -991,17 +1689,27 @@ int run_impl(hac_ctx *h, const hac_opts *o) {
     cudaEventRecord(e3.e, st);
     CK(cudaMemcpyAsync(&c, s.ctr, sizeof(Counters), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
-    if (c.err & ~ERR_NONFINITE) return HAC_EINTERNAL;
-    if (c.nactive != K) return HAC_EINTERNAL;
+    if ((c.err & ~ERR_NONFINITE) || c.nactive != K) {
+      if (trace)
+        fprintf(stderr, "hac round %d: consistency (err %d, active %d, expected %d)\n", round,
+                c.err, c.nactive, K);
+      return HAC_EINTERNAL;
+    }
     if (trace) {
-      float qms;
+      float qms, nms, mms, ums;
       cudaEventElapsedTime(&qms, eq0.e, eq1.e);
+      cudaEventElapsedTime(&nms, e0.e, e1.e);
+      cudaEventElapsedTime(&mms, e1.e, e2.e);
+      cudaEventElapsedTime(&ums, e2.e, e3.e);
       fprintf(stderr,
               "hac round %d K %d terms %d pairs %d query_ms %.3f leaf_tests %llu nodes %llu "
-              "cpairs %llu ppairs %llu rechecks %llu\n",
+              "cpairs %llu ppairs %llu rechecks %llu nn_ms %.3f merge_ms %.3f update_ms %.3f "
+              "big_iters %d big_reqs %d hits %llu big_pp %llu big_exact %llu\n",
               round, K + npairs, nterm, npairs, qms, c.ltests - cprev.ltests,
               c.nodes - cprev.nodes, c.cluster_pairs - cprev.cluster_pairs,
-              c.point_pairs - cprev.point_pairs, c.rechecks - cprev.rechecks);
+              c.point_pairs - cprev.point_pairs, c.rechecks - cprev.rechecks, nms, mms, ums,
+              big_iters, big_reqs, c.cache_hits - cprev.cache_hits, c.big_pp - cprev.big_pp,
+              c.big_exact - cprev.big_exact);
       cprev = c;
     }
     nterm = c.nterm;
@@ -1049,7 +1757,7 @@ int run_impl(hac_ctx *h, const hac_opts *o) {
   h->st.rounds = round;
   h->st.merges = c.nmerges;
   h->st.cluster_pairs = (int64_t)c.cluster_pairs;
-  h->st.point_pairs = (int64_t)c.point_pairs;
+  h->st.point_pairs = (int64_t)(c.point_pairs + c.big_pp);
   h->st.nodes_visited = (int64_t)c.nodes;
   h->st.rechecks = (int64_t)c.rechecks;
   h->st.ms_init = ms_init;
@@ -1057,6 +1765,8 @@ int run_impl(hac_ctx *h, const hac_opts *o) {
   h->st.query_launches = qlaunch;
   h->st.leaf_tests = (int64_t)c.ltests;
   h->st.kernel_launches = h->launches;
+  h->st.cache_hits = (int64_t)c.cache_hits;
+  h->st.cache_lw_entries = (int64_t)c.cache_lw;
   {
     // algorithmic bytes of the search kernel (true dimension d, not padded):
     // node test = centroid box (+ complete's hi-min / lo-max) + min size;
@@ -1262,6 +1972,9 @@ bool carve_state(hac_ctx &h, Carver &cv) {
   cv.take(&s.alive, n);
   cv.take(&s.rootof, n);
   cv.take(&s.reloff, n);
+  cv.take(&s.osize, n);
+  cv.take(&s.partner, n);
+  cv.take(&s.gen, n);
   cv.take(&s.pos, n);
   cv.take(&s.Ekey, n);
   cv.take(&s.Ecid, n);
@@ -1339,6 +2052,7 @@ int static_layout(hac_ctx &h, cudaStream_t st) {
   mp.bits = std::min(21, 64 / d);
   s.abs_slack = std::max(scale, 1e-300) * std::ldexp(1.0, -18);
   s.coord_scale = (float)(scale * (1.0 + 1e-6));
+  s.delta_pts = s.pts32_exact ? 0.f : 2.01f * 5.9604645e-8f * s.coord_scale * std::sqrt((float)d);
   k_morton<T><<<grid_for(n, TPB), TPB, 0, st>>>(X, n, d, mp, h.keys[0], h.vals[0]);
   CK(cudaGetLastError());
   const int sc = radix_sort(&h, (int)n, mp.bits * d, st);
@@ -1379,6 +2093,7 @@ int static_run(hac_ctx &h, const hac_opts &opt, cudaStream_t st, hac_merge *dev_
     qa.nterm = nterm;
     qa.abs_slack = s.abs_slack;
     qa.coord_scale = s.coord_scale;
+    qa.delta_pts = s.delta_pts;
     qa.term = s.term;
     qa.order = s.order[h.ocur];
     qa.pos = s.pos;
@@ -1406,6 +2121,16 @@ int static_run(hac_ctx &h, const hac_opts &opt, cudaStream_t st, hac_merge *dev_
     qa.Ekey = s.Ekey;
     qa.Ecid = s.Ecid;
     qa.ctr = s.ctr;
+    qa.cache_slots = s.cache_slots;
+    qa.ins_cap = s.ins_cap;
+    qa.ckey = s.ckey;
+    qa.cval = s.cval;
+    qa.cerr = s.cerr;
+    qa.gen = s.gen;
+    qa.ins_i = s.ins_i;
+    qa.ins_j = s.ins_j;
+    qa.ins_v = s.ins_v;
+    qa.ins_e = s.ins_e;
     CK(launch_query(qa, s.dp, s.prec, st));
     k_chain<<<grid_for(nterm, TPB), TPB, 0, st>>>(s, nterm);
     CK(cudaMemsetAsync(&s.ctr->npairs, 0, sizeof(int32_t), st));
@@ -1490,6 +2215,7 @@ extern "C" int hac_run_static(const void *dev_points, int64_t n, int d, hac_dtyp
   h.s.d = d;
   h.s.dp = pad_dim(d);
   h.s.linkage = (int)lk;
+  h.s.pts32_exact = dt == HAC_F32;
   h.s.prec = opt.precision;
   Carver cv{arena, 0, kStaticArenaBytes, true};
   if (!carve_state(h, cv)) return HAC_EINVAL;

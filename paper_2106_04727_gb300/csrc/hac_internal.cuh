@@ -23,11 +23,25 @@ struct Counters {
   int32_t nactive;   // active clusters
   int32_t nmerges;   // merges made so far
   int32_t err;       // sticky error bits (ERR_*)
-  int32_t pad_;
+  int32_t nins;      // pair distances queued for the cache this round
+  int32_t nbreq;     // big-pair requests queued by the search
+  int32_t npend;     // terminals waiting for their big pairs
+  int32_t pad2_;
   unsigned long long cluster_pairs, point_pairs, nodes, rechecks, searches, ltests, prows;
+  unsigned long long cache_hits, cache_lw;
+  unsigned long long big_pp, big_exact;  // point pairs / FP64 requests of the GPU-wide evaluation
 };
 
 enum : int32_t { ERR_NONFINITE = 1, ERR_NO_NN = 2, ERR_STACK = 4, ERR_WINDOW = 8 };
+
+constexpr unsigned long long CKEY_EMPTY = ~0ull;
+constexpr long long CACHE_MIN_PAIRS = 64;  // smaller pairs are cheaper to recompute
+constexpr int CACHE_MAX_SLOTS = 256;
+
+// cache key of neighbour `cid` at generation `gen`
+__host__ __device__ inline unsigned long long ckey_of(int cid, int gen) {
+  return ((unsigned long long)(unsigned)cid << 32) | (unsigned)gen;
+}
 
 // Everything a round's kernels read or write.  Arrays with [2] are double
 // buffered across the point re-layout; `cur` selects the live one.
@@ -37,6 +51,8 @@ struct State {
   int linkage, prec;
   double abs_slack;     // absolute pruning slack (coordinate scale * 2^-18)
   float coord_scale;    // largest |coordinate| after recentring
+  float delta_pts;      // absolute error term of an FP32 point distance (0 for FP32 input)
+  int pts32_exact;      // the FP32 point copy is the FP32 input itself
   // points, permuted into cluster-contiguous segments
   double *p64[2];
   float *p32[2];
@@ -55,6 +71,27 @@ struct State {
   uint8_t *alive;
   int32_t *rootof;      // retired cid -> surviving cid of its merge
   int32_t *reloff;      // retired cid -> offset of its points in the merged segment
+  int32_t *osize;       // size of each cid just before this round's merge
+  int32_t *partner;     // the other cid of this round's merge
+  int32_t *gen;         // generation of each cid, bumped whenever it takes part in a merge
+  // pair-distance cache (Section 5): cache_slots entries per cid; key =
+  // neighbour cid << 32 | neighbour generation; value = distance (D units)
+  // and its absolute error bound (0 for FP64 values)
+  int cache_slots;
+  unsigned long long *ckey;
+  double *cval;
+  float *cerr;
+  int ins_cap;          // queue of evaluated pairs to insert after the search
+  int32_t *ins_i, *ins_j;
+  double *ins_v;
+  float *ins_e;
+  // big pairs deferred by the search to the GPU-wide evaluation kernel
+  int breq_cap;
+  int32_t *breq_i, *breq_j, *breq_sa, *breq_na, *breq_sb, *breq_nb;
+  uint8_t *breq_exact;   // 1 = FP64 value wanted, 0 = FP32 estimate
+  int32_t *btile;        // tile prefix of the current batch
+  double *bpart;         // per-tile partial results of the current batch
+  int32_t *pend[2];      // terminals whose search deferred a pair
   int32_t *pos;         // position of each active cid in `order`
   double *Ekey;         // nearest-neighbour key of each terminal (linkage key space)
   int32_t *Ecid;
@@ -86,7 +123,7 @@ struct State {
 struct QueryArgs {
   int d, linkage, round, K, nterm;
   double abs_slack;
-  float coord_scale;
+  float coord_scale, delta_pts;
   const int32_t *term, *order, *pos, *csize, *seg;
   const double *cent, *p64;
   const float *cent32, *blo, *bhi, *p32;
@@ -100,7 +137,30 @@ struct QueryArgs {
   double *Ekey;
   int32_t *Ecid;
   Counters *ctr;
+  // pair-distance cache
+  int cache_slots, ins_cap;
+  const unsigned long long *ckey;
+  const double *cval;
+  const float *cerr;
+  const int32_t *gen;
+  int32_t *ins_i, *ins_j;
+  double *ins_v;
+  float *ins_e;
+  // big-pair deferral (needs the cache): 0 = evaluate big pairs in the warp
+  int defer;
+  long long big_pairs, big_pairs64;
+  int breq_cap;
+  int32_t *breq_i, *breq_j, *breq_sa, *breq_na, *breq_sb, *breq_nb;
+  uint8_t *breq_exact;
+  int32_t *pend_out;
 };
+
+// pairs of at least this many point pairs are evaluated by the whole GPU
+constexpr long long BIG_PAIRS = 1ll << 18;
+// FP64 point pairs cost ~64x more on this part: hand them over much earlier
+constexpr long long BIG_PAIRS_F64 = 1ll << 13;
+// error term stored with every cached FP32 estimate (0 marks an FP64 value)
+constexpr float EST_MARK = 1e-30f;
 
 // number of tree levels for K active clusters (>= 1)
 __host__ __device__ inline int tree_levels(int K) {

@@ -355,8 +355,10 @@ struct Searcher {
   float U;        // min over candidates of the FP32 upper bound
   float L1, L2;   // two smallest FP32 lower bounds
   int c1;         // cid holding L1
+  float d1, e1;   // FP32 value and error term of that candidate
+  bool deferred;  // a big pair was handed to the GPU-wide evaluation
   float delta0, rho;
-  unsigned long long cpairs, ppairs, nodes, ltests, prows, rechecks;
+  unsigned long long cpairs, ppairs, nodes, ltests, prows, rechecks, hits;
 
   __device__ Searcher(const QueryArgs &args, int lane_, int ci_, float Ufix)
       : a(args), lane(lane_), ci(ci_) {
@@ -384,8 +386,48 @@ struct Searcher {
     U = Ufix;
     L1 = L2 = INFINITY;
     c1 = INT_MAX;
-    cpairs = ppairs = nodes = ltests = prows = rechecks = 0;
+    d1 = e1 = INFINITY;
+    deferred = false;
+    cpairs = ppairs = nodes = ltests = prows = rechecks = hits = 0;
     refresh();
+  }
+
+  // Section 5 cache: look for the entry of `nbr` in the table of `owner`
+  // (warp-cooperative; valid only while the neighbour's generation matches)
+  __device__ bool cache_find(int owner, int nbr, double &v, float &e) const {
+    const int S = a.cache_slots;
+    const unsigned long long want = ckey_of(nbr, a.gen[nbr]);
+    for (int base = 0; base < S; base += 32) {
+      const int t = base + lane;
+      const bool m = t < S && a.ckey[(size_t)owner * S + t] == want;
+      const unsigned b = __ballot_sync(0xffffffffu, m);
+      if (b) {
+        const size_t slot = (size_t)owner * S + base + __ffs(b) - 1;
+        v = a.cval[slot];
+        e = a.cerr[slot];
+        return true;
+      }
+    }
+    return false;
+  }
+
+  __device__ bool cache_get(int cw, int nw, double &v, float &e) {
+    if (a.cache_slots <= 0 || (long long)na * nw < CACHE_MIN_PAIRS) return false;
+    const bool hit = cache_find(ci, cw, v, e) || cache_find(cw, ci, v, e);
+    hits += hit;
+    return hit;
+  }
+
+  // queue a computed distance for insertion into both tables (after the search)
+  __device__ void cache_put(int cw, int nw, double v, float e) const {
+    if (a.cache_slots <= 0 || (long long)na * nw < CACHE_MIN_PAIRS || lane != 0) return;
+    const int q = atomicAdd(&a.ctr->nins, 1);
+    if (q < a.ins_cap) {
+      a.ins_i[q] = ci;
+      a.ins_j[q] = cw;
+      a.ins_v[q] = v;
+      a.ins_e[q] = e;
+    }
   }
 
   __device__ void refresh() {
@@ -423,10 +465,14 @@ struct Searcher {
     warp_argmin_f(m1, ml);
     const float m2 = warp_minf(lane == ml ? INFINITY : lo);
     const int cmin = __shfl_sync(0xffffffffu, cc, ml);
+    const float dsel = __shfl_sync(0xffffffffu, d32, ml);
+    const float esel = __shfl_sync(0xffffffffu, dlt, ml);
     if (m1 < L1 || (m1 == L1 && cmin < c1)) {
       L2 = fminf(L1, m2);
       L1 = m1;
       c1 = cmin;
+      d1 = dsel;
+      e1 = esel;
     } else {
       L2 = fminf(L2, m1);
     }
@@ -515,7 +561,7 @@ struct Searcher {
     const float lb = valid ? fmaxf(sqrtf(dc2), bx) : INFINITY;
     const bool ok = valid && pass(lb);
     const int sb = valid ? a.qseg[idx] : 0;
-    const float dlt = delta0;
+    const float dlt = a.delta_pts;
     const bool small = ok && (long long)na * nb <= SMALLP;
     const unsigned sm = __ballot_sync(0xffffffffu, small);
     if (sm) {
@@ -558,45 +604,112 @@ struct Searcher {
       unsigned long long pp = 0;
       cpairs += 1;
       prows += (unsigned long long)(na + nw);
+      double cv = 0.0;
+      float ce = 0.f;
+      const bool cached = cache_get(cw, nw, cv, ce);
+      // values that will be cached are computed in full (no early exit)
+      const bool cacheable = a.cache_slots > 0 && (long long)na * nw >= CACHE_MIN_PAIRS;
+      const long long np = (long long)na * nw;
+      const bool huge = np >= a.big_pairs;
+      const bool huge64 = np >= a.big_pairs64;  // for FP64 evaluations
       if (MODE == M_F64) {
-        const double key = eval64_warp<LK, DP>(a.p64, sa, na, sw, nw, (double)bd, lane, pp);
-        ppairs += pp;
+        double key = cv;
+        if (!cached) {
+          if (huge64 && try_defer(cw, sw, nw, 1)) continue;
+          key = eval64_warp<LK, DP>(a.p64, sa, na, sw, nw, cacheable ? INFINITY : (double)bd,
+                                    lane, pp);
+          ppairs += pp;
+          if (key < INFINITY) cache_put(cw, nw, key, 0.f);
+        }
         const unsigned long long kb = kbits(key);
         if (key < INFINITY && kless(kb, cw, bk, bc)) {
           bk = kb;
           bc = cw;
           refresh();
         }
-      } else {
-        const float bnd = MODE == M_F32 ? bd : fminf(U, bd);
-        const float d32 = eval32_warp<LK, DP>(a.p32, sa, na, sw, nw, bnd, dlt, rho, lane, pp);
-        ppairs += pp;
-        if (MODE == M_F32) {
-          offer_f32(lane == 0 && d32 < INFINITY, d32, dlt, cw);
-        } else if (d32 < INFINITY && lower(d32, dlt) <= fminf(U, bd)) {
-          unsigned long long pp2 = 0;
-          const double key = eval64_warp<LK, DP>(a.p64, sa, na, sw, nw, INFINITY, lane, pp2);
-          ppairs += pp2;
-          rechecks += 1;
-          const unsigned long long kb = kbits(key);
-          if (kless(kb, cw, bk, bc)) {
-            bk = kb;
-            bc = cw;
-            refresh();
+      } else if (MODE == M_F32) {
+        float d32 = (float)cv, e32 = ce;
+        if (!cached) {
+          if (huge && try_defer(cw, sw, nw, 0)) continue;
+          d32 = eval32_warp<LK, DP>(a.p32, sa, na, sw, nw, cacheable ? INFINITY : bd, dlt, rho,
+                                    lane, pp);
+          ppairs += pp;
+          e32 = dlt;
+          // an estimate's error term is never 0 in the cache (0 marks FP64)
+          if (d32 < INFINITY) cache_put(cw, nw, (double)d32, fmaxf(dlt, EST_MARK));
+        }
+        offer_f32(lane == 0 && d32 < INFINITY, d32, e32, cw);
+      } else {  // M_RECHECK
+        double key = INFINITY;
+        if (cached && ce == 0.f) {
+          key = cv;
+        } else {
+          float d32 = (float)cv, e32 = ce;
+          if (!cached) {
+            if (huge && try_defer(cw, sw, nw, 1)) continue;
+            d32 = eval32_warp<LK, DP>(a.p32, sa, na, sw, nw, cacheable ? INFINITY : fminf(U, bd),
+                                      dlt, rho, lane, pp);
+            ppairs += pp;
+            e32 = dlt;
           }
+          if (d32 < INFINITY && lower(d32, e32) <= fminf(U, bd)) {
+            if (huge64 && try_defer(cw, sw, nw, 1)) continue;
+            unsigned long long pp2 = 0;
+            key = eval64_warp<LK, DP>(a.p64, sa, na, sw, nw, INFINITY, lane, pp2);
+            ppairs += pp2;
+            rechecks += 1;
+            cache_put(cw, nw, key, 0.f);
+          }
+        }
+        const unsigned long long kb = kbits(key);
+        if (key < INFINITY && kless(kb, cw, bk, bc)) {
+          bk = kb;
+          bc = cw;
+          refresh();
         }
       }
     }
   }
 
+  // Hand a big pair to the GPU-wide evaluation; the search is then re-run
+  // once the value is in the cache.  Returns false if deferral is off or the
+  // request queue is full (the warp evaluates the pair itself).
+  __device__ bool try_defer(int cw, int sw, int nw, int exact) {
+    if (!a.defer || a.cache_slots <= 0) return false;
+    int r = 0;
+    if (lane == 0) r = atomicAdd(&a.ctr->nbreq, 1);
+    r = __shfl_sync(0xffffffffu, r, 0);
+    if (r >= a.breq_cap) return false;
+    if (lane == 0) {
+      a.breq_i[r] = ci;
+      a.breq_j[r] = cw;
+      a.breq_sa[r] = sa;
+      a.breq_na[r] = na;
+      a.breq_sb[r] = sw;
+      a.breq_nb[r] = nw;
+      a.breq_exact[r] = (uint8_t)exact;
+    }
+    deferred = true;
+    return true;
+  }
+
   // FP64 key of (ci, the cluster at position q): the winner of an FP32 search
   // whose window held a single candidate
-  __device__ unsigned long long exact_of(int q) {
+  __device__ unsigned long long exact_of(int q, int c) {
     const int nb = a.qsz[q];
     if (LK == LK_WARD) return ward64(q, nb);
+    double cv;
+    float ce;
+    if (cache_get(c, nb, cv, ce) && ce == 0.f) return kbits(cv);
+    // an FP32 value whose stated bound is within 4e-6 stands in for FP64:
+    // its upper bound is returned (a valid beta; height error <= 8e-6)
+    if (d1 < INFINITY && e1 + rho * d1 <= 4e-6f * d1)
+      return kbits((double)((d1 + e1) * (1.f + rho)));
+    if ((long long)na * nb >= a.big_pairs64 && try_defer(c, a.qseg[q], nb, 1)) return KINF;
     unsigned long long pp = 0;
     const double key = eval64_warp<LK, DP>(a.p64, sa, na, a.qseg[q], nb, INFINITY, lane, pp);
     ppairs += pp;
+    cache_put(c, nb, key, 0.f);
     return kbits(key);
   }
 };
@@ -668,6 +781,7 @@ __device__ void tally(const Searcher<LK, DP, MODE> &S, unsigned long long *c) {
   c[3] += S.ltests;
   c[4] += S.prows;
   c[5] += S.rechecks;
+  c[6] += S.hits;
 }
 
 template <int LK, int DP, int PREC>
@@ -679,26 +793,35 @@ __global__ void __launch_bounds__(QWARPS * 32) k_query(QueryArgs a) {
   const int nw = (gridDim.x * blockDim.x) >> 5;
   uint32_t *sn = s_node[wib];
   float *sl = s_lb[wib];
-  unsigned long long c[6] = {0, 0, 0, 0, 0, 0};
+  unsigned long long c[7] = {0, 0, 0, 0, 0, 0, 0};
   for (int t = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; t < a.nterm; t += nw) {
     const int ci = a.term[t];
     const int own = a.pos[ci] / FAN;
     unsigned long long bk;
     int bc;
+    bool deferred = false;
     if (PREC == 0) {
       Searcher<LK, DP, M_F64> S(a, lane, ci, INFINITY);
       traverse(a, S, sn, sl, own, lane);
       bk = S.bk;
       bc = S.bc;
+      deferred = S.deferred;
       tally(S, c);
     } else {
       Searcher<LK, DP, M_F32> S(a, lane, ci, INFINITY);
       traverse(a, S, sn, sl, own, lane);
-      if (S.L2 > S.U && S.c1 != INT_MAX) {
+      if (S.deferred) {
+        // incomplete: some candidates still wait for their values
+        deferred = true;
+        bk = KINF;
+        bc = INT_MAX;
+        tally(S, c);
+      } else if (S.L2 > S.U && S.c1 != INT_MAX) {
         // exactly one candidate can be the FP64 winner
         bc = S.c1;
-        bk = S.exact_of(a.pos[bc]);
+        bk = S.exact_of(a.pos[bc], bc);
         S.rechecks += 1;
+        deferred = S.deferred;
         tally(S, c);
       } else {
         tally(S, c);
@@ -706,8 +829,14 @@ __global__ void __launch_bounds__(QWARPS * 32) k_query(QueryArgs a) {
         traverse(a, R, sn, sl, own, lane);
         bk = R.bk;
         bc = R.bc;
+        deferred = R.deferred;
         tally(R, c);
       }
+    }
+    if (deferred) {
+      // re-searched once its big pairs are in the cache
+      if (lane == 0) a.pend_out[atomicAdd(&a.ctr->npend, 1)] = ci;
+      continue;
     }
     if (lane == 0) {
       a.Ekey[ci] = __longlong_as_double((long long)bk);
@@ -727,6 +856,7 @@ __global__ void __launch_bounds__(QWARPS * 32) k_query(QueryArgs a) {
     atomicAdd(&a.ctr->ltests, c[3]);
     atomicAdd(&a.ctr->prows, c[4]);
     atomicAdd(&a.ctr->rechecks, c[5]);
+    atomicAdd(&a.ctr->cache_hits, c[6]);
   }
 }
 

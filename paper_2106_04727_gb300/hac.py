@@ -42,7 +42,8 @@ class hac_stats_t(ctypes.Structure):
                                                "ms_total")] + [("device_bytes", ctypes.c_int64),
                ("ms_query", ctypes.c_double)] + \
                [(k, ctypes.c_int64) for k in ("query_launches", "query_bytes", "leaf_tests",
-                                              "kernel_launches")]
+                                              "kernel_launches", "cache_hits",
+                                              "cache_lw_entries")]
 
 
 MERGE_DTYPE = np.dtype([("cid_a", np.int64), ("cid_b", np.int64), ("height", np.float64),
