@@ -1,15 +1,16 @@
-"""Benchmark: exact HAC dendrogram of 10^6 points (5-D Gaussian mixture) on GB300.
+"""Benchmark: exact HAC dendrograms of 10^6 points (5-D Gaussian mixture) on GB300.
 
-One step = one full hac_run (initial layout + every NN-chain round until one
-cluster remains) on a device-resident instance, i.e. the whole hot path.
-Prints ONE JSON line (rank 0).
+One step = the n = 10^6 workload's whole hot path: a full hac_run (initial
+layout + every NN-chain round until one cluster remains) under Ward AND under
+average linkage, on device-resident points, in the FP32-bulk + FP64-re-score
+mode (the Section 5 cache on for average).  Prints ONE JSON line (rank 0).
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--linkage ward]
-                  [--precision f64|f32] [--workload gmm5d_1m_f32] [--impl ours|reference]
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--linkages ward,average]
+                  [--precision f32|f64] [--workload gmm5d_1m_f32] [--impl ours|reference]
 
 --impl reference times the CPU oracle (FP64 Lance-Williams NN-chain) on a
 bounded sample of the same workload on the host cores.  Multi-GPU runs are
-independent replicas (the dendrogram computation does not shard): each rank
+independent replicas (a dendrogram computation does not shard): each rank
 clusters its own copy and value = all ranks' points / max time.
 """
 from __future__ import annotations
@@ -29,15 +30,16 @@ if ROOT not in sys.path:
 
 METRIC = "HAC wall time & distance evals/s vs HBM roofline at n=1M"
 UNIT = "points/s"
+SMS, FP32_LANES = 152, 128   # GB300: SMs and FP32 lanes per SM
 
 
 def _peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
             p = json.load(f)
-        return float(p["hbm_gbs"]), "measured"
+        return float(p["hbm_gbs"]), float(p.get("sm_max_mhz", 2070.0)), "measured"
     except Exception:
-        return 6800.0, "fallback"
+        return 6800.0, 2070.0, "fallback"
 
 
 class Clocks:
@@ -101,7 +103,7 @@ def dist_env():
     return ws, rank, local
 
 
-def cpu_baseline(workload: str, linkage: str, n_sample: int):
+def cpu_baseline(workload: str, linkages, n_sample: int):
     """The oracle, as it stands, on a bounded sample of the workload (1 core)."""
     import numpy as np
 
@@ -110,23 +112,23 @@ def cpu_baseline(workload: str, linkage: str, n_sample: int):
 
     X = inputs.workload(workload, n=n_sample).astype(np.float64)
     t0 = time.perf_counter()
-    oracle.nnchain(X, linkage)
+    for lk in linkages:
+        oracle.nnchain(X, lk)
     dt = time.perf_counter() - t0
     return {"value": n_sample / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"{n_sample} points of {workload} ({linkage}), serial FP64 "
-                      f"Lance-Williams NN-chain, {dt:.2f} s; O(n^2) so its points/s "
-                      f"falls further at 10^6 points"}, dt
+            "sample": f"{n_sample} points of {workload} ({'+'.join(linkages)}), serial FP64 "
+                      f"Lance-Williams NN-chain, {dt:.2f} s for all linkages; O(n^2) time "
+                      f"and memory, so its points/s falls further at 10^6 points"}, dt
 
 
 def run_reference(args):
     ws, rank, _ = dist_env()
     if rank != 0:
         return
-    import numpy as np  # noqa: F401
-
     ts = []
+    cb = None
     for i in range(args.warmup + args.steps):
-        cb, dt = cpu_baseline(args.workload, args.linkage, args.ref_sample)
+        cb, dt = cpu_baseline(args.workload, args.linkages, args.ref_sample)
         if i >= args.warmup:
             ts.append(dt)
     tot = sum(ts)
@@ -135,8 +137,8 @@ def run_reference(args):
             "warmup": args.warmup, "ms_per_step": 1e3 * tot / len(ts), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "impl": "reference",
-            "config": {"workload": args.workload, "linkage": args.linkage,
-                       "n": args.ref_sample, "note": "bounded sample; host cores"},
+            "config": {"workload": args.workload, "linkages": "+".join(args.linkages),
+                       "n": args.ref_sample, "note": "bounded sample of the workload; host core"},
             "cpu_baseline": {"kind": "oracle", "cores": 1, "value": v, "unit": UNIT,
                              "sample": cb["sample"]},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -150,21 +152,19 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="gmm5d_1m_f32")
-    ap.add_argument("--linkage", default="ward", choices=["ward", "average", "complete"])
-    ap.add_argument("--precision", default="f64", choices=["f64", "f32"])
-    ap.add_argument("--cache-slots", type=int, default=-1,
-                    help="Section 5 cache slots per cluster (default 64 for complete/average)")
+    ap.add_argument("--linkages", default="ward,average")
+    ap.add_argument("--precision", default="f32", choices=["f64", "f32"])
+    ap.add_argument("--cache-slots", type=int, default=64,
+                    help="Section 5 cache slots per cluster for complete/average")
     ap.add_argument("--ref-sample", type=int, default=20000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
-    if args.cache_slots < 0:
-        args.cache_slots = 0 if args.linkage == "ward" else 64
+    args.linkages = [x for x in args.linkages.split(",") if x]
     if args.impl == "reference":
         return run_reference(args)
 
-    import numpy as np
     import torch
 
     from paper_2106_04727_gb300 import hac, inputs
@@ -181,14 +181,18 @@ def main():
     n, d = X.shape
     stream = torch.cuda.current_stream()
     Xd = torch.from_numpy(X).to("cuda")
-    h = hac.hac_create_device(Xd.data_ptr(), n, d, X.dtype, args.linkage)
+    handles = {lk: hac.hac_create_device(Xd.data_ptr(), n, d, X.dtype, lk) for lk in args.linkages}
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
 
     def step():
-        rc = hac.hac_run(h, precision=prec, cache_slots=args.cache_slots,
-                         stream=stream.cuda_stream)
-        if rc != 0:
-            raise hac.HacError(rc, "hac_run")
+        out = {}
+        for lk, h in handles.items():
+            rc = hac.hac_run(h, precision=prec, cache_slots=args.cache_slots,
+                             stream=stream.cuda_stream)
+            if rc != 0:
+                raise hac.HacError(rc, "hac_run")
+            out[lk] = hac.hac_stats(h)
+        return out
 
     for _ in range(args.warmup):
         step()
@@ -196,19 +200,16 @@ def main():
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
-    times, stats = [], []
+    stats = []
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
           for _ in range(args.steps)]
     with Clocks(local) as clk:
-        wall0 = time.perf_counter()
         for i in range(args.steps):
-            flush.fill_(float(i))              # evict L2 between timed steps (untimed)
+            flush.fill_(float(i))              # evict L2 before each timed step (untimed)
             ev[i][0].record(stream)
-            step()
+            stats.append(step())
             ev[i][1].record(stream)
-            stats.append(hac.hac_stats(h))
         torch.cuda.synchronize()
-        wall = time.perf_counter() - wall0
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
@@ -220,13 +221,41 @@ def main():
         tot_ms = float(t.item())
     value = ws * n * args.steps / (tot_ms / 1e3)
 
-    # dominant kernel: the nearest-neighbour search
-    q_ms = sum(s["ms_query"] for s in stats)
-    q_bytes = sum(s["query_bytes"] for s in stats)
-    q_launch = sum(s["query_launches"] for s in stats)
-    peak, peak_kind = _peaks()
-    achieved = q_bytes / (q_ms / 1e3) / 1e9 if q_ms > 0 else 0.0
-    st = stats[-1]
+    def agg(key, lk=None):
+        return sum(s[l][key] for s in stats for l in s if lk is None or l == lk)
+
+    hbm, sm_mhz, peak_kind = _peaks()
+    fp32_tflops = SMS * FP32_LANES * 2 * sm_mhz * 1e6 / 1e12
+    # kernels, measured by the library with CUDA events on the launching stream
+    q_ms, q_bytes, q_launch = agg("ms_query"), agg("query_bytes"), agg("query_launches")
+    b_ms, b_pairs, b_launch = agg("ms_big"), agg("big_point_pairs"), agg("big_launches")
+    flops_per_pair = 3 * d + 2   # d subtractions, d multiply-adds (2 flops), sqrt, add
+    kern = {
+        "k_query": {"bound": "hbm", "ms": q_ms / args.steps, "launches": q_launch // args.steps,
+                    "achieved": q_bytes / (q_ms / 1e3) / 1e9 if q_ms else 0.0, "peak": hbm,
+                    "unit": "GB/s", "traffic": None},
+        "k_big_eval32": {"bound": "alu", "ms": b_ms / args.steps,
+                         "launches": b_launch // args.steps,
+                         "achieved": b_pairs * flops_per_pair / (b_ms / 1e3) / 1e12 if b_ms else 0.0,
+                         "peak": fp32_tflops, "unit": "TFLOP/s", "traffic": None},
+    }
+    for k in kern.values():
+        k["frac"] = k["achieved"] / k["peak"] if k["peak"] else 0.0
+    dom = max(kern, key=lambda k: kern[k]["ms"])
+    roof = dict(kern[dom])
+    roof["kernel"] = dom
+    roof["peak_source"] = peak_kind + (" (FP32: 152 SMs x 128 lanes x 2 flops x max SM clock)"
+                                       if roof["bound"] == "alu" else " (HBM copy)")
+    per_lk = {}
+    for lk in args.linkages:
+        ms = agg("ms_total", lk) / args.steps
+        s0 = stats[-1][lk]
+        per_lk[lk] = {"ms_per_run": ms, "rounds": s0["rounds"], "nn_searches": s0["nn_searches"],
+                      "cluster_pairs": s0["cluster_pairs"], "point_pairs": s0["point_pairs"],
+                      "cluster_pair_evals_per_s": s0["cluster_pairs"] / (ms / 1e3),
+                      "point_pair_evals_per_s": s0["point_pairs"] / (ms / 1e3),
+                      "cache_hits": s0["cache_hits"], "ms_search": s0["ms_query"],
+                      "ms_big_pairs": s0["ms_big"]}
     e2e = None
     cpu = None
     if rank == 0 and not args.no_e2e:
@@ -236,15 +265,18 @@ def main():
         for _ in range(2):
             torch.cuda.synchronize()
             t0 = time.perf_counter()
-            res = hac.cluster(Xp, args.linkage, precision=prec, with_rounds=False,
-                              cache_slots=args.cache_slots)
+            for lk in args.linkages:
+                res = hac.cluster(Xp, lk, precision=prec, with_rounds=False,
+                                  cache_slots=args.cache_slots)
+                assert len(res["a"]) == n - 1
             e2e_t.append(time.perf_counter() - t0)
-            assert len(res["a"]) == n - 1
-        e2e = {"value": n / min(e2e_t), "unit": UNIT, "h2d_bytes_per_step": int(X.nbytes),
-               "d2h_bytes_per_step": int((n - 1) * 24)}
+        e2e = {"value": n / min(e2e_t), "unit": UNIT,
+               "h2d_bytes_per_step": int(X.nbytes) * len(args.linkages),
+               "d2h_bytes_per_step": int((n - 1) * 32) * len(args.linkages)}
     if rank == 0 and not args.no_cpu_baseline and ws == 1:
-        cpu, _ = cpu_baseline(args.workload, args.linkage, args.ref_sample)
-    hac.hac_destroy(h)
+        cpu, _ = cpu_baseline(args.workload, args.linkages, args.ref_sample)
+    for h in handles.values():
+        hac.hac_destroy(h)
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
@@ -252,25 +284,15 @@ def main():
             "scaling": "weak", "vs_baseline": None,
             "dtype": "f64" if prec == hac.PREC_F64 else "f32+f64",
             "data": "synthetic",
-            "config": {"workload": args.workload, "n": n, "d": d, "linkage": args.linkage,
-                       "precision": args.precision, "cache_slots": args.cache_slots,
-                       "parallelism": f"replicas{ws}",
-                       "l2": "flushed between steps (256 MB write)"},
-            "hac": {"wall_s_per_run": tot_ms / args.steps / 1e3, "rounds": st["rounds"],
-                    "nn_searches": st["nn_searches"], "cluster_pairs": st["cluster_pairs"],
-                    "point_pairs": st["point_pairs"], "nodes_visited": st["nodes_visited"],
-                    "leaf_tests": st["leaf_tests"], "query_launches": st["query_launches"],
-                    "cluster_pair_evals_per_s": st["cluster_pairs"] / (times[-1] / 1e3),
-                    "point_pair_evals_per_s": st["point_pairs"] / (times[-1] / 1e3),
-                    "ms_init": st["ms_init"], "ms_nn": st["ms_nn"], "ms_merge": st["ms_merge"],
-                    "ms_update": st["ms_update"], "ms_query": st["ms_query"],
-                    "device_bytes": st["device_bytes"], "host_wall_s": wall / args.steps},
-            "roofline": {"kernel": "k_query64", "bound": "hbm", "achieved": achieved,
-                         "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                         "traffic": None, "peak_source": peak_kind,
-                         "bytes_per_launch": q_bytes / max(q_launch, 1),
-                         "ms_per_launch": q_ms / max(q_launch, 1)},
-            "gpu_launches": int(sum(s["kernel_launches"] for s in stats)),
+            "config": {"workload": args.workload, "n": n, "d": d,
+                       "linkages": "+".join(args.linkages), "precision": args.precision,
+                       "cache_slots": args.cache_slots, "parallelism": f"replicas{ws}",
+                       "step": "one full dendrogram per linkage",
+                       "l2": "flushed before each timed step (256 MB write)"},
+            "hac": per_lk,
+            "roofline": roof,
+            "kernels": kern,
+            "gpu_launches": int(agg("kernel_launches")),
             "clocks": clk.summary(),
             "e2e": e2e,
             "cpu_baseline": cpu,

@@ -101,6 +101,9 @@ typedef struct {
   int64_t kernel_launches;   /* all kernels the library launched in the run */
   int64_t cache_hits;        /* pair distances taken from the cache instead of evaluated */
   int64_t cache_lw_entries;  /* cache entries derived by Lance-Williams after merges */
+  double ms_big;             /* device time of the GPU-wide big-pair evaluation kernels */
+  int64_t big_point_pairs;   /* point pairs evaluated by those kernels (also in point_pairs) */
+  int64_t big_launches;      /* launches of those kernels */
 } hac_stats_t;
 
 /* Default options (FP64, no cache, no limits, own stream). */

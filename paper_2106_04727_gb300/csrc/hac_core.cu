@@ -663,6 +663,22 @@ constexpr int BIG_PPT = 2;         // points of the larger cluster per thread
 constexpr int BIG_TILE = BIG_TPB * BIG_PPT;  // FP64 tiles
 constexpr int B32_PPT = 4;
 constexpr int B32_TILE = BIG_TPB * B32_PPT;  // FP32 tiles
+// tiles also cut the smaller cluster into chunks, so one request spreads
+// over many CTAs: a tile is (points of the larger) x (points of the smaller)
+constexpr int BIG_SCH = 1024;   // FP64 tiles: 512 x 1024 point pairs (at least)
+constexpr int B32_SCH = 2048;   // FP32 tiles: 1024 x 2048 point pairs (at least)
+constexpr int BIG_MAXT = 32768; // tiles per request at most (chunks widen to fit)
+
+// chunk of the smaller cluster per tile, widened so that a request has at
+// most max(BIG_MAXT, tiles along the larger cluster) tiles
+__host__ __device__ inline int big_chunk(int nL, int nS, bool exact) {
+  const int w = exact ? BIG_TILE : B32_TILE;
+  const int tl = (nL + w - 1) / w;
+  int c = exact ? BIG_SCH : B32_SCH;
+  const int maxts = BIG_MAXT / tl > 1 ? BIG_MAXT / tl : 1;
+  if ((nS + c - 1) / c > maxts) c = (nS + maxts - 1) / maxts;
+  return c;
+}
 constexpr int BIG_BATCH = 512;     // requests per batch (one scan block)
 
 // tile prefix of the batch's requests: tiles = ceil(larger size / 256)
@@ -671,8 +687,10 @@ __global__ void k_big_tiles(State s, int r0, int m) {
   int v = 0;
   if (t < m) {
     const int nL = max(s.breq_na[r0 + t], s.breq_nb[r0 + t]);
-    const int w = s.breq_exact[r0 + t] ? BIG_TILE : B32_TILE;
-    v = s.breq_na[r0 + t] > 0 ? (nL + w - 1) / w : 0;  // na = 0: dropped duplicate
+    const int nS = min(s.breq_na[r0 + t], s.breq_nb[r0 + t]);
+    const bool ex = s.breq_exact[r0 + t] != 0;
+    const int w = ex ? BIG_TILE : B32_TILE, c = big_chunk(nL, nS, ex);
+    v = s.breq_na[r0 + t] > 0 ? ((nL + w - 1) / w) * ((nS + c - 1) / c) : 0;  // na = 0: dropped
   }
   __shared__ int ws[BIG_BATCH / 32];
   const int lane = t & 31, w = t >> 5;
@@ -723,7 +741,11 @@ __global__ void __launch_bounds__(BIG_TPB) k_big_eval(State s, int r0, int m) {
       int t0 = sL; sL = sS; sS = t0;
       t0 = nL; nL = nS; nS = t0;
     }
-    const int l0 = (tile - s.btile[lo]) * BIG_TILE + threadIdx.x, l1 = l0 + BIG_TPB;
+    const int sch = big_chunk(nL, nS, true);
+    const int ts = (nS + sch - 1) / sch;  // chunks of the smaller cluster
+    const int q = tile - s.btile[lo];
+    const int sc0 = (q % ts) * sch, sc1 = min(nS, sc0 + sch);
+    const int l0 = (q / ts) * BIG_TILE + threadIdx.x, l1 = l0 + BIG_TPB;
     const bool v0 = l0 < nL, v1 = l1 < nL;
     T x0[DP], x1[DP];
 #pragma unroll
@@ -733,8 +755,8 @@ __global__ void __launch_bounds__(BIG_TPB) k_big_eval(State s, int r0, int m) {
     }
     double acc = 0.0;
     T macc = 0;
-    for (int c0 = 0; c0 < nS; c0 += BIG_TPB) {
-      const int cn = min(BIG_TPB, nS - c0);
+    for (int c0 = sc0; c0 < sc1; c0 += BIG_TPB) {
+      const int cn = min(BIG_TPB, sc1 - c0);
       __syncthreads();
       for (int i = threadIdx.x; i < cn * DP; i += BIG_TPB) sh[i] = P[(size_t)(sS + c0) * DP + i];
       __syncthreads();
@@ -786,12 +808,53 @@ __global__ void __launch_bounds__(BIG_TPB) k_big_eval(State s, int r0, int m) {
 // smaller cluster staged through shared memory 256 points at a time.  Square
 // roots use the hardware approximation (sqrt.approx.f32); with it a term's
 // relative error stays within ((D+1)/2 + 4)u <= (D+16)u, the bound the search
-// states for FP32 distances.  FP32 partials sum 32 terms (8 staged points x 4)
-// before an FP64 add.
+// states for FP32 distances.
 __device__ __forceinline__ float sqrt_approx(float x) {
   float r;
   asm("sqrt.approx.f32 %0, %1;" : "=f"(r) : "f"(x));
   return r;
+}
+
+// One staged chunk of the smaller cluster against a thread's four points.
+// Average: FP32 partials of 16 terms (4 staged points x 4) are summed in FP32
+// in groups of 16 before each FP64 add (relative error <= 30u per FP64 add).
+template <int LK, int D, bool FULL>
+__device__ __forceinline__ void big32_chunk(const float *sh, int cn, const float (&x)[B32_PPT][D],
+                                            const bool (&v)[B32_PPT], double &acc, float &macc) {
+  float part2 = 0.f;
+  int groups = 0;
+  for (int j0 = 0; j0 < cn; j0 += 4) {
+    const int jn = min(4, cn - j0);
+    float part = 0.f;
+#pragma unroll
+    for (int jj = 0; jj < 4; ++jj) {
+      if (jj < jn) {
+        const float *y = sh + (j0 + jj) * D;
+#pragma unroll
+        for (int p = 0; p < B32_PPT; ++p) {
+          float d2 = 0.f;
+#pragma unroll
+          for (int k = 0; k < D; ++k) {
+            const float t = x[p][k] - y[k];
+            d2 = fmaf(t, t, d2);
+          }
+          if (LK == 0)
+            macc = (FULL || v[p]) ? fmaxf(macc, d2) : macc;
+          else
+            part += (FULL || v[p]) ? sqrt_approx(d2) : 0.f;
+        }
+      }
+    }
+    if (LK != 0) {
+      part2 += part;
+      if (++groups == 16) {
+        acc += (double)part2;
+        part2 = 0.f;
+        groups = 0;
+      }
+    }
+  }
+  if (LK != 0) acc += (double)part2;
 }
 
 template <int LK, int D, int DP>
@@ -813,7 +876,11 @@ __global__ void __launch_bounds__(BIG_TPB) k_big_eval32(State s, int r0, int m) 
       int t0 = sL; sL = sS; sS = t0;
       t0 = nL; nL = nS; nS = t0;
     }
-    const int q = tile - s.btile[lo];
+    const int sch = big_chunk(nL, nS, false);
+    const int ts = (nS + sch - 1) / sch;  // chunks of the smaller cluster
+    const int q0 = tile - s.btile[lo];
+    const int sc0 = (q0 % ts) * sch, sc1 = min(nS, sc0 + sch);
+    const int q = q0 / ts;
     float x[B32_PPT][D];
     bool v[B32_PPT];
 #pragma unroll
@@ -825,38 +892,19 @@ __global__ void __launch_bounds__(BIG_TPB) k_big_eval32(State s, int r0, int m) 
     }
     double acc = 0.0;
     float macc = 0.f;
-    for (int c0 = 0; c0 < nS; c0 += BIG_TPB) {
-      const int cn = min(BIG_TPB, nS - c0);
+    const bool full = v[B32_PPT - 1];  // all four points valid: no selects
+    for (int c0 = sc0; c0 < sc1; c0 += BIG_TPB) {
+      const int cn = min(BIG_TPB, sc1 - c0);
       __syncthreads();
       for (int i = threadIdx.x; i < cn * D; i += BIG_TPB) {
         const int j = i / D, k = i - j * D;
         sh[i] = P[(size_t)(sS + c0 + j) * DP + k];
       }
       __syncthreads();
-      for (int j0 = 0; j0 < cn; j0 += 8) {
-        float part = 0.f;
-        const int jn = min(8, cn - j0);
-#pragma unroll
-        for (int jj = 0; jj < 8; ++jj) {
-          if (jj < jn) {
-            const float *y = sh + (j0 + jj) * D;
-#pragma unroll
-            for (int p = 0; p < B32_PPT; ++p) {
-              float d2 = 0.f;
-#pragma unroll
-              for (int k = 0; k < D; ++k) {
-                const float t = x[p][k] - y[k];
-                d2 = fmaf(t, t, d2);
-              }
-              if (LK == 0)
-                macc = v[p] ? fmaxf(macc, d2) : macc;
-              else
-                part += v[p] ? sqrt_approx(d2) : 0.f;
-            }
-          }
-        }
-        if (LK != 0) acc += (double)part;
-      }
+      if (full)
+        big32_chunk<LK, D, true>(sh, cn, x, v, acc, macc);
+      else
+        big32_chunk<LK, D, false>(sh, cn, x, v, acc, macc);
     }
     double val = LK == 0 ? (double)macc : acc;
     for (int o = 16; o; o >>= 1) {
@@ -1485,7 +1533,9 @@ int run_impl(hac_ctx *h, const hac_opts *o) {
     s.ins_cap = (int)cap;
     if (!s.breq_i) {  // big-pair deferral buffers (sized once per handle)
       const int bcap = 1 << 18;
-      const size_t tiles = (size_t)BIG_BATCH * (size_t)cdiv(h->n, BIG_TILE) + BIG_BATCH;
+      // per request at most max(BIG_MAXT, tiles along the larger cluster)
+      const size_t per = (size_t)std::max(BIG_MAXT, cdiv(h->n, BIG_TILE) + 1);
+      const size_t tiles = (size_t)BIG_BATCH * per;
       if ((rc0 = dalloc(h, &s.breq_i, bcap)) || (rc0 = dalloc(h, &s.breq_j, bcap)) ||
           (rc0 = dalloc(h, &s.breq_sa, bcap)) || (rc0 = dalloc(h, &s.breq_na, bcap)) ||
           (rc0 = dalloc(h, &s.breq_sb, bcap)) || (rc0 = dalloc(h, &s.breq_nb, bcap)) ||
@@ -1503,8 +1553,9 @@ int run_impl(hac_ctx *h, const hac_opts *o) {
   h->st = hac_stats_t{};
   h->st.device_bytes = h->bytes;
   const auto t0 = std::chrono::steady_clock::now();
-  Ev e0, e1, e2, e3, eq0, eq1;
-  double ms_nn = 0, ms_merge = 0, ms_update = 0, ms_init = 0, ms_query = 0;
+  Ev e0, e1, e2, e3, eq0, eq1, eb0, eb1;
+  double ms_nn = 0, ms_merge = 0, ms_update = 0, ms_init = 0, ms_query = 0, ms_big = 0;
+  int64_t big_launch = 0;
   int64_t qlaunch = 0;
   h->launches = 0;
   cudaEventRecord(e0.e, st);
@@ -1619,8 +1670,17 @@ int run_impl(hac_ctx *h, const hac_opts *o) {
         const int m = std::min(BIG_BATCH, nreq - r0);
         k_big_dedup<<<1, BIG_BATCH, 0, st>>>(s, r0, m);
         k_big_tiles<<<1, BIG_BATCH, 0, st>>>(s, r0, m);
+        cudaEventRecord(eb0.e, st);
         rc = launch_big(s, r0, m, st);
+        cudaEventRecord(eb1.e, st);
         if (rc) return rc;
+        big_launch += 2;
+        {
+          CK(cudaEventSynchronize(eb1.e));
+          float bms;
+          cudaEventElapsedTime(&bms, eb0.e, eb1.e);
+          ms_big += bms;
+        }
         k_big_final<<<cdiv(m, 8), 256, 0, st>>>(s, r0, m);
         h->launches += 5;
       }
@@ -1766,6 +1826,9 @@ int run_impl(hac_ctx *h, const hac_opts *o) {
   h->st.leaf_tests = (int64_t)c.ltests;
   h->st.kernel_launches = h->launches;
   h->st.cache_hits = (int64_t)c.cache_hits;
+  h->st.ms_big = ms_big;
+  h->st.big_point_pairs = (int64_t)c.big_pp;
+  h->st.big_launches = big_launch;
   h->st.cache_lw_entries = (int64_t)c.cache_lw;
   {
     // algorithmic bytes of the search kernel (true dimension d, not padded):

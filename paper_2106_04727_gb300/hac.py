@@ -43,7 +43,9 @@ class hac_stats_t(ctypes.Structure):
                ("ms_query", ctypes.c_double)] + \
                [(k, ctypes.c_int64) for k in ("query_launches", "query_bytes", "leaf_tests",
                                               "kernel_launches", "cache_hits",
-                                              "cache_lw_entries")]
+                                              "cache_lw_entries")] + \
+               [("ms_big", ctypes.c_double), ("big_point_pairs", ctypes.c_int64),
+                ("big_launches", ctypes.c_int64)]
 
 
 MERGE_DTYPE = np.dtype([("cid_a", np.int64), ("cid_b", np.int64), ("height", np.float64),
