@@ -275,10 +275,24 @@ __global__ void k_layout(State s, const T *X, const int32_t *perm, MortonParams 
     s.rootof[i] = i;
     s.reloff[i] = 0;
     s.gen[i] = 0;
+    s.inst[i] = 0;
+    s.qinst[p] = 0;
     s.order[0][p] = i;
     s.pos[i] = (int32_t)p;
     s.term[p] = i;
   }
+}
+
+// one instance's parameters and progress counters
+__global__ void k_inst_set(State s, int slot, float slack, float scale, float dpts, int rec,
+                           int act) {
+  s.islack[slot] = slack;
+  s.iscale[slot] = scale;
+  s.idpts[slot] = dpts;
+  s.irec[slot] = rec;
+  s.irecn[slot] = 0;
+  s.iact[slot] = act;
+  s.idone[slot] = act <= 1;
 }
 
 // ---------------------------------------------------------------------------
@@ -294,8 +308,17 @@ __global__ void k_tree_leaf(State s, const int32_t *order, int K) {
     const bool v = idx < K;
     const size_t c = v ? (size_t)idx : 0;  // position-ordered records
     int nm = v ? s.qsz[c] : INT_MAX;
-    for (int o = 16; o; o >>= 1) nm = min(nm, __shfl_xor_sync(0xffffffffu, nm, o));
+    int il = v ? s.qinst[c] : INT_MAX, ih = v ? s.qinst[c] : INT_MIN;
+    for (int o = 16; o; o >>= 1) {
+      nm = min(nm, __shfl_xor_sync(0xffffffffu, nm, o));
+      il = min(il, __shfl_xor_sync(0xffffffffu, il, o));
+      ih = max(ih, __shfl_xor_sync(0xffffffffu, ih, o));
+    }
     const int node = s.lvl_base[0] + j;
+    if (lane == 0) {
+      s.ninlo[node] = il;
+      s.ninhi[node] = ih;
+    }
 #pragma unroll
     for (int k = 0; k < DP; ++k) {
       float lo = v ? s.q32[c * DP + k] : INFINITY;
@@ -329,8 +352,17 @@ __global__ void k_tree_up(State s, int K, int L) {
     const bool v = ch < ccnt;
     const int cn = s.lvl_base[L - 1] + (v ? ch : 0);
     int nm = v ? s.nnmin[cn] : INT_MAX;
-    for (int o = 16; o; o >>= 1) nm = min(nm, __shfl_xor_sync(0xffffffffu, nm, o));
+    int il = v ? s.ninlo[cn] : INT_MAX, ih = v ? s.ninhi[cn] : INT_MIN;
+    for (int o = 16; o; o >>= 1) {
+      nm = min(nm, __shfl_xor_sync(0xffffffffu, nm, o));
+      il = min(il, __shfl_xor_sync(0xffffffffu, il, o));
+      ih = max(ih, __shfl_xor_sync(0xffffffffu, ih, o));
+    }
     const int node = s.lvl_base[L] + j;
+    if (lane == 0) {
+      s.ninlo[node] = il;
+      s.ninhi[node] = ih;
+    }
 #pragma unroll
     for (int k = 0; k < DP; ++k) {
       float lo = v ? s.nclo[(size_t)cn * DP + k] : INFINITY;
@@ -394,7 +426,10 @@ __global__ void k_merge(State s, int round, int npairs) {
     const int lo = s.pair_lo[p], hi = s.pair_hi[p];
     const double key = s.pair_key[p];
     const int na = s.csize[lo], nb = s.csize[hi];
-    const int m = atomicAdd(&s.ctr->nmerges, 1);
+    const int ins = s.inst[lo];
+    atomicAdd(&s.ctr->nmerges, 1);
+    const int m = s.irec[ins] + atomicAdd(&s.irecn[ins], 1);
+    if (atomicSub(&s.iact[ins], 1) == 2) s.idone[ins] = 1;  // one cluster left
     s.m_a[m] = lo;
     s.m_b[m] = hi;
     s.m_h[m] = s.linkage == LK_WARD ? sqrt(key) : key;
@@ -984,7 +1019,7 @@ __global__ void k_big_final(State s, int r0, int m) {
       atomicAdd(&s.ctr->big_pp, (unsigned long long)s.breq_na[r] * (unsigned long long)s.breq_nb[r]);
       if (exact) atomicAdd(&s.ctr->big_exact, 1ull);
       const float e = exact ? 0.f
-: fmaxf(s.delta_pts, EST_MARK);
+: fmaxf(s.idpts[s.inst[i]], EST_MARK);
       cache_insert_evict(s, i, j, s.gen[j], D, e);
       cache_insert_evict(s, j, i, s.gen[i], D, e);
     }
@@ -1006,7 +1041,7 @@ __global__ void k_cmp_count(State s, const int32_t *order, int K, int round) {
   int keep = 0, ist = 0, sz = 0;
   if (p < K) {
     const int c = order[p];
-    if (s.alive[c]) {
+    if (s.alive[c] && !s.idone[s.inst[c]]) {
       keep = 1;
       int sc = s.succ[c];
       if (sc >= 0 && s.mround[sc] == round) {
@@ -1059,7 +1094,7 @@ __global__ void k_cmp_write(State s, const int32_t *order, int32_t *order_out, i
   int keep = 0, ist = 0, sz = 0, c = -1;
   if (p < K) {
     c = order[p];
-    if (s.alive[c]) {
+    if (s.alive[c] && !s.idone[s.inst[c]]) {
       keep = 1;
       ist = s.succ[c] < 0;
       sz = s.csize[c];
@@ -1082,6 +1117,7 @@ __global__ void k_cmp_write(State s, const int32_t *order, int32_t *order_out, i
     }
     s.qsz[ok] = sz;
     s.qseg[ok] = os;
+    s.qinst[ok] = s.inst[c];
     if (ist) {
       s.term[ot] = c;
       s.isterm[c] = round + 1;
@@ -1102,6 +1138,7 @@ __global__ void k_relayout(State s, int pc) {
       r = s.rootof[c];
       off += s.reloff[c];
     }
+    if (s.idone[s.inst[r]]) continue;  // finished instance: its points leave
     const int64_t q = (int64_t)s.seg[nx][r] + off;
     for (int k = 0; k < dp; ++k) {
       s.p64[nx][q * dp + k] = s.p64[pc][p * dp + k];
@@ -1240,6 +1277,16 @@ int alloc_state(hac_ctx *h) {
   A(s.osize, n);
   A(s.partner, n);
   A(s.gen, n);
+  A(s.inst, n);
+  A(s.qinst, n);
+  if (s.max_inst < 1) s.max_inst = 1;
+  A(s.islack, s.max_inst);
+  A(s.iscale, s.max_inst);
+  A(s.idpts, s.max_inst);
+  A(s.irec, s.max_inst);
+  A(s.irecn, s.max_inst);
+  A(s.iact, s.max_inst);
+  A(s.idone, s.max_inst);
   A(s.pos, n);
   A(s.Ekey, n);
   A(s.Ecid, n);
@@ -1265,6 +1312,8 @@ int alloc_state(hac_ctx *h) {
   A(s.nhmin, (int64_t)base * dp);
   A(s.nlmax, (int64_t)base * dp);
   A(s.nnmin, base);
+  A(s.ninlo, base);
+  A(s.ninhi, base);
   A(s.bsum, 3 * (int64_t)cdiv(n, TPB) + 3);
   A(s.ctr, 1);
   for (int b = 0; b < 2; ++b) {
@@ -1428,6 +1477,7 @@ int init_layout(hac_ctx *h, cudaStream_t st) {
   s.abs_slack = std::max(scale, 1e-300) * std::ldexp(1.0, -18);
   s.coord_scale = (float)(scale * (1.0 + 1e-6));
   s.delta_pts = s.pts32_exact ? 0.f : 2.01f * 5.9604645e-8f * s.coord_scale * std::sqrt((float)d);
+  k_inst_set<<<1, 1, 0, st>>>(s, 0, (float)s.abs_slack, s.coord_scale, s.delta_pts, 0, (int)n);
   k_morton<T><<<grid_for(n, TPB), TPB, 0, st>>>(X, n, d, mp, h->keys[0], h->vals[0]);
   CK(cudaGetLastError());
   int sc = radix_sort(h, (int)n, mp.bits * d, st);
@@ -1613,6 +1663,13 @@ int run_impl(hac_ctx *h, const hac_opts *o) {
     qa.nhmin = s.nhmin;
     qa.nlmax = s.nlmax;
     qa.nnmin = s.nnmin;
+    qa.inst = s.inst;
+    qa.qinst = s.qinst;
+    qa.ninlo = s.ninlo;
+    qa.ninhi = s.ninhi;
+    qa.islack = s.islack;
+    qa.iscale = s.iscale;
+    qa.idpts = s.idpts;
     for (int L = 0; L <= MAXLEV; ++L) qa.lvl_base[L] = s.lvl_base[L];
     qa.Ekey = s.Ekey;
     qa.Ecid = s.Ecid;
@@ -1749,7 +1806,8 @@ int run_impl(hac_ctx *h, const hac_opts *o) {
     cudaEventRecord(e3.e, st);
     CK(cudaMemcpyAsync(&c, s.ctr, sizeof(Counters), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
-    if ((c.err & ~ERR_NONFINITE) || c.nactive != K) {
+    // the last merge finishes the instance: its single cluster leaves the order
+    if ((c.err & ~ERR_NONFINITE) || (c.nactive != K && !(K == 1 && c.nactive == 0))) {
       if (trace)
         fprintf(stderr, "hac round %d: consistency (err %d, active %d, expected %d)\n", round,
                 c.err, c.nactive, K);
@@ -2038,6 +2096,16 @@ bool carve_state(hac_ctx &h, Carver &cv) {
   cv.take(&s.osize, n);
   cv.take(&s.partner, n);
   cv.take(&s.gen, n);
+  cv.take(&s.inst, n);
+  cv.take(&s.qinst, n);
+  s.max_inst = 1;
+  cv.take(&s.islack, 1);
+  cv.take(&s.iscale, 1);
+  cv.take(&s.idpts, 1);
+  cv.take(&s.irec, 1);
+  cv.take(&s.irecn, 1);
+  cv.take(&s.iact, 1);
+  cv.take(&s.idone, 1);
   cv.take(&s.pos, n);
   cv.take(&s.Ekey, n);
   cv.take(&s.Ecid, n);
@@ -2062,6 +2130,8 @@ bool carve_state(hac_ctx &h, Carver &cv) {
   cv.take(&s.nhmin, (size_t)base * dp);
   cv.take(&s.nlmax, (size_t)base * dp);
   cv.take(&s.nnmin, (size_t)base);
+  cv.take(&s.ninlo, (size_t)base);
+  cv.take(&s.ninhi, (size_t)base);
   cv.take(&s.bsum, 3 * (size_t)cdiv(n, TPB) + 3);
   cv.take(&s.ctr, 1);
   for (int b = 0; b < 2; ++b) {
@@ -2116,6 +2186,7 @@ int static_layout(hac_ctx &h, cudaStream_t st) {
   s.abs_slack = std::max(scale, 1e-300) * std::ldexp(1.0, -18);
   s.coord_scale = (float)(scale * (1.0 + 1e-6));
   s.delta_pts = s.pts32_exact ? 0.f : 2.01f * 5.9604645e-8f * s.coord_scale * std::sqrt((float)d);
+  k_inst_set<<<1, 1, 0, st>>>(s, 0, (float)s.abs_slack, s.coord_scale, s.delta_pts, 0, (int)n);
   k_morton<T><<<grid_for(n, TPB), TPB, 0, st>>>(X, n, d, mp, h.keys[0], h.vals[0]);
   CK(cudaGetLastError());
   const int sc = radix_sort(&h, (int)n, mp.bits * d, st);
@@ -2180,6 +2251,13 @@ int static_run(hac_ctx &h, const hac_opts &opt, cudaStream_t st, hac_merge *dev_
     qa.nhmin = s.nhmin;
     qa.nlmax = s.nlmax;
     qa.nnmin = s.nnmin;
+    qa.inst = s.inst;
+    qa.qinst = s.qinst;
+    qa.ninlo = s.ninlo;
+    qa.ninhi = s.ninhi;
+    qa.islack = s.islack;
+    qa.iscale = s.iscale;
+    qa.idpts = s.idpts;
     for (int L = 0; L <= MAXLEV; ++L) qa.lvl_base[L] = s.lvl_base[L];
     qa.Ekey = s.Ekey;
     qa.Ecid = s.Ecid;
@@ -2224,7 +2302,8 @@ int static_run(hac_ctx &h, const hac_opts &opt, cudaStream_t st, hac_merge *dev_
     }
     CK(cudaMemcpyAsync(&c, s.ctr, sizeof(Counters), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
-    if ((c.err & ~ERR_NONFINITE) || c.nactive != K) return HAC_EINTERNAL;
+    if ((c.err & ~ERR_NONFINITE) || (c.nactive != K && !(K == 1 && c.nactive == 0)))
+      return HAC_EINTERNAL;
     nterm = c.nterm;
     ++round;
   }

@@ -92,6 +92,19 @@ struct State {
   int32_t *btile;        // tile prefix of the current batch
   double *bpart;         // per-tile partial results of the current batch
   int32_t *pend[2];      // terminals whose search deferred a pair
+  // instances sharing this state (a server engine clusters many at once;
+  // hac_run is the one-instance case): instance of each cid / position,
+  // tree-node instance ranges, and per-instance parameters and progress
+  int32_t *inst, *qinst;
+  int32_t *ninlo, *ninhi;
+  int max_inst;
+  float *islack;        // absolute pruning slack (coordinate scale * 2^-18)
+  float *iscale;        // largest |coordinate| after recentring
+  float *idpts;         // error term of FP32 point distances (0 for FP32 input)
+  int32_t *irec;        // first merge-record slot (= first cid of the instance)
+  int32_t *irecn;       // merge records written
+  int32_t *iact;        // active clusters left
+  int32_t *idone;       // 1 once one cluster is left
   int32_t *pos;         // position of each active cid in `order`
   double *Ekey;         // nearest-neighbour key of each terminal (linkage key space)
   int32_t *Ecid;
@@ -137,6 +150,9 @@ struct QueryArgs {
   double *Ekey;
   int32_t *Ecid;
   Counters *ctr;
+  // instances
+  const int32_t *inst, *qinst, *ninlo, *ninhi;
+  const float *islack, *iscale, *idpts;
   // pair-distance cache
   int cache_slots, ins_cap;
   const unsigned long long *ckey;

@@ -342,7 +342,9 @@ template <int LK, int DP, int MODE>
 struct Searcher {
   const QueryArgs &a;
   int lane, ci, na, sa;
+  int myinst;     // instance of C_i: candidates come from the same instance only
   float fna;
+  float dpts;     // error term of FP32 point distances for this instance
   float ci32[DP], alo[DP], ahi[DP];
   float slack;
   float beta_d;   // pred bound, D units
@@ -364,6 +366,8 @@ struct Searcher {
       : a(args), lane(lane_), ci(ci_) {
     na = a.csize[ci];
     fna = (float)na;
+    myinst = a.inst[ci];
+    dpts = a.idpts[myinst];
     sa = a.seg[ci];
 #pragma unroll
     for (int k = 0; k < DP; ++k) {
@@ -378,8 +382,8 @@ struct Searcher {
       const float bkey = __uint_as_float((unsigned)(pv >> 32));
       beta_d = LK == LK_WARD ? __fsqrt_ru(bkey) : bkey;
     }
-    slack = (float)a.abs_slack * (LK == LK_WARD ? sqrtf(2.f * fna) : 2.f);
-    delta0 = 2.01f * U32 * a.coord_scale * sqrtf((float)a.d);
+    slack = a.islack[myinst] * (LK == LK_WARD ? sqrtf(2.f * fna) : 2.f);
+    delta0 = 2.01f * U32 * a.iscale[myinst] * sqrtf((float)a.d);
     rho = ((float)a.d + 16.f) * U32 + (LK == LK_AVERAGE ? 32.f * U32 : 0.f);
     bk = KINF;
     bc = INT_MAX;
@@ -496,7 +500,7 @@ struct Searcher {
     const int idx = j * FAN + lane;
     const bool in = idx < a.K;
     const int cb = in ? a.order[idx] : -1;
-    const bool valid = in && cb != ci;
+    const bool valid = in && cb != ci && a.qinst[idx] == myinst;
     const int nb = valid ? a.qsz[idx] : 1;
     float dc2 = INFINITY, bx = 0.f;
     if (valid) {
@@ -561,7 +565,7 @@ struct Searcher {
     const float lb = valid ? fmaxf(sqrtf(dc2), bx) : INFINITY;
     const bool ok = valid && pass(lb);
     const int sb = valid ? a.qseg[idx] : 0;
-    const float dlt = a.delta_pts;
+    const float dlt = dpts;
     const bool small = ok && (long long)na * nb <= SMALLP;
     const unsigned sm = __ballot_sync(0xffffffffu, small);
     if (sm) {
@@ -742,8 +746,11 @@ __device__ void traverse(const QueryArgs &a, Searcher<LK, DP, MODE> &S, uint32_t
     float lbc = INFINITY;
     bool ok = false;
     if (child < cnt) {
-      lbc = node_lb<LK, DP>(a, a.lvl_base[L - 1] + child, S.ci32, S.alo, S.ahi, S.fna);
-      ok = S.pass(lbc);
+      const int node = a.lvl_base[L - 1] + child;
+      if (a.ninlo[node] <= S.myinst && S.myinst <= a.ninhi[node]) {
+        lbc = node_lb<LK, DP>(a, node, S.ci32, S.alo, S.ahi, S.fna);
+        ok = S.pass(lbc);
+      }
       S.nodes += 1;
     }
     const unsigned m = __ballot_sync(0xffffffffu, ok);
