@@ -1559,6 +1559,203 @@ struct Ev {
   }
 };
 
+// Per-round timing / counters of round_step (events may be null: no timing)
+struct RoundCtl {
+  cudaEvent_t e1 = nullptr, e2 = nullptr, eq0 = nullptr, eq1 = nullptr, eb0 = nullptr,
+              eb1 = nullptr;
+  double ms_query = 0, ms_big = 0;
+  int64_t qlaunch = 0, big_launch = 0, searches = 0;
+  int big_iters = 0, big_reqs = 0;
+};
+
+void fill_query_args(hac_ctx *h, QueryArgs &qa, int round, int K, int nterm) {
+  State &s = h->s;
+  qa.d = s.d;
+  qa.linkage = s.linkage;
+  qa.round = round;
+  qa.K = K;
+  qa.nterm = nterm;
+  qa.abs_slack = s.abs_slack;
+  qa.coord_scale = s.coord_scale;
+  qa.delta_pts = s.delta_pts;
+  qa.term = s.term;
+  qa.order = s.order[h->ocur];
+  qa.pos = s.pos;
+  qa.csize = s.csize;
+  qa.seg = s.seg[h->pcur];
+  qa.cent = s.cent;
+  qa.p64 = s.p64[h->pcur];
+  qa.cent32 = s.cent32;
+  qa.blo = s.blo;
+  qa.bhi = s.bhi;
+  qa.p32 = s.p32[h->pcur];
+  qa.pred = s.pred;
+  qa.q32 = s.q32;
+  qa.q64 = s.q64;
+  qa.qblo = s.qblo;
+  qa.qbhi = s.qbhi;
+  qa.qsz = s.qsz;
+  qa.qseg = s.qseg;
+  qa.nclo = s.nclo;
+  qa.nchi = s.nchi;
+  qa.nhmin = s.nhmin;
+  qa.nlmax = s.nlmax;
+  qa.nnmin = s.nnmin;
+  qa.inst = s.inst;
+  qa.qinst = s.qinst;
+  qa.ninlo = s.ninlo;
+  qa.ninhi = s.ninhi;
+  qa.islack = s.islack;
+  qa.iscale = s.iscale;
+  qa.idpts = s.idpts;
+  for (int L = 0; L <= MAXLEV; ++L) qa.lvl_base[L] = s.lvl_base[L];
+  qa.Ekey = s.Ekey;
+  qa.Ecid = s.Ecid;
+  qa.ctr = s.ctr;
+  qa.cache_slots = s.cache_slots;
+  qa.ins_cap = s.ins_cap;
+  qa.ckey = s.ckey;
+  qa.cval = s.cval;
+  qa.cerr = s.cerr;
+  qa.gen = s.gen;
+  qa.ins_i = s.ins_i;
+  qa.ins_j = s.ins_j;
+  qa.ins_v = s.ins_v;
+  qa.ins_e = s.ins_e;
+  qa.defer = s.cache_slots > 0 && s.linkage != LK_WARD ? 1 : 0;
+  qa.big_pairs = h->big_pairs;
+  qa.big_pairs64 = h->big_pairs64;
+  qa.breq_cap = s.breq_cap;
+  qa.breq_i = s.breq_i;
+  qa.breq_j = s.breq_j;
+  qa.breq_sa = s.breq_sa;
+  qa.breq_na = s.breq_na;
+  qa.breq_sb = s.breq_sb;
+  qa.breq_nb = s.breq_nb;
+  qa.breq_exact = s.breq_exact;
+  qa.pend_out = s.pend[0];
+}
+
+#define EVREC(ev) \
+  do {            \
+    if (ev) cudaEventRecord(ev, st); \
+  } while (0)
+
+// One round of Algorithm 1 over the current terminal list: the searches (with
+// big pairs handed to the whole GPU and the deferring searches re-run), the
+// chain update, the R-NN filter, the merges, the cache update, the compaction
+// and the point re-layout.  *npairs_out receives the merges made; the caller
+// reads the counters and rebuilds the tree.
+int round_step(hac_ctx *h, cudaStream_t st, int round, int K, int nterm, RoundCtl &ctl,
+               int *npairs_out) {
+  State &s = h->s;
+  const bool need_points = s.linkage != LK_WARD;
+  int rc = 0;
+  s.cur = h->pcur;
+  QueryArgs qa{};
+  fill_query_args(h, qa, round, K, nterm);
+  const bool defer = qa.defer != 0;
+  EVREC(ctl.eq0);
+  CK(launch_query(qa, s.dp, s.prec, st));
+  EVREC(ctl.eq1);
+  ++ctl.qlaunch;
+  ctl.searches += nterm;
+  h->launches += 1;
+  if (s.cache_slots > 0) {
+    k_cache_insert<<<grid_for((int64_t)152 * 8 * TPB, TPB), TPB, 0, st>>>(s);
+    CK(cudaMemsetAsync(&s.ctr->nins, 0, sizeof(int32_t), st));
+    h->launches += 1;
+  }
+  // searches that handed big pairs to the whole GPU: evaluate those pairs
+  // (results go to the cache), then search again; the last re-run
+  // evaluates any remaining big pair itself, so the loop ends
+  for (int it = 0; defer; ++it) {
+    int cnt[2];
+    CK(cudaMemcpyAsync(cnt, &s.ctr->nbreq, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    const int nreq = std::min(cnt[0], s.breq_cap), npend = cnt[1];
+    if (npend == 0) break;
+    ++ctl.big_iters;
+    ctl.big_reqs += nreq;
+    if (ctl.eq0) {
+      float q;
+      cudaEventElapsedTime(&q, ctl.eq0, ctl.eq1);
+      ctl.ms_query += q;
+    }
+    for (int r0 = 0; r0 < nreq; r0 += BIG_BATCH) {
+      const int m = std::min(BIG_BATCH, nreq - r0);
+      k_big_dedup<<<1, BIG_BATCH, 0, st>>>(s, r0, m);
+      k_big_tiles<<<1, BIG_BATCH, 0, st>>>(s, r0, m);
+      EVREC(ctl.eb0);
+      rc = launch_big(s, r0, m, st);
+      EVREC(ctl.eb1);
+      if (rc) return rc;
+      ctl.big_launch += 2;
+      if (ctl.eb0) {
+        CK(cudaEventSynchronize(ctl.eb1));
+        float bms;
+        cudaEventElapsedTime(&bms, ctl.eb0, ctl.eb1);
+        ctl.ms_big += bms;
+      }
+      k_big_final<<<cdiv(m, 8), 256, 0, st>>>(s, r0, m);
+      h->launches += 5;
+    }
+    CK(cudaMemsetAsync(&s.ctr->nbreq, 0, 2 * sizeof(int32_t), st));
+    ctl.searches += npend;
+    qa.term = s.pend[it & 1];
+    qa.nterm = npend;
+    qa.pend_out = s.pend[(it & 1) ^ 1];
+    qa.defer = it < 4 ? 1 : 0;
+    EVREC(ctl.eq0);
+    CK(launch_query(qa, s.dp, s.prec, st));
+    EVREC(ctl.eq1);
+    ++ctl.qlaunch;
+    k_cache_insert<<<grid_for((int64_t)152 * 8 * TPB, TPB), TPB, 0, st>>>(s);
+    CK(cudaMemsetAsync(&s.ctr->nins, 0, sizeof(int32_t), st));
+    h->launches += 2;
+  }
+  k_chain<<<grid_for(nterm, TPB), TPB, 0, st>>>(s, nterm);
+  h->launches += 2;  // chain, rnn
+  EVREC(ctl.e1);
+  CK(cudaMemsetAsync(&s.ctr->npairs, 0, sizeof(int32_t), st));
+  k_rnn<<<grid_for(nterm, TPB), TPB, 0, st>>>(s, nterm, round);
+  CK(cudaGetLastError());
+  int npairs = 0;
+  CK(cudaMemcpyAsync(&npairs, &s.ctr->npairs, sizeof(int), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  *npairs_out = npairs;
+  if (npairs <= 0) return HAC_EINTERNAL;
+  k_merge<<<grid_for(npairs, TPB), TPB, 0, st>>>(s, round, npairs);
+  h->launches += 4;  // merge, 3 compaction kernels
+  if (s.cache_slots > 0) {
+    const int S = s.cache_slots;
+    const size_t smem = (size_t)CM_WARPS * 4 * S * sizeof(CEntry);
+    const int blocks = std::max(1, std::min(cdiv(npairs, CM_WARPS), 152 * 32));
+    if (s.linkage == LK_COMPLETE)
+      k_cache_merge<0><<<blocks, CM_WARPS * 32, smem, st>>>(s, npairs, round);
+    else
+      k_cache_merge<1><<<blocks, CM_WARPS * 32, smem, st>>>(s, npairs, round);
+    k_gen_bump<<<grid_for(npairs, TPB), TPB, 0, st>>>(s, npairs);
+    h->launches += 2;
+  }
+  EVREC(ctl.e2);
+  const int nb = cdiv(K, TPB);
+  const int32_t *ord = s.order[h->ocur];
+  int32_t *ordn = s.order[h->ocur ^ 1];
+  k_cmp_count<<<nb, TPB, 0, st>>>(s, ord, K, round);
+  k_cmp_top<<<1, TPB, 0, st>>>(s, nb);
+  k_cmp_write<<<nb, TPB, 0, st>>>(s, ord, ordn, need_points ? s.seg[h->pcur ^ 1] : nullptr, K,
+                                  round);
+  CK(cudaGetLastError());
+  h->ocur ^= 1;
+  if (need_points) {
+    k_relayout<<<grid_for(h->n, TPB), TPB, 0, st>>>(s, h->pcur);
+    h->launches += 1;
+    h->pcur ^= 1;
+  }
+  return HAC_OK;
+}
+
 int run_impl(hac_ctx *h, const hac_opts *o) {
   hac_opts opt;
   hac_default_opts(&opt);
@@ -1619,185 +1816,32 @@ int run_impl(hac_ctx *h, const hac_opts *o) {
     ms_init = ms;
   }
   int K = (int)h->n, nterm = (int)h->n, round = 0;
-  const bool need_points = s.linkage != LK_WARD;
   Counters c{}, cprev{};
   const char *tr = getenv("HAC_TRACE");
   const bool trace = tr && tr[0] && tr[0] != '0';
+  RoundCtl ctl;
+  ctl.e1 = e1.e;
+  ctl.e2 = e2.e;
+  ctl.eq0 = eq0.e;
+  ctl.eq1 = eq1.e;
+  ctl.eb0 = eb0.e;
+  ctl.eb1 = eb1.e;
   while (K > 1) {
     if (opt.max_rounds && round >= opt.max_rounds) return HAC_ETIMEOUT;
     if (opt.timeout_s > 0 &&
         std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count() >
             opt.timeout_s)
       return HAC_ETIMEOUT;
-    s.cur = h->pcur;
     cudaEventRecord(e0.e, st);
-    QueryArgs qa{};
-    qa.d = s.d;
-    qa.linkage = s.linkage;
-    qa.round = round;
-    qa.K = K;
-    qa.nterm = nterm;
-    qa.abs_slack = s.abs_slack;
-    qa.coord_scale = s.coord_scale;
-    qa.delta_pts = s.delta_pts;
-    qa.term = s.term;
-    qa.order = s.order[h->ocur];
-    qa.pos = s.pos;
-    qa.csize = s.csize;
-    qa.seg = s.seg[h->pcur];
-    qa.cent = s.cent;
-    qa.p64 = s.p64[h->pcur];
-    qa.cent32 = s.cent32;
-    qa.blo = s.blo;
-    qa.bhi = s.bhi;
-    qa.p32 = s.p32[h->pcur];
-    qa.pred = s.pred;
-    qa.q32 = s.q32;
-    qa.q64 = s.q64;
-    qa.qblo = s.qblo;
-    qa.qbhi = s.qbhi;
-    qa.qsz = s.qsz;
-    qa.qseg = s.qseg;
-    qa.nclo = s.nclo;
-    qa.nchi = s.nchi;
-    qa.nhmin = s.nhmin;
-    qa.nlmax = s.nlmax;
-    qa.nnmin = s.nnmin;
-    qa.inst = s.inst;
-    qa.qinst = s.qinst;
-    qa.ninlo = s.ninlo;
-    qa.ninhi = s.ninhi;
-    qa.islack = s.islack;
-    qa.iscale = s.iscale;
-    qa.idpts = s.idpts;
-    for (int L = 0; L <= MAXLEV; ++L) qa.lvl_base[L] = s.lvl_base[L];
-    qa.Ekey = s.Ekey;
-    qa.Ecid = s.Ecid;
-    qa.ctr = s.ctr;
-    qa.cache_slots = s.cache_slots;
-    qa.ins_cap = s.ins_cap;
-    qa.ckey = s.ckey;
-    qa.cval = s.cval;
-    qa.cerr = s.cerr;
-    qa.gen = s.gen;
-    qa.ins_i = s.ins_i;
-    qa.ins_j = s.ins_j;
-    qa.ins_v = s.ins_v;
-    qa.ins_e = s.ins_e;
-    const bool defer = s.cache_slots > 0 && need_points;
-    qa.defer = defer ? 1 : 0;
-    qa.big_pairs = h->big_pairs;
-    qa.big_pairs64 = h->big_pairs64;
-    qa.breq_cap = s.breq_cap;
-    qa.breq_i = s.breq_i;
-    qa.breq_j = s.breq_j;
-    qa.breq_sa = s.breq_sa;
-    qa.breq_na = s.breq_na;
-    qa.breq_sb = s.breq_sb;
-    qa.breq_nb = s.breq_nb;
-    qa.breq_exact = s.breq_exact;
-    qa.pend_out = s.pend[0];
-    cudaEventRecord(eq0.e, st);
-    CK(launch_query(qa, s.dp, s.prec, st));
-    cudaEventRecord(eq1.e, st);
-    ++qlaunch;
-    if (s.cache_slots > 0) {
-      k_cache_insert<<<grid_for((int64_t)152 * 8 * TPB, TPB), TPB, 0, st>>>(s);
-      CK(cudaMemsetAsync(&s.ctr->nins, 0, sizeof(int32_t), st));
-      h->launches += 1;
-    }
-    // searches that handed big pairs to the whole GPU: evaluate those pairs
-    // (results go to the cache), then search again; the last re-run
-    // evaluates any remaining big pair itself, so the loop ends
-    int big_iters = 0, big_reqs = 0;
-    for (int it = 0; defer; ++it) {
-      int cnt[2];
-      CK(cudaMemcpyAsync(cnt, &s.ctr->nbreq, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
-      CK(cudaStreamSynchronize(st));
-      const int nreq = std::min(cnt[0], s.breq_cap), npend = cnt[1];
-      if (npend == 0) break;
-      ++big_iters;
-      big_reqs += nreq;
-      {
-        float q;
-        cudaEventElapsedTime(&q, eq0.e, eq1.e);
-        ms_query += q;
-      }
-      for (int r0 = 0; r0 < nreq; r0 += BIG_BATCH) {
-        const int m = std::min(BIG_BATCH, nreq - r0);
-        k_big_dedup<<<1, BIG_BATCH, 0, st>>>(s, r0, m);
-        k_big_tiles<<<1, BIG_BATCH, 0, st>>>(s, r0, m);
-        cudaEventRecord(eb0.e, st);
-        rc = launch_big(s, r0, m, st);
-        cudaEventRecord(eb1.e, st);
-        if (rc) return rc;
-        big_launch += 2;
-        {
-          CK(cudaEventSynchronize(eb1.e));
-          float bms;
-          cudaEventElapsedTime(&bms, eb0.e, eb1.e);
-          ms_big += bms;
-        }
-        k_big_final<<<cdiv(m, 8), 256, 0, st>>>(s, r0, m);
-        h->launches += 5;
-      }
-      CK(cudaMemsetAsync(&s.ctr->nbreq, 0, 2 * sizeof(int32_t), st));
-      h->st.nn_searches += npend;
-      qa.term = s.pend[it & 1];
-      qa.nterm = npend;
-      qa.pend_out = s.pend[(it & 1) ^ 1];
-      qa.defer = it < 4 ? 1 : 0;
-      cudaEventRecord(eq0.e, st);
-      CK(launch_query(qa, s.dp, s.prec, st));
-      cudaEventRecord(eq1.e, st);
-      ++qlaunch;
-      k_cache_insert<<<grid_for((int64_t)152 * 8 * TPB, TPB), TPB, 0, st>>>(s);
-      CK(cudaMemsetAsync(&s.ctr->nins, 0, sizeof(int32_t), st));
-      h->launches += 2;
-    }
-    k_chain<<<grid_for(nterm, TPB), TPB, 0, st>>>(s, nterm);
-    h->launches += 3;  // query, chain, rnn
-    cudaEventRecord(e1.e, st);
-    CK(cudaMemsetAsync(&s.ctr->npairs, 0, sizeof(int32_t), st));
-    k_rnn<<<grid_for(nterm, TPB), TPB, 0, st>>>(s, nterm, round);
-    CK(cudaGetLastError());
+    const int big_iters0 = ctl.big_iters, big_reqs0 = ctl.big_reqs;
     int npairs = 0;
-    CK(cudaMemcpyAsync(&npairs, &s.ctr->npairs, sizeof(int), cudaMemcpyDeviceToHost, st));
-    CK(cudaStreamSynchronize(st));
-    if (npairs <= 0) {
+    rc = round_step(h, st, round, K, nterm, ctl, &npairs);
+    if (rc == HAC_EINTERNAL && npairs <= 0) {
       CK(cudaMemcpyAsync(&c, s.ctr, sizeof(Counters), cudaMemcpyDeviceToHost, st));
       CK(cudaStreamSynchronize(st));
       if (trace) fprintf(stderr, "hac round %d: no reciprocal pair (err %d)\n", round, c.err);
-      return HAC_EINTERNAL;
     }
-    k_merge<<<grid_for(npairs, TPB), TPB, 0, st>>>(s, round, npairs);
-    h->launches += 4;  // merge, 3 compaction kernels
-    if (s.cache_slots > 0) {
-      const int S = s.cache_slots;
-      const size_t smem = (size_t)CM_WARPS * 4 * S * sizeof(CEntry);
-      const int blocks = std::max(1, std::min(cdiv(npairs, CM_WARPS), 152 * 32));
-      if (s.linkage == LK_COMPLETE)
-        k_cache_merge<0><<<blocks, CM_WARPS * 32, smem, st>>>(s, npairs, round);
-      else
-        k_cache_merge<1><<<blocks, CM_WARPS * 32, smem, st>>>(s, npairs, round);
-      k_gen_bump<<<grid_for(npairs, TPB), TPB, 0, st>>>(s, npairs);
-      h->launches += 2;
-    }
-    cudaEventRecord(e2.e, st);
-    const int nb = cdiv(K, TPB);
-    const int32_t *ord = s.order[h->ocur];
-    int32_t *ordn = s.order[h->ocur ^ 1];
-    k_cmp_count<<<nb, TPB, 0, st>>>(s, ord, K, round);
-    k_cmp_top<<<1, TPB, 0, st>>>(s, nb);
-    k_cmp_write<<<nb, TPB, 0, st>>>(s, ord, ordn, need_points ? s.seg[h->pcur ^ 1] : nullptr,
-                                    K, round);
-    CK(cudaGetLastError());
-    h->ocur ^= 1;
-    if (need_points) {
-      k_relayout<<<grid_for(h->n, TPB), TPB, 0, st>>>(s, h->pcur);
-      h->launches += 1;
-      h->pcur ^= 1;
-    }
+    if (rc) return rc;
     K -= npairs;
     if (K > 1) {
       rc = build_tree(h, s.order[h->ocur], K, st);
@@ -1826,7 +1870,8 @@ int run_impl(hac_ctx *h, const hac_opts *o) {
               round, K + npairs, nterm, npairs, qms, c.ltests - cprev.ltests,
               c.nodes - cprev.nodes, c.cluster_pairs - cprev.cluster_pairs,
               c.point_pairs - cprev.point_pairs, c.rechecks - cprev.rechecks, nms, mms, ums,
-              big_iters, big_reqs, c.cache_hits - cprev.cache_hits, c.big_pp - cprev.big_pp,
+              ctl.big_iters - big_iters0, ctl.big_reqs - big_reqs0,
+              c.cache_hits - cprev.cache_hits, c.big_pp - cprev.big_pp,
               c.big_exact - cprev.big_exact);
       cprev = c;
     }
@@ -1838,14 +1883,18 @@ int run_impl(hac_ctx *h, const hac_opts *o) {
       cudaEventElapsedTime(&d3, e2.e, e3.e);
       float q;
       cudaEventElapsedTime(&q, eq0.e, eq1.e);
-      ms_query += q;
+      ctl.ms_query += q;
       ms_nn += a;
       ms_merge += b;
       ms_update += d3;
     }
-    h->st.nn_searches += qa.nterm;
     ++round;
   }
+  ms_query = ctl.ms_query;
+  ms_big = ctl.ms_big;
+  qlaunch = ctl.qlaunch;
+  big_launch = ctl.big_launch;
+  h->st.nn_searches = ctl.searches;
   CK(cudaMemcpyAsync(&c, s.ctr, sizeof(Counters), cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
   const int64_t m = h->n - 1;
@@ -2210,91 +2259,17 @@ int static_run(hac_ctx &h, const hac_opts &opt, cudaStream_t st, hac_merge *dev_
   if (rc) return rc;
   const auto t0 = std::chrono::steady_clock::now();
   int K = (int)h.n, nterm = (int)h.n, round = 0;
-  const bool need_points = s.linkage != LK_WARD;
   Counters c{};
+  RoundCtl ctl;  // no events: nothing is created here
   while (K > 1) {
     if (opt.max_rounds && round >= opt.max_rounds) return HAC_ETIMEOUT;
     if (opt.timeout_s > 0 &&
         std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count() >
             opt.timeout_s)
       return HAC_ETIMEOUT;
-    s.cur = h.pcur;
-    QueryArgs qa{};
-    qa.d = s.d;
-    qa.linkage = s.linkage;
-    qa.round = round;
-    qa.K = K;
-    qa.nterm = nterm;
-    qa.abs_slack = s.abs_slack;
-    qa.coord_scale = s.coord_scale;
-    qa.delta_pts = s.delta_pts;
-    qa.term = s.term;
-    qa.order = s.order[h.ocur];
-    qa.pos = s.pos;
-    qa.csize = s.csize;
-    qa.seg = s.seg[h.pcur];
-    qa.cent = s.cent;
-    qa.p64 = s.p64[h.pcur];
-    qa.cent32 = s.cent32;
-    qa.blo = s.blo;
-    qa.bhi = s.bhi;
-    qa.p32 = s.p32[h.pcur];
-    qa.pred = s.pred;
-    qa.q32 = s.q32;
-    qa.q64 = s.q64;
-    qa.qblo = s.qblo;
-    qa.qbhi = s.qbhi;
-    qa.qsz = s.qsz;
-    qa.qseg = s.qseg;
-    qa.nclo = s.nclo;
-    qa.nchi = s.nchi;
-    qa.nhmin = s.nhmin;
-    qa.nlmax = s.nlmax;
-    qa.nnmin = s.nnmin;
-    qa.inst = s.inst;
-    qa.qinst = s.qinst;
-    qa.ninlo = s.ninlo;
-    qa.ninhi = s.ninhi;
-    qa.islack = s.islack;
-    qa.iscale = s.iscale;
-    qa.idpts = s.idpts;
-    for (int L = 0; L <= MAXLEV; ++L) qa.lvl_base[L] = s.lvl_base[L];
-    qa.Ekey = s.Ekey;
-    qa.Ecid = s.Ecid;
-    qa.ctr = s.ctr;
-    qa.cache_slots = s.cache_slots;
-    qa.ins_cap = s.ins_cap;
-    qa.ckey = s.ckey;
-    qa.cval = s.cval;
-    qa.cerr = s.cerr;
-    qa.gen = s.gen;
-    qa.ins_i = s.ins_i;
-    qa.ins_j = s.ins_j;
-    qa.ins_v = s.ins_v;
-    qa.ins_e = s.ins_e;
-    CK(launch_query(qa, s.dp, s.prec, st));
-    k_chain<<<grid_for(nterm, TPB), TPB, 0, st>>>(s, nterm);
-    CK(cudaMemsetAsync(&s.ctr->npairs, 0, sizeof(int32_t), st));
-    k_rnn<<<grid_for(nterm, TPB), TPB, 0, st>>>(s, nterm, round);
-    CK(cudaGetLastError());
     int npairs = 0;
-    CK(cudaMemcpyAsync(&npairs, &s.ctr->npairs, sizeof(int), cudaMemcpyDeviceToHost, st));
-    CK(cudaStreamSynchronize(st));
-    if (npairs <= 0) return HAC_EINTERNAL;
-    k_merge<<<grid_for(npairs, TPB), TPB, 0, st>>>(s, round, npairs);
-    const int nb = cdiv(K, TPB);
-    const int32_t *ord = s.order[h.ocur];
-    int32_t *ordn = s.order[h.ocur ^ 1];
-    k_cmp_count<<<nb, TPB, 0, st>>>(s, ord, K, round);
-    k_cmp_top<<<1, TPB, 0, st>>>(s, nb);
-    k_cmp_write<<<nb, TPB, 0, st>>>(s, ord, ordn, need_points ? s.seg[h.pcur ^ 1] : nullptr, K,
-                                    round);
-    CK(cudaGetLastError());
-    h.ocur ^= 1;
-    if (need_points) {
-      k_relayout<<<grid_for(h.n, TPB), TPB, 0, st>>>(s, h.pcur);
-      h.pcur ^= 1;
-    }
+    rc = round_step(&h, st, round, K, nterm, ctl, &npairs);
+    if (rc) return rc;
     K -= npairs;
     if (K > 1) {
       rc = build_tree(&h, s.order[h.ocur], K, st);
@@ -2307,6 +2282,8 @@ int static_run(hac_ctx &h, const hac_opts &opt, cudaStream_t st, hac_merge *dev_
     nterm = c.nterm;
     ++round;
   }
+  CK(cudaMemcpyAsync(&c, s.ctr, sizeof(Counters), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
   const int64_t m = h.n - 1;
   if (c.nmerges != m && m > 0) return HAC_EINTERNAL;
   if (m > 0) {
