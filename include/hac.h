@@ -44,6 +44,7 @@ extern "C" {
 #define HAC_EPENDING (-5)  /* no dendrogram yet: hac_run has not completed */
 #define HAC_ECAP (-6)      /* output buffer smaller than n - 1 records */
 #define HAC_EINTERNAL (-7) /* an internal consistency check failed */
+#define HAC_ECANCELED (-8) /* a served request was cancelled (hac_cancel) */
 
 typedef struct hac_ctx *hac_t; /* opaque; owns all device memory of one instance */
 
@@ -178,6 +179,86 @@ const char *hac_strerror(int code);
  * serialised by the caller. */
 int hac_run_static(const void *dev_points, int64_t n, int d, hac_dtype dt, hac_linkage lk,
                    const hac_opts *opts, hac_merge *dev_out, int64_t cap);
+
+/* ------------------------------------------------------------------------
+ * Serving: many independent clusterings with continuous batching.
+ *
+ * The paper clusters one data set per run; a server (no counterpart in the
+ * paper) keeps many requests resident on the GPU at once.  Requests of the
+ * same linkage, dimension and input type share one ENGINE: one device state
+ * for `points_per_engine` points, run by its own host thread on its own CUDA
+ * stream.  Every round of Algorithm 1 is one launch per kernel for all of an
+ * engine's resident requests; a nearest-neighbour search never leaves its own
+ * request.  Between rounds, finished requests leave and queued ones are
+ * admitted while their n fits in a free range of the engine's points (first
+ * fit, in arrival order) and a request slot is free (4096 per engine), so
+ * requests that arrive while others run join at the next round.  Engines of
+ * different kinds run concurrently.  Each result is the dendrogram a lone
+ * hac_create + hac_run + hac_dendrogram with the server's options gives for
+ * the same points (cids local to the request, same canonical order), up to
+ * the rounding of FP64 sums whose order depends on the device layout.
+ * ------------------------------------------------------------------------ */
+typedef struct hac_server *hac_server_t; /* opaque */
+
+typedef struct {
+  int64_t engines;         /* engines created so far */
+  int64_t rounds;          /* rounds run, summed over engines */
+  int64_t admitted;        /* requests admitted to an engine */
+  int64_t completed;       /* requests that left an engine (finished, cancelled, timed out) */
+  int64_t queued;          /* requests waiting for admission now */
+  int64_t resident;        /* requests resident on the GPU now */
+  int64_t max_resident;    /* most requests resident at once in one engine */
+  int64_t device_bytes;    /* device memory held by all engines */
+  int64_t kernel_launches; /* kernels launched by all engines */
+} hac_server_stats_t;
+
+/* Create a server on the current CUDA device.  `points_per_engine` (2 ..
+ * 2^29) sizes every engine, and bounds the n of a request.  An engine holds
+ * about 0.35 KB (d <= 2) to 1.4 KB (d > 8) of device memory per point; with
+ * opts->cache_slots > 0, complete and average engines add 80 bytes plus 20
+ * bytes per slot per point and 128 MiB of big-pair buffers.  An engine is
+ * allocated when the first request of its kind arrives.  opts (may be NULL) gives precision
+ * and cache_slots for every request; its stream, max_rounds and timeout_s
+ * are ignored.  HAC_EINVAL for bad arguments, HAC_ENOMEM, HAC_EDEVICE. */
+int hac_server_create(int64_t points_per_engine, const hac_opts *opts, hac_server_t *out);
+
+/* Queue a request: HOST points, row-major n x d of `dt`, copied during the
+ * call.  timeout_s > 0 sets a deadline from now: a request not finished by
+ * then leaves at the next round boundary with HAC_ETIMEOUT.  *ticket names
+ * it for hac_poll / hac_server_wait / hac_cancel.  Never blocks on the GPU,
+ * except that the first request of a new kind allocates its engine.
+ * HAC_EINVAL as for hac_create; HAC_ENOMEM if n > points_per_engine or the
+ * engine cannot be allocated; after an engine failed, its code. */
+int hac_submit(hac_server_t srv, const void *points, int64_t n, int d, hac_dtype dt,
+               hac_linkage lk, double timeout_s, uint64_t *ticket);
+
+/* Cancel a request: a queued one leaves at once, a resident one at the next
+ * round boundary; either then completes with HAC_ECANCELED.  HAC_OK also if
+ * it had already finished (its result stays).  HAC_EINVAL: unknown ticket. */
+int hac_cancel(hac_server_t srv, uint64_t ticket);
+
+/* Non-blocking result of a request.  HAC_EPENDING while it runs.  Once it
+ * has finished, the n-1 merges go to host array `out` (capacity `cap`;
+ * HAC_ECAP if too small, ticket kept), *n_written receives their count,
+ * *latency_ms (may be NULL) the time from hac_submit to completion, and the
+ * ticket is released; a failed, cancelled or timed-out request returns its
+ * code (HAC_ECANCELED, HAC_ETIMEOUT, HAC_EDEVICE, ...) and is released too.
+ * HAC_EINVAL: unknown or already released ticket. */
+int hac_poll(hac_server_t srv, uint64_t ticket, hac_merge *out, int64_t cap, int64_t *n_written,
+             double *latency_ms);
+
+/* Block until the request has finished (hac_poll will not return
+ * HAC_EPENDING) or timeout_s seconds passed (HAC_ETIMEOUT); timeout_s = 0
+ * waits without limit.  HAC_EINVAL: unknown ticket. */
+int hac_server_wait(hac_server_t srv, uint64_t ticket, double timeout_s);
+
+/* Counters of the server; returns the sticky error of a failed engine
+ * (HAC_OK if none). */
+int hac_server_stats(hac_server_t srv, hac_server_stats_t *out);
+
+/* Stop every engine after its current round, free all device memory and
+ * every unreleased request.  NULL is a no-op. */
+void hac_server_destroy(hac_server_t srv);
 
 #ifdef __cplusplus
 }

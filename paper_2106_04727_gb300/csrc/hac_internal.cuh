@@ -95,8 +95,12 @@ struct State {
   // instances sharing this state (a server engine clusters many at once;
   // hac_run is the one-instance case): instance of each cid / position,
   // tree-node instance ranges, and per-instance parameters and progress
-  int32_t *inst, *qinst;
+  int32_t *inst;        // instance slot of each cid
+  int32_t *qinst;       // admission number of the instance at each position; it
+                        // never decreases along `order`, so tree nodes keep tight
+                        // [ninlo, ninhi] ranges of it
   int32_t *ninlo, *ninhi;
+  int32_t *iseq;        // admission number of each instance slot
   int max_inst;
   float *islack;        // absolute pruning slack (coordinate scale * 2^-18)
   float *iscale;        // largest |coordinate| after recentring

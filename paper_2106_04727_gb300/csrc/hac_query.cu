@@ -342,7 +342,8 @@ template <int LK, int DP, int MODE>
 struct Searcher {
   const QueryArgs &a;
   int lane, ci, na, sa;
-  int myinst;     // instance of C_i: candidates come from the same instance only
+  int myinst;     // instance slot of C_i (its parameters)
+  int myseq;      // its admission number: candidates come from the same instance only
   float fna;
   float dpts;     // error term of FP32 point distances for this instance
   float ci32[DP], alo[DP], ahi[DP];
@@ -367,6 +368,7 @@ struct Searcher {
     na = a.csize[ci];
     fna = (float)na;
     myinst = a.inst[ci];
+    myseq = a.qinst[a.pos[ci]];
     dpts = a.idpts[myinst];
     sa = a.seg[ci];
 #pragma unroll
@@ -500,7 +502,7 @@ struct Searcher {
     const int idx = j * FAN + lane;
     const bool in = idx < a.K;
     const int cb = in ? a.order[idx] : -1;
-    const bool valid = in && cb != ci && a.qinst[idx] == myinst;
+    const bool valid = in && cb != ci && a.qinst[idx] == myseq;
     const int nb = valid ? a.qsz[idx] : 1;
     float dc2 = INFINITY, bx = 0.f;
     if (valid) {
@@ -747,7 +749,7 @@ __device__ void traverse(const QueryArgs &a, Searcher<LK, DP, MODE> &S, uint32_t
     bool ok = false;
     if (child < cnt) {
       const int node = a.lvl_base[L - 1] + child;
-      if (a.ninlo[node] <= S.myinst && S.myinst <= a.ninhi[node]) {
+      if (a.ninlo[node] <= S.myseq && S.myseq <= a.ninhi[node]) {
         lbc = node_lb<LK, DP>(a, node, S.ci32, S.alo, S.ahi, S.fna);
         ok = S.pass(lbc);
       }

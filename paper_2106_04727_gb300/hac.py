@@ -22,6 +22,7 @@ PREC_F64, PREC_F32_RECHECK = 0, 1
 
 HAC_OK, HAC_EINVAL, HAC_ENOMEM, HAC_EDEVICE = 0, -1, -2, -3
 HAC_ETIMEOUT, HAC_EPENDING, HAC_ECAP, HAC_EINTERNAL = -4, -5, -6, -7
+HAC_ECANCELED = -8
 
 
 class hac_merge(ctypes.Structure):
@@ -46,6 +47,12 @@ class hac_stats_t(ctypes.Structure):
                                               "cache_lw_entries")] + \
                [("ms_big", ctypes.c_double), ("big_point_pairs", ctypes.c_int64),
                 ("big_launches", ctypes.c_int64)]
+
+
+class hac_server_stats_t(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_int64) for k in ("engines", "rounds", "admitted", "completed",
+                                              "queued", "resident", "max_resident",
+                                              "device_bytes", "kernel_launches")]
 
 
 MERGE_DTYPE = np.dtype([("cid_a", np.int64), ("cid_b", np.int64), ("height", np.float64),
@@ -96,6 +103,21 @@ def load(build_if_missing: bool = True):
         L.hac_strerror.restype = ctypes.c_char_p
         L.hac_run_static.argtypes = [P, i64, i32, i32, i32, ctypes.POINTER(hac_opts), P, i64]
         L.hac_run_static.restype = i32
+        u64, f64 = ctypes.c_uint64, ctypes.c_double
+        L.hac_server_create.argtypes = [i64, ctypes.POINTER(hac_opts), ctypes.POINTER(P)]
+        L.hac_server_create.restype = i32
+        L.hac_submit.argtypes = [P, P, i64, i32, i32, i32, f64, ctypes.POINTER(u64)]
+        L.hac_submit.restype = i32
+        L.hac_cancel.argtypes = [P, u64]
+        L.hac_cancel.restype = i32
+        L.hac_poll.argtypes = [P, u64, P, i64, ctypes.POINTER(i64), ctypes.POINTER(f64)]
+        L.hac_poll.restype = i32
+        L.hac_server_wait.argtypes = [P, u64, f64]
+        L.hac_server_wait.restype = i32
+        L.hac_server_stats.argtypes = [P, ctypes.POINTER(hac_server_stats_t)]
+        L.hac_server_stats.restype = i32
+        L.hac_server_destroy.argtypes = [P]
+        L.hac_server_destroy.restype = None
         _lib = L
         return L
 
@@ -220,3 +242,69 @@ def cluster(points: np.ndarray, linkage, precision: int = PREC_F64, with_rounds:
         return out
     finally:
         hac_destroy(h)
+
+
+# ---------------------------------------------------------------------------
+# serving (continuous batching of independent requests)
+# ---------------------------------------------------------------------------
+
+def hac_server_create(points_per_engine: int, precision: int = PREC_F64,
+                      cache_slots: int = 0) -> ctypes.c_void_p:
+    o = hac_default_opts()
+    o.precision = precision
+    o.cache_slots = cache_slots
+    srv = ctypes.c_void_p()
+    _check(load().hac_server_create(points_per_engine, ctypes.byref(o), ctypes.byref(srv)),
+           "hac_server_create")
+    return srv
+
+
+def hac_submit(srv, points: np.ndarray, linkage, timeout_s: float = 0.0) -> int:
+    """Queue one request (host points, float32/float64 (n, d)); returns its ticket."""
+    X = np.ascontiguousarray(points)
+    if X.dtype not in (np.float32, np.float64) or X.ndim != 2:
+        raise ValueError("points must be a float32/float64 (n, d) array")
+    t = ctypes.c_uint64()
+    _check(load().hac_submit(srv, X.ctypes.data_as(ctypes.c_void_p), X.shape[0], X.shape[1],
+                             F32 if X.dtype == np.float32 else F64, _lk(linkage),
+                             float(timeout_s), ctypes.byref(t)), "hac_submit")
+    return t.value
+
+
+def hac_cancel(srv, ticket: int) -> int:
+    return load().hac_cancel(srv, ticket)
+
+
+def hac_poll(srv, ticket: int, n: int):
+    """(status, merges or None, latency_ms): status HAC_EPENDING while it runs."""
+    out = np.zeros(max(n - 1, 1), dtype=MERGE_DTYPE)
+    got = ctypes.c_int64()
+    lat = ctypes.c_double()
+    rc = load().hac_poll(srv, ticket, ctypes.c_void_p(out.ctypes.data), max(n - 1, 0),
+                         ctypes.byref(got), ctypes.byref(lat))
+    if rc != HAC_OK:
+        return rc, None, (lat.value if rc != HAC_EPENDING else None)
+    return rc, out[:got.value], lat.value
+
+
+def hac_server_wait(srv, ticket: int, timeout_s: float = 0.0) -> int:
+    return load().hac_server_wait(srv, ticket, float(timeout_s))
+
+
+def hac_server_stats(srv) -> dict:
+    st = hac_server_stats_t()
+    rc = load().hac_server_stats(srv, ctypes.byref(st))
+    d = {k: getattr(st, k) for k, _ in hac_server_stats_t._fields_}
+    d["status"] = rc
+    return d
+
+
+def hac_server_destroy(srv) -> None:
+    if srv:
+        load().hac_server_destroy(srv)
+
+
+def result_dict(m: np.ndarray) -> dict:
+    """A merge array in the oracle's dict layout."""
+    return dict(a=m["cid_a"].copy(), b=m["cid_b"].copy(), h=m["height"].copy(),
+                size=m["size"].copy())
