@@ -145,6 +145,206 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+SERVING_METRIC = "serving p50/p99 ms and jobs/s (4,096-request stream)"
+
+
+def _pct(v, q):
+    import numpy as np
+    return float(np.percentile(np.asarray(v), q)) if len(v) else None
+
+
+def _serve(hac, srv, reqs, pts, arrivals=None):
+    """Submit a request stream (all at t=0, or at the given arrival times) and
+    wait for every result; latency = completion - arrival."""
+    t0 = time.perf_counter()
+    tickets, t_sub = [], []
+    for i, (r, X) in enumerate(zip(reqs, pts)):
+        if arrivals is not None:
+            dt = t0 + arrivals[i] - time.perf_counter()
+            if dt > 0:
+                time.sleep(dt)
+        t_sub.append(time.perf_counter() - t0)
+        tickets.append(hac.hac_submit(srv, X, r["linkage"]))
+    lat, res = [], []
+    for i, (t, r) in enumerate(zip(tickets, reqs)):
+        rc = hac.hac_server_wait(srv, t, 3600.0)
+        rc, m, ms = hac.hac_poll(srv, t, r["n"])
+        if rc != hac.HAC_OK:
+            raise hac.HacError(rc, "serving request")
+        late = t_sub[i] - (arrivals[i] if arrivals is not None else 0.0)
+        lat.append(ms + 1e3 * late)
+        res.append(m)
+    span = time.perf_counter() - t0
+    return {"jobs": len(reqs), "makespan_s": span, "jobs_per_s": len(reqs) / span,
+            "p50_ms": _pct(lat, 50), "p99_ms": _pct(lat, 99), "max_ms": max(lat)}, res
+
+
+def _per_instance(hac, reqs, pts, prec, slots):
+    """The plain per-instance GPU path: hac_create + hac_run + hac_dendrogram,
+    one request after the other; all requests arrive at t=0."""
+    t0 = time.perf_counter()
+    lat, res = [], []
+    for r, X in zip(reqs, pts):
+        res.append(hac.cluster(X, r["linkage"], precision=prec, cache_slots=slots,
+                               with_rounds=False))
+        lat.append(1e3 * (time.perf_counter() - t0))
+    span = time.perf_counter() - t0
+    return {"jobs": len(reqs), "makespan_s": span, "jobs_per_s": len(reqs) / span,
+            "p50_ms": _pct(lat, 50), "p99_ms": _pct(lat, 99), "max_ms": max(lat)}, res
+
+
+def run_serving(args):
+    """The serving stream: requests of uneven n, d and linkage, continuous
+    batching in the library's server (FP32 bulk + FP64 re-score) against the
+    per-instance FP64 path and the same requests run one after the other."""
+    import numpy as np
+    import torch
+
+    import oracle
+    from paper_2106_04727_gb300 import hac, inputs
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    if rank != 0:
+        return
+    slots = args.cache_slots
+    reqs = inputs.serving_requests(args.requests, seed=4)
+    pts = [inputs.request_points(r) for r in reqs]
+    cap = args.engine_points
+    srv = hac.hac_server_create(cap, precision=hac.PREC_F32_RECHECK, cache_slots=slots)
+    srv64 = None
+    try:
+        # warm-up: engines of every kind allocated, then W short streams
+        warm = inputs.serving_requests(96, seed=5, n_hi=4096)
+        wpts = [inputs.request_points(r) for r in warm]
+        for lk in range(3):
+            for d in (2, 3, 5, 10):
+                t = hac.hac_submit(srv, inputs.gaussian_mixture(100, d, 4, seed=d), lk)
+                hac.hac_server_wait(srv, t, 600.0)
+                hac.hac_poll(srv, t, 100)
+        for _ in range(args.warmup):
+            _serve(hac, srv, warm, wpts)
+        flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+        st0 = hac.hac_server_stats(srv)
+        sat = []
+        with Clocks(local) as clk:
+            for i in range(args.steps):
+                flush.fill_(float(i))
+                torch.cuda.synchronize()
+                sat.append(_serve(hac, srv, reqs, pts)[0])
+        st1 = hac.hac_server_stats(srv)
+        best = max(sat, key=lambda x: x["jobs_per_s"])
+        # Poisson arrivals at 0.7 x the saturated rate
+        rate = 0.7 * best["jobs_per_s"]
+        gaps = -np.log(1.0 - inputs.uniform(4, 77, len(reqs))) / rate
+        poisson, _ = _serve(hac, srv, reqs, pts, arrivals=np.cumsum(gaps))
+        poisson["rate_jobs_per_s"] = rate
+        # the per-instance paths on a sample of the same stream
+        k = min(args.sample, len(reqs))
+        sreq, spts = reqs[:k], pts[:k]
+        batched_s, res_b = _serve(hac, srv, sreq, spts)
+        per64, res_64 = _per_instance(hac, sreq, spts, hac.PREC_F64, slots)
+        seq32, _ = _per_instance(hac, sreq, spts, hac.PREC_F32_RECHECK, slots)
+        same, err = 0, 0.0
+        for a, b in zip(res_b, res_64):
+            c = oracle.compare(hac.result_dict(a), b, rtol=1e-5)
+            same += int(c["same_tree"])
+            err = max(err, c["max_rel_err"])
+        srv64 = hac.hac_server_create(cap, precision=hac.PREC_F64, cache_slots=slots)
+        for lk in range(3):
+            for d in (2, 3, 5, 10):
+                t = hac.hac_submit(srv64, inputs.gaussian_mixture(100, d, 4, seed=d), lk)
+                hac.hac_server_wait(srv64, t, 600.0)
+                hac.hac_poll(srv64, t, 100)
+        batched64_s, _ = _serve(hac, srv64, sreq, spts)
+    finally:
+        hac.hac_server_destroy(srv)
+        hac.hac_server_destroy(srv64)
+    cpu = None
+    if not args.no_cpu_baseline:
+        # the oracle on the stream's requests of n <= 4096 (O(n^2) memory), first 24
+        small = [(r, X) for r, X in zip(reqs, pts) if r["n"] <= 4096][:24]
+        t0 = time.perf_counter()
+        for r, X in small:
+            oracle.nnchain(X.astype(np.float64), r["linkage"])
+        dt = time.perf_counter() - t0
+        cpu = {"value": len(small) / dt, "unit": "jobs/s", "cores": 1, "kind": "oracle",
+               "sample": f"first {len(small)} requests of the stream with n <= 4096 "
+                         f"(sum n = {sum(r['n'] for r, _ in small)}), serial FP64 "
+                         f"Lance-Williams NN-chain, {dt:.2f} s"}
+    pts_bytes = sum(int(X.nbytes) for X in pts)
+    rec_bytes = sum(32 * (r["n"] - 1) for r in reqs)
+    ms_step = 1e3 * sum(x["makespan_s"] for x in sat) / len(sat)
+    line = {
+        "metric": SERVING_METRIC, "value": best["jobs_per_s"], "unit": "jobs/s",
+        "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
+        "data": "synthetic",
+        "config": {"workload": "serving_4096", "requests": len(reqs),
+                   "points": int(sum(r["n"] for r in reqs)),
+                   "n": "log-uniform [64, 65536]", "d": "{2,3,5,10}",
+                   "linkages": "complete+average+ward", "precision": "f32",
+                   "cache_slots": slots, "engine_points": cap,
+                   "step": "the whole stream submitted at t=0, every result read back",
+                   "l2": "flushed before each timed step (256 MB write); inputs are new "
+                         "host data each step"},
+        "serving": {"saturated": sat, "poisson": poisson,
+                    "sample": {"requests": k, "batched_f32_recheck": batched_s,
+                               "batched_f64": batched64_s,
+                               "per_instance_f64": per64, "sequential_f32_recheck": seq32,
+                               "speedup_batched_vs_per_instance_f64":
+                                   batched_s["jobs_per_s"] / per64["jobs_per_s"],
+                               "same_trees_as_f64": f"{same}/{k}",
+                               "max_rel_height_err_vs_f64": err}},
+        "server": {k2: st1[k2] - st0.get(k2, 0) if isinstance(st1[k2], (int, float)) and
+                   k2 not in ("engines", "max_resident", "device_bytes", "status") else st1[k2]
+                   for k2 in st1},
+        "roofline": None,
+        "gpu_launches": int(st1["kernel_launches"] - st0["kernel_launches"]),
+        "clocks": clk.summary(),
+        "e2e": {"value": best["jobs_per_s"], "unit": "jobs/s",
+                "h2d_bytes_per_step": pts_bytes, "d2h_bytes_per_step": rec_bytes,
+                "note": "the server API takes host points and returns host records: "
+                        "value is already end to end"},
+        "cpu_baseline": cpu,
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_serving_reference(args):
+    """The oracle on the serving stream's small requests (host core)."""
+    import numpy as np
+
+    import oracle
+    from paper_2106_04727_gb300 import inputs
+
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    reqs = inputs.serving_requests(args.requests, seed=4)
+    small = [r for r in reqs if r["n"] <= 4096][:24]
+    ts = []
+    for i in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        for r in small:
+            oracle.nnchain(inputs.request_points(r).astype(np.float64), r["linkage"])
+        if i >= args.warmup:
+            ts.append(time.perf_counter() - t0)
+    v = len(small) * len(ts) / sum(ts)
+    sample = (f"first {len(small)} requests of the stream with n <= 4096 per step, serial FP64 "
+              f"Lance-Williams NN-chain")
+    print(json.dumps({
+        "metric": SERVING_METRIC, "value": v, "unit": "jobs/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(ts) / len(ts),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "impl": "reference",
+        "config": {"workload": "serving_4096", "note": "bounded sample; host core"},
+        "cpu_baseline": {"kind": "oracle", "cores": 1, "value": v, "unit": "jobs/s",
+                         "sample": sample},
+        "e2e": {"value": v, "unit": "jobs/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0}}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -159,9 +359,18 @@ def main():
     ap.add_argument("--ref-sample", type=int, default=20000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--requests", type=int, default=4096, help="serving: stream length")
+    ap.add_argument("--sample", type=int, default=256,
+                    help="serving: requests timed on the per-instance paths")
+    ap.add_argument("--engine-points", type=int, default=1 << 21,
+                    help="serving: points per engine (one engine per linkage and d)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     args.linkages = [x for x in args.linkages.split(",") if x]
+    if args.workload == "serving":
+        if args.impl == "reference":
+            return run_serving_reference(args)
+        return run_serving(args)
     if args.impl == "reference":
         return run_reference(args)
 

@@ -210,6 +210,9 @@ typedef struct {
   int64_t max_resident;    /* most requests resident at once in one engine */
   int64_t device_bytes;    /* device memory held by all engines */
   int64_t kernel_launches; /* kernels launched by all engines */
+  double ms_admit;         /* host wall time engines spent admitting requests */
+  double ms_rounds;        /* ... running rounds (kernels, and waits on them) */
+  double ms_harvest;       /* ... handing out finished requests */
 } hac_server_stats_t;
 
 /* Create a server on the current CUDA device.  `points_per_engine` (2 ..
@@ -259,6 +262,22 @@ int hac_server_stats(hac_server_t srv, hac_server_stats_t *out);
 /* Stop every engine after its current round, free all device memory and
  * every unreleased request.  NULL is a no-op. */
 void hac_server_destroy(hac_server_t srv);
+
+/* Cluster the points of `count` distinct handles together (the batched form
+ * of hac_run; the paper has no counterpart).  Handles of the same linkage,
+ * dimension and input type share one engine of a private server, so each
+ * round is one launch per kernel for all of them; different kinds run
+ * concurrently.  Afterwards each handle holds what hac_run(h, opts) would
+ * leave: hac_dendrogram and hac_merge_rounds give the same merges in the same
+ * rounds (heights up to the rounding of FP64 sums whose order depends on the
+ * device layout).  hac_stats reports only rounds, merges, device_bytes and
+ * ms_total (the batch's wall time).  opts may be NULL; its stream is ignored,
+ * max_rounds must be 0, timeout_s applies to each handle.  Blocks until all
+ * are done; allocates the engines for the call (about the size of the
+ * handles' own state) and frees them before returning.  Returns HAC_OK, or
+ * the first error of any handle (that handle then has no dendrogram;
+ * HAC_EINVAL also for a NULL or repeated handle or a non-finite coordinate). */
+int hac_run_batch(hac_t *hs, int count, const hac_opts *opts);
 
 #ifdef __cplusplus
 }

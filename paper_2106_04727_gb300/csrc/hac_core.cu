@@ -435,7 +435,10 @@ __global__ void k_merge(State s, int round, int npairs) {
     const int ins = s.inst[lo];
     atomicAdd(&s.ctr->nmerges, 1);
     const int m = s.irec[ins] + atomicAdd(&s.irecn[ins], 1);
-    if (atomicSub(&s.iact[ins], 1) == 2) s.idone[ins] = 1;  // one cluster left
+    if (atomicSub(&s.iact[ins], 1) == 2) {  // one cluster left
+      s.idone[ins] = 1;
+      s.done_list[atomicAdd(&s.ctr->ndone, 1)] = ins;
+    }
     s.m_a[m] = lo;
     s.m_b[m] = hi;
     s.m_h[m] = s.linkage == LK_WARD ? sqrt(key) : key;
@@ -1294,6 +1297,7 @@ int alloc_state(hac_ctx *h) {
   A(s.iact, s.max_inst);
   A(s.idone, s.max_inst);
   A(s.iseq, s.max_inst);
+  A(s.done_list, 2 * s.max_inst);  // a dropped instance can be listed twice
   A(s.pos, n);
   A(s.Ekey, n);
   A(s.Ecid, n);
@@ -2161,6 +2165,7 @@ bool carve_state(hac_ctx &h, Carver &cv) {
   cv.take(&s.iscale, 1);
   cv.take(&s.idpts, 1);
   cv.take(&s.iseq, 1);
+  cv.take(&s.done_list, 2);
   cv.take(&s.irec, 1);
   cv.take(&s.irecn, 1);
   cv.take(&s.iact, 1);
@@ -2376,8 +2381,46 @@ constexpr int SRV_ADMIT_MAX = 1024;  // requests admitted between two rounds
 
 struct AdmitInst {
   int base, n, off, slot, seq, bits;
+  float slack, scale, dpts;               // the instance's pruning and error parameters
   double lo[MAXD], inv[MAXD], ctr[MAXD];  // Morton box and recentring offset
 };
+
+// parameters and progress counters of every admitted instance
+__global__ void k_admit_inst(State s, const AdmitInst *ai, int na) {
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < na; t += gridDim.x * blockDim.x) {
+    const AdmitInst &a = ai[t];
+    s.iseq[a.slot] = a.seq;
+    s.islack[a.slot] = a.slack;
+    s.iscale[a.slot] = a.scale;
+    s.idpts[a.slot] = a.dpts;
+    s.irec[a.slot] = a.base;
+    s.irecn[a.slot] = 0;
+    s.iact[a.slot] = a.n;
+    s.idone[a.slot] = a.n <= 1;
+  }
+}
+
+// merge records of the instances that finished, packed for one copy to the
+// host: record j of instance t goes to dst[off[t] + j] with local cids
+struct RecOut {
+  int32_t a, b, size, round;
+  double h;
+};
+
+__global__ void k_rec_pack(State s, const int4 *fin, int nf, int total, RecOut *dst) {
+  // fin[t] = (base, records, offset, admission round)
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x) {
+    int lo = 0, hi = nf;
+    while (hi - lo > 1) {
+      const int mid = (lo + hi) >> 1;
+      if (fin[mid].z <= i) lo = mid;
+      else hi = mid;
+    }
+    const int4 f = fin[lo];
+    const int m = f.x + (i - f.z);
+    dst[i] = RecOut{s.m_a[m] - f.x, s.m_b[m] - f.x, s.m_size[m], s.m_round[m] - f.w, s.m_h[m]};
+  }
+}
 
 __device__ __forceinline__ int admit_find(const AdmitInst *ai, int na, int i) {
   int lo = 0, hi = na;  // last instance with off <= i
@@ -2459,6 +2502,7 @@ __global__ void k_admit_layout(State s, const T *stage, int m, const AdmitInst *
     s.qsz[op] = 1;
     s.qseg[op] = (int32_t)pp;
     s.qinst[op] = a.seq;
+    for (int q = 0; q < s.cache_slots; ++q) s.ckey[(size_t)c * s.cache_slots + q] = CKEY_EMPTY;
   }
 }
 
@@ -2479,6 +2523,9 @@ struct SrvReq {
   bool dropped = false;    // its instance was told to leave
   int status = HAC_EPENDING;
   std::vector<hac_merge> out;
+  std::vector<int32_t> out_round;  // round of each merge (want_rounds only)
+  bool want_rounds = false;
+  int round0 = 0;                  // engine round at admission
   int slot = -1, base = -1;
   struct Engine *eng = nullptr;
 };
@@ -2493,12 +2540,18 @@ struct Engine {
   int K = 0, nterm = 0, round = 0, nres = 0, seq_next = 0;
   int64_t P = 0;                                 // points in the layout (not Ward)
   unsigned char *stage = nullptr;                // admitted points, staged on the device
+  unsigned char *h_stage = nullptr;              // ... and in pinned host memory
+  RecOut *d_rec = nullptr, *h_rec = nullptr;     // packed records of finished instances
+  int4 *d_fin = nullptr;
+  std::vector<int4> h_fin;
+  std::vector<int32_t> h_list;
   AdmitInst *d_ai = nullptr;
   std::vector<AdmitInst> h_ai;
   std::vector<int32_t> h_done;
   std::thread thr;
   int64_t rounds = 0, admitted = 0, completed = 0;
   int max_res = 0;
+  double ms_admit = 0, ms_rounds = 0, ms_harvest = 0;
 };
 
 }  // namespace
@@ -2573,8 +2626,14 @@ int engine_init(Engine &e, hac_linkage lk, int d, hac_dtype dt, int64_t cap, con
   if (rc) return rc;
   const size_t esz = dt == HAC_F32 ? 4 : 8;
   if ((rc = dalloc(&h, &e.stage, (size_t)cap * d * esz)) ||
-      (rc = dalloc(&h, &e.d_ai, (size_t)SRV_ADMIT_MAX)))
+      (rc = dalloc(&h, &e.d_ai, (size_t)SRV_ADMIT_MAX)) ||
+      (rc = dalloc(&h, &e.d_rec, (size_t)cap)) || (rc = dalloc(&h, &e.d_fin, 2 * SRV_MAX_INST)))
     return rc;
+  if (cudaMallocHost(&e.h_stage, (size_t)cap * d * esz) != cudaSuccess ||
+      cudaMallocHost(&e.h_rec, (size_t)cap * sizeof(RecOut)) != cudaSuccess) {
+    cudaGetLastError();
+    return HAC_ENOMEM;
+  }
   // Section 5 cache and the big-pair buffers, as hac_run allocates them
   const int slots = lk == HAC_WARD ? 0 : std::min(opt.cache_slots, CACHE_MAX_SLOTS);
   if (slots > 0) {
@@ -2612,9 +2671,9 @@ int engine_init(Engine &e, hac_linkage lk, int d, hac_dtype dt, int64_t cap, con
   return HAC_OK;
 }
 
-// Copy the batch's points in, give each request its parameters, and lay
-// its points out behind the resident clusters.  Device work only: the
-// batch's ids and slots were taken under the server lock.
+// Copy the batch's points in (one copy through pinned memory), give each
+// request its parameters, and lay its points out behind the resident
+// clusters.  The batch's ids and slots were taken under the server lock.
 int engine_admit(Engine &e, const std::vector<SrvReq *> &batch) {
   if (batch.empty()) return HAC_OK;
   hac_ctx &h = e.h;
@@ -2656,20 +2715,16 @@ int engine_admit(Engine &e, const std::vector<SrvReq *> &batch) {
       if (k < d)
         scale = std::max(scale, std::max(std::fabs(lo[k] - a.ctr[k]), std::fabs(hi[k] - a.ctr[k])));
     }
-    const double slack = std::max(scale, 1e-300) * std::ldexp(1.0, -18);
-    const float fscale = (float)(scale * (1.0 + 1e-6));
-    const float dpts = f32 ? 0.f : 2.01f * 5.9604645e-8f * fscale * std::sqrt((float)d);
-    CK(cudaMemcpyAsync(e.stage + (size_t)m * d * esz, r->pts.data(), (size_t)r->n * d * esz,
-                       cudaMemcpyHostToDevice, st));
-    k_inst_set<<<1, 1, 0, st>>>(s, r->slot, (float)slack, fscale, dpts, r->base, (int)r->n,
-                                a.seq);
-    if (s.cache_slots > 0)
-      CK(cudaMemsetAsync(s.ckey + (size_t)r->base * s.cache_slots, 0xff,
-                         (size_t)r->n * s.cache_slots * sizeof(unsigned long long), st));
+    a.slack = (float)(std::max(scale, 1e-300) * std::ldexp(1.0, -18));
+    a.scale = (float)(scale * (1.0 + 1e-6));
+    a.dpts = f32 ? 0.f : 2.01f * 5.9604645e-8f * a.scale * std::sqrt((float)d);
+    memcpy(e.h_stage + (size_t)m * d * esz, r->pts.data(), (size_t)r->n * d * esz);
     m += (int)r->n;
   }
   const int na = (int)batch.size();
+  CK(cudaMemcpyAsync(e.stage, e.h_stage, (size_t)m * d * esz, cudaMemcpyHostToDevice, st));
   CK(cudaMemcpyAsync(e.d_ai, e.h_ai.data(), na * sizeof(AdmitInst), cudaMemcpyHostToDevice, st));
+  k_admit_inst<<<grid_for(na, TPB), TPB, 0, st>>>(s, e.d_ai, na);
   if (f32)
     k_admit_keys<float><<<grid_for(m, TPB), TPB, 0, st>>>((const float *)e.stage, m, d, e.d_ai,
                                                           na, h.keys[0], h.vals[0]);
@@ -2690,53 +2745,88 @@ int engine_admit(Engine &e, const std::vector<SrvReq *> &batch) {
         s, (const double *)e.stage, m, e.d_ai, na, h.vals[sc], ord, e.K, e.nterm, e.P, h.pcur,
         e.round, ward);
   CK(cudaGetLastError());
-  h.launches += 3 + na;
+  h.launches += 3;
   e.K += m;
   e.nterm += m;
   if (!ward) e.P += m;
   h.lay_n = e.P;
-  // the stage and the batch table are reused by the next admission
+  // the pinned stage and the batch table are reused by the next admission
   CK(cudaStreamSynchronize(st));
   return HAC_OK;
 }
 
-// hand out the requests whose instance finished (or left) this round
-int engine_harvest(hac_server *srv, Engine &e) {
+// Hand out the requests whose instance finished (or was dropped) this round:
+// `ndone` slots in the device list plus the dropped ones; all their records
+// come back in one copy.
+int engine_harvest(hac_server *srv, Engine &e, int ndone, const std::vector<int> &drop) {
   hac_ctx &h = e.h;
   State &s = h.s;
   const cudaStream_t st = h.own;
-  CK(cudaMemcpyAsync(e.h_done.data(), s.idone, SRV_MAX_INST * sizeof(int32_t),
-                     cudaMemcpyDeviceToHost, st));
-  CK(cudaStreamSynchronize(st));
-  for (int slot = 0; slot < SRV_MAX_INST; ++slot) {
+  e.h_list.assign(drop.begin(), drop.end());
+  if (ndone > 0) {
+    const size_t at = e.h_list.size();
+    e.h_list.resize(at + ndone);
+    CK(cudaMemcpyAsync(e.h_list.data() + at, s.done_list, ndone * sizeof(int32_t),
+                       cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+  }
+  std::sort(e.h_list.begin(), e.h_list.end());
+  e.h_list.erase(std::unique(e.h_list.begin(), e.h_list.end()), e.h_list.end());
+  if (e.h_list.empty()) return HAC_OK;
+  // records of the instances that finished (dropped ones bring none)
+  e.h_fin.clear();
+  int total = 0;
+  for (int slot : e.h_list) {
     SrvReq *r = e.active[slot];
-    if (!r || !e.h_done[slot]) continue;
+    if (!r || r->dropped) continue;
+    e.h_fin.push_back(make_int4(r->base, (int)r->n - 1, total, r->round0));
+    total += (int)r->n - 1;
+  }
+  if (total > 0) {
+    const int nf = (int)e.h_fin.size();
+    CK(cudaMemcpyAsync(e.d_fin, e.h_fin.data(), nf * sizeof(int4), cudaMemcpyHostToDevice, st));
+    k_rec_pack<<<grid_for(total, TPB), TPB, 0, st>>>(s, e.d_fin, nf, total, e.d_rec);
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(e.h_rec, e.d_rec, (size_t)total * sizeof(RecOut), cudaMemcpyDeviceToHost,
+                       st));
+    CK(cudaStreamSynchronize(st));
+    h.launches += 1;
+  }
+  int fi = 0;
+  std::vector<int32_t> perm;
+  for (int slot : e.h_list) {
+    SrvReq *r = e.active[slot];
+    if (!r) continue;
     std::vector<hac_merge> out;
+    std::vector<int32_t> out_round;
     int status = HAC_OK;
     if (r->dropped) {
       status = r->cancel ? HAC_ECANCELED : HAC_ETIMEOUT;
     } else {
+      const RecOut *rec = e.h_rec + e.h_fin[fi++].z;
       const int64_t m = r->n - 1;
-      std::vector<int32_t> a(m), b(m), sz(m);
-      std::vector<double> hh(m);
-      CK(cudaMemcpyAsync(a.data(), s.m_a + r->base, m * 4, cudaMemcpyDeviceToHost, st));
-      CK(cudaMemcpyAsync(b.data(), s.m_b + r->base, m * 4, cudaMemcpyDeviceToHost, st));
-      CK(cudaMemcpyAsync(sz.data(), s.m_size + r->base, m * 4, cudaMemcpyDeviceToHost, st));
-      CK(cudaMemcpyAsync(hh.data(), s.m_h + r->base, m * 8, cudaMemcpyDeviceToHost, st));
-      CK(cudaStreamSynchronize(st));
-      out.resize(m);
-      for (int64_t i = 0; i < m; ++i)
-        out[i] = hac_merge{a[i] - r->base, b[i] - r->base, hh[i], sz[i]};
       // the canonical order of hac_dendrogram: (height, size, cid_a)
-      std::sort(out.begin(), out.end(), [](const hac_merge &x, const hac_merge &y) {
-        if (x.height != y.height) return x.height < y.height;
-        if (x.size != y.size) return x.size < y.size;
-        return x.cid_a < y.cid_a;
+      perm.resize(m);
+      for (int64_t i = 0; i < m; ++i) perm[i] = (int32_t)i;
+      std::sort(perm.begin(), perm.end(), [&](int32_t x, int32_t y) {
+        if (rec[x].h != rec[y].h) return rec[x].h < rec[y].h;
+        if (rec[x].size != rec[y].size) return rec[x].size < rec[y].size;
+        return rec[x].a < rec[y].a;
       });
+      out.resize(m);
+      for (int64_t i = 0; i < m; ++i) {
+        const RecOut &q = rec[perm[i]];
+        out[i] = hac_merge{q.a, q.b, q.h, q.size};
+      }
+      if (r->want_rounds) {
+        out_round.resize(m);
+        for (int64_t i = 0; i < m; ++i) out_round[i] = rec[perm[i]].round;
+      }
     }
     {
       std::lock_guard<std::mutex> g(srv->mu);
       r->out.swap(out);
+      r->out_round.swap(out_round);
       r->status = status;
       r->t_done = std::chrono::steady_clock::now();
       range_give(e, r->base, (int)r->n);
@@ -2750,6 +2840,14 @@ int engine_harvest(hac_server *srv, Engine &e) {
   }
   h.lay_n = e.P;
   return HAC_OK;
+}
+
+void engine_free(Engine *e) {
+  if (e->h_stage) cudaFreeHost(e->h_stage);
+  if (e->h_rec) cudaFreeHost(e->h_rec);
+  e->h_stage = nullptr;
+  e->h_rec = nullptr;
+  free_all(&e->h);
 }
 
 void engine_fail(hac_server *srv, Engine &e, int rc) {
@@ -2782,6 +2880,8 @@ void engine_loop(hac_server *srv, Engine *ep) {
   RoundCtl ctl;
   std::vector<SrvReq *> batch;
   std::vector<int> drop;
+  const char *tr = getenv("HAC_TRACE");
+  const bool trace = tr && tr[0] && tr[0] != '0';
   for (;;) {
     batch.clear();
     drop.clear();
@@ -2808,6 +2908,7 @@ void engine_loop(hac_server *srv, Engine *ep) {
           srv->done_cv.notify_all();
         } else if (!e.free_slots.empty() && range_take(e, (int)r->n, &base)) {
           r->base = base;
+          r->round0 = e.round;
           r->slot = e.free_slots.back();
           e.free_slots.pop_back();
           e.active[r->slot] = r;
@@ -2821,12 +2922,25 @@ void engine_loop(hac_server *srv, Engine *ep) {
       }
       e.max_res = std::max(e.max_res, e.nres);
     }
+    using clk = std::chrono::steady_clock;
+    auto ms_since = [](clk::time_point t) {
+      return std::chrono::duration<double, std::milli>(clk::now() - t).count();
+    };
     int rc = HAC_OK;
+    auto t0 = clk::now();
     for (int slot : drop) k_inst_drop<<<1, 1, 0, st>>>(h.s, slot);
+    if (cudaMemsetAsync(&h.s.ctr->ndone, 0, sizeof(int32_t), st) != cudaSuccess) {
+      cudaGetLastError();
+      engine_fail(srv, e, HAC_EDEVICE);
+      return;
+    }
     rc = engine_admit(e, batch);
+    e.ms_admit += ms_since(t0);
     if (rc == HAC_OK && e.K > 0) {
+      t0 = clk::now();
       rc = build_tree(&h, h.s.order[h.ocur], e.K, st);
-      int npairs = 0;
+      int npairs = 0, ndone = 0;
+      ctl.big_iters = ctl.big_reqs = 0;
       if (rc == HAC_OK) rc = round_step(&h, st, e.round, e.K, e.nterm, ctl, &npairs);
       if (rc == HAC_OK) {
         Counters c{};
@@ -2840,13 +2954,22 @@ void engine_loop(hac_server *srv, Engine *ep) {
         } else {
           e.K = c.nactive;
           e.nterm = c.nterm;
+          ndone = c.ndone;
         }
       }
       ++e.round;
       ++e.rounds;
-      if (rc == HAC_OK) rc = engine_harvest(srv, e);
+      const double ms_r = ms_since(t0);
+      e.ms_rounds += ms_r;
+      if (trace)
+        fprintf(stderr, "srv lk=%d d=%d round %d: admitted %zu resident %d K %d nterm %d pairs %d "
+                "big %d/%d %.3f ms\n", (int)h.lk, h.d, e.round - 1, batch.size(), e.nres, e.K,
+                e.nterm, npairs, ctl.big_iters, ctl.big_reqs, ms_r);
+      t0 = clk::now();
+      if (rc == HAC_OK) rc = engine_harvest(srv, e, ndone, drop);
+      e.ms_harvest += ms_since(t0);
     } else if (rc == HAC_OK && !drop.empty()) {
-      rc = engine_harvest(srv, e);
+      rc = engine_harvest(srv, e, 0, drop);
     }
     if (rc != HAC_OK) {
       engine_fail(srv, e, rc);
@@ -2880,8 +3003,19 @@ extern "C" int hac_server_create(int64_t points_per_engine, const hac_opts *opts
   return HAC_OK;
 }
 
+namespace {
+int submit_impl(hac_server_t srv, const void *points, int64_t n, int d, hac_dtype dt,
+                hac_linkage lk, double timeout_s, bool want_rounds, uint64_t *ticket);
+}
+
 extern "C" int hac_submit(hac_server_t srv, const void *points, int64_t n, int d, hac_dtype dt,
                           hac_linkage lk, double timeout_s, uint64_t *ticket) {
+  return submit_impl(srv, points, n, d, dt, lk, timeout_s, false, ticket);
+}
+
+namespace {
+int submit_impl(hac_server_t srv, const void *points, int64_t n, int d, hac_dtype dt,
+                hac_linkage lk, double timeout_s, bool want_rounds, uint64_t *ticket) {
   if (!srv || !points || !ticket || n < 1 || d < 1 || d > MAXD || !(timeout_s >= 0))
     return HAC_EINVAL;
   if (dt != HAC_F32 && dt != HAC_F64) return HAC_EINVAL;
@@ -2900,6 +3034,7 @@ extern "C" int hac_submit(hac_server_t srv, const void *points, int64_t n, int d
   r->d = d;
   r->dt = dt;
   r->lk = lk;
+  r->want_rounds = want_rounds;
   r->t_submit = std::chrono::steady_clock::now();
   if (timeout_s > 0) {
     r->has_deadline = true;
@@ -2932,7 +3067,7 @@ extern "C" int hac_submit(hac_server_t srv, const void *points, int64_t n, int d
     }
     const int rc = engine_init(*e, lk, d, dt, srv->cap, srv->opt);
     if (rc) {
-      free_all(&e->h);
+      engine_free(e);
       delete e;
       delete r;
       return rc;
@@ -2940,7 +3075,7 @@ extern "C" int hac_submit(hac_server_t srv, const void *points, int64_t n, int d
     try {
       e->thr = std::thread(engine_loop, srv, e);
     } catch (...) {
-      free_all(&e->h);
+      engine_free(e);
       delete e;
       delete r;
       return HAC_ENOMEM;
@@ -2955,6 +3090,7 @@ extern "C" int hac_submit(hac_server_t srv, const void *points, int64_t n, int d
   srv->cv.notify_all();
   return HAC_OK;
 }
+}  // namespace
 
 extern "C" int hac_cancel(hac_server_t srv, uint64_t ticket) {
   if (!srv) return HAC_EINVAL;
@@ -3030,6 +3166,9 @@ extern "C" int hac_server_stats(hac_server_t srv, hac_server_stats_t *out) {
     st.max_resident = std::max<int64_t>(st.max_resident, e.max_res);
     st.device_bytes += e.h.bytes;
     st.kernel_launches += e.h.launches;
+    st.ms_admit += e.ms_admit;
+    st.ms_rounds += e.ms_rounds;
+    st.ms_harvest += e.ms_harvest;
   }
   *out = st;
   return srv->err;
@@ -3045,9 +3184,86 @@ extern "C" void hac_server_destroy(hac_server_t srv) {
   for (auto &kv : srv->engines) {
     if (kv.second->thr.joinable()) kv.second->thr.join();
     if (kv.second->h.own) cudaStreamSynchronize(kv.second->h.own);
-    free_all(&kv.second->h);
+    engine_free(kv.second);
     delete kv.second;
   }
   for (auto &kv : srv->reqs) delete kv.second;
   delete srv;
+}
+
+// Several handles clustered together: a private server with one engine per
+// kind, every handle submitted at once, results written back into the handles
+// as hac_run would leave them.
+extern "C" int hac_run_batch(hac_t *hs, int count, const hac_opts *opts) {
+  if (count < 0 || (count > 0 && !hs)) return HAC_EINVAL;
+  hac_opts o;
+  hac_default_opts(&o);
+  if (opts) o = *opts;
+  if (o.precision != HAC_PREC_F64 && o.precision != HAC_PREC_F32_RECHECK) return HAC_EINVAL;
+  if (o.cache_slots < 0 || o.max_rounds != 0 || !(o.timeout_s >= 0)) return HAC_EINVAL;
+  std::map<int, int64_t> kind_n;
+  for (int i = 0; i < count; ++i) {
+    if (!hs[i]) return HAC_EINVAL;
+    for (int j = 0; j < i; ++j)
+      if (hs[j] == hs[i]) return HAC_EINVAL;
+    kind_n[((int)hs[i]->lk * 32 + hs[i]->d) * 2 + (hs[i]->dt == HAC_F32 ? 0 : 1)] += hs[i]->n;
+  }
+  if (count == 0) return HAC_OK;
+  int64_t cap = 2;
+  for (auto &kv : kind_n) cap = std::max(cap, kv.second);
+  const auto t0 = std::chrono::steady_clock::now();
+  for (int i = 0; i < count; ++i) hs[i]->done = false;
+  hac_server_t srv = nullptr;
+  hac_opts so = o;
+  so.timeout_s = 0;
+  int rc = hac_server_create(cap, &so, &srv);
+  if (rc) return rc;
+  std::vector<uint64_t> tickets(count, 0);
+  std::vector<int> st(count, HAC_OK);
+  std::vector<unsigned char> host;
+  for (int i = 0; i < count && !rc; ++i) {
+    hac_ctx *h = hs[i];
+    const size_t bytes = (size_t)h->n * h->d * (h->dt == HAC_F32 ? 4 : 8);
+    host.resize(bytes);
+    if (cudaMemcpy(host.data(), h->raw, bytes, cudaMemcpyDeviceToHost) != cudaSuccess) {
+      cudaGetLastError();
+      rc = HAC_EDEVICE;
+      break;
+    }
+    st[i] = submit_impl(srv, host.data(), h->n, h->d, h->dt, h->lk, o.timeout_s, true,
+                        &tickets[i]);
+  }
+  for (int i = 0; i < count && !rc; ++i) {
+    if (st[i] != HAC_OK) continue;
+    hac_server_wait(srv, tickets[i], 0);
+    hac_ctx *h = hs[i];
+    std::unique_lock<std::mutex> g(srv->mu);
+    SrvReq *r = srv->reqs[tickets[i]];
+    st[i] = r->status;
+    if (r->status != HAC_OK) continue;
+    const int64_t m = (int64_t)r->out.size();
+    int32_t rounds = 0;
+    for (int32_t v : r->out_round) rounds = std::max(rounds, v + 1);
+    if (m && (cudaMemcpy(h->dout, r->out.data(), m * sizeof(hac_merge),
+                         cudaMemcpyHostToDevice) != cudaSuccess ||
+              cudaMemcpy(h->dout_round, r->out_round.data(), m * sizeof(int32_t),
+                         cudaMemcpyHostToDevice) != cudaSuccess)) {
+      cudaGetLastError();
+      st[i] = HAC_EDEVICE;
+      continue;
+    }
+    h->n_merges = m;
+    h->st = hac_stats_t{};
+    h->st.rounds = rounds;
+    h->st.merges = m;
+    h->st.device_bytes = h->bytes;
+    h->st.ms_total =
+        std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    h->done = true;
+  }
+  hac_server_destroy(srv);
+  if (rc) return rc;
+  for (int i = 0; i < count; ++i)
+    if (st[i] != HAC_OK) return st[i];
+  return HAC_OK;
 }

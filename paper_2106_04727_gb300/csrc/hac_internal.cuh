@@ -26,7 +26,7 @@ struct Counters {
   int32_t nins;      // pair distances queued for the cache this round
   int32_t nbreq;     // big-pair requests queued by the search
   int32_t npend;     // terminals waiting for their big pairs
-  int32_t pad2_;
+  int32_t ndone;     // instances that finished this round (entries of done_list)
   unsigned long long cluster_pairs, point_pairs, nodes, rechecks, searches, ltests, prows;
   unsigned long long cache_hits, cache_lw;
   unsigned long long big_pp, big_exact;  // point pairs / FP64 requests of the GPU-wide evaluation
@@ -101,6 +101,7 @@ struct State {
                         // [ninlo, ninhi] ranges of it
   int32_t *ninlo, *ninhi;
   int32_t *iseq;        // admission number of each instance slot
+  int32_t *done_list;   // slots of the instances that finished this round
   int max_inst;
   float *islack;        // absolute pruning slack (coordinate scale * 2^-18)
   float *iscale;        // largest |coordinate| after recentring

@@ -52,7 +52,8 @@ class hac_stats_t(ctypes.Structure):
 class hac_server_stats_t(ctypes.Structure):
     _fields_ = [(k, ctypes.c_int64) for k in ("engines", "rounds", "admitted", "completed",
                                               "queued", "resident", "max_resident",
-                                              "device_bytes", "kernel_launches")]
+                                              "device_bytes", "kernel_launches")] + \
+               [(k, ctypes.c_double) for k in ("ms_admit", "ms_rounds", "ms_harvest")]
 
 
 MERGE_DTYPE = np.dtype([("cid_a", np.int64), ("cid_b", np.int64), ("height", np.float64),
@@ -118,6 +119,8 @@ def load(build_if_missing: bool = True):
         L.hac_server_stats.restype = i32
         L.hac_server_destroy.argtypes = [P]
         L.hac_server_destroy.restype = None
+        L.hac_run_batch.argtypes = [ctypes.POINTER(P), i32, ctypes.POINTER(hac_opts)]
+        L.hac_run_batch.restype = i32
         _lib = L
         return L
 
@@ -308,3 +311,14 @@ def result_dict(m: np.ndarray) -> dict:
     """A merge array in the oracle's dict layout."""
     return dict(a=m["cid_a"].copy(), b=m["cid_b"].copy(), h=m["height"].copy(),
                 size=m["size"].copy())
+
+
+def hac_run_batch(handles, precision: int = PREC_F64, cache_slots: int = 0,
+                  timeout_s: float = 0.0) -> int:
+    """hac_run for several handles at once (one engine per kind); returns the status."""
+    o = hac_default_opts()
+    o.precision = precision
+    o.cache_slots = cache_slots
+    o.timeout_s = timeout_s
+    arr = (ctypes.c_void_p * max(len(handles), 1))(*[h.value for h in handles])
+    return load().hac_run_batch(arr, len(handles), ctypes.byref(o))

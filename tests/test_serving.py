@@ -200,3 +200,39 @@ def test_destroy_with_requests_in_flight():
     c = oracle.compare(hac.cluster(X, "ward", with_rounds=False), oracle.nnchain(X, "ward"),
                        rtol=RTOL64)
     assert c["ok"], c
+
+
+def _round_sets(a, b, rounds):
+    out = {}
+    for x, y, r in zip(a, b, rounds):
+        out.setdefault(int(r), set()).add((int(x), int(y)))
+    return out
+
+
+@pytest.mark.parametrize("prec,slots", [(hac.PREC_F64, 0), (hac.PREC_F32_RECHECK, 64)],
+                         ids=["f64", "f32recheck_cache"])
+def test_run_batch_matches_hac_run(prec, slots):
+    reqs = inputs.serving_requests(18, seed=23, n_lo=2, n_hi=3000)
+    pts = [inputs.request_points(r) for r in reqs]
+    pts += [inputs.uniform_cube(1, 2, seed=1), inputs.uniform_cube(500, 3, seed=2)]
+    lks = [r["linkage"] for r in reqs] + [hac.WARD, hac.COMPLETE]
+    hs = [hac.hac_create(X, lk) for X, lk in zip(pts, lks)]
+    try:
+        assert hac.hac_run_batch(hs, precision=prec, cache_slots=slots) == hac.HAC_OK
+        for h, X, lk in zip(hs, pts, lks):
+            n = len(X)
+            m = hac.hac_dendrogram(h, n)
+            rd = hac.hac_merge_rounds(h, n)
+            alone = hac.cluster(X, lk, precision=prec, cache_slots=slots)
+            got = hac.result_dict(m)
+            c = oracle.compare(got, alone, rtol=_rtol(lk, prec))
+            assert c["ok"], (n, lk, c)
+            assert _round_sets(m["cid_a"], m["cid_b"], rd) == \
+                _round_sets(alone["a"], alone["b"], alone["round"])
+            assert hac.hac_stats(h)["rounds"] == alone["stats"]["rounds"]
+        # the handles stay usable for a plain run
+        assert hac.hac_run(hs[-1], precision=prec, cache_slots=slots) == hac.HAC_OK
+        assert hac.hac_run_batch([hs[0], hs[0]]) == hac.HAC_EINVAL
+    finally:
+        for h in hs:
+            hac.hac_destroy(h)
