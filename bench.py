@@ -103,6 +103,17 @@ def dist_env():
     return ws, rank, local
 
 
+def max_over_ranks(value: float, dist, device) -> float:
+    """The largest value over all ranks: a replicated job takes as long as its
+    slowest rank.  `dist` is torch.distributed (initialised) or None."""
+    if dist is None:
+        return value
+    import torch
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def cpu_baseline(workload: str, linkages, n_sample: int):
     """The oracle, as it stands, on a bounded sample of the workload (1 core)."""
     import numpy as np
@@ -423,11 +434,7 @@ def main():
         dist.barrier()
     torch.cuda.synchronize()
     times = [a.elapsed_time(b) for a, b in ev]
-    tot_ms = sum(times)
-    if dist:
-        t = torch.tensor([tot_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        tot_ms = float(t.item())
+    tot_ms = max_over_ranks(sum(times), dist, "cuda")
     value = ws * n * args.steps / (tot_ms / 1e3)
 
     def agg(key, lk=None):
