@@ -267,6 +267,13 @@ __global__ void k_layout(State s, const T *X, const int32_t *perm, MortonParams 
       s.qblo[p * dp + k] = __double2float_rd(x);
       s.qbhi[p * dp + k] = __double2float_ru(x);
     }
+    double sq = 0.0;
+    for (int k = 0; k < d; ++k) {
+      const double x = (double)X[(int64_t)i * d + k] - ctr_.lo[k];
+      sq += x * x;
+    }
+    s.csq[i] = sq;
+    s.qvar[p] = 0.f;
     s.qsz[p] = 1;
     s.qseg[p] = (int32_t)p;
     s.plab[0][p] = i;
@@ -454,6 +461,7 @@ __global__ void k_merge(State s, int round, int npairs) {
       s.blo[(size_t)lo * dp + k] = fminf(s.blo[(size_t)lo * dp + k], s.blo[(size_t)hi * dp + k]);
       s.bhi[(size_t)lo * dp + k] = fmaxf(s.bhi[(size_t)lo * dp + k], s.bhi[(size_t)hi * dp + k]);
     }
+    s.csq[lo] += s.csq[hi];
     s.csize[lo] = na + nb;
     s.succ[lo] = -1;
     s.pred[lo] = PRED_EMPTY;
@@ -703,265 +711,373 @@ __global__ void k_cache_merge(State s, int npairs, int round) {
 // big pairs: evaluated by the whole GPU, then cached for the re-run search
 // ---------------------------------------------------------------------------
 constexpr int BIG_TPB = 256;       // threads per tile
-constexpr int BIG_PPT = 2;         // points of the larger cluster per thread
-constexpr int BIG_TILE = BIG_TPB * BIG_PPT;  // FP64 tiles
-constexpr int B32_PPT = 4;
-constexpr int B32_TILE = BIG_TPB * B32_PPT;  // FP32 tiles
-// tiles also cut the smaller cluster into chunks, so one request spreads
-// over many CTAs: a tile is (points of the larger) x (points of the smaller)
-constexpr int BIG_SCH = 1024;   // FP64 tiles: 512 x 1024 point pairs (at least)
-constexpr int B32_SCH = 2048;   // FP32 tiles: 1024 x 2048 point pairs (at least)
+constexpr int BIG_TILE = BIG_TPB * 2;  // narrowest tile along the larger cluster
 constexpr int BIG_MAXT = 32768; // tiles per request at most (chunks widen to fit)
+constexpr int BIG_BATCH = 512;     // requests per batch (one scan block)
 
-// chunk of the smaller cluster per tile, widened so that a request has at
-// most max(BIG_MAXT, tiles along the larger cluster) tiles
-__host__ __device__ inline int big_chunk(int nL, int nS, bool exact) {
-  const int w = exact ? BIG_TILE : B32_TILE;
+// Three kinds of request, each its own tile list and kernel:
+//   0  FP32, larger cluster >= 256 x 8 points: 8 of its points per thread
+//      (4 for d > 8)
+//   1  FP32, smaller requests: 2 points per thread
+//   2  FP64 (exact values wanted): 2 points per thread
+// A tile is (points of the larger cluster) x (a chunk of the smaller one).
+constexpr int BK_KINDS = 3;
+__host__ __device__ inline int bk_ppt(int kind, int d) { return kind == 0 ? (d <= 8 ? 8 : 4) : 2; }
+__host__ __device__ inline int bk_width(int kind, int d) { return BIG_TPB * bk_ppt(kind, d); }
+
+__host__ __device__ inline int bk_kind(int nL, bool exact, int d) {
+  return exact ? 2 : nL >= bk_width(0, d) ? 0 : 1;
+}
+
+// chunk of the smaller cluster per tile (2048 points FP32, 1024 FP64),
+// widened so that a request has at most max(BIG_MAXT, tiles along the larger
+// cluster) tiles
+__host__ __device__ inline int bk_chunk(int kind, int nL, int nS, int d) {
+  const int w = bk_width(kind, d);
   const int tl = (nL + w - 1) / w;
-  int c = exact ? BIG_SCH : B32_SCH;
+  int c = kind == 2 ? 1024 : 2048;
   const int maxts = BIG_MAXT / tl > 1 ? BIG_MAXT / tl : 1;
   if ((nS + c - 1) / c > maxts) c = (nS + maxts - 1) / maxts;
   return c;
 }
-constexpr int BIG_BATCH = 512;     // requests per batch (one scan block)
 
-// tile prefix of the batch's requests: tiles = ceil(larger size / 256)
-__global__ void k_big_tiles(State s, int r0, int m) {
-  const int t = threadIdx.x;
-  int v = 0;
-  if (t < m) {
-    const int nL = max(s.breq_na[r0 + t], s.breq_nb[r0 + t]);
-    const int nS = min(s.breq_na[r0 + t], s.breq_nb[r0 + t]);
-    const bool ex = s.breq_exact[r0 + t] != 0;
-    const int w = ex ? BIG_TILE : B32_TILE, c = big_chunk(nL, nS, ex);
-    v = s.breq_na[r0 + t] > 0 ? ((nL + w - 1) / w) * ((nS + c - 1) / c) : 0;  // na = 0: dropped
-  }
-  __shared__ int ws[BIG_BATCH / 32];
-  const int lane = t & 31, w = t >> 5;
+// Schedule of one batch, in s.bsched (ints):
+//   [0, B)            tile start of each request in bpart (all kinds)
+//   [B, 2B)           tile count of each request
+//   per kind k at 2B + k (2B + 1): B request indices, then B + 1 tile prefix
+//   at 2B + 3 (2B + 1): n_k (requests of kind k), T_k (tiles), next_k (work
+//   counter) for each kind
+constexpr int BS_B = BIG_BATCH;
+constexpr int BS_LIST = 2 * BS_B;
+constexpr int BS_META = 2 * BS_B + BK_KINDS * (2 * BS_B + 1);
+constexpr int BS_SIZE = BS_META + 3 * BK_KINDS;
+
+__device__ __forceinline__ int *bs_req(const State &s, int k) {
+  return s.bsched + BS_LIST + k * (2 * BS_B + 1);
+}
+__device__ __forceinline__ int *bs_pre(const State &s, int k) { return bs_req(s, k) + BS_B; }
+
+__device__ int block_incl_scan_big(int v, int *ws) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   int x = v;
   for (int o = 1; o < 32; o <<= 1) {
-    int y = __shfl_up_sync(0xffffffffu, x, o);
+    const int y = __shfl_up_sync(0xffffffffu, x, o);
     if (lane >= o) x += y;
   }
+  __syncthreads();
   if (lane == 31) ws[w] = x;
   __syncthreads();
   if (w == 0) {
     int z = lane < BIG_BATCH / 32 ? ws[lane] : 0;
     for (int o = 1; o < 32; o <<= 1) {
-      int y = __shfl_up_sync(0xffffffffu, z, o);
+      const int y = __shfl_up_sync(0xffffffffu, z, o);
       if (lane >= o) z += y;
     }
     if (lane < BIG_BATCH / 32) ws[lane] = z;
   }
   __syncthreads();
-  const int incl = x + (w ? ws[w - 1] : 0);
-  if (t < m) s.btile[t + 1] = incl;
-  if (t == 0) s.btile[0] = 0;
+  return x + (w ? ws[w - 1] : 0);
 }
 
-// One CTA per tile: 512 points of the larger cluster (two per thread)
-// against every point of the smaller one, staged through shared memory, so
-// each staged point feeds two distances.  The tile's partial (sum of
-// distances, or max of squared distances) goes to bpart[tile].  FP32 partial
-// sums of at most 32 terms are flushed into FP64 accumulators.  Tiles whose
-// request wants the other precision are left to the other launch.
-template <int LK, int DP, typename T>
-__global__ void __launch_bounds__(BIG_TPB) k_big_eval(State s, int r0, int m) {
-  constexpr bool EXACT = sizeof(T) == 8;
-  __shared__ T sh[BIG_TPB * DP];
-  __shared__ double red[BIG_TPB / 32];
-  const T *P = EXACT ? (const T *)s.p64[s.cur] : (const T *)s.p32[s.cur];
-  const int total = s.btile[m];
-  for (int tile = blockIdx.x; tile < total; tile += gridDim.x) {
-    int lo = 0, hi = m;  // request with btile[lo] <= tile < btile[lo + 1]
-    while (hi - lo > 1) {
-      const int mid = (lo + hi) >> 1;
-      if (s.btile[mid] <= tile) lo = mid; else hi = mid;
+// per-kind request lists and tile prefixes of the batch (one block of
+// BIG_BATCH threads); dropped duplicates (na = 0) get no tiles
+__global__ void k_big_tiles(State s, int r0, int m) {
+  __shared__ int ws[BIG_BATCH / 32];
+  const int t = threadIdx.x;
+  int kind = -1, tiles = 0;
+  if (t < m && s.breq_na[r0 + t] > 0) {
+    const int nL = max(s.breq_na[r0 + t], s.breq_nb[r0 + t]);
+    const int nS = min(s.breq_na[r0 + t], s.breq_nb[r0 + t]);
+    kind = bk_kind(nL, s.breq_exact[r0 + t] != 0, s.d);
+    const int w = bk_width(kind, s.d), c = bk_chunk(kind, nL, nS, s.d);
+    tiles = ((nL + w - 1) / w) * ((nS + c - 1) / c);
+  }
+  int base = 0, start = 0;
+  for (int k = 0; k < BK_KINDS; ++k) {
+    const int mine = kind == k;
+    const int rank = block_incl_scan_big(mine, ws) - mine;
+    const int nk = ws[BIG_BATCH / 32 - 1];
+    const int v = mine ? tiles : 0;
+    const int pre = block_incl_scan_big(v, ws) - v;
+    const int tk = ws[BIG_BATCH / 32 - 1];
+    int *req = bs_req(s, k), *pr = bs_pre(s, k);
+    if (mine) {
+      req[rank] = t;
+      pr[rank] = pre;
+      start = base + pre;
     }
-    const int r = r0 + lo;
-    if ((s.breq_exact[r] != 0) != EXACT) continue;  // uniform over the CTA
+    if (t == 0) {
+      pr[nk] = tk;
+      s.bsched[BS_META + 3 * k] = nk;
+      s.bsched[BS_META + 3 * k + 1] = tk;
+      s.bsched[BS_META + 3 * k + 2] = 0;
+    }
+    base += tk;
+    __syncthreads();
+  }
+  if (t < m) {
+    s.bsched[t] = kind >= 0 ? start : 0;
+    s.bsched[BS_B + t] = tiles;
+  }
+}
+
+// tile `tile` of kind k: the request (index within the batch) and the
+// tile's position inside it
+__device__ __forceinline__ int bk_find(const State &s, int k, int tile, int &q0) {
+  const int n = s.bsched[BS_META + 3 * k];
+  const int *pr = bs_pre(s, k);
+  int lo = 0, hi = n;
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (pr[mid] <= tile) lo = mid;
+    else hi = mid;
+  }
+  q0 = tile - pr[lo];
+  return bs_req(s, k)[lo];
+}
+
+// the next tile of kind k for this CTA (dynamic: CTAs that finish early take
+// more), or -1 when none is left
+__device__ __forceinline__ int bk_next(const State &s, int k, int *sh_tile) {
+  if (threadIdx.x == 0) {
+    const int t = atomicAdd(&s.bsched[BS_META + 3 * k + 2], 1);
+    *sh_tile = t < s.bsched[BS_META + 3 * k + 1] ? t : -1;
+  }
+  __syncthreads();
+  const int t = *sh_tile;
+  return t;
+}
+
+// block reduction of the tile's partial in a fixed order (deterministic)
+template <int LK>
+__device__ __forceinline__ void bk_store(const State &s, double v, double *red, int slot) {
+  for (int o = 16; o; o >>= 1) {
+    const double u = __shfl_xor_sync(0xffffffffu, v, o);
+    v = LK == 0 ? fmax(v, u) : v + u;
+  }
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = red[0];
+    for (int w = 1; w < BIG_TPB / 32; ++w) t = LK == 0 ? fmax(t, red[w]) : t + red[w];
+    s.bpart[slot] = t;
+  }
+}
+
+// FP64 tiles (kind 2): 512 points of the larger cluster (two per thread)
+// against the smaller one staged through shared memory.
+template <int LK, int DP>
+__global__ void __launch_bounds__(BIG_TPB) k_big_eval64(State s, int r0) {
+  __shared__ double sh[BIG_TPB * DP];
+  __shared__ double red[BIG_TPB / 32];
+  __shared__ int sh_tile;
+  const double *P = s.p64[s.cur];
+  const int base = s.bsched[BS_META + 1] + s.bsched[BS_META + 3 + 1];  // after kinds 0, 1
+  for (;;) {
+    const int tile = bk_next(s, 2, &sh_tile);
+    if (tile < 0) break;
+    int q0;
+    const int r = r0 + bk_find(s, 2, tile, q0);
     int sL = s.breq_sa[r], nL = s.breq_na[r], sS = s.breq_sb[r], nS = s.breq_nb[r];
     if (nS > nL) {
       int t0 = sL; sL = sS; sS = t0;
       t0 = nL; nL = nS; nS = t0;
     }
-    const int sch = big_chunk(nL, nS, true);
+    const int sch = bk_chunk(2, nL, nS, s.d);
     const int ts = (nS + sch - 1) / sch;  // chunks of the smaller cluster
-    const int q = tile - s.btile[lo];
-    const int sc0 = (q % ts) * sch, sc1 = min(nS, sc0 + sch);
-    const int l0 = (q / ts) * BIG_TILE + threadIdx.x, l1 = l0 + BIG_TPB;
+    const int sc0 = (q0 % ts) * sch, sc1 = min(nS, sc0 + sch);
+    const int l0 = (q0 / ts) * BIG_TILE + threadIdx.x, l1 = l0 + BIG_TPB;
     const bool v0 = l0 < nL, v1 = l1 < nL;
-    T x0[DP], x1[DP];
+    double x0[DP], x1[DP];
 #pragma unroll
     for (int k = 0; k < DP; ++k) {
-      x0[k] = v0 ? P[(size_t)(sL + l0) * DP + k] : (T)0;
-      x1[k] = v1 ? P[(size_t)(sL + l1) * DP + k] : (T)0;
+      x0[k] = v0 ? P[(size_t)(sL + l0) * DP + k] : 0.0;
+      x1[k] = v1 ? P[(size_t)(sL + l1) * DP + k] : 0.0;
     }
-    double acc = 0.0;
-    T macc = 0;
+    double acc = 0.0, macc = 0.0;
     for (int c0 = sc0; c0 < sc1; c0 += BIG_TPB) {
       const int cn = min(BIG_TPB, sc1 - c0);
       __syncthreads();
       for (int i = threadIdx.x; i < cn * DP; i += BIG_TPB) sh[i] = P[(size_t)(sS + c0) * DP + i];
       __syncthreads();
-      T part = 0;
-      int cnt = 0;
       for (int j = 0; j < cn; ++j) {
-        T d0 = 0, d1 = 0;
+        double d0 = 0, d1 = 0;
 #pragma unroll
         for (int k = 0; k < DP; ++k) {
-          const T y = sh[j * DP + k];
-          const T t0 = x0[k] - y, t1 = x1[k] - y;
+          const double y = sh[j * DP + k];
+          const double t0 = x0[k] - y, t1 = x1[k] - y;
           d0 = d0 + t0 * t0;
           d1 = d1 + t1 * t1;
         }
         if (LK == 0) {
-          if (v0) macc = d0 > macc ? d0 : macc;
-          if (v1) macc = d1 > macc ? d1 : macc;
+          if (v0) macc = fmax(macc, d0);
+          if (v1) macc = fmax(macc, d1);
         } else {
-          const T s0 = v0 ? (EXACT ? (T)sqrt((double)d0) : (T)sqrtf((float)d0)) : (T)0;
-          const T s1 = v1 ? (EXACT ? (T)sqrt((double)d1) : (T)sqrtf((float)d1)) : (T)0;
-          part += s0 + s1;
-          if (!EXACT && ++cnt == 16) {  // at most 32 terms per FP32 partial
-            acc += (double)part;
-            part = 0;
-            cnt = 0;
-          }
+          acc += (v0 ? sqrt(d0) : 0.0) + (v1 ? sqrt(d1) : 0.0);
         }
       }
-      if (LK != 0) acc += (double)part;
     }
-    // block reduction in a fixed order (deterministic)
-    double v = LK == 0 ? (double)macc : acc;
-    for (int o = 16; o; o >>= 1) {
-      const double u = __shfl_xor_sync(0xffffffffu, v, o);
-      v = LK == 0 ? fmax(v, u) : v + u;
-    }
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      double t = red[0];
-      for (int w = 1; w < BIG_TPB / 32; ++w) t = LK == 0 ? fmax(t, red[w]) : t + red[w];
-      s.bpart[tile] = t;
-    }
+    bk_store<LK>(s, LK == 0 ? macc : acc, red, base + tile);
   }
 }
 
 // FP32 tiles, specialised on the true dimension D (rows have stride DP):
-// 1024 points of the larger cluster per CTA (four per thread) against the
-// smaller cluster staged through shared memory 256 points at a time.  Square
+// PPT points of the larger cluster per thread, packed in pairs so that every
+// subtract and multiply-add is one f32x2 instruction for two point pairs;
+// the smaller cluster is staged through shared memory 256 points at a time,
+// each coordinate duplicated into both halves of a 64-bit word.  Square
 // roots use the hardware approximation (sqrt.approx.f32); with it a term's
 // relative error stays within ((D+1)/2 + 4)u <= (D+16)u, the bound the search
-// states for FP32 distances.
+// states for FP32 distances.  Packed operations round each half as the scalar
+// instruction would.
 __device__ __forceinline__ float sqrt_approx(float x) {
   float r;
   asm("sqrt.approx.f32 %0, %1;" : "=f"(r) : "f"(x));
   return r;
 }
+__device__ __forceinline__ unsigned long long f2_pack(float a, float b) {
+  unsigned long long r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+  return r;
+}
+__device__ __forceinline__ void f2_unpack(unsigned long long v, float &a, float &b) {
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v));
+}
+__device__ __forceinline__ unsigned long long f2_sub(unsigned long long a, unsigned long long b) {
+  unsigned long long r;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+  return r;
+}
+__device__ __forceinline__ unsigned long long f2_mul(unsigned long long a, unsigned long long b) {
+  unsigned long long r;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+  return r;
+}
+__device__ __forceinline__ unsigned long long f2_fma(unsigned long long a, unsigned long long b,
+                                                     unsigned long long c) {
+  unsigned long long r;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
+  return r;
+}
+__device__ __forceinline__ unsigned long long f2_add(unsigned long long a, unsigned long long b) {
+  unsigned long long r;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+  return r;
+}
 
-// One staged chunk of the smaller cluster against a thread's four points.
-// Average: FP32 partials of 16 terms (4 staged points x 4) are summed in FP32
-// in groups of 16 before each FP64 add (relative error <= 30u per FP64 add).
-template <int LK, int D, bool FULL>
-__device__ __forceinline__ void big32_chunk(const float *sh, int cn, const float (&x)[B32_PPT][D],
-                                            const bool (&v)[B32_PPT], double &acc, float &macc) {
-  float part2 = 0.f;
+// One staged chunk of the smaller cluster against a thread's NP point pairs.
+// Average: each half of `part` takes 4 x NP terms per group of 4 staged
+// points (at most 16); 16 groups are summed in FP32 before each FP64 add
+// (relative error <= 30u per FP64 add, as before packing).
+template <int LK, int D, int NP, bool FULL>
+__device__ __forceinline__ void big32_chunk(const unsigned long long *sh, int cn,
+                                            const unsigned long long (&x)[NP][D],
+                                            const bool (&v)[2 * NP], double &acc, float &macc) {
+  unsigned long long part2 = 0ull;  // (0.f, 0.f)
   int groups = 0;
   for (int j0 = 0; j0 < cn; j0 += 4) {
     const int jn = min(4, cn - j0);
-    float part = 0.f;
+    unsigned long long part = 0ull;
 #pragma unroll
     for (int jj = 0; jj < 4; ++jj) {
       if (jj < jn) {
-        const float *y = sh + (j0 + jj) * D;
+        const unsigned long long *y = sh + (j0 + jj) * D;
+        unsigned long long yk[D];
 #pragma unroll
-        for (int p = 0; p < B32_PPT; ++p) {
-          float d2 = 0.f;
+        for (int k = 0; k < D; ++k) yk[k] = y[k];
 #pragma unroll
-          for (int k = 0; k < D; ++k) {
-            const float t = x[p][k] - y[k];
-            d2 = fmaf(t, t, d2);
+        for (int q = 0; q < NP; ++q) {
+          unsigned long long t = f2_sub(x[q][0], yk[0]);
+          unsigned long long d2 = f2_mul(t, t);
+#pragma unroll
+          for (int k = 1; k < D; ++k) {
+            t = f2_sub(x[q][k], yk[k]);
+            d2 = f2_fma(t, t, d2);
           }
-          if (LK == 0)
-            macc = (FULL || v[p]) ? fmaxf(macc, d2) : macc;
-          else
-            part += (FULL || v[p]) ? sqrt_approx(d2) : 0.f;
+          float a, b;
+          f2_unpack(d2, a, b);
+          if (LK == 0) {
+            macc = fmaxf(macc, (FULL || v[2 * q]) ? a : 0.f);
+            macc = fmaxf(macc, (FULL || v[2 * q + 1]) ? b : 0.f);
+          } else {
+            const float ra = (FULL || v[2 * q]) ? sqrt_approx(a) : 0.f;
+            const float rb = (FULL || v[2 * q + 1]) ? sqrt_approx(b) : 0.f;
+            part = f2_add(part, f2_pack(ra, rb));
+          }
         }
       }
     }
     if (LK != 0) {
-      part2 += part;
+      part2 = f2_add(part2, part);
       if (++groups == 16) {
-        acc += (double)part2;
-        part2 = 0.f;
+        float a, b;
+        f2_unpack(part2, a, b);
+        acc += (double)a + (double)b;
+        part2 = 0ull;
         groups = 0;
       }
     }
   }
-  if (LK != 0) acc += (double)part2;
+  if (LK != 0) {
+    float a, b;
+    f2_unpack(part2, a, b);
+    acc += (double)a + (double)b;
+  }
 }
 
-template <int LK, int D, int DP>
-__global__ void __launch_bounds__(BIG_TPB) k_big_eval32(State s, int r0, int m) {
-  __shared__ float sh[BIG_TPB * D];
+template <int LK, int D, int DP, int KIND>
+__global__ void __launch_bounds__(BIG_TPB) k_big_eval32(State s, int r0) {
+  constexpr int PPT = KIND == 0 ? (D <= 8 ? 8 : 4) : 2, NP = PPT / 2;
+  __shared__ unsigned long long sh[BIG_TPB * D];
   __shared__ double red[BIG_TPB / 32];
+  __shared__ int sh_tile;
   const float *P = s.p32[s.cur];
-  const int total = s.btile[m];
-  for (int tile = blockIdx.x; tile < total; tile += gridDim.x) {
-    int lo = 0, hi = m;  // request with btile[lo] <= tile < btile[lo + 1]
-    while (hi - lo > 1) {
-      const int mid = (lo + hi) >> 1;
-      if (s.btile[mid] <= tile) lo = mid; else hi = mid;
-    }
-    const int r = r0 + lo;
-    if (s.breq_exact[r] != 0) continue;  // FP64 requests: k_big_eval<..., double>
+  const int base = KIND == 0 ? 0 : s.bsched[BS_META + 1];  // kind 1 tiles follow kind 0's
+  for (;;) {
+    const int tile = bk_next(s, KIND, &sh_tile);
+    if (tile < 0) break;
+    int q0;
+    const int r = r0 + bk_find(s, KIND, tile, q0);
     int sL = s.breq_sa[r], nL = s.breq_na[r], sS = s.breq_sb[r], nS = s.breq_nb[r];
     if (nS > nL) {
       int t0 = sL; sL = sS; sS = t0;
       t0 = nL; nL = nS; nS = t0;
     }
-    const int sch = big_chunk(nL, nS, false);
+    const int sch = bk_chunk(KIND, nL, nS, D);
     const int ts = (nS + sch - 1) / sch;  // chunks of the smaller cluster
-    const int q0 = tile - s.btile[lo];
     const int sc0 = (q0 % ts) * sch, sc1 = min(nS, sc0 + sch);
     const int q = q0 / ts;
-    float x[B32_PPT][D];
-    bool v[B32_PPT];
+    unsigned long long x[NP][D];
+    bool v[PPT];
 #pragma unroll
-    for (int p = 0; p < B32_PPT; ++p) {
-      const int l = q * B32_TILE + p * BIG_TPB + threadIdx.x;
-      v[p] = l < nL;
+    for (int p = 0; p < PPT; ++p) v[p] = q * (BIG_TPB * PPT) + p * BIG_TPB + (int)threadIdx.x < nL;
 #pragma unroll
-      for (int k = 0; k < D; ++k) x[p][k] = v[p] ? P[(size_t)(sL + l) * DP + k] : 0.f;
+    for (int h = 0; h < NP; ++h) {
+      const int l0 = q * (BIG_TPB * PPT) + (2 * h) * BIG_TPB + threadIdx.x;
+      const int l1 = l0 + BIG_TPB;
+#pragma unroll
+      for (int k = 0; k < D; ++k)
+        x[h][k] = f2_pack(v[2 * h] ? P[(size_t)(sL + l0) * DP + k] : 0.f,
+                          v[2 * h + 1] ? P[(size_t)(sL + l1) * DP + k] : 0.f);
     }
     double acc = 0.0;
     float macc = 0.f;
-    const bool full = v[B32_PPT - 1];  // all four points valid: no selects
+    const bool full = v[PPT - 1];  // all points valid: no selects
     for (int c0 = sc0; c0 < sc1; c0 += BIG_TPB) {
       const int cn = min(BIG_TPB, sc1 - c0);
       __syncthreads();
       for (int i = threadIdx.x; i < cn * D; i += BIG_TPB) {
         const int j = i / D, k = i - j * D;
-        sh[i] = P[(size_t)(sS + c0 + j) * DP + k];
+        const float y = P[(size_t)(sS + c0 + j) * DP + k];
+        sh[i] = f2_pack(y, y);
       }
       __syncthreads();
       if (full)
-        big32_chunk<LK, D, true>(sh, cn, x, v, acc, macc);
+        big32_chunk<LK, D, NP, true>(sh, cn, x, v, acc, macc);
       else
-        big32_chunk<LK, D, false>(sh, cn, x, v, acc, macc);
+        big32_chunk<LK, D, NP, false>(sh, cn, x, v, acc, macc);
     }
-    double val = LK == 0 ? (double)macc : acc;
-    for (int o = 16; o; o >>= 1) {
-      const double u = __shfl_xor_sync(0xffffffffu, val, o);
-      val = LK == 0 ? fmax(val, u) : val + u;
-    }
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = val;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      double t = red[0];
-      for (int w = 1; w < BIG_TPB / 32; ++w) t = LK == 0 ? fmax(t, red[w]) : t + red[w];
-      s.bpart[tile] = t;
-    }
+    bk_store<LK>(s, LK == 0 ? (double)macc : acc, red, base + tile);
   }
 }
 
@@ -984,26 +1100,58 @@ __global__ void k_big_dedup(State s, int r0, int m) {
   }
 }
 
-// insert that may evict: a big pair's value must land in both tables
-// (if a concurrent writer holds the home slot the value is dropped; the
-// re-run search then asks for it again or evaluates it itself)
+// Insert that may evict: a big pair's value must land in both tables, since
+// the re-run search reads it there.  A free or stale slot is taken if there
+// is one; otherwise the live entry with the largest distance (the neighbour
+// least likely to be anyone's nearest) makes room.  Slots claimed by
+// concurrent writers are skipped; after a few lost races the value is dropped
+// (the re-run search then asks for it again or evaluates it itself).
 __device__ void cache_insert_evict(const State &s, int owner, int nbr, int nbr_gen, double v,
                                    float e) {
   const int S = s.cache_slots;
   const unsigned long long want = ckey_of(nbr, nbr_gen);
   const size_t base = (size_t)owner * S;
-  const int t0 = (int)(((unsigned)nbr * 2654435761u) % (unsigned)S);
-  for (int q = 0; q < S; ++q) {
-    const int t = (t0 + q) % S;
-    for (;;) {
+  for (int attempt = 0; attempt < 4; ++attempt) {
+    int victim = -1;
+    double vmax = -1.0;
+    unsigned long long vkey = 0;
+    for (int t = 0; t < S; ++t) {
       const unsigned long long cur = slot_key(s, base + t);
       if (cur == want) return;
-      if (!slot_free(s, cur)) break;
-      if (slot_put(s, base + t, cur, want, v, e)) return;
+      if (slot_free(s, cur)) {
+        if (slot_put(s, base + t, cur, want, v, e)) return;
+        continue;
+      }
+      if (cur == CKEY_BUSY) continue;
+      const double cv = *(volatile double *)&s.cval[base + t];
+      if (cv > vmax) {
+        vmax = cv;
+        victim = t;
+        vkey = cur;
+      }
     }
+    if (victim < 0) return;
+    if (slot_put(s, base + victim, vkey, want, v, e)) return;
   }
-  const unsigned long long cur = slot_key(s, base + t0);  // full of live entries
-  if (cur != CKEY_BUSY && cur != want) slot_put(s, base + t0, cur, want, v, e);
+}
+
+// this round's result table: a slot is claimed by CAS to BUSY, filled, then
+// published (readers run in later kernels); a result that finds no slot
+// within SIDE_PROBES is dropped (the re-run search asks again)
+__device__ void side_put(const State &s, int lo, int hi, double v, float e) {
+  const unsigned long long want = ((unsigned long long)(unsigned)lo << 32) | (unsigned)hi;
+  unsigned h = side_hash(lo, hi, s.side_cap);
+  for (int q = 0; q < SIDE_PROBES; ++q, h = (h + 1) & (unsigned)(s.side_cap - 1)) {
+    const unsigned long long cur = *(volatile unsigned long long *)&s.side_key[h];
+    if (cur == want) return;
+    if (cur != CKEY_EMPTY) continue;
+    if (atomicCAS(&s.side_key[h], CKEY_EMPTY, CKEY_BUSY) != CKEY_EMPTY) continue;
+    s.side_val[h] = v;
+    s.side_err[h] = e;
+    __threadfence();
+    atomicExch(&s.side_key[h], want);
+    return;
+  }
 }
 
 // one warp per request: fold its tiles in order, cache the distance
@@ -1013,7 +1161,7 @@ __global__ void k_big_final(State s, int r0, int m) {
   for (int q = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; q < m; q += warps) {
     const int r = r0 + q;
     if (s.breq_na[r] == 0) continue;  // duplicate dropped by k_big_dedup
-    const int t0 = s.btile[q], t1 = s.btile[q + 1];
+    const int t0 = s.bsched[q], t1 = t0 + s.bsched[BS_B + q];
     double v = 0.0;
     for (int t = t0 + lane; t < t1; t += 32) v = s.linkage == 0 ? fmax(v, s.bpart[t]) : v + s.bpart[t];
     for (int o = 16; o; o >>= 1) {
@@ -1031,6 +1179,7 @@ __global__ void k_big_final(State s, int r0, int m) {
 : fmaxf(s.idpts[s.inst[i]], EST_MARK);
       cache_insert_evict(s, i, j, s.gen[j], D, e);
       cache_insert_evict(s, j, i, s.gen[i], D, e);
+      side_put(s, min(i, j), max(i, j), D, e);
     }
   }
 }
@@ -1096,6 +1245,23 @@ __global__ void k_cmp_top(State s, int nb) {
   }
 }
 
+// Variance of cluster c (mean squared distance of its points to the
+// centroid) from the FP64 sums, rounded up with a margin that covers the
+// worst-case rounding of sums of sz terms: an upper bound for the search.
+__device__ float cluster_var_up(const State &s, int c, int sz) {
+  const int dp = s.dp;
+  const double inv = 1.0 / (double)sz;
+  double c2 = 0.0;
+  for (int k = 0; k < dp; ++k) {
+    const double m = s.csum[(size_t)c * dp + k] * inv;
+    c2 += m * m;
+  }
+  const double M = (double)s.iscale[s.inst[c]];
+  const double v = fmax(s.csq[c] * inv - c2, 0.0);
+  const double margin = ldexp((double)sz * s.d * M * M, -50);
+  return __double2float_ru(v + margin);
+}
+
 __global__ void k_cmp_write(State s, const int32_t *order, int32_t *order_out, int32_t *seg_out,
                             int K, int round) {
   const int p = blockIdx.x * TPB + threadIdx.x;
@@ -1126,6 +1292,7 @@ __global__ void k_cmp_write(State s, const int32_t *order, int32_t *order_out, i
     }
     s.qsz[ok] = sz;
     s.qseg[ok] = os;
+    s.qvar[ok] = sz > 1 ? cluster_var_up(s, c, sz) : 0.f;
     s.qinst[ok] = s.iseq[s.inst[c]];
     if (ist) {
       s.term[ot] = c;
@@ -1214,6 +1381,7 @@ struct hac_ctx {
   // pairs of at least this many point pairs go to the GPU-wide evaluation
   // (FP32 / FP64 values); HAC_BIG_PAIRS / HAC_BIG_PAIRS_F64 override them
   long long big_pairs = BIG_PAIRS, big_pairs64 = BIG_PAIRS_F64;
+  long long warp_budget = WARP_BUDGET;  // HAC_WARP_BUDGET overrides it
   int64_t launches = 0;  // kernels launched in the current run
   int ocur = 0, pcur = 0;
   bool done = false;
@@ -1272,6 +1440,8 @@ int alloc_state(hac_ctx *h) {
   A(s.qsz, n);
   A(s.qseg, n);
   A(s.csum, n * dp);
+  A(s.csq, n);
+  A(s.qvar, n);
   A(s.cent, n * dp);
   A(s.cent32, n * dp);
   A(s.blo, n * dp);
@@ -1354,47 +1524,68 @@ int grid_for(int64_t work, int tpb) {
   return (int)g;
 }
 
+// CTAs that stay resident together: one wave, tiles handed out dynamically
+template <typename F>
+int resident_grid(F kernel) {
+  int dev = 0, sms = 0, per = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kernel, BIG_TPB, 0) != cudaSuccess) {
+    cudaGetLastError();
+    return 152 * 4;
+  }
+  return std::max(1, sms) * std::max(1, per);
+}
+
 template <int LK, int D>
-void launch_big32(const State &s, int r0, int m, cudaStream_t st) {
+void launch_big32(const State &s, int r0, cudaStream_t st) {
   constexpr int DP = D <= 2 ? 2 : D <= 4 ? 4 : D <= 8 ? 8 : 16;
-  k_big_eval32<LK, D, DP><<<152 * 8, BIG_TPB, 0, st>>>(s, r0, m);
+  static const int g0 = resident_grid(k_big_eval32<LK, D, DP, 0>);
+  static const int g1 = resident_grid(k_big_eval32<LK, D, DP, 1>);
+  k_big_eval32<LK, D, DP, 0><<<g0, BIG_TPB, 0, st>>>(s, r0);
+  k_big_eval32<LK, D, DP, 1><<<g1, BIG_TPB, 0, st>>>(s, r0);
+}
+
+template <int LK, int DP>
+void launch_big64(const State &s, int r0, cudaStream_t st) {
+  static const int g = resident_grid(k_big_eval64<LK, DP>);
+  k_big_eval64<LK, DP><<<g, BIG_TPB, 0, st>>>(s, r0);
 }
 
 template <int LK>
-int launch_big_lk(const State &s, int r0, int m, cudaStream_t st) {
-  const int g = 152 * 8;
+int launch_big_lk(const State &s, int r0, cudaStream_t st) {
   switch (s.d) {  // FP32 requests, specialised on the true dimension
-    case 1: launch_big32<LK, 1>(s, r0, m, st); break;
-    case 2: launch_big32<LK, 2>(s, r0, m, st); break;
-    case 3: launch_big32<LK, 3>(s, r0, m, st); break;
-    case 4: launch_big32<LK, 4>(s, r0, m, st); break;
-    case 5: launch_big32<LK, 5>(s, r0, m, st); break;
-    case 6: launch_big32<LK, 6>(s, r0, m, st); break;
-    case 7: launch_big32<LK, 7>(s, r0, m, st); break;
-    case 8: launch_big32<LK, 8>(s, r0, m, st); break;
-    case 9: launch_big32<LK, 9>(s, r0, m, st); break;
-    case 10: launch_big32<LK, 10>(s, r0, m, st); break;
-    case 11: launch_big32<LK, 11>(s, r0, m, st); break;
-    case 12: launch_big32<LK, 12>(s, r0, m, st); break;
-    case 13: launch_big32<LK, 13>(s, r0, m, st); break;
-    case 14: launch_big32<LK, 14>(s, r0, m, st); break;
-    case 15: launch_big32<LK, 15>(s, r0, m, st); break;
-    case 16: launch_big32<LK, 16>(s, r0, m, st); break;
+    case 1: launch_big32<LK, 1>(s, r0, st); break;
+    case 2: launch_big32<LK, 2>(s, r0, st); break;
+    case 3: launch_big32<LK, 3>(s, r0, st); break;
+    case 4: launch_big32<LK, 4>(s, r0, st); break;
+    case 5: launch_big32<LK, 5>(s, r0, st); break;
+    case 6: launch_big32<LK, 6>(s, r0, st); break;
+    case 7: launch_big32<LK, 7>(s, r0, st); break;
+    case 8: launch_big32<LK, 8>(s, r0, st); break;
+    case 9: launch_big32<LK, 9>(s, r0, st); break;
+    case 10: launch_big32<LK, 10>(s, r0, st); break;
+    case 11: launch_big32<LK, 11>(s, r0, st); break;
+    case 12: launch_big32<LK, 12>(s, r0, st); break;
+    case 13: launch_big32<LK, 13>(s, r0, st); break;
+    case 14: launch_big32<LK, 14>(s, r0, st); break;
+    case 15: launch_big32<LK, 15>(s, r0, st); break;
+    case 16: launch_big32<LK, 16>(s, r0, st); break;
     default: return HAC_EINTERNAL;
   }
   switch (s.dp) {  // FP64 requests
-    case 2: k_big_eval<LK, 2, double><<<g, BIG_TPB, 0, st>>>(s, r0, m); break;
-    case 4: k_big_eval<LK, 4, double><<<g, BIG_TPB, 0, st>>>(s, r0, m); break;
-    case 8: k_big_eval<LK, 8, double><<<g, BIG_TPB, 0, st>>>(s, r0, m); break;
-    case 16: k_big_eval<LK, 16, double><<<g, BIG_TPB, 0, st>>>(s, r0, m); break;
+    case 2: launch_big64<LK, 2>(s, r0, st); break;
+    case 4: launch_big64<LK, 4>(s, r0, st); break;
+    case 8: launch_big64<LK, 8>(s, r0, st); break;
+    case 16: launch_big64<LK, 16>(s, r0, st); break;
     default: return HAC_EINTERNAL;
   }
   CK(cudaGetLastError());
   return HAC_OK;
 }
 
-int launch_big(const State &s, int r0, int m, cudaStream_t st) {
-  return s.linkage == 0 ? launch_big_lk<0>(s, r0, m, st) : launch_big_lk<1>(s, r0, m, st);
+int launch_big(const State &s, int r0, cudaStream_t st) {
+  return s.linkage == 0 ? launch_big_lk<0>(s, r0, st) : launch_big_lk<1>(s, r0, st);
 }
 
 template <int DP>
@@ -1532,6 +1723,7 @@ int create_common(const void *pts, bool dev, int64_t n, int d, hac_dtype dt, hac
   h->s.pts32_exact = dt == HAC_F32;
   if (const char *e = getenv("HAC_BIG_PAIRS")) h->big_pairs = std::max(1ll, atoll(e));
   if (const char *e = getenv("HAC_BIG_PAIRS_F64")) h->big_pairs64 = std::max(1ll, atoll(e));
+  if (const char *e = getenv("HAC_WARP_BUDGET")) h->warp_budget = std::max(1ll, atoll(e));
   if (cudaStreamCreateWithFlags(&h->own, cudaStreamNonBlocking) != cudaSuccess) {
     cudaGetLastError();
     delete h;
@@ -1608,6 +1800,7 @@ void fill_query_args(hac_ctx *h, QueryArgs &qa, int round, int K, int nterm) {
   qa.qbhi = s.qbhi;
   qa.qsz = s.qsz;
   qa.qseg = s.qseg;
+  qa.qvar = s.qvar;
   qa.nclo = s.nclo;
   qa.nchi = s.nchi;
   qa.nhmin = s.nhmin;
@@ -1637,6 +1830,11 @@ void fill_query_args(hac_ctx *h, QueryArgs &qa, int round, int K, int nterm) {
   qa.defer = s.cache_slots > 0 && s.linkage != LK_WARD ? 1 : 0;
   qa.big_pairs = h->big_pairs;
   qa.big_pairs64 = h->big_pairs64;
+  qa.warp_budget = h->warp_budget;
+  qa.side_cap = s.side_cap;
+  qa.side_key = s.side_key;
+  qa.side_val = s.side_val;
+  qa.side_err = s.side_err;
   qa.breq_cap = s.breq_cap;
   qa.breq_i = s.breq_i;
   qa.breq_j = s.breq_j;
@@ -1667,6 +1865,8 @@ int round_step(hac_ctx *h, cudaStream_t st, int round, int K, int nterm, RoundCt
   QueryArgs qa{};
   fill_query_args(h, qa, round, K, nterm);
   const bool defer = qa.defer != 0;
+  if (defer)
+    CK(cudaMemsetAsync(s.side_key, 0xff, (size_t)s.side_cap * sizeof(unsigned long long), st));
   EVREC(ctl.eq0);
   CK(launch_query(qa, s.dp, s.prec, st));
   EVREC(ctl.eq1);
@@ -1699,7 +1899,7 @@ int round_step(hac_ctx *h, cudaStream_t st, int round, int K, int nterm, RoundCt
       k_big_dedup<<<1, BIG_BATCH, 0, st>>>(s, r0, m);
       k_big_tiles<<<1, BIG_BATCH, 0, st>>>(s, r0, m);
       EVREC(ctl.eb0);
-      rc = launch_big(s, r0, m, st);
+      rc = launch_big(s, r0, st);
       EVREC(ctl.eb1);
       if (rc) return rc;
       ctl.big_launch += 2;
@@ -1710,7 +1910,7 @@ int round_step(hac_ctx *h, cudaStream_t st, int round, int K, int nterm, RoundCt
         ctl.ms_big += bms;
       }
       k_big_final<<<cdiv(m, 8), 256, 0, st>>>(s, r0, m);
-      h->launches += 5;
+      h->launches += 6;
     }
     CK(cudaMemsetAsync(&s.ctr->nbreq, 0, 2 * sizeof(int32_t), st));
     ctl.searches += npend;
@@ -1798,11 +1998,13 @@ int run_impl(hac_ctx *h, const hac_opts *o) {
       if ((rc0 = dalloc(h, &s.breq_i, bcap)) || (rc0 = dalloc(h, &s.breq_j, bcap)) ||
           (rc0 = dalloc(h, &s.breq_sa, bcap)) || (rc0 = dalloc(h, &s.breq_na, bcap)) ||
           (rc0 = dalloc(h, &s.breq_sb, bcap)) || (rc0 = dalloc(h, &s.breq_nb, bcap)) ||
-          (rc0 = dalloc(h, &s.breq_exact, bcap)) || (rc0 = dalloc(h, &s.btile, BIG_BATCH + 1)) ||
+          (rc0 = dalloc(h, &s.breq_exact, bcap)) || (rc0 = dalloc(h, &s.bsched, BS_SIZE)) ||
           (rc0 = dalloc(h, &s.bpart, tiles)) || (rc0 = dalloc(h, &s.pend[0], h->n)) ||
-          (rc0 = dalloc(h, &s.pend[1], h->n)))
+          (rc0 = dalloc(h, &s.pend[1], h->n)) || (rc0 = dalloc(h, &s.side_key, 2 * bcap)) ||
+          (rc0 = dalloc(h, &s.side_val, 2 * bcap)) || (rc0 = dalloc(h, &s.side_err, 2 * bcap)))
         return rc0;
       s.breq_cap = bcap;
+      s.side_cap = 2 * bcap;
     }
     h->cache_alloc_slots = slots;
   }
@@ -2144,6 +2346,8 @@ bool carve_state(hac_ctx &h, Carver &cv) {
   cv.take(&s.qsz, n);
   cv.take(&s.qseg, n);
   cv.take(&s.csum, n * dp);
+  cv.take(&s.csq, n);
+  cv.take(&s.qvar, n);
   cv.take(&s.cent, n * dp);
   cv.take(&s.cent32, n * dp);
   cv.take(&s.blo, n * dp);
@@ -2484,6 +2688,13 @@ __global__ void k_admit_layout(State s, const T *stage, int m, const AdmitInst *
       s.qblo[(size_t)op * dp + k] = __double2float_rd(x);
       s.qbhi[(size_t)op * dp + k] = __double2float_ru(x);
     }
+    double sq = 0.0;
+    for (int k = 0; k < d; ++k) {
+      const double x = (double)stage[(size_t)i * d + k] - a.ctr[k];
+      sq += x * x;
+    }
+    s.csq[c] = sq;
+    s.qvar[op] = 0.f;
     s.plab[pc][pp] = c;
     s.seg[pc][c] = (int32_t)pp;
     s.csize[c] = 1;
@@ -2618,6 +2829,7 @@ int engine_init(Engine &e, hac_linkage lk, int d, hac_dtype dt, int64_t cap, con
   s.max_inst = SRV_MAX_INST;
   if (const char *v = getenv("HAC_BIG_PAIRS")) h.big_pairs = std::max(1ll, atoll(v));
   if (const char *v = getenv("HAC_BIG_PAIRS_F64")) h.big_pairs64 = std::max(1ll, atoll(v));
+  if (const char *v = getenv("HAC_WARP_BUDGET")) h.warp_budget = std::max(1ll, atoll(v));
   if (cudaStreamCreateWithFlags(&h.own, cudaStreamNonBlocking) != cudaSuccess) {
     cudaGetLastError();
     return HAC_EDEVICE;
@@ -2648,12 +2860,15 @@ int engine_init(Engine &e, hac_linkage lk, int d, hac_dtype dt, int64_t cap, con
         (rc = dalloc(&h, &s.breq_j, bcap)) || (rc = dalloc(&h, &s.breq_sa, bcap)) ||
         (rc = dalloc(&h, &s.breq_na, bcap)) || (rc = dalloc(&h, &s.breq_sb, bcap)) ||
         (rc = dalloc(&h, &s.breq_nb, bcap)) || (rc = dalloc(&h, &s.breq_exact, bcap)) ||
-        (rc = dalloc(&h, &s.btile, BIG_BATCH + 1)) ||
+        (rc = dalloc(&h, &s.bsched, BS_SIZE)) ||
         (rc = dalloc(&h, &s.bpart, (size_t)BIG_BATCH * per)) ||
-        (rc = dalloc(&h, &s.pend[0], cap)) || (rc = dalloc(&h, &s.pend[1], cap)))
+        (rc = dalloc(&h, &s.pend[0], cap)) || (rc = dalloc(&h, &s.pend[1], cap)) ||
+        (rc = dalloc(&h, &s.side_key, 2 * bcap)) || (rc = dalloc(&h, &s.side_val, 2 * bcap)) ||
+        (rc = dalloc(&h, &s.side_err, 2 * bcap)))
       return rc;
     s.ins_cap = (int)icap;
     s.breq_cap = bcap;
+    s.side_cap = 2 * bcap;
     h.cache_alloc_slots = slots;
   }
   s.cache_slots = slots;

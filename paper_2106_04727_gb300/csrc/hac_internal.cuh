@@ -61,6 +61,7 @@ struct State {
   // per-cid cluster state
   int32_t *csize;
   double *csum;         // coordinate sums (FP64), n x dp
+  double *csq;          // sums of squared norms (FP64): the cluster's variance
   double *cent;         // centroids (FP64), n x dp
   float *cent32;        // centroid rounded to FP32, n x dp
   float *blo, *bhi;     // point bounding box, rounded outward to FP32, n x dp
@@ -89,9 +90,15 @@ struct State {
   int breq_cap;
   int32_t *breq_i, *breq_j, *breq_sa, *breq_na, *breq_sb, *breq_nb;
   uint8_t *breq_exact;   // 1 = FP64 value wanted, 0 = FP32 estimate
-  int32_t *btile;        // tile prefix of the current batch
+  int32_t *bsched;       // tile schedule of the current batch (per-kind lists)
   double *bpart;         // per-tile partial results of the current batch
   int32_t *pend[2];      // terminals whose search deferred a pair
+  // this round's big-pair results by unordered cid pair (cleared every round):
+  // the re-run search reads them here even when a cache table had no room
+  int side_cap;          // power of two
+  unsigned long long *side_key;  // lo << 32 | hi, ~0 = empty
+  double *side_val;
+  float *side_err;
   // instances sharing this state (a server engine clusters many at once;
   // hac_run is the one-instance case): instance of each cid / position,
   // tree-node instance ranges, and per-instance parameters and progress
@@ -118,6 +125,7 @@ struct State {
   float *q32, *qblo, *qbhi;  // FP32 centroid and box, K x dp
   double *q64;               // FP64 centroid, K x dp
   int32_t *qsz, *qseg;       // size and segment start
+  float *qvar;               // variance (mean squared distance to the centroid), rounded up
   // lists
   int32_t *order[2];    // active cids in spatial order
   int32_t *term;        // terminal cids
@@ -149,6 +157,7 @@ struct QueryArgs {
   const float *q32, *qblo, *qbhi;
   const double *q64;
   const int32_t *qsz, *qseg;
+  const float *qvar;
   const float *nclo, *nchi, *nhmin, *nlmax;
   const int32_t *nnmin;
   int32_t lvl_base[MAXLEV + 1];
@@ -170,6 +179,11 @@ struct QueryArgs {
   // big-pair deferral (needs the cache): 0 = evaluate big pairs in the warp
   int defer;
   long long big_pairs, big_pairs64;
+  long long warp_budget;  // point pairs a search evaluates itself before deferring more
+  int side_cap;
+  const unsigned long long *side_key;
+  const double *side_val;
+  const float *side_err;
   int breq_cap;
   int32_t *breq_i, *breq_j, *breq_sa, *breq_na, *breq_sb, *breq_nb;
   uint8_t *breq_exact;
@@ -180,6 +194,16 @@ struct QueryArgs {
 constexpr long long BIG_PAIRS = 1ll << 18;
 // FP64 point pairs cost ~64x more on this part: hand them over much earlier
 constexpr long long BIG_PAIRS_F64 = 1ll << 13;
+// point pairs one search evaluates in its own warp before it hands every
+// further pair of at least BIG_MIN_PAIRS to the GPU-wide kernels
+constexpr long long WARP_BUDGET = 1ll << 20;
+constexpr long long BIG_MIN_PAIRS = 1ll << 12;
+constexpr int SIDE_PROBES = 64;
+
+__host__ __device__ inline unsigned side_hash(int lo, int hi, int cap) {
+  return ((unsigned)lo * 2654435761u ^ (unsigned)hi * 0x85EBCA77u) & (unsigned)(cap - 1);
+}
+
 // error term stored with every cached FP32 estimate (0 marks an FP64 value)
 constexpr float EST_MARK = 1e-30f;
 

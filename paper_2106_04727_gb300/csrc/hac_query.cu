@@ -280,12 +280,47 @@ __device__ float eval32_lane(const float *P, int sa, int na, int sb, int nb) {
   return acc / ((float)na * (float)nb);
 }
 
-// Warp-cooperative FP32 evaluation; average flushes FP32 partial sums of at
-// most 32 terms into an FP64 accumulator.  Returns +inf once the partial
-// result's lower bound exceeds `bound` (D units).
-template <int LK, int DP>
-__device__ float eval32_warp(const float *P, int sa, int na, int sb, int nb, float bound,
-                             float delta, float rho, int lane, unsigned long long &pp) {
+// Packed FP32 pairs (f32x2): each half is rounded as the scalar instruction
+// would round it.
+__device__ __forceinline__ unsigned long long f2_sub(unsigned long long a, unsigned long long b) {
+  unsigned long long r;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+  return r;
+}
+__device__ __forceinline__ unsigned long long f2_mul(unsigned long long a, unsigned long long b) {
+  unsigned long long r;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+  return r;
+}
+__device__ __forceinline__ unsigned long long f2_fma(unsigned long long a, unsigned long long b,
+                                                     unsigned long long c) {
+  unsigned long long r;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
+  return r;
+}
+__device__ __forceinline__ float f2_hsum(unsigned long long v) {
+  float a, b;
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v));
+  return a + b;
+}
+// hardware square root (sqrt.approx.f32): with it a distance's relative error
+// stays within ((d+1)/2 + 4)u <= (d+16)u, the bound stated for FP32 distances
+__device__ __forceinline__ float sqrt_approx(float x) {
+  float r;
+  asm("sqrt.approx.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+
+// Warp-cooperative FP32 evaluation: lanes stride over the larger cluster's
+// points, each lane loops over the smaller one (broadcast loads).  A squared
+// distance takes H = ceil(d/2) coordinate pairs as f32x2 words (even and odd
+// coordinates summed apart, then added; padding coordinates are 0 on both
+// sides).  Average flushes FP32 partial sums of at most 16 terms into an FP64
+// accumulator.  Returns +inf once the partial result's lower bound exceeds
+// `bound` (D units).
+template <int LK, int H, int DP>
+__device__ float eval32_warp_h(const float *P, int sa, int na, int sb, int nb, float bound,
+                               float delta, float rho, int lane, unsigned long long &pp) {
   int sL = sa, nL = na, sS = sb, nS = nb;
   if (nb > na) {
     sL = sb;
@@ -299,18 +334,27 @@ __device__ float eval32_warp(const float *P, int sa, int na, int sb, int nb, flo
   for (int base = 0; base < nL; base += 32) {
     const int l = base + lane;
     if (l < nL) {
-      float x[DP];
+      const unsigned long long *xr = (const unsigned long long *)(P + (size_t)(sL + l) * DP);
+      unsigned long long x[H];
 #pragma unroll
-      for (int k = 0; k < DP; ++k) x[k] = P[(size_t)(sL + l) * DP + k];
+      for (int h = 0; h < H; ++h) x[h] = xr[h];
       float part = 0.f;
       int cnt = 0;
       for (int j = 0; j < nS; ++j) {
-        const float d2 = pt_d2<DP>(x, P + (size_t)(sS + j) * DP);
+        const unsigned long long *yr = (const unsigned long long *)(P + (size_t)(sS + j) * DP);
+        unsigned long long t = f2_sub(x[0], yr[0]);
+        unsigned long long d2 = f2_mul(t, t);
+#pragma unroll
+        for (int h = 1; h < H; ++h) {
+          t = f2_sub(x[h], yr[h]);
+          d2 = f2_fma(t, t, d2);
+        }
+        const float s2 = f2_hsum(d2);
         if (LK == LK_COMPLETE) {
-          macc = fmaxf(macc, d2);
+          macc = fmaxf(macc, s2);
         } else {
-          part += sqrtf(d2);
-          if (++cnt == 32) {
+          part += sqrt_approx(s2);
+          if (++cnt == 16) {
             sacc += (double)part;
             part = 0.f;
             cnt = 0;
@@ -336,6 +380,23 @@ __device__ float eval32_warp(const float *P, int sa, int na, int sb, int nb, flo
   return (float)(warp_sum(sacc) / nn);
 }
 
+// eval32_warp_h for the instance's true dimension d (rows have stride DP)
+template <int LK, int DP>
+__device__ float eval32_warp(const float *P, int d, int sa, int na, int sb, int nb, float bound,
+                             float delta, float rho, int lane, unsigned long long &pp) {
+  const int H = (d + 1) >> 1;
+  if (DP == 2) return eval32_warp_h<LK, 1, DP>(P, sa, na, sb, nb, bound, delta, rho, lane, pp);
+  if (DP == 4) return eval32_warp_h<LK, 2, DP>(P, sa, na, sb, nb, bound, delta, rho, lane, pp);
+  if (DP == 8) {
+    if (H <= 3) return eval32_warp_h<LK, 3, DP>(P, sa, na, sb, nb, bound, delta, rho, lane, pp);
+    return eval32_warp_h<LK, 4, DP>(P, sa, na, sb, nb, bound, delta, rho, lane, pp);
+  }
+  if (H <= 5) return eval32_warp_h<LK, 5, DP>(P, sa, na, sb, nb, bound, delta, rho, lane, pp);
+  if (H == 6) return eval32_warp_h<LK, 6, DP>(P, sa, na, sb, nb, bound, delta, rho, lane, pp);
+  if (H == 7) return eval32_warp_h<LK, 7, DP>(P, sa, na, sb, nb, bound, delta, rho, lane, pp);
+  return eval32_warp_h<LK, 8, DP>(P, sa, na, sb, nb, bound, delta, rho, lane, pp);
+}
+
 // ---------------------------------------------------------------------------
 
 template <int LK, int DP, int MODE>
@@ -349,6 +410,8 @@ struct Searcher {
   float ci32[DP], alo[DP], ahi[DP];
   float slack;
   float beta_d;   // pred bound, D units
+  float Uv;       // least upper bound on D(C_i, candidate) from cluster summaries
+  float vA;       // variance of C_i, rounded up (average linkage)
   float bd;       // current upper bound on the NN distance, D units
   float T;        // pruning threshold: bd * (1 + EPS) + slack
   // exact (FP64) best, as key bits and cid
@@ -390,6 +453,8 @@ struct Searcher {
     bk = KINF;
     bc = INT_MAX;
     U = Ufix;
+    Uv = INFINITY;
+    vA = LK == LK_AVERAGE ? a.qvar[a.pos[ci]] : 0.f;
     L1 = L2 = INFINITY;
     c1 = INT_MAX;
     d1 = e1 = INFINITY;
@@ -417,9 +482,34 @@ struct Searcher {
     return false;
   }
 
+  // this round's big-pair results (lane 0 probes, the warp shares the answer)
+  __device__ bool side_find(int cw, double &v, float &e) const {
+    if (!a.defer || a.side_cap <= 0) return false;
+    int at = -1;
+    if (lane == 0) {
+      const int lo = min(ci, cw), hi = max(ci, cw);
+      const unsigned long long want = ((unsigned long long)(unsigned)lo << 32) | (unsigned)hi;
+      unsigned h = side_hash(lo, hi, a.side_cap);
+      for (int q = 0; q < SIDE_PROBES; ++q, h = (h + 1) & (unsigned)(a.side_cap - 1)) {
+        const unsigned long long cur = a.side_key[h];
+        if (cur == want) {
+          at = (int)h;
+          break;
+        }
+        if (cur == CKEY_EMPTY) break;
+      }
+    }
+    at = __shfl_sync(0xffffffffu, at, 0);
+    if (at < 0) return false;
+    v = a.side_val[at];
+    e = a.side_err[at];
+    return true;
+  }
+
   __device__ bool cache_get(int cw, int nw, double &v, float &e) {
     if (a.cache_slots <= 0 || (long long)na * nw < CACHE_MIN_PAIRS) return false;
-    const bool hit = cache_find(ci, cw, v, e) || cache_find(cw, ci, v, e);
+    const bool hit = cache_find(ci, cw, v, e) || cache_find(cw, ci, v, e) ||
+                     ((long long)na * nw >= BIG_MIN_PAIRS && side_find(cw, v, e));
     hits += hit;
     return hit;
   }
@@ -442,8 +532,21 @@ struct Searcher {
     else if (MODE == M_RECHECK)
       bd = fminf(U, key_dist_ru<LK>(bk));
     else
-      bd = fminf(beta_d, key_dist_ru<LK>(bk));
+      bd = fminf(fminf(beta_d, key_dist_ru<LK>(bk)), Uv);
     T = bd * (1.f + EPS) + slack;
+  }
+
+  // Upper bounds on D(C_i, B) that need no point pairs (one per lane, INF if
+  // none): the nearest neighbour is no farther than the least of them, so
+  // candidates whose lower bound exceeds it are pruned before any evaluation.
+  // In the FP32 passes the bound also joins U (it bounds the true distance).
+  __device__ void offer_ub(float ub) {
+    const float m = warp_minf(ub);
+    if (m < Uv) {
+      Uv = m;
+      if (MODE != M_F64) U = fminf(U, m);
+      refresh();
+    }
   }
 
   __device__ bool pass(float lb) const { return lb <= T; }
@@ -564,6 +667,28 @@ struct Searcher {
       return;
     }
     // ---- complete / average ----
+    if (__any_sync(0xffffffffu, valid)) {
+      float ub = INFINITY;
+      if (valid) {
+        if (LK == LK_AVERAGE) {
+          // mean ||x - y|| <= sqrt(mean ||x - y||^2) = sqrt(||c_A - c_B||^2 + var A + var B)
+          // (Jensen); the FP32 centroid distance is widened by its error bound
+          const float r = __fadd_ru(__fmul_ru(__fsqrt_ru(dc2), 1.f + rho), delta0);
+          ub = __fsqrt_ru(__fadd_ru(__fadd_ru(__fmul_ru(r, r), vA), a.qvar[idx]));
+        } else {
+          // max ||x - y|| <= distance between the farthest corners of the boxes
+          float s2 = 0.f;
+#pragma unroll
+          for (int k = 0; k < DP; ++k) {
+            const float m = fmaxf(fmaxf(__fsub_ru(a.qbhi[(size_t)idx * DP + k], alo[k]),
+                                        __fsub_ru(ahi[k], a.qblo[(size_t)idx * DP + k])), 0.f);
+            s2 = __fadd_ru(s2, __fmul_ru(m, m));
+          }
+          ub = __fsqrt_ru(s2);
+        }
+      }
+      offer_ub(ub);
+    }
     const float lb = valid ? fmaxf(sqrtf(dc2), bx) : INFINITY;
     const bool ok = valid && pass(lb);
     const int sb = valid ? a.qseg[idx] : 0;
@@ -616,8 +741,11 @@ struct Searcher {
       // values that will be cached are computed in full (no early exit)
       const bool cacheable = a.cache_slots > 0 && (long long)na * nw >= CACHE_MIN_PAIRS;
       const long long np = (long long)na * nw;
-      const bool huge = np >= a.big_pairs;
-      const bool huge64 = np >= a.big_pairs64;  // for FP64 evaluations
+      // big pairs go to the GPU-wide kernels, and so does every pair of at
+      // least BIG_MIN_PAIRS once this search has spent its own budget
+      const bool over = ppairs >= (unsigned long long)a.warp_budget && np >= BIG_MIN_PAIRS;
+      const bool huge = np >= a.big_pairs || over;
+      const bool huge64 = np >= a.big_pairs64 || over;  // for FP64 evaluations
       if (MODE == M_F64) {
         double key = cv;
         if (!cached) {
@@ -637,7 +765,7 @@ struct Searcher {
         float d32 = (float)cv, e32 = ce;
         if (!cached) {
           if (huge && try_defer(cw, sw, nw, 0)) continue;
-          d32 = eval32_warp<LK, DP>(a.p32, sa, na, sw, nw, cacheable ? INFINITY : bd, dlt, rho,
+          d32 = eval32_warp<LK, DP>(a.p32, a.d, sa, na, sw, nw, cacheable ? INFINITY : bd, dlt, rho,
                                     lane, pp);
           ppairs += pp;
           e32 = dlt;
@@ -653,7 +781,7 @@ struct Searcher {
           float d32 = (float)cv, e32 = ce;
           if (!cached) {
             if (huge && try_defer(cw, sw, nw, 1)) continue;
-            d32 = eval32_warp<LK, DP>(a.p32, sa, na, sw, nw, cacheable ? INFINITY : fminf(U, bd),
+            d32 = eval32_warp<LK, DP>(a.p32, a.d, sa, na, sw, nw, cacheable ? INFINITY : fminf(U, bd),
                                       dlt, rho, lane, pp);
             ppairs += pp;
             e32 = dlt;
