@@ -498,17 +498,18 @@ __device__ __forceinline__ bool slot_free(const State &s, unsigned long long cur
 // publish the key: concurrent writers skip BUSY slots, so a slot's key and
 // value always come from the same writer.  Readers run in later kernels.
 __device__ bool slot_put(const State &s, size_t idx, unsigned long long cur,
-                         unsigned long long want, double v, float e) {
+                         unsigned long long want, double v, float e, int part = 0) {
   if (atomicCAS(&s.ckey[idx], cur, CKEY_BUSY) != cur) return false;
   s.cval[idx] = v;
   s.cerr[idx] = e;
+  s.cpart[idx] = part;
   __threadfence();
   atomicExch(&s.ckey[idx], want);
   return true;
 }
 
 // Insert (nbr -> v, e) into the table of `owner` if there is a free slot;
-// an entry already present is kept.
+// an entry already present is kept (a partial one is completed by it).
 __device__ void cache_insert(const State &s, int owner, int nbr, int nbr_gen, double v, float e) {
   const int S = s.cache_slots;
   const unsigned long long want = ckey_of(nbr, nbr_gen);
@@ -518,7 +519,10 @@ __device__ void cache_insert(const State &s, int owner, int nbr, int nbr_gen, do
     // a free slot only turns BUSY or live within a kernel, so this ends
     for (;;) {
       const unsigned long long cur = slot_key(s, base + t);
-      if (cur == want) return;
+      if (cur == want) {
+        if (s.cpart[base + t] != 0) slot_put(s, base + t, cur, want, v, e);
+        return;
+      }
       if (!slot_free(s, cur)) break;
       if (slot_put(s, base + t, cur, want, v, e)) return;
     }
@@ -541,7 +545,7 @@ struct CEntry {
   double val;
 };
 
-constexpr int CM_WARPS = 2;  // warps per block of k_cache_merge (4 * slots entries each)
+constexpr int CM_WARPS = 2;  // warps per block of k_cache_merge (5 * slots entries each)
 
 // look for neighbour `g` in a warp-local list
 __device__ __forceinline__ int clist_find(const CEntry *L, int n, int g) {
@@ -555,7 +559,7 @@ __device__ bool ctable_find(const State &s, int owner, int nbr, double &v, float
   const int S = s.cache_slots;
   const unsigned long long want = ckey_of(nbr, s.gen[nbr]);
   for (int t = 0; t < S; ++t)
-    if (s.ckey[(size_t)owner * S + t] == want) {
+    if (s.ckey[(size_t)owner * S + t] == want && s.cpart[(size_t)owner * S + t] == 0) {
       v = s.cval[(size_t)owner * S + t];
       e = s.cerr[(size_t)owner * S + t];
       return true;
@@ -577,17 +581,22 @@ __global__ void k_cache_merge(State s, int npairs, int round) {
   extern __shared__ unsigned char smem_raw[];
   const int S = s.cache_slots;
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-  CEntry *A = (CEntry *)smem_raw + (size_t)wib * 4 * S;
+  CEntry *A = (CEntry *)smem_raw + (size_t)wib * 5 * S;
   CEntry *B = A + S;
   CEntry *N = B + S;  // up to 2S new entries (cid, err, val); gen kept in a parallel array
-  __shared__ int cnt[CM_WARPS][3];
+  CEntry *Q = N + 2 * S;  // up to S partial entries (one side known), part kept apart
+  __shared__ int cnt[CM_WARPS][4];
   __shared__ int ngen_s[CM_WARPS][2 * CACHE_MAX_SLOTS];
+  __shared__ int qgen_s[CM_WARPS][CACHE_MAX_SLOTS];
+  __shared__ int qpart_s[CM_WARPS][CACHE_MAX_SLOTS];
   int *ngen = ngen_s[wib];
+  int *qgen = qgen_s[wib];
+  int *qpart = qpart_s[wib];
   const int warps = (gridDim.x * blockDim.x) >> 5;
   for (int p = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; p < npairs; p += warps) {
     const int lo = s.pair_lo[p], hi = s.pair_hi[p];
     const double na = (double)s.osize[lo], nb = (double)s.osize[hi];
-    if (lane == 0) cnt[wib][0] = cnt[wib][1] = cnt[wib][2] = 0;
+    if (lane == 0) cnt[wib][0] = cnt[wib][1] = cnt[wib][2] = cnt[wib][3] = 0;
     __syncwarp();
     // valid entries of the two old tables
     for (int side = 0; side < 2; ++side) {
@@ -599,7 +608,8 @@ __global__ void k_cache_merge(State s, int npairs, int round) {
         unsigned long long key = CKEY_EMPTY;
         if (t < S) {
           key = s.ckey[(size_t)owner * S + t];
-          v = key != CKEY_EMPTY && (unsigned)key == (unsigned)s.gen[(int)(key >> 32)];
+          v = key != CKEY_EMPTY && (unsigned)key == (unsigned)s.gen[(int)(key >> 32)] &&
+              s.cpart[(size_t)owner * S + t] == 0;
         }
         const unsigned m = __ballot_sync(0xffffffffu, v);
         if (v) {
@@ -647,6 +657,17 @@ __global__ void k_cache_merge(State s, int npairs, int round) {
           vh = B[b1].val;
           eh = B[b1].err;
         } else if (!ctable_find(s, g, hi, vh, eh)) {
+          // only D(lo, g) is known: keep it as a partial entry of the merged
+          // cluster (its first |lo| points), completed later by evaluating
+          // the other points only
+          const int at = atomicAdd(&cnt[wib][3], 1);
+          if (at < S) {
+            Q[at].cid = g;
+            Q[at].val = A[t].val;
+            Q[at].err = A[t].err;
+            qgen[at] = s.gen[g];
+            qpart[at] = (int)na;
+          }
           continue;
         }
         if (LK == 0) {
@@ -672,7 +693,18 @@ __global__ void k_cache_merge(State s, int npairs, int round) {
       if (g == lo || s.mround[g] == round || clist_find(A, nA, g) >= 0) continue;
       double vl;
       float el;
-      if (!ctable_find(s, g, lo, vl, el)) continue;
+      if (!ctable_find(s, g, lo, vl, el)) {
+        // only D(hi, g) is known: a partial entry for the last |hi| points
+        const int at = atomicAdd(&cnt[wib][3], 1);
+        if (at < S) {
+          Q[at].cid = g;
+          Q[at].val = B[t].val;
+          Q[at].err = B[t].err;
+          qgen[at] = s.gen[g];
+          qpart[at] = -(int)nb;
+        }
+        continue;
+      }
       double v;
       float e;
       if (LK == 0) {
@@ -690,14 +722,23 @@ __global__ void k_cache_merge(State s, int npairs, int round) {
       ngen[at] = s.gen[g];
     }
     __syncwarp();
-    // the merged cluster's new table (first S entries), replacing lo's
+    // the merged cluster's new table, replacing lo's: derived entries first,
+    // then partial ones while there is room
     const int nN = min(cnt[wib][2], S);
+    const int nQ = min(cnt[wib][3], S - nN);
     for (int t = lane; t < S; t += 32) {
       const size_t slot = (size_t)lo * S + t;
       if (t < nN) {
         s.ckey[slot] = ckey_of(N[t].cid, ngen[t]);
         s.cval[slot] = N[t].val;
         s.cerr[slot] = N[t].err;
+        s.cpart[slot] = 0;
+      } else if (t < nN + nQ) {
+        const int u = t - nN;
+        s.ckey[slot] = ckey_of(Q[u].cid, qgen[u]);
+        s.cval[slot] = Q[u].val;
+        s.cerr[slot] = Q[u].err;
+        s.cpart[slot] = qpart[u];
       } else {
         s.ckey[slot] = CKEY_EMPTY;
       }
@@ -1117,7 +1158,10 @@ __device__ void cache_insert_evict(const State &s, int owner, int nbr, int nbr_g
     unsigned long long vkey = 0;
     for (int t = 0; t < S; ++t) {
       const unsigned long long cur = slot_key(s, base + t);
-      if (cur == want) return;
+      if (cur == want) {
+        if (s.cpart[base + t] != 0) slot_put(s, base + t, cur, want, v, e);
+        return;
+      }
       if (slot_free(s, cur)) {
         if (slot_put(s, base + t, cur, want, v, e)) return;
         continue;
@@ -1170,13 +1214,24 @@ __global__ void k_big_final(State s, int r0, int m) {
     }
     if (lane == 0) {
       const int i = s.breq_i[r], j = s.breq_j[r];
-      const double nn = (double)s.breq_na[r] * (double)s.breq_nb[r];
-      const double D = s.linkage == 0 ? sqrt(v) : v / nn;
+      const int cov = s.breq_cov[r];  // points of side a covered by the partial entry
+      const double na = (double)s.breq_na[r], nb = (double)s.breq_nb[r];
       const bool exact = s.breq_exact[r] != 0;
+      float e = exact ? 0.f : fmaxf(s.idpts[s.inst[i]], EST_MARK);
+      double D;
+      if (s.linkage == 0) {
+        D = sqrt(v);
+        if (cov > 0) {
+          D = fmax(D, s.breq_base[r]);
+          e = fmaxf(e, s.breq_berr[r]);
+        }
+      } else {
+        D = (v + (cov > 0 ? s.breq_base[r] : 0.0)) / ((na + cov) * nb);
+        if (cov > 0) e = (float)((cov * (double)s.breq_berr[r] + na * e) / (na + cov));
+      }
+      if (!exact) e = fmaxf(e, EST_MARK);
       atomicAdd(&s.ctr->big_pp, (unsigned long long)s.breq_na[r] * (unsigned long long)s.breq_nb[r]);
       if (exact) atomicAdd(&s.ctr->big_exact, 1ull);
-      const float e = exact ? 0.f
-: fmaxf(s.idpts[s.inst[i]], EST_MARK);
       cache_insert_evict(s, i, j, s.gen[j], D, e);
       cache_insert_evict(s, j, i, s.gen[i], D, e);
       side_put(s, min(i, j), max(i, j), D, e);
@@ -1822,6 +1877,7 @@ void fill_query_args(hac_ctx *h, QueryArgs &qa, int round, int K, int nterm) {
   qa.ckey = s.ckey;
   qa.cval = s.cval;
   qa.cerr = s.cerr;
+  qa.cpart = s.cpart;
   qa.gen = s.gen;
   qa.ins_i = s.ins_i;
   qa.ins_j = s.ins_j;
@@ -1843,6 +1899,9 @@ void fill_query_args(hac_ctx *h, QueryArgs &qa, int round, int K, int nterm) {
   qa.breq_sb = s.breq_sb;
   qa.breq_nb = s.breq_nb;
   qa.breq_exact = s.breq_exact;
+  qa.breq_base = s.breq_base;
+  qa.breq_cov = s.breq_cov;
+  qa.breq_berr = s.breq_berr;
   qa.pend_out = s.pend[0];
 }
 
@@ -1941,7 +2000,7 @@ int round_step(hac_ctx *h, cudaStream_t st, int round, int K, int nterm, RoundCt
   h->launches += 4;  // merge, 3 compaction kernels
   if (s.cache_slots > 0) {
     const int S = s.cache_slots;
-    const size_t smem = (size_t)CM_WARPS * 4 * S * sizeof(CEntry);
+    const size_t smem = (size_t)CM_WARPS * 5 * S * sizeof(CEntry);
     const int blocks = std::max(1, std::min(cdiv(npairs, CM_WARPS), 152 * 32));
     if (s.linkage == LK_COMPLETE)
       k_cache_merge<0><<<blocks, CM_WARPS * 32, smem, st>>>(s, npairs, round);
@@ -1985,7 +2044,7 @@ int run_impl(hac_ctx *h, const hac_opts *o) {
     const size_t cells = (size_t)h->n * slots;
     const int64_t cap = std::max<int64_t>(4 * h->n, 1 << 16);
     if ((rc0 = dalloc(h, &s.ckey, cells)) || (rc0 = dalloc(h, &s.cval, cells)) ||
-        (rc0 = dalloc(h, &s.cerr, cells)) || (rc0 = dalloc(h, &s.ins_i, cap)) ||
+        (rc0 = dalloc(h, &s.cerr, cells)) || (rc0 = dalloc(h, &s.cpart, cells)) || (rc0 = dalloc(h, &s.ins_i, cap)) ||
         (rc0 = dalloc(h, &s.ins_j, cap)) || (rc0 = dalloc(h, &s.ins_v, cap)) ||
         (rc0 = dalloc(h, &s.ins_e, cap)))
       return rc0;
@@ -1999,6 +2058,8 @@ int run_impl(hac_ctx *h, const hac_opts *o) {
           (rc0 = dalloc(h, &s.breq_sa, bcap)) || (rc0 = dalloc(h, &s.breq_na, bcap)) ||
           (rc0 = dalloc(h, &s.breq_sb, bcap)) || (rc0 = dalloc(h, &s.breq_nb, bcap)) ||
           (rc0 = dalloc(h, &s.breq_exact, bcap)) || (rc0 = dalloc(h, &s.bsched, BS_SIZE)) ||
+          (rc0 = dalloc(h, &s.breq_base, bcap)) || (rc0 = dalloc(h, &s.breq_cov, bcap)) ||
+          (rc0 = dalloc(h, &s.breq_berr, bcap)) ||
           (rc0 = dalloc(h, &s.bpart, tiles)) || (rc0 = dalloc(h, &s.pend[0], h->n)) ||
           (rc0 = dalloc(h, &s.pend[1], h->n)) || (rc0 = dalloc(h, &s.side_key, 2 * bcap)) ||
           (rc0 = dalloc(h, &s.side_val, 2 * bcap)) || (rc0 = dalloc(h, &s.side_err, 2 * bcap)))
@@ -2854,7 +2915,9 @@ int engine_init(Engine &e, hac_linkage lk, int d, hac_dtype dt, int64_t cap, con
     const int bcap = 1 << 18;
     const size_t per = (size_t)std::max(BIG_MAXT, cdiv(cap, BIG_TILE) + 1);
     if ((rc = dalloc(&h, &s.ckey, cells)) || (rc = dalloc(&h, &s.cval, cells)) ||
-        (rc = dalloc(&h, &s.cerr, cells)) || (rc = dalloc(&h, &s.ins_i, icap)) ||
+        (rc = dalloc(&h, &s.cerr, cells)) || (rc = dalloc(&h, &s.cpart, cells)) ||
+        (rc = dalloc(&h, &s.breq_base, bcap)) || (rc = dalloc(&h, &s.breq_cov, bcap)) ||
+        (rc = dalloc(&h, &s.breq_berr, bcap)) || (rc = dalloc(&h, &s.ins_i, icap)) ||
         (rc = dalloc(&h, &s.ins_j, icap)) || (rc = dalloc(&h, &s.ins_v, icap)) ||
         (rc = dalloc(&h, &s.ins_e, icap)) || (rc = dalloc(&h, &s.breq_i, bcap)) ||
         (rc = dalloc(&h, &s.breq_j, bcap)) || (rc = dalloc(&h, &s.breq_sa, bcap)) ||

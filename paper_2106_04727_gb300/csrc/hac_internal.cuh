@@ -82,6 +82,10 @@ struct State {
   unsigned long long *ckey;
   double *cval;
   float *cerr;
+  // partial entries (Lance-Williams with one side unknown): 0 = the value is
+  // D(owner, neighbour); c > 0 = it is D(first c points of the owner,
+  // neighbour); c < 0 = D(last -c points of the owner, neighbour)
+  int32_t *cpart;
   int ins_cap;          // queue of evaluated pairs to insert after the search
   int32_t *ins_i, *ins_j;
   double *ins_v;
@@ -90,6 +94,12 @@ struct State {
   int breq_cap;
   int32_t *breq_i, *breq_j, *breq_sa, *breq_na, *breq_sb, *breq_nb;
   uint8_t *breq_exact;   // 1 = FP64 value wanted, 0 = FP32 estimate
+  // completion of a partial entry: the request evaluates the missing points
+  // only; `cov` more points of side a are already covered by `base` (the sum
+  // of their distances, average; their distance, complete) with error `berr`
+  double *breq_base;
+  int32_t *breq_cov;
+  float *breq_berr;
   int32_t *bsched;       // tile schedule of the current batch (per-kind lists)
   double *bpart;         // per-tile partial results of the current batch
   int32_t *pend[2];      // terminals whose search deferred a pair
@@ -172,6 +182,7 @@ struct QueryArgs {
   const unsigned long long *ckey;
   const double *cval;
   const float *cerr;
+  const int32_t *cpart;
   const int32_t *gen;
   int32_t *ins_i, *ins_j;
   double *ins_v;
@@ -187,6 +198,9 @@ struct QueryArgs {
   int breq_cap;
   int32_t *breq_i, *breq_j, *breq_sa, *breq_na, *breq_sb, *breq_nb;
   uint8_t *breq_exact;
+  double *breq_base;
+  int32_t *breq_cov;
+  float *breq_berr;
   int32_t *pend_out;
 };
 

@@ -422,6 +422,10 @@ struct Searcher {
   float L1, L2;   // two smallest FP32 lower bounds
   int c1;         // cid holding L1
   float d1, e1;   // FP32 value and error term of that candidate
+  double pv;      // partial entry found by the last cache_get: value,
+  float pe;       //   error term,
+  int ppart;      //   covered points of its owner (> 0 prefix, < 0 suffix),
+  bool pown_ci;   //   and whether C_i owns it
   bool deferred;  // a big pair was handed to the GPU-wide evaluation
   float delta0, rho;
   unsigned long long cpairs, ppairs, nodes, ltests, prows, rechecks, hits;
@@ -465,7 +469,8 @@ struct Searcher {
 
   // Section 5 cache: look for the entry of `nbr` in the table of `owner`
   // (warp-cooperative; valid only while the neighbour's generation matches)
-  __device__ bool cache_find(int owner, int nbr, double &v, float &e) const {
+  // (`part` receives the entry's partial tag, 0 for a full value)
+  __device__ bool cache_find(int owner, int nbr, double &v, float &e, int &part) const {
     const int S = a.cache_slots;
     const unsigned long long want = ckey_of(nbr, a.gen[nbr]);
     for (int base = 0; base < S; base += 32) {
@@ -476,6 +481,7 @@ struct Searcher {
         const size_t slot = (size_t)owner * S + base + __ffs(b) - 1;
         v = a.cval[slot];
         e = a.cerr[slot];
+        part = a.cpart[slot];
         return true;
       }
     }
@@ -506,12 +512,39 @@ struct Searcher {
     return true;
   }
 
-  __device__ bool cache_get(int cw, int nw, double &v, float &e) {
-    if (a.cache_slots <= 0 || (long long)na * nw < CACHE_MIN_PAIRS) return false;
-    const bool hit = cache_find(ci, cw, v, e) || cache_find(cw, ci, v, e) ||
-                     ((long long)na * nw >= BIG_MIN_PAIRS && side_find(cw, v, e));
-    hits += hit;
-    return hit;
+  // 0: nothing known; 1: D(C_i, C_w) in v, e; 2: only a partial entry
+  // (kept in pv, pe, ppart, pown_ci for try_defer_part)
+  __device__ int cache_get(int cw, int nw, double &v, float &e) {
+    if (a.cache_slots <= 0 || (long long)na * nw < CACHE_MIN_PAIRS) return 0;
+    double v1, v2;
+    float f1, f2;
+    int p1 = 0, p2 = 0;
+    const bool h1 = cache_find(ci, cw, v1, f1, p1);
+    if (h1 && p1 == 0) {
+      v = v1;
+      e = f1;
+      hits += 1;
+      return 1;
+    }
+    const bool h2 = cache_find(cw, ci, v2, f2, p2);
+    if (h2 && p2 == 0) {
+      v = v2;
+      e = f2;
+      hits += 1;
+      return 1;
+    }
+    if ((long long)na * nw >= BIG_MIN_PAIRS && side_find(cw, v, e)) {
+      hits += 1;
+      return 1;
+    }
+    if (h1 || h2) {
+      pv = h1 ? v1 : v2;
+      pe = h1 ? f1 : f2;
+      ppart = h1 ? p1 : p2;
+      pown_ci = h1;
+      return 2;
+    }
+    return 0;
   }
 
   // queue a computed distance for insertion into both tables (after the search)
@@ -737,7 +770,8 @@ struct Searcher {
       prows += (unsigned long long)(na + nw);
       double cv = 0.0;
       float ce = 0.f;
-      const bool cached = cache_get(cw, nw, cv, ce);
+      const int hit = cache_get(cw, nw, cv, ce);
+      const bool cached = hit == 1;
       // values that will be cached are computed in full (no early exit)
       const bool cacheable = a.cache_slots > 0 && (long long)na * nw >= CACHE_MIN_PAIRS;
       const long long np = (long long)na * nw;
@@ -746,12 +780,22 @@ struct Searcher {
       const bool over = ppairs >= (unsigned long long)a.warp_budget && np >= BIG_MIN_PAIRS;
       const bool huge = np >= a.big_pairs || over;
       const bool huge64 = np >= a.big_pairs64 || over;  // for FP64 evaluations
+      // a partial entry is completed by evaluating its missing points only:
+      // by the GPU-wide kernels if they are many, else in this warp
+      const bool partial = hit == 2;
+      const long long npm = partial ? part_pairs(nw) : 0;
+      const bool hugep = npm >= a.big_pairs || (over && npm >= BIG_MIN_PAIRS);
+      const bool hugep64 = npm >= a.big_pairs64 || (over && npm >= BIG_MIN_PAIRS);
       if (MODE == M_F64) {
         double key = cv;
         if (!cached) {
-          if (huge64 && try_defer(cw, sw, nw, 1)) continue;
-          key = eval64_warp<LK, DP>(a.p64, sa, na, sw, nw, cacheable ? INFINITY : (double)bd,
-                                    lane, pp);
+          if (partial && hugep64 && try_defer_part(cw, sw, nw, 1)) continue;
+          if (!partial && huge64 && try_defer(cw, sw, nw, 1)) continue;
+          if (partial && pe == 0.f)
+            key = part64(cw, sw, nw, pp);
+          else
+            key = eval64_warp<LK, DP>(a.p64, sa, na, sw, nw, cacheable ? INFINITY : (double)bd,
+                                      lane, pp);
           ppairs += pp;
           if (key < INFINITY) cache_put(cw, nw, key, 0.f);
         }
@@ -764,13 +808,18 @@ struct Searcher {
       } else if (MODE == M_F32) {
         float d32 = (float)cv, e32 = ce;
         if (!cached) {
-          if (huge && try_defer(cw, sw, nw, 0)) continue;
-          d32 = eval32_warp<LK, DP>(a.p32, a.d, sa, na, sw, nw, cacheable ? INFINITY : bd, dlt, rho,
-                                    lane, pp);
+          if (partial && hugep && try_defer_part(cw, sw, nw, 0)) continue;
+          if (!partial && huge && try_defer(cw, sw, nw, 0)) continue;
+          if (partial) {
+            d32 = part32(cw, sw, nw, dlt, pp, e32);
+          } else {
+            d32 = eval32_warp<LK, DP>(a.p32, a.d, sa, na, sw, nw, cacheable ? INFINITY : bd, dlt,
+                                      rho, lane, pp);
+            e32 = dlt;
+          }
           ppairs += pp;
-          e32 = dlt;
           // an estimate's error term is never 0 in the cache (0 marks FP64)
-          if (d32 < INFINITY) cache_put(cw, nw, (double)d32, fmaxf(dlt, EST_MARK));
+          if (d32 < INFINITY) cache_put(cw, nw, (double)d32, fmaxf(e32, EST_MARK));
         }
         offer_f32(lane == 0 && d32 < INFINITY, d32, e32, cw);
       } else {  // M_RECHECK
@@ -780,11 +829,16 @@ struct Searcher {
         } else {
           float d32 = (float)cv, e32 = ce;
           if (!cached) {
-            if (huge && try_defer(cw, sw, nw, 1)) continue;
-            d32 = eval32_warp<LK, DP>(a.p32, a.d, sa, na, sw, nw, cacheable ? INFINITY : fminf(U, bd),
-                                      dlt, rho, lane, pp);
+            if (partial && hugep && try_defer_part(cw, sw, nw, 0)) continue;
+            if (!partial && huge && try_defer(cw, sw, nw, 1)) continue;
+            if (partial) {
+              d32 = part32(cw, sw, nw, dlt, pp, e32);
+            } else {
+              d32 = eval32_warp<LK, DP>(a.p32, a.d, sa, na, sw, nw,
+                                        cacheable ? INFINITY : fminf(U, bd), dlt, rho, lane, pp);
+              e32 = dlt;
+            }
             ppairs += pp;
-            e32 = dlt;
           }
           if (d32 < INFINITY && lower(d32, e32) <= fminf(U, bd)) {
             if (huge64 && try_defer(cw, sw, nw, 1)) continue;
@@ -822,6 +876,76 @@ struct Searcher {
       a.breq_sb[r] = sw;
       a.breq_nb[r] = nw;
       a.breq_exact[r] = (uint8_t)exact;
+      a.breq_cov[r] = 0;
+      a.breq_base[r] = 0.0;
+      a.breq_berr[r] = 0.f;
+    }
+    deferred = true;
+    return true;
+  }
+
+  // point pairs left to evaluate for the partial entry found by cache_get
+  __device__ long long part_pairs(int nw) const {
+    const int cov = ppart > 0 ? ppart : -ppart;
+    const int on = pown_ci ? na : nw, xn = pown_ci ? nw : na;
+    return (long long)(on - cov) * xn;
+  }
+
+  // the partial entry found by cache_get completed in this warp: FP32
+  // estimate of the missing points, combined with the covered part (the
+  // error terms combine the same way: weighted mean, or max)
+  __device__ float part32(int cw, int sw, int nw, float dlt, unsigned long long &pp, float &err) {
+    const int cov = ppart > 0 ? ppart : -ppart;
+    const int os = pown_ci ? sa : sw, on = pown_ci ? na : nw;
+    const int xs = pown_ci ? sw : sa, xn = pown_ci ? nw : na;
+    const int mn = on - cov;
+    const float dm = eval32_warp<LK, DP>(a.p32, a.d, ppart > 0 ? os + cov : os, mn, xs, xn,
+                                         INFINITY, dlt, rho, lane, pp);
+    if (LK == LK_COMPLETE) {
+      err = fmaxf(pe, dlt);
+      return fmaxf((float)pv, dm);
+    }
+    err = (float)(((double)cov * pe + (double)mn * dlt) / on);
+    return (float)(((double)cov * pv + (double)mn * dm) / on);
+  }
+
+  // the same in FP64 (an FP64 partial entry)
+  __device__ double part64(int cw, int sw, int nw, unsigned long long &pp) {
+    const int cov = ppart > 0 ? ppart : -ppart;
+    const int os = pown_ci ? sa : sw, on = pown_ci ? na : nw;
+    const int xs = pown_ci ? sw : sa, xn = pown_ci ? nw : na;
+    const int mn = on - cov;
+    const double dm =
+        eval64_warp<LK, DP>(a.p64, ppart > 0 ? os + cov : os, mn, xs, xn, INFINITY, lane, pp);
+    if (LK == LK_COMPLETE) return fmax(pv, dm);
+    return ((double)cov * pv + (double)mn * dm) / on;
+  }
+
+  // Complete the partial entry found by cache_get: only the points of its
+  // owner that it does not cover are evaluated against the other cluster;
+  // the covered part's distance (sum of distances for average) rides along.
+  // An FP64 value needs an FP64 partial (pe == 0).
+  __device__ bool try_defer_part(int cw, int sw, int nw, int exact) {
+    if (!a.defer || a.cache_slots <= 0 || (exact && pe != 0.f)) return false;
+    const int cov = ppart > 0 ? ppart : -ppart;
+    const int os = pown_ci ? sa : sw, on = pown_ci ? na : nw;  // owner's points
+    const int xs = pown_ci ? sw : sa, xn = pown_ci ? nw : na;  // the other cluster's
+    if (cov <= 0 || cov >= on) return false;
+    int r = 0;
+    if (lane == 0) r = atomicAdd(&a.ctr->nbreq, 1);
+    r = __shfl_sync(0xffffffffu, r, 0);
+    if (r >= a.breq_cap) return false;
+    if (lane == 0) {
+      a.breq_i[r] = pown_ci ? ci : cw;
+      a.breq_j[r] = pown_ci ? cw : ci;
+      a.breq_sa[r] = ppart > 0 ? os + cov : os;  // a prefix is covered: the rest follows it
+      a.breq_na[r] = on - cov;
+      a.breq_sb[r] = xs;
+      a.breq_nb[r] = xn;
+      a.breq_exact[r] = (uint8_t)exact;
+      a.breq_cov[r] = cov;
+      a.breq_base[r] = LK == LK_COMPLETE ? pv : pv * (double)cov * (double)xn;
+      a.breq_berr[r] = pe;
     }
     deferred = true;
     return true;
@@ -834,11 +958,14 @@ struct Searcher {
     if (LK == LK_WARD) return ward64(q, nb);
     double cv;
     float ce;
-    if (cache_get(c, nb, cv, ce) && ce == 0.f) return kbits(cv);
+    const int hit = cache_get(c, nb, cv, ce);
+    if (hit == 1 && ce == 0.f) return kbits(cv);
     // an FP32 value whose stated bound is within 4e-6 stands in for FP64:
     // its upper bound is returned (a valid beta; height error <= 8e-6)
     if (d1 < INFINITY && e1 + rho * d1 <= 4e-6f * d1)
       return kbits((double)((d1 + e1) * (1.f + rho)));
+    if (hit == 2 && (long long)na * nb >= BIG_MIN_PAIRS && try_defer_part(c, a.qseg[q], nb, 1))
+      return KINF;
     if ((long long)na * nb >= a.big_pairs64 && try_defer(c, a.qseg[q], nb, 1)) return KINF;
     unsigned long long pp = 0;
     const double key = eval64_warp<LK, DP>(a.p64, sa, na, a.qseg[q], nb, INFINITY, lane, pp);
