@@ -218,7 +218,7 @@ def run_serving(args):
     torch.cuda.set_device(local)
     if rank != 0:
         return
-    slots = args.cache_slots
+    slots = args.serving_cache_slots
     reqs = inputs.serving_requests(args.requests, seed=4)
     pts = [inputs.request_points(r) for r in reqs]
     cap = args.engine_points
@@ -365,7 +365,7 @@ def main():
     ap.add_argument("--workload", default="gmm5d_1m_f32")
     ap.add_argument("--linkages", default="ward,average")
     ap.add_argument("--precision", default="f32", choices=["f64", "f32"])
-    ap.add_argument("--cache-slots", type=int, default=64,
+    ap.add_argument("--cache-slots", type=int, default=128,
                     help="Section 5 cache slots per cluster for complete/average")
     ap.add_argument("--ref-sample", type=int, default=20000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -373,6 +373,8 @@ def main():
     ap.add_argument("--requests", type=int, default=4096, help="serving: stream length")
     ap.add_argument("--sample", type=int, default=256,
                     help="serving: requests timed on the per-instance paths")
+    ap.add_argument("--serving-cache-slots", type=int, default=64,
+                    help="serving: cache slots per cluster (complete/average engines)")
     ap.add_argument("--engine-points", type=int, default=1 << 21,
                     help="serving: points per engine (one engine per linkage and d)")
     args = ap.parse_args()

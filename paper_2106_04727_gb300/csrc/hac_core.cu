@@ -2002,10 +2002,16 @@ int round_step(hac_ctx *h, cudaStream_t st, int round, int K, int nterm, RoundCt
     const int S = s.cache_slots;
     const size_t smem = (size_t)CM_WARPS * 5 * S * sizeof(CEntry);
     const int blocks = std::max(1, std::min(cdiv(npairs, CM_WARPS), 152 * 32));
-    if (s.linkage == LK_COMPLETE)
+    // more than the default 48 KB of shared memory per block for large tables
+    if (s.linkage == LK_COMPLETE) {
+      CK(cudaFuncSetAttribute(k_cache_merge<0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)smem));
       k_cache_merge<0><<<blocks, CM_WARPS * 32, smem, st>>>(s, npairs, round);
-    else
+    } else {
+      CK(cudaFuncSetAttribute(k_cache_merge<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)smem));
       k_cache_merge<1><<<blocks, CM_WARPS * 32, smem, st>>>(s, npairs, round);
+    }
     k_gen_bump<<<grid_for(npairs, TPB), TPB, 0, st>>>(s, npairs);
     h->launches += 2;
   }

@@ -205,12 +205,12 @@ struct QueryArgs {
 };
 
 // pairs of at least this many point pairs are evaluated by the whole GPU
-constexpr long long BIG_PAIRS = 1ll << 18;
+constexpr long long BIG_PAIRS = 1ll << 16;
 // FP64 point pairs cost ~64x more on this part: hand them over much earlier
 constexpr long long BIG_PAIRS_F64 = 1ll << 13;
 // point pairs one search evaluates in its own warp before it hands every
 // further pair of at least BIG_MIN_PAIRS to the GPU-wide kernels
-constexpr long long WARP_BUDGET = 1ll << 20;
+constexpr long long WARP_BUDGET = 1ll << 18;
 constexpr long long BIG_MIN_PAIRS = 1ll << 12;
 constexpr int SIDE_PROBES = 64;
 
