@@ -32,6 +32,16 @@ METRIC = "HAC wall time & distance evals/s vs HBM roofline at n=1M"
 UNIT = "points/s"
 SMS, FP32_LANES = 152, 128   # GB300: SMs and FP32 lanes per SM
 
+# DRAM bytes (read + write) per launch, from one ncu capture of this bench's
+# command (profiles/launches_gmm5d_1m_ward_average.md); valid for the kernels
+# as captured.  Big pairs: one batch launches three evaluation kernels
+# (4.825 + 4.852 + 0.053 MB), the entry is the mean per launch; the search:
+# 628 average + 256 Ward launches.
+TRAFFIC = {
+    ("k_big_eval32", "gmm5d_1m_f32"): 9.730e6 / 3,
+    ("k_query", "gmm5d_1m_f32"): (628 * 30.419e6 + 256 * 27.290e6) / 884,
+}
+
 
 def _peaks():
     try:
@@ -451,11 +461,12 @@ def main():
     kern = {
         "k_query": {"bound": "hbm", "ms": q_ms / args.steps, "launches": q_launch // args.steps,
                     "achieved": q_bytes / (q_ms / 1e3) / 1e9 if q_ms else 0.0, "peak": hbm,
-                    "unit": "GB/s", "traffic": None},
+                    "unit": "GB/s", "traffic": TRAFFIC.get(("k_query", args.workload))},
         "k_big_eval32": {"bound": "alu", "ms": b_ms / args.steps,
                          "launches": b_launch // args.steps,
                          "achieved": b_pairs * flops_per_pair / (b_ms / 1e3) / 1e12 if b_ms else 0.0,
-                         "peak": fp32_tflops, "unit": "TFLOP/s", "traffic": None},
+                         "peak": fp32_tflops, "unit": "TFLOP/s",
+                         "traffic": TRAFFIC.get(("k_big_eval32", args.workload))},
     }
     for k in kern.values():
         k["frac"] = k["achieved"] / k["peak"] if k["peak"] else 0.0

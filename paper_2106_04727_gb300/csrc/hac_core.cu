@@ -1961,7 +1961,7 @@ int round_step(hac_ctx *h, cudaStream_t st, int round, int K, int nterm, RoundCt
       rc = launch_big(s, r0, st);
       EVREC(ctl.eb1);
       if (rc) return rc;
-      ctl.big_launch += 2;
+      ctl.big_launch += 3;  // kinds 0 and 1 (FP32), FP64
       if (ctl.eb0) {
         CK(cudaEventSynchronize(ctl.eb1));
         float bms;
