@@ -21,8 +21,8 @@ import threading
 
 import numpy as np
 
-COMPLETE, AVERAGE, WARD = 0, 1, 2
-LINKAGES = {"complete": COMPLETE, "average": AVERAGE, "ward": WARD}
+COMPLETE, AVERAGE, WARD, AVERAGE_SQ = 0, 1, 2, 3
+LINKAGES = {"complete": COMPLETE, "average": AVERAGE, "ward": WARD, "average_sq": AVERAGE_SQ}
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "hac_oracle.c")

@@ -21,7 +21,8 @@
  *     (D, min cid, max cid).
  *   - linkages (Table 1): complete = max point distance, average (avg-1) =
  *     mean Euclidean point distance, Ward = sqrt(2|A||B|/(|A|+|B|)) *
- *     ||mean_A - mean_B||.
+ *     ||mean_A - mean_B||, avg-2 = mean SQUARED Euclidean point distance
+ *     (reported as is: its height is in squared units).
  *   - Lance-Williams update (Section 2, "Lance-Williams Formula", Table 2).
  *     The Ward coefficients are applied to SQUARED Ward distances: with D
  *     defined by the square-root form of Table 1, the update is exact only on
@@ -53,7 +54,7 @@
 #include <stdlib.h>
 #include <string.h>
 
-enum { LK_COMPLETE = 0, LK_AVERAGE = 1, LK_WARD = 2 };
+enum { LK_COMPLETE = 0, LK_AVERAGE = 1, LK_WARD = 2, LK_AVG2 = 3 };
 
 /* ------------------------------------------------------------------------ */
 /* helpers                                                                   */
@@ -92,7 +93,9 @@ double oracle_lw(int linkage, double dac, double dbc, double dab,
       /* a1 = a2 = c = 1/2, b = 0:  (dac + dbc + |dac - dbc|) / 2 = max */
       return fmax(dac, dbc);
     case LK_AVERAGE:
-      /* a1 = |A|/(|A|+|B|), a2 = |B|/(|A|+|B|), b = c = 0 */
+    case LK_AVG2:
+      /* a1 = |A|/(|A|+|B|), a2 = |B|/(|A|+|B|), b = c = 0 (avg-2: on squared
+       * point distances, which is exactly its own distance) */
       return (na * dac + nb * dbc) / (na + nb);
     case LK_WARD:
       /* a1 = (|A|+|C|)/T, a2 = (|B|+|C|)/T, b = -|C|/T, c = 0, T = |A|+|B|+|C| */
@@ -104,7 +107,8 @@ double oracle_lw(int linkage, double dac, double dbc, double dab,
 
 /* Initial matrix entry between singletons i and j. */
 static double singleton_entry(int linkage, const double *X, int d, int64_t i, int64_t j) {
-  if (linkage == LK_WARD) return point_dist2(X + i * d, X + j * d, d); /* D^2 */
+  if (linkage == LK_WARD || linkage == LK_AVG2)
+    return point_dist2(X + i * d, X + j * d, d); /* Ward: D^2; avg-2: D */
   return point_dist(X + i * d, X + j * d, d);
 }
 
@@ -130,6 +134,12 @@ double oracle_cluster_dist(int linkage, const double *A, int64_t na,
     double s = 0.0;
     for (int64_t i = 0; i < na; ++i)
       for (int64_t j = 0; j < nb; ++j) s += point_dist(A + i * d, B + j * d, d);
+    return s / ((double)na * (double)nb);
+  }
+  if (linkage == LK_AVG2) {
+    double s = 0.0;
+    for (int64_t i = 0; i < na; ++i)
+      for (int64_t j = 0; j < nb; ++j) s += point_dist2(A + i * d, B + j * d, d);
     return s / ((double)na * (double)nb);
   }
   if (linkage == LK_WARD) {
@@ -212,7 +222,7 @@ static void ms_merge(mstate *s, int64_t a, int64_t b) {
 }
 
 static int check_args(const double *X, int64_t n, int d, int linkage) {
-  if (!X || n < 1 || d < 1 || linkage < 0 || linkage > 2) return -1;
+  if (!X || n < 1 || d < 1 || linkage < 0 || linkage > 3) return -1;
   for (int64_t i = 0; i < n * d; ++i)
     if (!isfinite(X[i])) return -1;
   return 0;

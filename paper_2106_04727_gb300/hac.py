@@ -15,8 +15,8 @@ import numpy as np
 
 from . import build as _build
 
-COMPLETE, AVERAGE, WARD = 0, 1, 2
-LINKAGES = {"complete": COMPLETE, "average": AVERAGE, "ward": WARD}
+COMPLETE, AVERAGE, WARD, AVERAGE_SQ = 0, 1, 2, 3
+LINKAGES = {"complete": COMPLETE, "average": AVERAGE, "ward": WARD, "average_sq": AVERAGE_SQ}
 F32, F64 = 0, 1
 PREC_F64, PREC_F32_RECHECK = 0, 1
 

@@ -19,7 +19,7 @@ import oracle
 from paper_2106_04727_gb300 import inputs
 
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
-LKS = ["complete", "average", "ward"]
+LKS = ["complete", "average", "ward", "average_sq"]
 
 
 def _fig1():
@@ -78,7 +78,8 @@ def test_two_points(lk):
     for fn in (oracle.nnchain, oracle.rounds, oracle.greedy):
         d = fn(X, lk)
         assert list(d["a"]) == [0] and list(d["b"]) == [1] and list(d["size"]) == [2]
-        assert d["h"][0] == pytest.approx(5.0, rel=1e-15)
+        # avg-2 is the mean SQUARED distance (Table 1)
+        assert d["h"][0] == pytest.approx(25.0 if lk == "average_sq" else 5.0, rel=1e-15)
 
 
 @pytest.mark.parametrize("lk", LKS)
@@ -92,7 +93,9 @@ def test_collinear_equally_spaced(lk):
     """16 points 0, h, 2h, ...: ties everywhere; the (D, cid) key merges
     neighbours pairwise, then pairs of pairs, ... (a balanced tree).  Merging
     two blocks of s points at centroid spacing s*h gives complete (2s-1)h,
-    average s*h and Ward sqrt(2 s^2/(2s) (s h)^2) = s^1.5 h."""
+    average s*h, Ward sqrt(2 s^2/(2s) (s h)^2) = s^1.5 h and avg-2
+    (s h)^2 + 2 h^2 (s^2 - 1)/12 (squared centroid gap plus both blocks'
+    per-point variances)."""
     m, hsp = 16, 0.5
     X = np.zeros((m, 3))
     X[:, 1] = hsp * np.arange(m)
@@ -104,8 +107,10 @@ def test_collinear_equally_spaced(lk):
                 h = (2 * s - 1) * hsp
             elif lk == "average":
                 h = s * hsp
-            else:
+            elif lk == "ward":
                 h = s ** 1.5 * hsp
+            else:
+                h = (s * hsp) ** 2 + hsp ** 2 * (s * s - 1) / 6.0
             want[(start, start + s)] = (h, 2 * s)
         s *= 2
     for fn in (oracle.nnchain, oracle.rounds, oracle.greedy):
@@ -169,6 +174,21 @@ def test_lance_williams_complete_coefficients():
     for x, y in [(1.0, 2.0), (3.0, 0.5), (2.0, 2.0)]:
         lw = 0.5 * x + 0.5 * y + 0.5 * abs(x - y)
         assert oracle.lw("complete", x, y, 7.0, 3, 4, 5) == lw == max(x, y)
+
+
+def test_avg2_closed_form():
+    """Table 1: the mean squared distance between A and B equals the squared
+    centroid gap plus both clusters' per-point variances (computed here from
+    the points with numpy, not by the oracle)."""
+    rng = np.random.default_rng(16)
+    for _ in range(40):
+        A = rng.normal(size=(rng.integers(1, 9), 3)) * rng.uniform(0.2, 2)
+        B = rng.normal(size=(rng.integers(1, 9), 3)) + rng.normal(size=3) * 2
+        pv = lambda P: ((P - P.mean(0)) ** 2).sum(1).mean()
+        want = ((A.mean(0) - B.mean(0)) ** 2).sum() + pv(A) + pv(B)
+        assert oracle.cluster_dist("average_sq", A, B) == pytest.approx(want, rel=1e-12)
+        brute = np.mean([((x - y) ** 2).sum() for x in A for y in B])
+        assert oracle.cluster_dist("average_sq", A, B) == pytest.approx(brute, rel=1e-13)
 
 
 def test_centroid_lower_bound():
@@ -239,7 +259,7 @@ def test_lattice_complete_exact_ties():
             assert c["ok"], (seed, fn.__name__, c)
 
 
-@pytest.mark.parametrize("lk", ["average", "ward"])
+@pytest.mark.parametrize("lk", ["average", "ward", "average_sq"])
 def test_lattice_ties_validate(lk):
     """With exact real ties, average/Ward values from different rounding
     orders may break ties differently (and a different early choice changes
@@ -262,7 +282,8 @@ def test_validate_detects_planted_errors(lk):
     bad["h"][i] *= 1.01
     assert oracle.validate(X, lk, bad)[0] != 0
     # a tree built for another linkage is (generically) not valid for this one
-    other = oracle.nnchain(X, {"complete": "ward", "average": "complete", "ward": "average"}[lk])
+    other = oracle.nnchain(X, {"complete": "ward", "average": "complete", "ward": "average",
+                               "average_sq": "complete"}[lk])
     assert oracle.validate(X, lk, other)[0] != 0
 
 
@@ -285,8 +306,12 @@ def test_scipy_crosscheck():
     sch = pytest.importorskip("scipy.cluster.hierarchy")
     X = inputs.gaussian_mixture(200, 3, 5, seed=31).astype(np.float64)
     n = len(X)
+    from scipy.spatial.distance import pdist
     for lk in LKS:
-        Z = sch.linkage(X, method=lk)
+        if lk == "average_sq":  # average linkage on squared Euclidean distances
+            Z = sch.linkage(pdist(X, "sqeuclidean"), method="average")
+        else:
+            Z = sch.linkage(X, method=lk)
         cid = list(range(n))
         m = {}
         for i, (p, q, h, cnt) in enumerate(Z):
@@ -311,8 +336,10 @@ MUTANTS = {
                             "return (nb * dac + na * dbc) / (na + nb);"),
     "complete_min": ("return fmax(dac, dbc);", "return fmin(dac, dbc);"),
     "tie_prefers_larger_cid": ("if (best < 0 || v < bd) {", "if (best < 0 || v <= bd) {"),
-    "ward_not_squared": ("if (linkage == LK_WARD) return point_dist2(",
-                         "if (linkage == LK_WARD) return point_dist("),
+    "ward_not_squared": ("if (linkage == LK_WARD || linkage == LK_AVG2)",
+                         "if (linkage == LK_AVG2)"),
+    "avg2_not_squared": ("if (linkage == LK_WARD || linkage == LK_AVG2)",
+                         "if (linkage == LK_WARD)"),
 }
 
 
@@ -333,7 +360,7 @@ def test_pins_catch_mutants(mut, tmp_path):
     caught = False
     cases = list(_random_sets()) + [("dups", np.tile([[0.0, 1.0]], (5, 1))),
                                     ("collinear", np.c_[np.arange(8.0), np.zeros(8)])]
-    for lk, (name, X) in itertools.product(range(3), cases):
+    for lk, (name, X) in itertools.product(range(4), cases):
         X = np.ascontiguousarray(X, dtype=np.float64)
         n = len(X)
         a, b, h, s = (np.zeros(n - 1, np.int64), np.zeros(n - 1, np.int64),
