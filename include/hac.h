@@ -3,7 +3,8 @@
  *
  * The library computes the exact hierarchical agglomerative clustering
  * dendrogram of n points in d <= 16 dimensions under complete, average
- * (Euclidean, "avg-1") or Ward linkage (ParChain, arXiv 2106.04727, Table 1),
+ * (Euclidean, "avg-1"), Ward, or average linkage on squared Euclidean
+ * distances ("avg-2") (ParChain, arXiv 2106.04727, Table 1),
  * with the parallel nearest-neighbor-chain rounds of Algorithm 1: every round,
  * each terminal cluster finds its nearest active cluster (Algorithms 2-4,
  * range-pruned), all reciprocal-nearest-neighbor pairs merge at once, and the
@@ -48,7 +49,11 @@ extern "C" {
 
 typedef struct hac_ctx *hac_t; /* opaque; owns all device memory of one instance */
 
-typedef enum { HAC_COMPLETE = 0, HAC_AVERAGE = 1, HAC_WARD = 2 } hac_linkage;
+/* HAC_AVERAGE_SQ: average linkage with the squared Euclidean metric ("avg-2",
+ * Table 1): the mean squared point distance, reported as is (its heights are
+ * in squared units); computed in O(1) from centroids, per-point variances and
+ * sizes. */
+typedef enum { HAC_COMPLETE = 0, HAC_AVERAGE = 1, HAC_WARD = 2, HAC_AVERAGE_SQ = 3 } hac_linkage;
 typedef enum { HAC_F32 = 0, HAC_F64 = 1 } hac_dtype;
 typedef enum {
   HAC_PREC_F64 = 0,         /* every distance in FP64 */

@@ -36,7 +36,7 @@ namespace {
 
 constexpr int TPB = 256;
 
-enum { LK_COMPLETE = 0, LK_AVERAGE = 1, LK_WARD = 2 };
+enum { LK_COMPLETE = 0, LK_AVERAGE = 1, LK_WARD = 2, LK_AVG2 = 3 };
 
 __host__ __device__ inline int cdiv(long long a, long long b) { return (int)((a + b - 1) / b); }
 
@@ -273,6 +273,7 @@ __global__ void k_layout(State s, const T *X, const int32_t *perm, MortonParams 
       sq += x * x;
     }
     s.csq[i] = sq;
+    s.sse[i] = 0.0;
     s.qvar[p] = 0.f;
     s.qsz[p] = 1;
     s.qseg[p] = (int32_t)p;
@@ -452,6 +453,14 @@ __global__ void k_merge(State s, int round, int npairs) {
     s.m_size[m] = na + nb;
     s.m_round[m] = round;
     const double inv = 1.0 / (double)(na + nb);
+    // variance update (Section 2): SSE(A u B) = SSE(A) + SSE(B)
+    // + |A||B|/(|A|+|B|) ||c_A - c_B||^2, from the centroids before the merge
+    double g2 = 0.0;
+    for (int k = 0; k < dp; ++k) {
+      const double t = s.cent[(size_t)lo * dp + k] - s.cent[(size_t)hi * dp + k];
+      g2 += t * t;
+    }
+    s.sse[lo] = s.sse[lo] + s.sse[hi] + (double)na * (double)nb * inv * g2;
     for (int k = 0; k < dp; ++k) {
       const double sum = s.csum[(size_t)lo * dp + k] + s.csum[(size_t)hi * dp + k];
       s.csum[(size_t)lo * dp + k] = sum;
@@ -1301,9 +1310,13 @@ __global__ void k_cmp_top(State s, int nb) {
 }
 
 // Variance of cluster c (mean squared distance of its points to the
-// centroid) from the FP64 sums, rounded up with a margin that covers the
-// worst-case rounding of sums of sz terms: an upper bound for the search.
+// centroid).  Average linkage needs a rigorous upper bound: it comes from the
+// sums of squared norms with a margin covering the worst-case rounding of
+// sums of sz terms.  avg-2 needs the value its FP64 distances use (SSE / sz),
+// rounded up (the search's FP32 error bound covers the difference).
 __device__ float cluster_var_up(const State &s, int c, int sz) {
+  if (s.linkage == LK_AVG2) return __double2float_ru(s.sse[c] / (double)sz);
+  if (s.linkage != LK_AVERAGE) return 0.f;
   const int dp = s.dp;
   const double inv = 1.0 / (double)sz;
   double c2 = 0.0;
@@ -1496,6 +1509,7 @@ int alloc_state(hac_ctx *h) {
   A(s.qseg, n);
   A(s.csum, n * dp);
   A(s.csq, n);
+  A(s.sse, n);
   A(s.qvar, n);
   A(s.cent, n * dp);
   A(s.cent32, n * dp);
@@ -1757,7 +1771,8 @@ int create_common(const void *pts, bool dev, int64_t n, int d, hac_dtype dt, hac
   *out = nullptr;
   if (!pts || n < 1 || n > (int64_t)INT32_MAX / 2 || d < 1 || d > MAXD) return HAC_EINVAL;
   if (dt != HAC_F32 && dt != HAC_F64) return HAC_EINVAL;
-  if (lk != HAC_COMPLETE && lk != HAC_AVERAGE && lk != HAC_WARD) return HAC_EINVAL;
+  if (lk != HAC_COMPLETE && lk != HAC_AVERAGE && lk != HAC_WARD && lk != HAC_AVERAGE_SQ)
+    return HAC_EINVAL;
   const size_t esz = dt == HAC_F32 ? 4 : 8;
   if (!dev) {
     for (int64_t i = 0; i < n * d; ++i) {
@@ -1856,6 +1871,7 @@ void fill_query_args(hac_ctx *h, QueryArgs &qa, int round, int K, int nterm) {
   qa.qsz = s.qsz;
   qa.qseg = s.qseg;
   qa.qvar = s.qvar;
+  qa.sse = s.sse;
   qa.nclo = s.nclo;
   qa.nchi = s.nchi;
   qa.nhmin = s.nhmin;
@@ -1883,7 +1899,7 @@ void fill_query_args(hac_ctx *h, QueryArgs &qa, int round, int K, int nterm) {
   qa.ins_j = s.ins_j;
   qa.ins_v = s.ins_v;
   qa.ins_e = s.ins_e;
-  qa.defer = s.cache_slots > 0 && s.linkage != LK_WARD ? 1 : 0;
+  qa.defer = s.cache_slots > 0 && !closed_form(s.linkage) ? 1 : 0;
   qa.big_pairs = h->big_pairs;
   qa.big_pairs64 = h->big_pairs64;
   qa.warp_budget = h->warp_budget;
@@ -1918,7 +1934,7 @@ void fill_query_args(hac_ctx *h, QueryArgs &qa, int round, int K, int nterm) {
 int round_step(hac_ctx *h, cudaStream_t st, int round, int K, int nterm, RoundCtl &ctl,
                int *npairs_out) {
   State &s = h->s;
-  const bool need_points = s.linkage != LK_WARD;
+  const bool need_points = !closed_form(s.linkage);
   int rc = 0;
   s.cur = h->pcur;
   QueryArgs qa{};
@@ -2044,7 +2060,7 @@ int run_impl(hac_ctx *h, const hac_opts *o) {
   s.prec = opt.precision;
   h->done = false;
   // Section 5 cache tables (complete / average only: Ward distances are O(1))
-  const int slots = s.linkage == LK_WARD ? 0 : std::min(opt.cache_slots, CACHE_MAX_SLOTS);
+  const int slots = closed_form(s.linkage) ? 0 : std::min(opt.cache_slots, CACHE_MAX_SLOTS);
   if (slots > h->cache_alloc_slots) {
     int rc0 = 0;
     const size_t cells = (size_t)h->n * slots;
@@ -2232,7 +2248,7 @@ int run_impl(hac_ctx *h, const hac_opts *o) {
     const int64_t term_b = d * 4 + 2 * d * 4 + 4 + 8 + 4 + 16;
     int64_t qb = (int64_t)c.nodes * node_b + (int64_t)c.ltests * leaf_b +
                  h->st.nn_searches * term_b;
-    if (s.linkage == LK_WARD)
+    if (closed_form(s.linkage))
       qb += (int64_t)c.cluster_pairs * d * ew;
     else
       qb += (int64_t)c.prows * d * ew;
@@ -2414,6 +2430,7 @@ bool carve_state(hac_ctx &h, Carver &cv) {
   cv.take(&s.qseg, n);
   cv.take(&s.csum, n * dp);
   cv.take(&s.csq, n);
+  cv.take(&s.sse, n);
   cv.take(&s.qvar, n);
   cv.take(&s.cent, n * dp);
   cv.take(&s.cent32, n * dp);
@@ -2601,7 +2618,8 @@ extern "C" int hac_run_static(const void *dev_points, int64_t n, int d, hac_dtyp
   if (!dev_points || !dev_out || n < 1 || n > HAC_STATIC_MAX_N || d < 1 || d > MAXD)
     return HAC_EINVAL;
   if (dt != HAC_F32 && dt != HAC_F64) return HAC_EINVAL;
-  if (lk != HAC_COMPLETE && lk != HAC_AVERAGE && lk != HAC_WARD) return HAC_EINVAL;
+  if (lk != HAC_COMPLETE && lk != HAC_AVERAGE && lk != HAC_WARD && lk != HAC_AVERAGE_SQ)
+    return HAC_EINVAL;
   if (cap < n - 1) return HAC_ECAP;
   hac_opts opt;
   hac_default_opts(&opt);
@@ -2761,6 +2779,7 @@ __global__ void k_admit_layout(State s, const T *stage, int m, const AdmitInst *
       sq += x * x;
     }
     s.csq[c] = sq;
+    s.sse[c] = 0.0;
     s.qvar[op] = 0.f;
     s.plab[pc][pp] = c;
     s.seg[pc][c] = (int32_t)pp;
@@ -2914,7 +2933,7 @@ int engine_init(Engine &e, hac_linkage lk, int d, hac_dtype dt, int64_t cap, con
     return HAC_ENOMEM;
   }
   // Section 5 cache and the big-pair buffers, as hac_run allocates them
-  const int slots = lk == HAC_WARD ? 0 : std::min(opt.cache_slots, CACHE_MAX_SLOTS);
+  const int slots = closed_form((int)lk) ? 0 : std::min(opt.cache_slots, CACHE_MAX_SLOTS);
   if (slots > 0) {
     const size_t cells = (size_t)cap * slots;
     const int64_t icap = std::max<int64_t>(4 * cap, 1 << 16);
@@ -3018,7 +3037,7 @@ int engine_admit(Engine &e, const std::vector<SrvReq *> &batch) {
   CK(cudaGetLastError());
   const int sc = radix_sort(&h, m, 40 + bits_for(na), st);
   if (sc < 0) return sc;
-  const int ward = s.linkage == LK_WARD;
+  const int ward = closed_form(s.linkage);  // no points needed after admission
   int32_t *ord = s.order[h.ocur];
   if (f32)
     k_admit_layout<float><<<grid_for(m, TPB), TPB, 0, st>>>(
@@ -3118,7 +3137,7 @@ int engine_harvest(hac_server *srv, Engine &e, int ndone, const std::vector<int>
       e.active[slot] = nullptr;
       e.nres -= 1;
       e.completed += 1;
-      if (s.linkage != LK_WARD) e.P -= r->n;  // the re-layout left its points out
+      if (!closed_form(s.linkage)) e.P -= r->n;  // the re-layout left its points out
     }
     srv->done_cv.notify_all();
   }
@@ -3303,7 +3322,8 @@ int submit_impl(hac_server_t srv, const void *points, int64_t n, int d, hac_dtyp
   if (!srv || !points || !ticket || n < 1 || d < 1 || d > MAXD || !(timeout_s >= 0))
     return HAC_EINVAL;
   if (dt != HAC_F32 && dt != HAC_F64) return HAC_EINVAL;
-  if (lk != HAC_COMPLETE && lk != HAC_AVERAGE && lk != HAC_WARD) return HAC_EINVAL;
+  if (lk != HAC_COMPLETE && lk != HAC_AVERAGE && lk != HAC_WARD && lk != HAC_AVERAGE_SQ)
+    return HAC_EINVAL;
   if (n > srv->cap) return HAC_ENOMEM;
   const size_t esz = dt == HAC_F32 ? 4 : 8;
   for (int64_t i = 0; i < n * d; ++i) {

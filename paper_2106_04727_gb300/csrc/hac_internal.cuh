@@ -61,7 +61,9 @@ struct State {
   // per-cid cluster state
   int32_t *csize;
   double *csum;         // coordinate sums (FP64), n x dp
-  double *csq;          // sums of squared norms (FP64): the cluster's variance
+  double *csq;          // sums of squared norms (FP64): a rigorous variance bound
+  double *sse;          // sums of squared deviations from the centroid (FP64), merged
+                        // exactly as the paper's variance update: avg-2 distances
   double *cent;         // centroids (FP64), n x dp
   float *cent32;        // centroid rounded to FP32, n x dp
   float *blo, *bhi;     // point bounding box, rounded outward to FP32, n x dp
@@ -168,6 +170,7 @@ struct QueryArgs {
   const double *q64;
   const int32_t *qsz, *qseg;
   const float *qvar;
+  const double *sse;
   const float *nclo, *nchi, *nhmin, *nlmax;
   const int32_t *nnmin;
   int32_t lvl_base[MAXLEV + 1];
@@ -220,6 +223,10 @@ __host__ __device__ inline unsigned side_hash(int lo, int hi, int cap) {
 
 // error term stored with every cached FP32 estimate (0 marks an FP64 value)
 constexpr float EST_MARK = 1e-30f;
+
+// linkages whose cluster distance is O(1) from centroids, variances and
+// sizes (Ward, avg-2): no point pairs, no cache, no point re-layout
+__host__ __device__ inline bool closed_form(int linkage) { return linkage >= 2; }
 
 // number of tree levels for K active clusters (>= 1)
 __host__ __device__ inline int tree_levels(int K) {

@@ -58,7 +58,7 @@ constexpr long long SMALLP = 32;   // pairs of at most this many point pairs run
 constexpr float U32 = 5.9604645e-8f;  // 2^-24
 constexpr unsigned long long KINF = 0x7ff0000000000000ull;  // bits of +inf
 
-enum { LK_COMPLETE = 0, LK_AVERAGE = 1, LK_WARD = 2 };
+enum { LK_COMPLETE = 0, LK_AVERAGE = 1, LK_WARD = 2, LK_AVG2 = 3 };
 enum { M_F64 = 0, M_F32 = 1, M_RECHECK = 2 };
 
 __device__ __forceinline__ unsigned long long kbits(double k) {
@@ -124,7 +124,7 @@ template <int LK>
 __device__ __forceinline__ float key_dist_ru(unsigned long long kb) {
   if (kb >= KINF) return INFINITY;
   const float f = __double2float_ru(__longlong_as_double((long long)kb));
-  return LK == LK_WARD ? __fsqrt_ru(f) : f;
+  return LK == LK_WARD || LK == LK_AVG2 ? __fsqrt_ru(f) : f;  // squared-unit keys
 }
 
 // Squared distance from point c to box [lo, hi] (0 inside).
@@ -147,7 +147,8 @@ __device__ __forceinline__ float ward_w(float na, float nb) {
 // Lower bound on D(C_i, B) for every cluster B under a node, in D units.
 template <int LK, int DP>
 __device__ __forceinline__ float node_lb(const QueryArgs &a, int node, const float *ci32,
-                                         const float *alo, const float *ahi, float na) {
+                                         const float *alo, const float *ahi, float na,
+                                         float va) {
   float lo[DP], hi[DP];
 #pragma unroll
   for (int k = 0; k < DP; ++k) {
@@ -156,6 +157,8 @@ __device__ __forceinline__ float node_lb(const QueryArgs &a, int node, const flo
   }
   const float dc2 = box_d2<DP>(ci32, lo, hi);
   if (LK == LK_WARD) return sqrtf(ward_w(na, (float)a.nnmin[node]) * dc2);
+  // avg-2: D = ||c_A - c_B||^2 + var A + var B >= dc2 + var A
+  if (LK == LK_AVG2) return sqrtf(dc2 + va);
   float lb = sqrtf(dc2);
   if (LK == LK_COMPLETE) {
 #pragma unroll
@@ -449,7 +452,7 @@ struct Searcher {
       beta_d = INFINITY;
     } else {
       const float bkey = __uint_as_float((unsigned)(pv >> 32));
-      beta_d = LK == LK_WARD ? __fsqrt_ru(bkey) : bkey;
+      beta_d = LK == LK_WARD || LK == LK_AVG2 ? __fsqrt_ru(bkey) : bkey;
     }
     slack = a.islack[myinst] * (LK == LK_WARD ? sqrtf(2.f * fna) : 2.f);
     delta0 = 2.01f * U32 * a.iscale[myinst] * sqrtf((float)a.d);
@@ -458,7 +461,7 @@ struct Searcher {
     bc = INT_MAX;
     U = Ufix;
     Uv = INFINITY;
-    vA = LK == LK_AVERAGE ? a.qvar[a.pos[ci]] : 0.f;
+    vA = LK == LK_AVERAGE || LK == LK_AVG2 ? a.qvar[a.pos[ci]] : 0.f;
     L1 = L2 = INFINITY;
     c1 = INT_MAX;
     d1 = e1 = INFINITY;
@@ -624,12 +627,23 @@ struct Searcher {
     }
   }
 
-  __device__ unsigned long long ward64(int q, int nb) const {
+  // exact (FP64) key of a closed-form linkage: Ward from the centroids and
+  // sizes; avg-2 = ||c_A - c_B||^2 + SSE_A/|A| + SSE_B/|B| (Table 1)
+  __device__ unsigned long long ward64(int q, int nb, int cb) const {
     double cA[DP], cB[DP];
 #pragma unroll
     for (int k = 0; k < DP; ++k) {
       cA[k] = a.cent[(size_t)ci * DP + k];
       cB[k] = a.q64[(size_t)q * DP + k];
+    }
+    if (LK == LK_AVG2) {
+      double g2 = 0.0;
+#pragma unroll
+      for (int k = 0; k < DP; ++k) {
+        const double t = cA[k] - cB[k];
+        g2 += t * t;
+      }
+      return kbits(g2 + a.sse[ci] / (double)na + a.sse[cb] / (double)nb);
     }
     return kbits(ward_key<DP>(cA, cB, na, nb));
   }
@@ -654,10 +668,16 @@ struct Searcher {
       }
       ltests += 1;
     }
-    if (LK == LK_WARD) {
-      const float w = valid ? ward_w(fna, (float)nb) : 0.f;
-      const float d32 = valid ? sqrtf(w * dc2) : INFINITY;  // FP32 Ward distance
-      const float dlt = delta0 * sqrtf(w);
+    if (LK == LK_WARD || LK == LK_AVG2) {
+      float d32, dlt;  // FP32 distance (D units) and its absolute error term
+      if (LK == LK_WARD) {
+        const float w = valid ? ward_w(fna, (float)nb) : 0.f;
+        d32 = valid ? sqrtf(w * dc2) : INFINITY;
+        dlt = delta0 * sqrtf(w);
+      } else {
+        d32 = valid ? sqrtf(dc2 + vA + a.qvar[idx]) : INFINITY;
+        dlt = delta0;
+      }
       if (MODE == M_F32) {
         const bool has = valid && lower(d32, dlt) <= T;
         if (__any_sync(0xffffffffu, has)) {
@@ -678,7 +698,7 @@ struct Searcher {
         unsigned long long k = KINF;
         int c = INT_MAX;
         if (lane == who) {
-          k = ward64(idx, nb);
+          k = ward64(idx, nb, cb);
           c = cb;
         }
         cpairs += 1;
@@ -691,7 +711,7 @@ struct Searcher {
       unsigned long long k = KINF;
       int c = INT_MAX;
       if (ok) {
-        k = ward64(idx, nb);
+        k = ward64(idx, nb, cb);
         c = cb;
       }
       cpairs += __popc(m);
@@ -955,7 +975,7 @@ struct Searcher {
   // whose window held a single candidate
   __device__ unsigned long long exact_of(int q, int c) {
     const int nb = a.qsz[q];
-    if (LK == LK_WARD) return ward64(q, nb);
+    if (LK == LK_WARD || LK == LK_AVG2) return ward64(q, nb, c);
     double cv;
     float ce;
     const int hit = cache_get(c, nb, cv, ce);
@@ -1005,7 +1025,7 @@ __device__ void traverse(const QueryArgs &a, Searcher<LK, DP, MODE> &S, uint32_t
     if (child < cnt) {
       const int node = a.lvl_base[L - 1] + child;
       if (a.ninlo[node] <= S.myseq && S.myseq <= a.ninhi[node]) {
-        lbc = node_lb<LK, DP>(a, node, S.ci32, S.alo, S.ahi, S.fna);
+        lbc = node_lb<LK, DP>(a, node, S.ci32, S.alo, S.ahi, S.fna, S.vA);
         ok = S.pass(lbc);
       }
       S.nodes += 1;
@@ -1144,6 +1164,7 @@ cudaError_t launch_prec(const QueryArgs &a, int dp, cudaStream_t s) {
     case LK_COMPLETE: return launch_lk<LK_COMPLETE, PREC>(a, dp, s);
     case LK_AVERAGE: return launch_lk<LK_AVERAGE, PREC>(a, dp, s);
     case LK_WARD: return launch_lk<LK_WARD, PREC>(a, dp, s);
+    case LK_AVG2: return launch_lk<LK_AVG2, PREC>(a, dp, s);
   }
   return cudaErrorInvalidValue;
 }

@@ -75,8 +75,9 @@ def test_bad_enums_rejected():
     h = ctypes.c_void_p()
     assert lib.hac_create(X.ctypes.data_as(ctypes.c_void_p), 4, 2, 7, hac.WARD,
                           ctypes.byref(h)) == hac.HAC_EINVAL
-    assert lib.hac_create(X.ctypes.data_as(ctypes.c_void_p), 4, 2, hac.F64, 3,
-                          ctypes.byref(h)) == hac.HAC_EINVAL
+    for lk in (-1, 4):
+        assert lib.hac_create(X.ctypes.data_as(ctypes.c_void_p), 4, 2, hac.F64, lk,
+                              ctypes.byref(h)) == hac.HAC_EINVAL
 
 
 def test_null_handle_calls():

@@ -18,7 +18,7 @@ from paper_2106_04727_gb300 import hac, inputs
 
 pytestmark = pytest.mark.gpu
 
-LKS = ["complete", "average", "ward"]
+LKS = ["complete", "average", "ward", "average_sq"]
 PRECS = [hac.PREC_F64, hac.PREC_F32_RECHECK]
 PREC_IDS = ["f64", "f32recheck"]
 RTOL64 = 1e-9
@@ -36,7 +36,7 @@ def _round_sets(d):
 def _rtol(lk, prec):
     """FP64 heights everywhere except complete/average in FP32 mode, whose
     unambiguous winners keep their FP32 upper bound (<= 8e-6 relative)."""
-    return RTOL64 if prec == hac.PREC_F64 or lk == "ward" else RTOL32
+    return RTOL64 if prec == hac.PREC_F64 or lk in ("ward", "average_sq") else RTOL32
 
 
 def _assert_same(got, want, rtol=RTOL64, rounds=True):
@@ -109,7 +109,8 @@ def test_collinear_closed_form(lk):
     s = 1
     while s < m:
         for start in range(0, m, 2 * s):
-            want = {"complete": (2 * s - 1) * hsp, "average": s * hsp, "ward": s ** 1.5 * hsp}[lk]
+            want = {"complete": (2 * s - 1) * hsp, "average": s * hsp, "ward": s ** 1.5 * hsp,
+                    "average_sq": (s * hsp) ** 2 + hsp ** 2 * (s * s - 1) / 6.0}[lk]
             h, size = got[(start, start + s)]
             assert size == 2 * s and h == pytest.approx(want, rel=1e-12)
         s *= 2
@@ -125,7 +126,7 @@ def test_lattice_complete_exact_ties(prec):
 
 
 @pytest.mark.parametrize("prec", PRECS, ids=PREC_IDS)
-@pytest.mark.parametrize("lk", ["average", "ward"])
+@pytest.mark.parametrize("lk", ["average", "ward", "average_sq"])
 def test_lattice_ties_valid(lk, prec):
     X = inputs.lattice(300, 4, seed=7, levels=10)
     got = hac.cluster(X, lk, precision=prec)
@@ -153,7 +154,7 @@ def test_gmm5d_sample(lk, prec):
 
 
 @pytest.mark.parametrize("prec", PRECS, ids=PREC_IDS)
-@pytest.mark.parametrize("lk", ["average", "ward"])
+@pytest.mark.parametrize("lk", ["average", "ward", "average_sq"])
 def test_lattice16d_sample(lk, prec):
     """The 16-D lattice tie-stress recipe at oracle size: exact ties among
     singletons break by cid identically; later near-ties are checked by the
@@ -245,7 +246,7 @@ def _members_small(d, n, cap=64):
 
 
 @pytest.mark.parametrize("prec", PRECS, ids=PREC_IDS)
-@pytest.mark.parametrize("lk", ["ward"])
+@pytest.mark.parametrize("lk", ["ward", "average_sq"])
 def test_full_size_1m_properties(lk, prec):
     """The 10^6-point 5-D workload in the benchmark's launch configuration:
     a valid tree with monotone heights, and sampled merge heights equal to the
