@@ -139,6 +139,32 @@ def lattice(n: int, d: int, seed: int, levels: int = 1024, step: float = 1.0 / 2
     return np.ascontiguousarray((k * step).reshape(n, d).astype(dtype))
 
 
+def uniform_fill(n: int, d: int, seed: int, dtype=np.float32) -> np.ndarray:
+    """The paper's UniformFill shape (Section 6, data sets): n points uniform
+    in a hypergrid of side sqrt(n)."""
+    side = math.sqrt(n)
+    return np.ascontiguousarray((side * uniform(seed, 61, n * d)).reshape(n, d).astype(dtype))
+
+
+def gaussian_disc(n: int, d: int, seed: int, clusters: int = 5, frac: float = 0.9,
+                  dtype=np.float32) -> np.ndarray:
+    """The paper's GaussianDisc shape (Section 6, data sets): a hypergrid of
+    side 5 sqrt(n); 90% of the points split equally among five Gaussian
+    clusters with means uniform in the hypergrid and diameter sqrt(n) (read
+    as standard deviation sqrt(n) / 6 per axis, clipped to the hypergrid);
+    the other 10% uniform in the hypergrid.  Points are interleaved."""
+    side = 5.0 * math.sqrt(n)
+    sigma = math.sqrt(n) / 6.0
+    m = int(round(frac * n))
+    centers = side * uniform(seed, 62, clusters * d).reshape(clusters, d)
+    comp = np.arange(m) % clusters
+    pts = np.empty((n, d), dtype=np.float64)
+    pts[:m] = np.clip(centers[comp] + sigma * normal(seed, 63, m * d).reshape(m, d), 0.0, side)
+    pts[m:] = side * uniform(seed, 64, (n - m) * d).reshape(n - m, d)
+    perm = np.argsort(u64(seed, 65, n), kind="stable")
+    return np.ascontiguousarray(pts[perm].astype(dtype))
+
+
 # ----------------------------------------------------------------------------
 # Named workloads (sizes as the HAC benchmarks use them)
 # ----------------------------------------------------------------------------
@@ -152,6 +178,15 @@ WORKLOADS = {
     "spread2d_10m_f32": dict(kind="spreaders", n=10_000_000, seed=3000, dtype=np.float32),
     # 10^6 FP32 points on the 2^-8 lattice in [0,4)^16.
     "lattice16d_1m_f32": dict(kind="lattice", n=1_000_000, d=16, seed=5000, dtype=np.float32),
+    # the paper's synthetic shapes (2U/2G/5U/5G at 10^6 and 10^7 points)
+    "uniformfill2d_1m_f32": dict(kind="uniformfill", n=1_000_000, d=2, seed=6000),
+    "gaussiandisc2d_1m_f32": dict(kind="gaussiandisc", n=1_000_000, d=2, seed=6100),
+    "uniformfill5d_1m_f32": dict(kind="uniformfill", n=1_000_000, d=5, seed=6200),
+    "gaussiandisc5d_1m_f32": dict(kind="gaussiandisc", n=1_000_000, d=5, seed=6300),
+    "uniformfill2d_10m_f32": dict(kind="uniformfill", n=10_000_000, d=2, seed=6400),
+    "gaussiandisc2d_10m_f32": dict(kind="gaussiandisc", n=10_000_000, d=2, seed=6500),
+    "uniformfill5d_10m_f32": dict(kind="uniformfill", n=10_000_000, d=5, seed=6600),
+    "gaussiandisc5d_10m_f32": dict(kind="gaussiandisc", n=10_000_000, d=5, seed=6700),
 }
 
 
@@ -166,6 +201,10 @@ def make(kind: str, n: int, d: int = 2, seed: int = 0, k: int = 64,
         return spreaders(n, seed, dtype=dtype)
     if kind == "lattice":
         return lattice(n, d, seed, dtype=dtype)
+    if kind == "uniformfill":
+        return uniform_fill(n, d, seed, dtype=dtype)
+    if kind == "gaussiandisc":
+        return gaussian_disc(n, d, seed, dtype=dtype)
     raise ValueError(f"unknown workload kind {kind!r}")
 
 

@@ -310,3 +310,23 @@ def test_big_pair_deferral(lk, prec, slots, monkeypatch):
         X = inputs.gaussian_mixture(n, 4, 10, seed=seed)
         got = hac.cluster(X, lk, precision=prec, cache_slots=slots)
         _assert_same(got, oracle.rounds(X.astype(np.float64), lk), rtol=_rtol(lk, prec))
+
+
+_PAPER_ORACLE = {}
+
+
+@pytest.mark.parametrize("prec", PRECS, ids=PREC_IDS)
+@pytest.mark.parametrize("name", ["uniformfill2d_1m_f32", "gaussiandisc2d_1m_f32",
+                                  "uniformfill5d_1m_f32", "gaussiandisc5d_1m_f32"])
+def test_paper_shapes_sample(name, prec):
+    """The paper's UniformFill / GaussianDisc shapes at oracle size, every
+    linkage (the cache on for complete and average, as the bench runs them)."""
+    X = inputs.workload(name, n=3000)
+    X64 = X.astype(np.float64)
+    for lk in LKS:
+        key = (name, lk)
+        if key not in _PAPER_ORACLE:
+            _PAPER_ORACLE[key] = oracle.rounds(X64, lk)
+        slots = 64 if lk in ("complete", "average") else 0
+        _assert_same(hac.cluster(X, lk, precision=prec, cache_slots=slots), _PAPER_ORACLE[key],
+                     rtol=_rtol(lk, prec))
