@@ -332,6 +332,63 @@ def run_serving(args):
     print(json.dumps(line), flush=True)
 
 
+ABLATION_METRIC = "range-query ablation: time and distance evaluations, pruning on vs off"
+
+
+def run_ablation(args):
+    """The range query's effect (the paper's pruning-off comparison and its
+    D / naive-work statistics): each linkage clustered with the range query
+    and with every cluster as a candidate (HAC_FLAG_NO_PRUNE), on the paper's
+    GaussianDisc and UniformFill shapes at growing n."""
+    import numpy as np
+    import torch
+
+    from paper_2106_04727_gb300 import hac, inputs
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    if rank != 0:
+        return
+    prec = hac.PREC_F64 if args.precision == "f64" else hac.PREC_F32_RECHECK
+    rows = []
+    sizes = [int(x) for x in args.ablation_sizes.split(",")]
+    for shape in ("gaussiandisc2d_1m_f32", "uniformfill2d_1m_f32"):
+        for n in sizes:
+            X = inputs.workload(shape, n=n)
+            for lk in args.linkages:
+                slots = args.cache_slots if lk in ("complete", "average") else 0
+                r = {}
+                for mode, flag in (("pruned", False), ("all_pairs", True)):
+                    for _ in range(args.warmup if mode == "pruned" else 1):
+                        hac.cluster(X, lk, precision=prec, cache_slots=slots, no_prune=flag,
+                                    with_rounds=False)
+                    res = hac.cluster(X, lk, precision=prec, cache_slots=slots, no_prune=flag,
+                                      with_rounds=False)
+                    st = res["stats"]
+                    r[mode] = {"ms": st["ms_total"], "cluster_pairs": st["cluster_pairs"],
+                               "point_pairs": st["point_pairs"], "leaf_tests": st["leaf_tests"],
+                               "nodes": st["nodes_visited"]}
+                    r["naive_pairs"] = st["naive_pairs"]
+                    r["rounds"] = st["rounds"]
+                    r["_h"] = r.get("_h", []) + [res]
+                a, b = r.pop("_h")
+                same = bool(np.array_equal(a["a"], b["a"]) and np.array_equal(a["b"], b["b"]))
+                rows.append({"shape": shape.split("_")[0], "n": n, "linkage": lk, **r,
+                             "same_tree": same,
+                             "speedup": r["all_pairs"]["ms"] / r["pruned"]["ms"],
+                             "cluster_pair_fraction": r["pruned"]["cluster_pairs"] / r["naive_pairs"]})
+    top = [x["speedup"] for x in rows if x["n"] == max(sizes)]
+    line = {"metric": ABLATION_METRIC, "value": float(np.exp(np.mean(np.log(top)))),
+            "unit": "x (geometric-mean speedup of the range query at the largest n)",
+            "n_gpus": 1, "steps": 1, "warmup": args.warmup, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64" if prec == hac.PREC_F64 else "f32+f64", "data": "synthetic",
+            "config": {"workload": "ablation", "shapes": "GaussianDisc, UniformFill (2-D)",
+                       "sizes": sizes, "linkages": "+".join(args.linkages)},
+            "rows": rows}
+    print(json.dumps(line), flush=True)
+
+
 def run_serving_reference(args):
     """The oracle on the serving stream's small requests (host core)."""
     import numpy as np
@@ -383,6 +440,8 @@ def main():
     ap.add_argument("--requests", type=int, default=4096, help="serving: stream length")
     ap.add_argument("--sample", type=int, default=256,
                     help="serving: requests timed on the per-instance paths")
+    ap.add_argument("--ablation-sizes", default="5000,10000,20000,50000",
+                    help="ablation: point counts")
     ap.add_argument("--serving-cache-slots", type=int, default=64,
                     help="serving: cache slots per cluster (complete/average engines)")
     ap.add_argument("--engine-points", type=int, default=1 << 21,
@@ -390,6 +449,8 @@ def main():
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     args.linkages = [x for x in args.linkages.split(",") if x]
+    if args.workload == "ablation":
+        return run_ablation(args)
     if args.workload == "serving":
         if args.impl == "reference":
             return run_serving_reference(args)

@@ -81,7 +81,14 @@ typedef struct {
   int64_t max_rounds; /* 0 = unlimited; else HAC_ETIMEOUT after this many rounds */
   double timeout_s;   /* 0 = none; else HAC_ETIMEOUT once exceeded (checked per round) */
   void *stream;       /* cudaStream_t to run on; NULL = the handle's own stream */
+  int flags;          /* HAC_FLAG_* bits; 0 = none */
 } hac_opts;
+
+/* Range-query ablation: every active cluster of the instance is a candidate
+ * of every search (the pruning of Algorithms 2-3 and the summary upper bounds
+ * are off).  Same dendrogram, much more work; for measuring what the range
+ * query saves (hac_stats: cluster_pairs, point_pairs vs naive_pairs). */
+#define HAC_FLAG_NO_PRUNE 1
 
 typedef struct {
   int64_t rounds;            /* rounds of Algorithm 1 executed */
@@ -110,6 +117,9 @@ typedef struct {
   double ms_big;             /* device time of the GPU-wide big-pair evaluation kernels */
   int64_t big_point_pairs;   /* point pairs evaluated by those kernels (also in point_pairs) */
   int64_t big_launches;      /* launches of those kernels */
+  int64_t naive_pairs;       /* cluster pairs a search without range queries would
+                                evaluate: terminals x (active clusters - 1), summed
+                                over rounds */
 } hac_stats_t;
 
 /* Default options (FP64, no cache, no limits, own stream). */

@@ -1903,6 +1903,7 @@ void fill_query_args(hac_ctx *h, QueryArgs &qa, int round, int K, int nterm) {
   qa.big_pairs = h->big_pairs;
   qa.big_pairs64 = h->big_pairs64;
   qa.warp_budget = h->warp_budget;
+  qa.noprune = s.noprune;
   qa.side_cap = s.side_cap;
   qa.side_key = s.side_key;
   qa.side_val = s.side_val;
@@ -2058,6 +2059,7 @@ int run_impl(hac_ctx *h, const hac_opts *o) {
   cudaStream_t st = opt.stream ? (cudaStream_t)opt.stream : h->own;
   State &s = h->s;
   s.prec = opt.precision;
+  s.noprune = (opt.flags & HAC_FLAG_NO_PRUNE) ? 1 : 0;
   h->done = false;
   // Section 5 cache tables (complete / average only: Ward distances are O(1))
   const int slots = closed_form(s.linkage) ? 0 : std::min(opt.cache_slots, CACHE_MAX_SLOTS);
@@ -2113,6 +2115,7 @@ int run_impl(hac_ctx *h, const hac_opts *o) {
     ms_init = ms;
   }
   int K = (int)h->n, nterm = (int)h->n, round = 0;
+  int64_t naive = 0;  // cluster pairs a search without range queries would test
   Counters c{}, cprev{};
   const char *tr = getenv("HAC_TRACE");
   const bool trace = tr && tr[0] && tr[0] != '0';
@@ -2131,6 +2134,7 @@ int run_impl(hac_ctx *h, const hac_opts *o) {
       return HAC_ETIMEOUT;
     cudaEventRecord(e0.e, st);
     const int big_iters0 = ctl.big_iters, big_reqs0 = ctl.big_reqs;
+    naive += (int64_t)nterm * (K - 1);
     int npairs = 0;
     rc = round_step(h, st, round, K, nterm, ctl, &npairs);
     if (rc == HAC_EINTERNAL && npairs <= 0) {
@@ -2192,6 +2196,7 @@ int run_impl(hac_ctx *h, const hac_opts *o) {
   qlaunch = ctl.qlaunch;
   big_launch = ctl.big_launch;
   h->st.nn_searches = ctl.searches;
+  h->st.naive_pairs = naive;
   CK(cudaMemcpyAsync(&c, s.ctr, sizeof(Counters), cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
   const int64_t m = h->n - 1;
@@ -2277,6 +2282,7 @@ void hac_default_opts(hac_opts *o) {
   o->max_rounds = 0;
   o->timeout_s = 0.0;
   o->stream = nullptr;
+  o->flags = 0;
 }
 
 int hac_create(const void *points, int64_t n, int d, hac_dtype dt, hac_linkage lk, hac_t *out) {

@@ -81,6 +81,7 @@ struct State {
   // neighbour cid << 32 | neighbour generation; value = distance (D units)
   // and its absolute error bound (0 for FP64 values)
   int cache_slots;
+  int noprune;          // range-query ablation (HAC_FLAG_NO_PRUNE)
   unsigned long long *ckey;
   double *cval;
   float *cerr;
@@ -194,6 +195,7 @@ struct QueryArgs {
   int defer;
   long long big_pairs, big_pairs64;
   long long warp_budget;  // point pairs a search evaluates itself before deferring more
+  int noprune;            // ablation: every cluster of the instance is a candidate
   int side_cap;
   const unsigned long long *side_key;
   const double *side_val;

@@ -585,7 +585,7 @@ struct Searcher {
     }
   }
 
-  __device__ bool pass(float lb) const { return lb <= T; }
+  __device__ bool pass(float lb) const { return lb <= T || a.noprune; }
 
   __device__ float lower(float d32, float dlt) const { return fmaxf(d32 - dlt, 0.f) * (1.f - rho); }
 
@@ -679,7 +679,7 @@ struct Searcher {
         dlt = delta0;
       }
       if (MODE == M_F32) {
-        const bool has = valid && lower(d32, dlt) <= T;
+        const bool has = valid && (lower(d32, dlt) <= T || a.noprune);
         if (__any_sync(0xffffffffu, has)) {
           cpairs += __popc(__ballot_sync(0xffffffffu, has));
           offer_f32(has, d32, dlt, cb);

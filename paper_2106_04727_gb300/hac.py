@@ -33,7 +33,7 @@ class hac_merge(ctypes.Structure):
 class hac_opts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("cache_slots", ctypes.c_int),
                 ("max_rounds", ctypes.c_int64), ("timeout_s", ctypes.c_double),
-                ("stream", ctypes.c_void_p)]
+                ("stream", ctypes.c_void_p), ("flags", ctypes.c_int)]
 
 
 class hac_stats_t(ctypes.Structure):
@@ -46,7 +46,7 @@ class hac_stats_t(ctypes.Structure):
                                               "kernel_launches", "cache_hits",
                                               "cache_lw_entries")] + \
                [("ms_big", ctypes.c_double), ("big_point_pairs", ctypes.c_int64),
-                ("big_launches", ctypes.c_int64)]
+                ("big_launches", ctypes.c_int64), ("naive_pairs", ctypes.c_int64)]
 
 
 class hac_server_stats_t(ctypes.Structure):
@@ -165,12 +165,17 @@ def hac_create_device(dev_ptr: int, n: int, d: int, dtype, linkage) -> ctypes.c_
     return h
 
 
+HAC_FLAG_NO_PRUNE = 1
+
+
 def hac_run(h, precision: int = PREC_F64, cache_slots: int = 0, max_rounds: int = 0,
-            timeout_s: float = 0.0, stream: int | None = None) -> int:
-    """hac_run; returns the status code (raises on device/internal errors)."""
+            timeout_s: float = 0.0, stream: int | None = None, no_prune: bool = False) -> int:
+    """hac_run; returns the status code (raises on device/internal errors).
+    ``no_prune`` sets HAC_FLAG_NO_PRUNE (the range-query ablation)."""
     o = hac_default_opts()
     o.precision, o.cache_slots, o.max_rounds, o.timeout_s = precision, cache_slots, max_rounds, timeout_s
     o.stream = stream
+    o.flags = HAC_FLAG_NO_PRUNE if no_prune else 0
     rc = load().hac_run(h, ctypes.byref(o))
     if rc in (HAC_EDEVICE, HAC_EINTERNAL):
         raise HacError(rc, "hac_run")

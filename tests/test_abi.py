@@ -34,7 +34,7 @@ def test_library_exports_every_declared_symbol():
 
 def test_struct_layouts_match_header():
     assert ctypes.sizeof(hac.hac_merge) == 32
-    assert ctypes.sizeof(hac.hac_opts) == 32
+    assert ctypes.sizeof(hac.hac_opts) == 40
     assert hac.MERGE_DTYPE.itemsize == 32
 
 

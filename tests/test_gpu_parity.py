@@ -330,3 +330,20 @@ def test_paper_shapes_sample(name, prec):
         slots = 64 if lk in ("complete", "average") else 0
         _assert_same(hac.cluster(X, lk, precision=prec, cache_slots=slots), _PAPER_ORACLE[key],
                      rtol=_rtol(lk, prec))
+
+
+@pytest.mark.parametrize("lk", LKS)
+def test_no_prune_ablation_same_tree(lk):
+    """HAC_FLAG_NO_PRUNE makes every cluster a candidate: the same tree, and
+    the range query is what keeps the evaluations far below the naive count."""
+    X = inputs.workload("gaussiandisc2d_1m_f32", n=2500)
+    slots = 64 if lk in ("complete", "average") else 0
+    a = hac.cluster(X, lk, precision=hac.PREC_F32_RECHECK, cache_slots=slots)
+    b = hac.cluster(X, lk, precision=hac.PREC_F32_RECHECK, cache_slots=slots, no_prune=True)
+    want = oracle.rounds(X.astype(np.float64), lk)
+    _assert_same(a, want, rtol=_rtol(lk, hac.PREC_F32_RECHECK))
+    _assert_same(b, want, rtol=_rtol(lk, hac.PREC_F32_RECHECK))
+    naive = a["stats"]["naive_pairs"]
+    assert naive == b["stats"]["naive_pairs"] > 0
+    assert b["stats"]["leaf_tests"] >= a["stats"]["leaf_tests"]
+    assert a["stats"]["cluster_pairs"] < 0.2 * naive
