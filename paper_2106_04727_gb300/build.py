@@ -65,7 +65,7 @@ def build(force: bool = False, verbose: bool = False, ptxas_v: bool = False) -> 
             sys.stderr.write(r.stdout + r.stderr)
         return obj
 
-    with ThreadPoolExecutor(max_workers=max(1, min(8, len(sources())))) as ex:
+    with ThreadPoolExecutor(max_workers=max(1, min(16, os.cpu_count() or 1, len(sources())))) as ex:
         objs = list(ex.map(compile_one, sources()))
     tmp = LIB + f".{os.getpid()}.tmp"
     r = subprocess.run([nv, *ARCH, "-shared", "-o", tmp, *objs],
