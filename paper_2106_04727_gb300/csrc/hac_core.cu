@@ -1285,24 +1285,26 @@ int round_step(hac_ctx *h, cudaStream_t st, int round, int K, int nterm, RoundCt
       cudaEventElapsedTime(&q, ctl.eq0, ctl.eq1);
       ctl.ms_query += q;
     }
+    // the batches of one pass run back to back; their device time (with
+    // the small scheduling and folding kernels) is read once per pass
+    EVREC(ctl.eb0);
     for (int r0 = 0; r0 < nreq; r0 += BIG_BATCH) {
       const int m = std::min(BIG_BATCH, nreq - r0);
       rc = big_prepare(s, r0, m, st);
       if (rc) return rc;
-      EVREC(ctl.eb0);
       rc = launch_big(s, r0, st);
-      EVREC(ctl.eb1);
       if (rc) return rc;
       ctl.big_launch += 3;  // kinds 0 and 1 (FP32), FP64
-      if (ctl.eb0) {
-        CK(cudaEventSynchronize(ctl.eb1));
-        float bms;
-        cudaEventElapsedTime(&bms, ctl.eb0, ctl.eb1);
-        ctl.ms_big += bms;
-      }
       rc = big_finish(s, r0, m, st);
       if (rc) return rc;
       h->launches += 6;
+    }
+    EVREC(ctl.eb1);
+    if (ctl.eb0) {
+      CK(cudaEventSynchronize(ctl.eb1));
+      float bms;
+      cudaEventElapsedTime(&bms, ctl.eb0, ctl.eb1);
+      ctl.ms_big += bms;
     }
     CK(cudaMemsetAsync(&s.ctr->nbreq, 0, 2 * sizeof(int32_t), st));
     ctl.searches += npend;

@@ -74,7 +74,7 @@ __device__ inline void cache_insert(const State &s, int owner, int nbr, int nbr_
 constexpr int BIG_TPB = 256;       // threads per tile
 constexpr int BIG_TILE = BIG_TPB * 2;  // narrowest tile along the larger cluster
 constexpr int BIG_MAXT = 32768; // tiles per request at most (chunks widen to fit)
-constexpr int BIG_BATCH = 512;     // requests per batch (one scan block)
+constexpr int BIG_BATCH = 1024;    // requests per batch (one scan block of 32 warps)
 
 // Three kinds of request, each its own tile list and kernel:
 //   0  FP32, larger cluster >= 256 x 8 points: 8 of its points per thread
