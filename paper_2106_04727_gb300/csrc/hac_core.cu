@@ -942,6 +942,7 @@ int alloc_state(hac_ctx *h) {
   A(s.Ekey, n);
   A(s.Ecid, n);
   A(s.term, n);
+  A(s.blist, n);
   A(s.pair_lo, n / 2 + 1);
   A(s.pair_hi, n / 2 + 1);
   A(s.pair_key, n / 2 + 1);
@@ -1118,6 +1119,7 @@ int create_common(const void *pts, bool dev, int64_t n, int d, hac_dtype dt, hac
   if (const char *e = getenv("HAC_BIG_PAIRS")) h->big_pairs = std::max(1ll, atoll(e));
   if (const char *e = getenv("HAC_BIG_PAIRS_F64")) h->big_pairs64 = std::max(1ll, atoll(e));
   if (const char *e = getenv("HAC_WARP_BUDGET")) h->warp_budget = std::max(1ll, atoll(e));
+  if (const char *e = getenv("HAC_BRUTE")) h->brute_env = atoi(e) ? 1 : 0;
   if (cudaStreamCreateWithFlags(&h->own, cudaStreamNonBlocking) != cudaSuccess) {
     cudaGetLastError();
     delete h;
@@ -1242,6 +1244,16 @@ void fill_query_args(hac_ctx *h, QueryArgs &qa, int round, int K, int nterm) {
     if (ev) cudaEventRecord(ev, st); \
   } while (0)
 
+// Exhaustive tiled search instead of the tree: closed-form linkages in the
+// FP32 mode, one instance, and d > 8 (where the tree prunes little);
+// HAC_BRUTE=0 / 1 turns it off / on for any row stride of 8 or 16.
+bool use_brute(const hac_ctx *h) {
+  const State &s = h->s;
+  if (!closed_form(s.linkage) || s.prec != HAC_PREC_F32_RECHECK || s.max_inst != 1) return false;
+  if (h->brute_env >= 0) return h->brute_env == 1 && (s.dp == 8 || s.dp == 16);
+  return s.dp == 16;
+}
+
 // One round of Algorithm 1 over the current terminal list: the searches (with
 // big pairs handed to the whole GPU and the deferring searches re-run), the
 // chain update, the R-NN filter, the merges, the cache update, the compaction
@@ -1258,8 +1270,16 @@ int round_step(hac_ctx *h, cudaStream_t st, int round, int K, int nterm, RoundCt
   const bool defer = qa.defer != 0;
   if (defer)
     CK(cudaMemsetAsync(s.side_key, 0xff, (size_t)s.side_cap * sizeof(unsigned long long), st));
+  const bool brute = use_brute(h);
+  if (brute) {
+    CK(cudaMemsetAsync(&s.ctr->npend, 0, sizeof(int32_t), st));
+    qa.pend_out = s.blist;
+  }
   EVREC(ctl.eq0);
-  CK(launch_query(qa, s.dp, s.prec, st));
+  if (brute)
+    CK(launch_brute(qa, s.dp, st));
+  else
+    CK(launch_query(qa, s.dp, s.prec, st));
   EVREC(ctl.eq1);
   ++ctl.qlaunch;
   ctl.searches += nterm;
@@ -1785,6 +1805,7 @@ bool carve_state(hac_ctx &h, Carver &cv) {
   cv.take(&s.pos, n);
   cv.take(&s.Ekey, n);
   cv.take(&s.Ecid, n);
+  cv.take(&s.blist, n);
   cv.take(&s.term, n);
   cv.take(&s.pair_lo, n / 2 + 1);
   cv.take(&s.pair_hi, n / 2 + 1);

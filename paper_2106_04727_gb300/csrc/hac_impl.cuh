@@ -140,6 +140,7 @@ struct hac_ctx {
   // (FP32 / FP64 values); HAC_BIG_PAIRS / HAC_BIG_PAIRS_F64 override them
   long long big_pairs = hacg::BIG_PAIRS, big_pairs64 = hacg::BIG_PAIRS_F64;
   long long warp_budget = hacg::WARP_BUDGET;  // HAC_WARP_BUDGET overrides it
+  int brute_env = -1;   // HAC_BRUTE: -1 unset, 0 never, 1 whenever allowed
   int64_t launches = 0;  // kernels launched in the current run
   int ocur = 0, pcur = 0;
   bool done = false;

@@ -142,6 +142,7 @@ struct State {
   // lists
   int32_t *order[2];    // active cids in spatial order
   int32_t *term;        // terminal cids
+  int32_t *blist;       // terminals left to the FP64 re-score of the exhaustive search
   int32_t *pair_lo, *pair_hi;
   double *pair_key;
   // dendrogram records
@@ -248,5 +249,9 @@ __host__ __device__ inline int level_count(int K, int L) {
 
 // launches the nearest-neighbour query of every terminal (hac_query.cu)
 cudaError_t launch_query(const QueryArgs &a, int dp, int prec, cudaStream_t s);
+// the same search done exhaustively with tiles of cluster records staged in
+// shared memory (hac_brute.cu): closed-form linkages, FP32 + FP64 re-score,
+// one instance; uses pend_out (nterm entries) and ctr->npend (zeroed first)
+cudaError_t launch_brute(const QueryArgs &a, int dp, cudaStream_t s);
 
 }  // namespace hacg

@@ -347,3 +347,18 @@ def test_no_prune_ablation_same_tree(lk):
     assert naive == b["stats"]["naive_pairs"] > 0
     assert b["stats"]["leaf_tests"] >= a["stats"]["leaf_tests"]
     assert a["stats"]["cluster_pairs"] < 0.2 * naive
+
+
+@pytest.mark.parametrize("lk", ["ward", "average_sq"])
+@pytest.mark.parametrize("shape", [(4000, 5), (3000, 10), (2500, 16)], ids=lambda s: f"n{s[0]}d{s[1]}")
+def test_exhaustive_search_matches(lk, shape, monkeypatch):
+    """The tiled exhaustive search (on by default for d > 8 in the FP32 mode,
+    forced here for d = 5 too) gives the oracle's tree."""
+    monkeypatch.setenv("HAC_BRUTE", "1")
+    n, d = shape
+    X = inputs.gaussian_mixture(n, d, 7, seed=n + d)
+    got = hac.cluster(X, lk, precision=hac.PREC_F32_RECHECK)
+    _assert_same(got, oracle.rounds(X.astype(np.float64), lk), rtol=RTOL64)
+    st = got["stats"]
+    assert st["nodes_visited"] == 0          # no tree traversal
+    assert st["leaf_tests"] >= st["naive_pairs"]  # every cluster scanned per terminal
