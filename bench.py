@@ -34,12 +34,12 @@ SMS, FP32_LANES = 152, 128   # GB300: SMs and FP32 lanes per SM
 
 # DRAM bytes (read + write) per launch, from one ncu capture of this bench's
 # command (profiles/launches_gmm5d_1m_ward_average.md); valid for the kernels
-# as captured.  Big pairs: one batch launches three evaluation kernels
-# (4.825 + 4.852 + 0.053 MB), the entry is the mean per launch; the search:
-# 628 average + 256 Ward launches.
+# and batching as captured.  Big pairs: one batch launches three evaluation
+# kernels (6.229 + 5.569 + 0.067 MB), the entry is the mean per launch; the
+# search: 628 average + 256 Ward launches.
 TRAFFIC = {
-    ("k_big_eval32", "gmm5d_1m_f32"): 9.730e6 / 3,
-    ("k_query", "gmm5d_1m_f32"): (628 * 30.419e6 + 256 * 27.290e6) / 884,
+    ("k_big_eval32", "gmm5d_1m_f32"): 11.865e6 / 3,
+    ("k_query", "gmm5d_1m_f32"): (628 * 30.481e6 + 256 * 27.348e6) / 884,
 }
 
 
