@@ -389,6 +389,39 @@ def run_ablation(args):
     print(json.dumps(line), flush=True)
 
 
+def run_ablation_reference(args):
+    """The oracle on the ablation's smallest samples (host core): its NN-chain
+    over the full distance matrix is the no-range-query baseline of the CPU."""
+    import numpy as np
+
+    import oracle
+    from paper_2106_04727_gb300 import inputs
+
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    n = int(args.ablation_sizes.split(",")[0])
+    rows, tot = [], 0.0
+    for shape in ("gaussiandisc2d_1m_f32", "uniformfill2d_1m_f32"):
+        X = inputs.workload(shape, n=n).astype(np.float64)
+        for lk in args.linkages:
+            t0 = time.perf_counter()
+            oracle.nnchain(X, lk)
+            dt = time.perf_counter() - t0
+            tot += dt
+            rows.append({"shape": shape.split("_")[0], "n": n, "linkage": lk, "ms": 1e3 * dt})
+    v = len(rows) / tot
+    print(json.dumps({
+        "metric": ABLATION_METRIC, "value": v, "unit": "clusterings/s", "n_gpus": args.gpus,
+        "steps": 1, "warmup": 0, "ms_per_step": 1e3 * tot, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "impl": "reference", "config": {"workload": "ablation", "sizes": [n]}, "rows": rows,
+        "cpu_baseline": {"kind": "oracle", "cores": 1, "value": v, "unit": "clusterings/s",
+                         "sample": f"{len(rows)} clusterings of {n} points"},
+        "e2e": {"value": v, "unit": "clusterings/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0}}), flush=True)
+
+
 def run_serving_reference(args):
     """The oracle on the serving stream's small requests (host core)."""
     import numpy as np
@@ -450,6 +483,8 @@ def main():
     args.warmup = max(args.warmup, 3)
     args.linkages = [x for x in args.linkages.split(",") if x]
     if args.workload == "ablation":
+        if args.impl == "reference":
+            return run_ablation_reference(args)
         return run_ablation(args)
     if args.workload == "serving":
         if args.impl == "reference":

@@ -236,3 +236,46 @@ def test_run_batch_matches_hac_run(prec, slots):
     finally:
         for h in hs:
             hac.hac_destroy(h)
+
+
+def test_poll_capacity_cancel_after_done_and_bad_arguments():
+    X = inputs.gaussian_mixture(500, 3, 4, seed=61).astype(np.float64)
+    srv = hac.hac_server_create(4096)
+    try:
+        t = hac.hac_submit(srv, X, hac.AVERAGE_SQ)
+        assert hac.hac_server_wait(srv, t, 120.0) == hac.HAC_OK
+        # too small an output buffer keeps the ticket
+        out = np.zeros(10, dtype=hac.MERGE_DTYPE)
+        import ctypes
+        got = ctypes.c_int64()
+        rc = hac.load().hac_poll(srv, t, ctypes.c_void_p(out.ctypes.data), 10, ctypes.byref(got),
+                                 None)
+        assert rc == hac.HAC_ECAP
+        # cancelling a finished request keeps its result
+        assert hac.hac_cancel(srv, t) == hac.HAC_OK
+        rc, m, lat = hac.hac_poll(srv, t, len(X))
+        assert rc == hac.HAC_OK and len(m) == len(X) - 1
+        c = oracle.compare(hac.result_dict(m), oracle.nnchain(X, "average_sq"), rtol=RTOL64)
+        assert c["ok"], c
+        # unknown tickets and bad arguments
+        assert hac.hac_cancel(srv, 987654) == hac.HAC_EINVAL
+        assert hac.hac_server_wait(srv, 987654, 0.1) == hac.HAC_EINVAL
+        with pytest.raises(hac.HacError) as e:
+            hac.hac_submit(srv, np.zeros((4, 17)), hac.WARD)  # d > 16
+        assert e.value.code == hac.HAC_EINVAL
+        with pytest.raises(hac.HacError) as e:
+            hac.hac_submit(srv, X, 9)  # unknown linkage
+        assert e.value.code == hac.HAC_EINVAL
+        st = hac.hac_server_stats(srv)
+        assert st["status"] == hac.HAC_OK and st["queued"] == 0 and st["resident"] == 0
+    finally:
+        hac.hac_server_destroy(srv)
+
+
+def test_server_rejects_bad_options():
+    import ctypes
+    o = hac.hac_default_opts()
+    o.precision = 7
+    srv = ctypes.c_void_p()
+    assert hac.load().hac_server_create(1024, ctypes.byref(o), ctypes.byref(srv)) == hac.HAC_EINVAL
+    assert hac.load().hac_server_create(1, None, ctypes.byref(srv)) == hac.HAC_EINVAL
