@@ -115,7 +115,9 @@ typedef struct {
   int64_t cache_hits;        /* pair distances taken from the cache instead of evaluated */
   int64_t cache_lw_entries;  /* cache entries derived by Lance-Williams after merges */
   double ms_big;             /* device time of the GPU-wide big-pair evaluation kernels */
-  int64_t big_point_pairs;   /* point pairs evaluated by those kernels (also in point_pairs) */
+  int64_t big_point_pairs;   /* point pairs evaluated by those kernels (also in point_pairs);
+                                complete linkage skips chunks whose box bound cannot raise
+                                the maximum, and those pairs are not counted */
   int64_t big_launches;      /* launches of those kernels */
   int64_t naive_pairs;       /* cluster pairs a search without range queries would
                                 evaluate: terminals x (active clusters - 1), summed

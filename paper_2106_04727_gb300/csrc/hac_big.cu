@@ -67,6 +67,7 @@ __global__ void k_big_tiles(State s, int r0, int m) {
   if (t < m) {
     s.bsched[t] = kind >= 0 ? start : 0;
     s.bsched[BS_B + t] = tiles;
+    s.bmax2[t] = 0;  // +0.0f
   }
 }
 

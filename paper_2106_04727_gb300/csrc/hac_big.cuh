@@ -185,10 +185,77 @@ __device__ __forceinline__ void big32_chunk(const unsigned long long *sh, int cn
   }
 }
 
+__device__ __forceinline__ float warp_maxf_big(float v) {
+#pragma unroll
+  for (int o = 16; o; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+
+// per-dimension box of the valid points a warp holds (every lane gets it)
+template <int D, int NP>
+__device__ __forceinline__ void warp_box(const unsigned long long (&x)[NP][D],
+                                         const bool (&v)[2 * NP], float (&lo)[D],
+                                         float (&hi)[D]) {
+#pragma unroll
+  for (int k = 0; k < D; ++k) {
+    lo[k] = INFINITY;
+    hi[k] = -INFINITY;
+#pragma unroll
+    for (int h = 0; h < NP; ++h) {
+      float a, b;
+      f2_unpack(x[h][k], a, b);
+      if (v[2 * h]) {
+        lo[k] = fminf(lo[k], a);
+        hi[k] = fmaxf(hi[k], a);
+      }
+      if (v[2 * h + 1]) {
+        lo[k] = fminf(lo[k], b);
+        hi[k] = fmaxf(hi[k], b);
+      }
+    }
+#pragma unroll
+    for (int o = 16; o; o >>= 1) {
+      lo[k] = fminf(lo[k], __shfl_xor_sync(0xffffffffu, lo[k], o));
+      hi[k] = fmaxf(hi[k], __shfl_xor_sync(0xffffffffu, hi[k], o));
+    }
+  }
+}
+
+// block-wide box of per-thread boxes into out[0, D) (lo) and out[D, 2D)
+// (hi); the caller synchronises before reading it
+template <int D>
+__device__ __forceinline__ void block_box(float (&lo)[D], float (&hi)[D], float *out) {
+  __shared__ float wb[BIG_TPB / 32][2 * D];
+#pragma unroll
+  for (int k = 0; k < D; ++k) {
+#pragma unroll
+    for (int o = 16; o; o >>= 1) {
+      lo[k] = fminf(lo[k], __shfl_xor_sync(0xffffffffu, lo[k], o));
+      hi[k] = fmaxf(hi[k], __shfl_xor_sync(0xffffffffu, hi[k], o));
+    }
+  }
+  const int w = threadIdx.x >> 5;
+  if ((threadIdx.x & 31) == 0) {
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+      wb[w][k] = lo[k];
+      wb[w][D + k] = hi[k];
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x < 2 * D) {
+    const int k = threadIdx.x;
+    float m = wb[0][k];
+    for (int i = 1; i < BIG_TPB / 32; ++i) m = k < D ? fminf(m, wb[i][k]) : fmaxf(m, wb[i][k]);
+    out[k] = m;
+  }
+}
+
 template <int LK, int D, int DP, int KIND>
 __global__ void __launch_bounds__(BIG_TPB) k_big_eval32(State s, int r0) {
   constexpr int PPT = KIND == 0 ? (D <= 8 ? 8 : 4) : 2, NP = PPT / 2;
   __shared__ unsigned long long sh[BIG_TPB * D];
+  __shared__ float boxs[2 * D];
   __shared__ double red[BIG_TPB / 32];
   __shared__ int sh_tile;
   const float *P = s.p32[s.cur];
@@ -223,19 +290,69 @@ __global__ void __launch_bounds__(BIG_TPB) k_big_eval32(State s, int r0) {
     double acc = 0.0;
     float macc = 0.f;
     const bool full = v[PPT - 1];  // all points valid: no selects
+    // complete linkage: the box of this warp's points, for skipping staged
+    // chunks that cannot raise the pair's maximum
+    float wlo[D], whi[D];
+    int wpts = 0;  // valid points of this warp
+    if (LK == 0) {
+      warp_box<D, NP>(x, v, wlo, whi);
+#pragma unroll
+      for (int p = 0; p < PPT; ++p) wpts += v[p];
+      wpts = __reduce_add_sync(0xffffffffu, wpts);
+    }
+    const int lq = r - r0;  // the request's slot in this batch
     for (int c0 = sc0; c0 < sc1; c0 += BIG_TPB) {
       const int cn = min(BIG_TPB, sc1 - c0);
       __syncthreads();
+      float slo[D], shi[D];
+#pragma unroll
+      for (int k = 0; k < D; ++k) {
+        slo[k] = INFINITY;
+        shi[k] = -INFINITY;
+      }
       for (int i = threadIdx.x; i < cn * D; i += BIG_TPB) {
         const int j = i / D, k = i - j * D;
         const float y = P[(size_t)(sS + c0 + j) * DP + k];
         sh[i] = f2_pack(y, y);
+        if (LK == 0) {
+#pragma unroll
+          for (int kk = 0; kk < D; ++kk)
+            if (kk == k) {
+              slo[kk] = fminf(slo[kk], y);
+              shi[kk] = fmaxf(shi[kk], y);
+            }
+        }
       }
+      if (LK == 0) block_box<D>(slo, shi, boxs);
       __syncthreads();
+      if (LK == 0) {
+        // every pair of this warp's points with the chunk is at most the
+        // distance of the boxes' farthest corners; if that (rounded up and
+        // widened by the FP32 error of a squared distance) is within a
+        // maximum already computed for this pair, the chunk changes nothing
+        float far2 = 0.f;
+#pragma unroll
+        for (int k = 0; k < D; ++k) {
+          const float m = fmaxf(fmaxf(__fsub_ru(boxs[D + k], wlo[k]), __fsub_ru(whi[k], boxs[k])), 0.f);
+          far2 = __fadd_ru(far2, __fmul_ru(m, m));
+        }
+        far2 = __fmul_ru(far2, 1.f + 2.f * (D + 4) * 5.9604645e-8f);
+        const float seen = __shfl_sync(0xffffffffu, __int_as_float(*(volatile int *)&s.bmax2[lq]), 0);
+        const float known = fmaxf(warp_maxf_big(macc), seen);
+        if (far2 <= known) {  // uniform over the warp
+          if ((threadIdx.x & 31) == 0)
+            atomicAdd(&s.ctr->big_skip, (unsigned long long)wpts * (unsigned long long)cn);
+          continue;
+        }
+      }
       if (full)
         big32_chunk<LK, D, NP, true>(sh, cn, x, v, acc, macc);
       else
         big32_chunk<LK, D, NP, false>(sh, cn, x, v, acc, macc);
+    }
+    if (LK == 0) {
+      const float wm = warp_maxf_big(macc);
+      if ((threadIdx.x & 31) == 0) atomicMax(&s.bmax2[lq], __float_as_int(wm));
     }
     bk_store<LK>(s, LK == 0 ? (double)macc : acc, red, base + tile);
   }

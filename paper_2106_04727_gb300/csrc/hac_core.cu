@@ -1420,6 +1420,7 @@ int run_impl(hac_ctx *h, const hac_opts *o) {
           (rc0 = dalloc(h, &s.breq_sa, bcap)) || (rc0 = dalloc(h, &s.breq_na, bcap)) ||
           (rc0 = dalloc(h, &s.breq_sb, bcap)) || (rc0 = dalloc(h, &s.breq_nb, bcap)) ||
           (rc0 = dalloc(h, &s.breq_exact, bcap)) || (rc0 = dalloc(h, &s.bsched, BS_SIZE)) ||
+          (rc0 = dalloc(h, &s.bmax2, BIG_BATCH)) ||
           (rc0 = dalloc(h, &s.breq_base, bcap)) || (rc0 = dalloc(h, &s.breq_cov, bcap)) ||
           (rc0 = dalloc(h, &s.breq_berr, bcap)) ||
           (rc0 = dalloc(h, &s.bpart, tiles)) || (rc0 = dalloc(h, &s.pend[0], h->n)) ||
@@ -1564,7 +1565,7 @@ int run_impl(hac_ctx *h, const hac_opts *o) {
   h->st.rounds = round;
   h->st.merges = c.nmerges;
   h->st.cluster_pairs = (int64_t)c.cluster_pairs;
-  h->st.point_pairs = (int64_t)(c.point_pairs + c.big_pp);
+  h->st.point_pairs = (int64_t)(c.point_pairs + c.big_pp - c.big_skip);
   h->st.nodes_visited = (int64_t)c.nodes;
   h->st.rechecks = (int64_t)c.rechecks;
   h->st.ms_init = ms_init;
@@ -1574,7 +1575,7 @@ int run_impl(hac_ctx *h, const hac_opts *o) {
   h->st.kernel_launches = h->launches;
   h->st.cache_hits = (int64_t)c.cache_hits;
   h->st.ms_big = ms_big;
-  h->st.big_point_pairs = (int64_t)c.big_pp;
+  h->st.big_point_pairs = (int64_t)(c.big_pp - c.big_skip);
   h->st.big_launches = big_launch;
   h->st.cache_lw_entries = (int64_t)c.cache_lw;
   {

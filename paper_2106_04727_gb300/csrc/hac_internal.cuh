@@ -30,6 +30,7 @@ struct Counters {
   unsigned long long cluster_pairs, point_pairs, nodes, rechecks, searches, ltests, prows;
   unsigned long long cache_hits, cache_lw;
   unsigned long long big_pp, big_exact;  // point pairs / FP64 requests of the GPU-wide evaluation
+  unsigned long long big_skip;  // of those, pairs complete linkage skipped by box bounds
 };
 
 enum : int32_t { ERR_NONFINITE = 1, ERR_NO_NN = 2, ERR_STACK = 4, ERR_WINDOW = 8 };
@@ -104,6 +105,8 @@ struct State {
   int32_t *breq_cov;
   float *breq_berr;
   int32_t *bsched;       // tile schedule of the current batch (per-kind lists)
+  int32_t *bmax2;        // complete linkage: largest squared distance found so far
+                         // for each request of the batch (FP32 bits)
   double *bpart;         // per-tile partial results of the current batch
   int32_t *pend[2];      // terminals whose search deferred a pair
   // this round's big-pair results by unordered cid pair (cleared every round):

@@ -319,6 +319,7 @@ int engine_init(Engine &e, hac_linkage lk, int d, hac_dtype dt, int64_t cap, con
         (rc = dalloc(&h, &s.breq_na, bcap)) || (rc = dalloc(&h, &s.breq_sb, bcap)) ||
         (rc = dalloc(&h, &s.breq_nb, bcap)) || (rc = dalloc(&h, &s.breq_exact, bcap)) ||
         (rc = dalloc(&h, &s.bsched, BS_SIZE)) ||
+        (rc = dalloc(&h, &s.bmax2, BIG_BATCH)) ||
         (rc = dalloc(&h, &s.bpart, (size_t)BIG_BATCH * per)) ||
         (rc = dalloc(&h, &s.pend[0], cap)) || (rc = dalloc(&h, &s.pend[1], cap)) ||
         (rc = dalloc(&h, &s.side_key, 2 * bcap)) || (rc = dalloc(&h, &s.side_val, 2 * bcap)) ||
