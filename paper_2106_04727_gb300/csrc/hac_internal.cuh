@@ -219,7 +219,7 @@ constexpr long long BIG_PAIRS = 1ll << 16;
 constexpr long long BIG_PAIRS_F64 = 1ll << 13;
 // point pairs one search evaluates in its own warp before it hands every
 // further pair of at least BIG_MIN_PAIRS to the GPU-wide kernels
-constexpr long long WARP_BUDGET = 1ll << 17;
+constexpr long long WARP_BUDGET = 1ll << 18;
 constexpr long long BIG_MIN_PAIRS = 1ll << 12;
 constexpr int SIDE_PROBES = 64;
 
