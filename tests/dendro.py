@@ -1,0 +1,109 @@
+"""Vectorised structure checks for large dendrograms (no linkage arithmetic).
+
+A merge record t joins the clusters named by cids a < b in round r; the
+cluster named b retires and the union keeps the name a.  A cluster merges at
+most once per round, so the merges in which one cid takes part have strictly
+increasing rounds, and the child of merge t on the side of cid c is the
+previous merge in which c took part (none while c is still the singleton
+point c).  These checks state the same invariants as the oracle's
+`check_tree`, but as sorts and array comparisons, so that dendrograms of 10^7
+merges are checked in seconds.
+"""
+import numpy as np
+
+
+def children(d):
+    """(child_a, child_b): for every merge, the merge index that produced each
+    side, or -1 for a singleton, plus a list of problems with the round
+    structure."""
+    a = np.asarray(d["a"], np.int64)
+    b = np.asarray(d["b"], np.int64)
+    r = np.asarray(d["round"], np.int64)
+    m = len(a)
+    cid = np.concatenate([a, b])
+    rnd = np.concatenate([r, r])
+    t = np.concatenate([np.arange(m), np.arange(m)])
+    order = np.lexsort((rnd, cid))  # by cid, then round
+    cs, rs, ts = cid[order], rnd[order], t[order]
+    same = cs[1:] == cs[:-1]
+    probs = []
+    bad = np.flatnonzero(same & (rs[1:] <= rs[:-1]))
+    if len(bad):
+        probs.append(f"cid {cs[bad[0]]} merges twice in round {rs[bad[0]]} or out of order")
+    # a retired cid (side b) takes part in nothing later
+    retired = order >= m
+    after_b = np.flatnonzero(retired[:-1] & same)
+    if len(after_b):
+        probs.append(f"cid {cs[after_b[0]]} used after it retired")
+    prev = np.full(2 * m, -1, np.int64)
+    prev[1:][same] = ts[:-1][same]
+    child = np.empty(2 * m, np.int64)
+    child[order] = prev
+    return child[:m], child[m:], probs
+
+
+def check(d, n, rtol=1e-12):
+    """Problems with a dendrogram of n points (empty when it is a valid tree
+    whose heights do not decrease from child to parent beyond rtol)."""
+    a = np.asarray(d["a"], np.int64)
+    b = np.asarray(d["b"], np.int64)
+    size = np.asarray(d["size"], np.int64)
+    h = np.asarray(d["h"], np.float64)
+    m = len(a)
+    if m != n - 1:
+        return [f"{m} merges for n={n}"]
+    probs = []
+    if m == 0:
+        return probs
+    if not (np.all(a >= 0) and np.all(a < b) and np.all(b < n)):
+        probs.append("ids out of order or range")
+        return probs
+    ca, cb, p = children(d)
+    probs += p
+    if probs:
+        return probs
+    sa = np.where(ca >= 0, size[np.maximum(ca, 0)], 1)
+    sb = np.where(cb >= 0, size[np.maximum(cb, 0)], 1)
+    bad = np.flatnonzero(sa + sb != size)
+    if len(bad):
+        probs.append(f"merge {bad[0]}: sizes {sa[bad[0]]}+{sb[bad[0]]} != {size[bad[0]]}")
+    if size.max() != n:
+        probs.append(f"largest cluster has {size.max()} points, not {n}")
+    for c in (ca, cb):
+        k = c >= 0
+        low = np.flatnonzero(h[k] < h[c[k]] * (1 - rtol) - 1e-300)
+        if len(low):
+            t = np.flatnonzero(k)[low[0]]
+            probs.append(f"merge {t}: height {h[t]} below child height {h[c[t]]}")
+    return probs
+
+
+def members(d, t, ca, cb):
+    """Point indices of the cluster made by merge t."""
+    out, stack = [], [t]
+    a, b = d["a"], d["b"]
+    while stack:
+        u = stack.pop()
+        for cid, ch in ((a[u], ca[u]), (b[u], cb[u])):
+            if ch >= 0:
+                stack.append(int(ch))
+            else:
+                out.append(int(cid))
+    return out
+
+
+def sample_small(d, k, cap=64, seed=0):
+    """Up to k merges whose cluster has at most cap points, with the point
+    sets of their two sides: [(t, side_a, side_b)]."""
+    ca, cb, probs = children(d)
+    assert not probs, probs
+    size = np.asarray(d["size"])
+    small = np.flatnonzero(size <= cap)
+    rng = np.random.default_rng(seed)
+    pick = rng.choice(small, size=min(k, len(small)), replace=False)
+    out = []
+    for t in pick:
+        sa = members(d, ca[t], ca, cb) if ca[t] >= 0 else [int(d["a"][t])]
+        sb = members(d, cb[t], ca, cb) if cb[t] >= 0 else [int(d["b"][t])]
+        out.append((int(t), sa, sb))
+    return out

@@ -13,6 +13,7 @@ import os
 import numpy as np
 import pytest
 
+import dendro
 import oracle
 from paper_2106_04727_gb300 import hac, inputs
 
@@ -273,6 +274,71 @@ def test_full_size_1m_properties(lk, prec):
 
 
 _FULL = {}
+_WL = {}
+
+
+def _workload(name):
+    if name not in _WL:
+        _WL[name] = inputs.workload(name)
+    return _WL[name]
+
+
+def _check_sampled(got, X, lk, rtol, k=300):
+    """Sampled merges of at most 64 points: the height equals the oracle's
+    Table 1 value of the two merged point sets."""
+    X64 = X.astype(np.float64)
+    picks = dendro.sample_small(got, k)
+    assert len(picks) == k
+    for t, sa, sb in picks:
+        want = oracle.cluster_dist(lk, X64[sa], X64[sb])
+        assert got["h"][t] == pytest.approx(want, rel=rtol, abs=1e-12), (t, len(sa), len(sb))
+
+
+@pytest.mark.parametrize("prec", PRECS, ids=PREC_IDS)
+def test_full_size_1m_average(prec):
+    """The benchmark's average-linkage run (10^6 points, 5-D mixture, 128
+    cache slots): a valid tree, sampled heights equal to the oracle's value of
+    the merged point sets, and the FP32 + FP64 re-score tree equal to the
+    all-FP64 tree, merge for merge and round for round."""
+    X = _workload("gmm5d_1m_f32")
+    got = hac.cluster(X, "average", precision=prec, cache_slots=128)
+    rtol = _rtol("average", prec)
+    assert dendro.check(got, len(X), rtol=2 * rtol) == []
+    _check_sampled(got, X, "average", rtol)
+    if prec == hac.PREC_F64:
+        _FULL["average"] = got
+    else:
+        ref = _FULL.get("average") or hac.cluster(X, "average", precision=hac.PREC_F64,
+                                                  cache_slots=128)
+        c = oracle.compare(got, ref, rtol=RTOL32)
+        assert c["ok"], c
+        assert _round_sets(got) == _round_sets(ref)
+
+
+@pytest.mark.parametrize("lk", ["ward", "complete"])
+def test_full_size_10m_spreaders(lk):
+    """The 10^7-point 2-D spreader workload as one instance (FP32 + FP64
+    re-score, 128 cache slots for complete): a valid tree and sampled heights
+    equal to the oracle's value of the merged point sets."""
+    X = _workload("spread2d_10m_f32")
+    got = hac.cluster(X, lk, precision=hac.PREC_F32_RECHECK,
+                      cache_slots=0 if lk == "ward" else 128)
+    rtol = _rtol(lk, hac.PREC_F32_RECHECK)
+    assert dendro.check(got, len(X), rtol=2 * rtol) == []
+    _check_sampled(got, X, lk, rtol)
+
+
+@pytest.mark.parametrize("lk", ["ward", "average_sq"])
+def test_full_size_16d_lattice(lk):
+    """The 10^6-point 16-D lattice (exact ties everywhere) with the FP32 bulk
+    and the exhaustive search: a valid tree and sampled heights equal to the
+    oracle's value of the merged point sets.  (Average linkage on Euclidean
+    distances does not finish at this size: its centroid bound prunes almost
+    nothing in 16-D.)"""
+    X = _workload("lattice16d_1m_f32")
+    got = hac.cluster(X, lk, precision=hac.PREC_F32_RECHECK)
+    assert dendro.check(got, len(X), rtol=1e-12) == []
+    _check_sampled(got, X, lk, RTOL64)
 
 
 @pytest.mark.parametrize("slots", [8, 64])
