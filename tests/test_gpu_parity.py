@@ -71,7 +71,9 @@ def test_uniform_1024_fp64(lk, prec):
 
 SHAPES = [(2, 2, np.float64), (3, 1, np.float64), (33, 3, np.float32), (100, 5, np.float32),
           (257, 2, np.float64), (1100, 2, np.float32), (600, 10, np.float32),
-          (300, 16, np.float32), (70, 7, np.float64)]
+          (300, 16, np.float32), (70, 7, np.float64), (32, 4, np.float32),
+          (1025, 3, np.float64), (130, 4, np.float32), (520, 8, np.float32),
+          (400, 9, np.float32), (200, 12, np.float64), (90, 15, np.float32)]
 
 
 @pytest.mark.parametrize("prec", PRECS, ids=PREC_IDS)
@@ -376,6 +378,25 @@ def test_big_pair_deferral(lk, prec, slots, monkeypatch):
         X = inputs.gaussian_mixture(n, 4, 10, seed=seed)
         got = hac.cluster(X, lk, precision=prec, cache_slots=slots)
         _assert_same(got, oracle.rounds(X.astype(np.float64), lk), rtol=_rtol(lk, prec))
+
+
+@pytest.mark.parametrize("lk", ["complete", "average"])
+@pytest.mark.parametrize("d", list(range(1, 17)))
+def test_big_pairs_every_dimension(lk, d, monkeypatch):
+    """The GPU-wide FP32 kernels are specialised on the true dimension and
+    the FP64 ones on the padded width: with tiny thresholds nearly every
+    evaluated pair of >= 256 point pairs goes through them, at every d from 1
+    to 16 (pairs up to ~2,100 x 1,100 points), FP32 with the FP64 re-score,
+    and all-FP64 at d = 3 and 12 (padded widths 4 and 16)."""
+    monkeypatch.setenv("HAC_BIG_PAIRS", "256")
+    monkeypatch.setenv("HAC_BIG_PAIRS_F64", "128")
+    X = inputs.gaussian_mixture(3200, d, 3, seed=100 + d,
+                                dtype=np.float64 if d == 1 else np.float32)
+    want = oracle.rounds(X.astype(np.float64), lk)
+    for prec in [hac.PREC_F32_RECHECK] + ([hac.PREC_F64] if d in (3, 12) else []):
+        got = hac.cluster(X, lk, precision=prec, cache_slots=8)
+        _assert_same(got, want, rtol=_rtol(lk, prec))
+        assert got["stats"]["big_point_pairs"] > 0
 
 
 _PAPER_ORACLE = {}
