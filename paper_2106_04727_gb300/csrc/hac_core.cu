@@ -1388,6 +1388,21 @@ int round_step(hac_ctx *h, cudaStream_t st, int round, int K, int nterm, RoundCt
   return HAC_OK;
 }
 
+// Release one array taken by dalloc (count elements) before the handle is
+// destroyed; a null pointer is left alone.
+template <typename T>
+static void dfree(hac_ctx *h, T *&p, size_t count) {
+  if (!p) return;
+  for (auto it = h->allocs.begin(); it != h->allocs.end(); ++it)
+    if (*it == (void *)p) {
+      h->allocs.erase(it);
+      cudaFree(p);
+      h->bytes -= (int64_t)(std::max<size_t>(count, 1) * sizeof(T));
+      break;
+    }
+  p = nullptr;
+}
+
 int run_impl(hac_ctx *h, const hac_opts *o) {
   hac_opts opt;
   hac_default_opts(&opt);
@@ -1403,14 +1418,24 @@ int run_impl(hac_ctx *h, const hac_opts *o) {
   const int slots = closed_form(s.linkage) ? 0 : std::min(opt.cache_slots, CACHE_MAX_SLOTS);
   if (slots > h->cache_alloc_slots) {
     int rc0 = 0;
+    // a larger table replaces the old one (a smaller request reuses it)
+    const size_t old_cells = (size_t)h->n * h->cache_alloc_slots;
+    dfree(h, s.ckey, old_cells);
+    dfree(h, s.cval, old_cells);
+    dfree(h, s.cerr, old_cells);
+    dfree(h, s.cpart, old_cells);
+    h->cache_alloc_slots = 0;
     const size_t cells = (size_t)h->n * slots;
-    const int64_t cap = std::max<int64_t>(4 * h->n, 1 << 16);
     if ((rc0 = dalloc(h, &s.ckey, cells)) || (rc0 = dalloc(h, &s.cval, cells)) ||
-        (rc0 = dalloc(h, &s.cerr, cells)) || (rc0 = dalloc(h, &s.cpart, cells)) || (rc0 = dalloc(h, &s.ins_i, cap)) ||
-        (rc0 = dalloc(h, &s.ins_j, cap)) || (rc0 = dalloc(h, &s.ins_v, cap)) ||
-        (rc0 = dalloc(h, &s.ins_e, cap)))
+        (rc0 = dalloc(h, &s.cerr, cells)) || (rc0 = dalloc(h, &s.cpart, cells)))
       return rc0;
-    s.ins_cap = (int)cap;
+    if (!s.ins_i) {  // queue of evaluated pairs to insert (sized once per handle)
+      const int64_t cap = std::max<int64_t>(4 * h->n, 1 << 16);
+      if ((rc0 = dalloc(h, &s.ins_i, cap)) || (rc0 = dalloc(h, &s.ins_j, cap)) ||
+          (rc0 = dalloc(h, &s.ins_v, cap)) || (rc0 = dalloc(h, &s.ins_e, cap)))
+        return rc0;
+      s.ins_cap = (int)cap;
+    }
     if (!s.breq_i) {  // big-pair deferral buffers (sized once per handle)
       const int bcap = 1 << 18;
       // per request at most max(BIG_MAXT, tiles along the larger cluster)

@@ -4,6 +4,8 @@ the device (no compute call runs here)."""
 import ctypes
 import os
 import re
+import shutil
+import subprocess
 
 import numpy as np
 import pytest
@@ -36,6 +38,46 @@ def test_struct_layouts_match_header():
     assert ctypes.sizeof(hac.hac_merge) == 32
     assert ctypes.sizeof(hac.hac_opts) == 40
     assert hac.MERGE_DTYPE.itemsize == 32
+
+
+def test_header_is_plain_c_and_matches_the_binding(tmp_path):
+    """A C11 program built against include/hac.h alone (gcc -pedantic
+    -Werror) and linked with the library: every declared entry point
+    resolves, and every struct's size and field offsets equal the binding's
+    ctypes layout."""
+    gcc = shutil.which("gcc")
+    if not gcc:
+        pytest.skip("gcc not found")
+    lib = hac.lib_path()
+    if not os.path.exists(lib):
+        hac.load()
+    structs = {"hac_merge": hac.hac_merge, "hac_opts": hac.hac_opts,
+               "hac_stats_t": hac.hac_stats_t, "hac_server_stats_t": hac.hac_server_stats_t}
+    body = []
+    for name, cls in structs.items():
+        body.append(f'  printf("{name} %zu\\n", sizeof({name}));')
+        for f, _ in cls._fields_:
+            body.append(f'  printf("{name}.{f} %zu\\n", offsetof({name}, {f}));')
+    body.append("  void (*volatile fp)(void);")
+    for fn in _declared():
+        body.append(f"  fp = (void (*)(void)){fn};")
+        body.append(f'  printf("fn {fn} %d\\n", fp != 0);')
+    src = tmp_path / "abi.c"
+    src.write_text("#include <stddef.h>\n#include <stdio.h>\n#include \"hac.h\"\n"
+                   "int main(void) {\n" + "\n".join(body) + "\n  return 0;\n}\n")
+    exe = tmp_path / "abi"
+    libdir = os.path.dirname(lib)
+    subprocess.run([gcc, "-std=c11", "-Wall", "-Wextra", "-pedantic", "-Werror",
+                    "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe),
+                    lib, f"-Wl,-rpath,{libdir}"], check=True, capture_output=True, text=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout
+    got = dict(line.rsplit(" ", 1) for line in out.splitlines())
+    for name, cls in structs.items():
+        assert int(got[name]) == ctypes.sizeof(cls), name
+        for f, _ in cls._fields_:
+            assert int(got[f"{name}.{f}"]) == getattr(cls, f).offset, f"{name}.{f}"
+    for fn in _declared():
+        assert got[f"fn {fn}"] == "1", fn
 
 
 def test_default_opts_and_strerror():

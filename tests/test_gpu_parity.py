@@ -230,6 +230,29 @@ def test_round_limit_and_rerun():
         hac.hac_destroy(h)
 
 
+def test_cache_resize_between_runs():
+    """Reruns of one handle with another cache size give the same tree; a
+    larger table replaces the old one (its memory is released) and a smaller
+    request reuses it."""
+    n = 3000
+    X = inputs.gaussian_mixture(n, 3, 8, seed=21)
+    want = oracle.rounds(X.astype(np.float64), "average")
+    h = hac.hac_create(X, "average")
+    sizes = []
+    try:
+        for slots in (8, 64, 16):
+            assert hac.hac_run(h, precision=hac.PREC_F32_RECHECK, cache_slots=slots) == 0
+            sizes.append(hac.hac_stats(h)["device_bytes"])
+            m = hac.hac_dendrogram(h, n)
+            got = dict(a=m["cid_a"], b=m["cid_b"], h=m["height"], size=m["size"])
+            _assert_same(got, want, rtol=RTOL32, rounds=False)
+    finally:
+        hac.hac_destroy(h)
+    cell = 8 + 8 + 4 + 4  # key, value, error term, covered part
+    assert sizes[1] - sizes[0] == n * (64 - 8) * cell
+    assert sizes[2] == sizes[1]
+
+
 def _members_small(d, n, cap=64):
     """Members of every merged cluster of size <= cap, by replaying merges in
     size order (children before parents)."""
