@@ -62,6 +62,8 @@ def _load():
             lib.oracle_lw.restype = f64
             lib.oracle_cluster_dist.argtypes = [i32, P, i64, P, i64, i32]
             lib.oracle_cluster_dist.restype = f64
+            lib.oracle_dist_to_all.argtypes = [i32, P, i64, i32, P, i64, i64, P]
+            lib.oracle_dist_to_all.restype = i32
             _lib = lib
     return _lib
 
@@ -169,6 +171,22 @@ def cluster_dist(linkage, A, B) -> float:
     """Linkage distance between two point sets from the points (Table 1)."""
     A, B = _pts(A), _pts(B)
     return _load().oracle_cluster_dist(_lk(linkage), _p(A), len(A), _p(B), len(B), A.shape[1])
+
+
+def dist_to_all(linkage, X, label, q) -> np.ndarray:
+    """Linkage distance (Table 1) from the cluster labelled q to every label of
+    a labelling of X's points (NaN for q itself and for unused labels)."""
+    X = _pts(X)
+    label = np.ascontiguousarray(label, dtype=np.int64)
+    if label.shape != (len(X),):
+        raise ValueError("one label per point")
+    ncl = int(label.max()) + 1 if len(label) else 1
+    out = np.empty(max(ncl, int(q) + 1), np.float64)
+    rc = _load().oracle_dist_to_all(_lk(linkage), _p(X), len(X), X.shape[1], _p(label),
+                                    len(out), int(q), _p(out))
+    if rc:
+        raise ValueError(f"oracle_dist_to_all failed ({rc})")
+    return out
 
 
 # ----------------------------------------------------------------------------

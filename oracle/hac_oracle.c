@@ -48,6 +48,9 @@
  *                    minimal pair within a relative tolerance.
  *   oracle_lw        one Lance-Williams update, exposed for unit tests.
  *   oracle_cluster_dist  a linkage distance between two explicit point sets.
+ *   oracle_dist_to_all   the linkage distance from one cluster of a labelling
+ *                    to every other cluster, from the points (linear memory,
+ *                    for checks at sizes the matrix cannot hold).
  */
 #include <math.h>
 #include <stdint.h>
@@ -155,6 +158,97 @@ double oracle_cluster_dist(int linkage, const double *A, int64_t na,
     return sqrt(2.0 * (double)na * (double)nb / (double)(na + nb) * dd);
   }
   return NAN;
+}
+
+/* Linkage distance (Table 1) from the cluster labelled q to every cluster of
+ * a labelling, from the points alone: label[i] in [0, ncl) names the cluster
+ * of point i.  out[c] = D(Q, C_c) for every label c != q that has points, NAN
+ * for c == q and for labels without points.  Time O(|Q| n d) (Ward and
+ * avg-2 as for the others: no centroid shortcut), memory O(ncl d). */
+int oracle_dist_to_all(int linkage, const double *X, int64_t n, int d, const int64_t *label,
+                       int64_t ncl, int64_t q, double *out) {
+  if (!X || !label || !out || n < 1 || d < 1 || ncl < 1 || q < 0 || q >= ncl) return -1;
+  if (linkage < LK_COMPLETE || linkage > LK_AVG2) return -1;
+  int64_t *cnt = (int64_t *)calloc((size_t)ncl, sizeof(int64_t));
+  double *acc = (double *)calloc((size_t)ncl * (linkage == LK_WARD ? (size_t)d : 1), sizeof(double));
+  int64_t *qi = (int64_t *)malloc((size_t)n * sizeof(int64_t));
+  if (!cnt || !acc || !qi) {
+    free(cnt);
+    free(acc);
+    free(qi);
+    return -2;
+  }
+  int64_t nq = 0;
+  for (int64_t i = 0; i < n; ++i) {
+    if (label[i] < 0 || label[i] >= ncl) {
+      free(cnt);
+      free(acc);
+      free(qi);
+      return -1;
+    }
+    cnt[label[i]] += 1;
+    if (label[i] == q) qi[nq++] = i;
+  }
+  if (nq == 0) {
+    free(cnt);
+    free(acc);
+    free(qi);
+    return -1;
+  }
+  if (linkage == LK_WARD) {
+    /* means of Q and of every cluster, then the Table 1 formula */
+    double *mq = (double *)calloc((size_t)d, sizeof(double));
+    if (!mq) {
+      free(cnt);
+      free(acc);
+      free(qi);
+      return -2;
+    }
+    for (int64_t i = 0; i < n; ++i)
+      for (int k = 0; k < d; ++k) acc[label[i] * d + k] += X[i * d + k];
+    for (int64_t t = 0; t < nq; ++t)
+      for (int k = 0; k < d; ++k) mq[k] += X[qi[t] * d + k];
+    for (int k = 0; k < d; ++k) mq[k] /= (double)nq;
+    for (int64_t c = 0; c < ncl; ++c) {
+      if (c == q || cnt[c] == 0) {
+        out[c] = NAN;
+        continue;
+      }
+      double dd = 0.0;
+      for (int k = 0; k < d; ++k) {
+        double t = mq[k] - acc[c * d + k] / (double)cnt[c];
+        dd += t * t;
+      }
+      out[c] = sqrt(2.0 * (double)nq * (double)cnt[c] / (double)(nq + cnt[c]) * dd);
+    }
+    free(mq);
+  } else {
+    /* every point pair (x in Q, y anywhere), folded into y's cluster */
+    for (int64_t i = 0; i < n; ++i) {
+      const int64_t c = label[i];
+      if (c == q) continue;
+      for (int64_t t = 0; t < nq; ++t) {
+        const double *x = X + qi[t] * d, *y = X + i * d;
+        if (linkage == LK_COMPLETE) {
+          double v = point_dist(x, y, d);
+          if (v > acc[c]) acc[c] = v;
+        } else if (linkage == LK_AVERAGE) {
+          acc[c] += point_dist(x, y, d);
+        } else {
+          acc[c] += point_dist2(x, y, d);
+        }
+      }
+    }
+    for (int64_t c = 0; c < ncl; ++c) {
+      if (c == q || cnt[c] == 0) out[c] = NAN;
+      else if (linkage == LK_COMPLETE) out[c] = acc[c];
+      else out[c] = acc[c] / ((double)nq * (double)cnt[c]);
+    }
+  }
+  free(cnt);
+  free(acc);
+  free(qi);
+  return 0;
 }
 
 /* ------------------------------------------------------------------------ */

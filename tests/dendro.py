@@ -107,3 +107,73 @@ def sample_small(d, k, cap=64, seed=0):
         sb = members(d, cb[t], ca, cb) if cb[t] >= 0 else [int(d["b"][t])]
         out.append((int(t), sa, sb))
     return out
+
+
+def pick_merges(d, k_small, cap=32, k_big=0, big_cap=2048, every_size=False, seed=0):
+    """Merges to check: k_small random ones whose cluster has at most cap
+    points (any size with every_size), plus the k_big largest whose smaller
+    side has at most big_cap points (every_size: the k_big last merges)."""
+    size = np.asarray(d["size"])
+    rng = np.random.default_rng(seed)
+    pool = np.arange(len(size)) if every_size else np.flatnonzero(size <= cap)
+    out = list(rng.choice(pool, size=min(k_small, len(pool)), replace=False))
+    if k_big:
+        ca, cb, _ = children(d)
+        sa = np.where(ca >= 0, size[np.maximum(ca, 0)], 1)
+        sb = np.where(cb >= 0, size[np.maximum(cb, 0)], 1)
+        ok = np.ones(len(size), bool) if every_size else np.minimum(sa, sb) <= big_cap
+        big = np.flatnonzero(ok)
+        big = big[np.argsort(size[big], kind="stable")][-k_big:]
+        out += [int(t) for t in big if t not in out]
+    return [int(t) for t in out]
+
+
+def rnn_check(d, X, linkage, picks, dist_to_all, rtol=1e-9, side_cap=None):
+    """For every picked merge t (cids a < b, round r): among the clusters
+    active when round r starts, b is a nearest neighbour of a (and a of b),
+    every distance taken from the points by `dist_to_all` (the oracle's).
+    Only sides of at most side_cap points are queried (None: both).
+
+    Returns (problems, near_ties, values): a cluster closer than the partner
+    by more than rtol is a problem; one within rtol and with a smaller cid is
+    a near tie (its order is not decidable at this precision); values maps t
+    to the partner distance seen from the first queried side."""
+    a = np.asarray(d["a"], np.int64)
+    b = np.asarray(d["b"], np.int64)
+    r = np.asarray(d["round"], np.int64)
+    n = len(X)
+    order = np.argsort(r, kind="stable")
+    rs = r[order]
+    label = np.arange(n, dtype=np.int64)
+    mp = np.arange(n, dtype=np.int64)
+    cur = 0  # label holds the clusters at the start of round `cur`
+    problems, ties, values = [], 0, {}
+    for t in sorted(picks, key=lambda t: r[t]):
+        while cur < r[t]:
+            lo, hi = np.searchsorted(rs, cur), np.searchsorted(rs, cur, side="right")
+            ta = a[order[lo:hi]]
+            tb = b[order[lo:hi]]
+            mp[tb] = ta
+            label = mp[label]
+            mp[tb] = tb
+            cur += 1
+        for q, other in ((a[t], b[t]), (b[t], a[t])):
+            nq = int(np.count_nonzero(label == q))
+            if nq == 0 or np.count_nonzero(label == other) == 0:
+                problems.append(f"merge {t}: cid {q} or {other} not active in round {r[t]}")
+                break
+            if side_cap is not None and nq > side_cap:
+                continue
+            D = dist_to_all(linkage, X, label, q)
+            dqo = D[other]
+            values.setdefault(t, dqo)
+            idx = np.arange(len(D))
+            with np.errstate(invalid="ignore"):
+                closer = np.flatnonzero((D < dqo * (1 - rtol)) & (idx != other))
+                near = np.flatnonzero((np.abs(D - dqo) <= rtol * dqo) & (idx < other))
+            if len(closer):
+                c = int(closer[np.argmin(D[closer])])
+                problems.append(f"merge {t} (round {r[t]}): cluster {c} at {D[c]!r} is closer "
+                                f"to {q} than its partner {other} at {dqo!r}")
+            ties += len(near)
+    return problems, ties, values

@@ -87,3 +87,45 @@ def test_sampled_members_reproduce_heights(lk):
         assert min(sa) == t["a"][m] and min(sb) == t["b"][m]
         want = oracle.cluster_dist(lk, X[sa], X[sb])
         assert t["h"][m] == pytest.approx(want, rel=1e-9, abs=1e-12)
+
+
+@pytest.mark.parametrize("lk", ["complete", "average", "ward", "average_sq"])
+def test_rnn_check_accepts_oracle_trees(lk):
+    """Every merge of the oracle's Algorithm 1 joins reciprocal nearest
+    neighbours among the clusters active in its round, and the partner
+    distance from the points equals the recorded height."""
+    X = inputs.gaussian_mixture(2500, 3, 8, seed=3).astype(np.float64)
+    t = oracle.rounds(X, lk)
+    picks = dendro.pick_merges(t, 40, cap=32, k_big=3, every_size=lk == "ward")
+    probs, ties, vals = dendro.rnn_check(t, X, lk, picks, oracle.dist_to_all)
+    assert probs == [] and len(vals) == len(picks)
+    for m, v in vals.items():
+        assert v == pytest.approx(t["h"][m], rel=1e-12)
+
+
+def test_rnn_check_on_exact_ties():
+    """Lattice points: exact ties among candidates are near ties, never
+    problems, when the tree breaks them by the smaller cid."""
+    X = inputs.lattice(500, 3, seed=2, levels=8).astype(np.float64)
+    t = oracle.rounds(X, "ward")
+    picks = dendro.pick_merges(t, 60, every_size=True)
+    probs, ties, _ = dendro.rnn_check(t, X, "ward", picks, oracle.dist_to_all)
+    assert probs == []
+
+
+@pytest.mark.parametrize("lk", ["average", "ward"])
+def test_rnn_check_catches_a_wrong_partner(lk):
+    """A merge whose partner is replaced by a farther active cluster fails."""
+    X = inputs.gaussian_mixture(1500, 2, 6, seed=9).astype(np.float64)
+    t = oracle.rounds(X, lk)
+    r0 = np.flatnonzero(t["round"] == 0)
+    m = int(r0[0])
+    # the active clusters of round 0 are the singletons: take a farther one
+    q = int(t["a"][m])
+    D = oracle.dist_to_all(lk, X, np.arange(len(X)), q)
+    D[q] = np.inf
+    far = int(np.argsort(D)[5])
+    bad = {k: np.array(v, copy=True) if isinstance(v, np.ndarray) else v for k, v in t.items()}
+    bad["b"][m] = far
+    probs, _, _ = dendro.rnn_check(bad, X, lk, [m], oracle.dist_to_all)
+    assert probs and "closer" in probs[0]

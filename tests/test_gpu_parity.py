@@ -289,6 +289,10 @@ def test_full_size_1m_properties(lk, prec):
         ma, mb = mem[keys[t]]
         want = oracle.cluster_dist(lk, X64[ma], X64[mb])
         assert got["h"][keys[t]] == pytest.approx(want, rel=RTOL64, abs=1e-12)
+    if lk == "ward":
+        _check_rnn(got, X, lk, 24, k_big=2, every_size=True)
+    else:
+        _check_rnn(got, X, lk, 12, k_big=1, side_cap=512)
     if prec == hac.PREC_F64:
         _FULL[lk] = got
     else:
@@ -319,6 +323,19 @@ def _check_sampled(got, X, lk, rtol, k=300):
         assert got["h"][t] == pytest.approx(want, rel=rtol, abs=1e-12), (t, len(sa), len(sb))
 
 
+def _check_rnn(got, X, lk, k_small, k_big=0, every_size=False, side_cap=None):
+    """Sampled merges were reciprocal nearest neighbours among the clusters
+    active in their round, every distance from the points by the oracle (for
+    complete / average / avg-2 only from sides of at most side_cap points:
+    the oracle's scan costs |side| x n point pairs)."""
+    picks = dendro.pick_merges(got, k_small, cap=32, k_big=k_big, every_size=every_size,
+                               big_cap=side_cap or 0)
+    probs, ties, vals = dendro.rnn_check(got, X.astype(np.float64), lk, picks,
+                                         oracle.dist_to_all, rtol=1e-9, side_cap=side_cap)
+    assert probs == [], probs[:3]
+    assert len(vals) == len(picks)
+
+
 @pytest.mark.parametrize("prec", PRECS, ids=PREC_IDS)
 def test_full_size_1m_average(prec):
     """The benchmark's average-linkage run (10^6 points, 5-D mixture, 128
@@ -330,6 +347,7 @@ def test_full_size_1m_average(prec):
     rtol = _rtol("average", prec)
     assert dendro.check(got, len(X), rtol=2 * rtol) == []
     _check_sampled(got, X, "average", rtol)
+    _check_rnn(got, X, "average", 12, k_big=1, side_cap=512)
     if prec == hac.PREC_F64:
         _FULL["average"] = got
     else:
@@ -351,6 +369,10 @@ def test_full_size_10m_spreaders(lk):
     rtol = _rtol(lk, hac.PREC_F32_RECHECK)
     assert dendro.check(got, len(X), rtol=2 * rtol) == []
     _check_sampled(got, X, lk, rtol)
+    if lk == "ward":
+        _check_rnn(got, X, lk, 8, k_big=2, every_size=True)
+    else:
+        _check_rnn(got, X, lk, 6, side_cap=32)
 
 
 @pytest.mark.parametrize("lk", ["ward", "average_sq"])
@@ -364,6 +386,10 @@ def test_full_size_16d_lattice(lk):
     got = hac.cluster(X, lk, precision=hac.PREC_F32_RECHECK)
     assert dendro.check(got, len(X), rtol=1e-12) == []
     _check_sampled(got, X, lk, RTOL64)
+    if lk == "ward":
+        _check_rnn(got, X, lk, 20, k_big=2, every_size=True)
+    else:
+        _check_rnn(got, X, lk, 8, side_cap=32)
 
 
 @pytest.mark.parametrize("slots", [8, 64])

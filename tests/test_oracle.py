@@ -191,6 +191,33 @@ def test_avg2_closed_form():
         assert oracle.cluster_dist("average_sq", A, B) == pytest.approx(brute, rel=1e-13)
 
 
+@pytest.mark.parametrize("lk", LKS)
+def test_dist_to_all_matches_library_and_variance_forms(lk):
+    """The linear-memory distance from one cluster of a labelling to all
+    others: mean / max / mean square of scipy's point-distance matrix, and for
+    Ward the variance-increase form sqrt(2 (SSE(Q u C) - SSE(Q) - SSE(C)))
+    computed with numpy; NaN for the query itself and for unused labels."""
+    cdist = pytest.importorskip("scipy.spatial.distance").cdist
+    rng = np.random.default_rng(23)
+    X = rng.normal(size=(90, 3)) * rng.uniform(0.5, 2, size=3)
+    label = rng.integers(0, 9, size=90) * 2  # odd labels unused
+    label[:9] = np.arange(9) * 2
+    sse = lambda P: ((P - P.mean(0)) ** 2).sum()
+    for q in (0, 6, 16):
+        got = oracle.dist_to_all(lk, X, label, q)
+        Q = X[label == q]
+        assert len(got) == 17 and math.isnan(got[q])
+        for c in range(17):
+            C = X[label == c]
+            if c == q or not len(C):
+                assert math.isnan(got[c])
+                continue
+            M = cdist(Q, C)
+            want = {"complete": M.max(), "average": M.mean(), "average_sq": (M ** 2).mean(),
+                    "ward": math.sqrt(2 * (sse(np.vstack([Q, C])) - sse(Q) - sse(C)))}[lk]
+            assert got[c] == pytest.approx(want, rel=1e-11)
+
+
 def test_centroid_lower_bound():
     """Section 4.2 proof: ||c_A - c_B|| <= D_avg(A,B) <= D_comp(A,B)."""
     rng = np.random.default_rng(8)
