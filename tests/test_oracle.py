@@ -399,3 +399,54 @@ def test_pins_catch_mutants(mut, tmp_path):
             caught = True
             break
     assert caught, mut
+
+
+DIST_MUTANTS = {
+    "avg_mean_over_one_side": ("else out[c] = acc[c] / ((double)nq * (double)cnt[c]);",
+                               "else out[c] = acc[c] / (double)cnt[c];"),
+    "complete_min": ("if (v > acc[c]) acc[c] = v;", "if (v < acc[c] || acc[c] == 0.0) acc[c] = v;"),
+    "avg2_unsquared": ("acc[c] += point_dist2(x, y, d);", "acc[c] += point_dist(x, y, d);"),
+    "ward_no_two": ("out[c] = sqrt(2.0 * (double)nq * (double)cnt[c] / (double)(nq + cnt[c]) * dd);",
+                    "out[c] = sqrt((double)nq * (double)cnt[c] / (double)(nq + cnt[c]) * dd);"),
+    "ward_query_sum_not_mean": ("for (int k = 0; k < d; ++k) mq[k] /= (double)nq;", ""),
+}
+
+
+@pytest.mark.parametrize("mut", sorted(DIST_MUTANTS))
+def test_dist_to_all_pin_catches_mutants(mut, tmp_path):
+    """The library-based pin of oracle_dist_to_all rejects plausible mistakes
+    planted in a copy of the oracle source."""
+    import ctypes
+    cdist = pytest.importorskip("scipy.spatial.distance").cdist
+    src = open(os.path.join(os.path.dirname(oracle.__file__), "hac_oracle.c")).read()
+    old, new = DIST_MUTANTS[mut]
+    assert src.count(old) == 1
+    path = tmp_path / "m.c"
+    path.write_text(src.replace(old, new))
+    so = tmp_path / "m.so"
+    subprocess.check_call(["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-shared", "-fPIC",
+                           "-o", str(so), str(path), "-lm"])
+    lib = ctypes.CDLL(str(so))
+    P, i64, i32 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int
+    lib.oracle_dist_to_all.argtypes = [i32, P, i64, i32, P, i64, i64, P]
+    rng = np.random.default_rng(29)
+    X = np.ascontiguousarray(rng.normal(size=(60, 3)) * 2.0)
+    label = np.ascontiguousarray(rng.integers(0, 5, size=60), dtype=np.int64)
+    label[:5] = np.arange(5)
+    sse = lambda Q: ((Q - Q.mean(0)) ** 2).sum()
+    caught = False
+    for lk, q in itertools.product(range(4), range(5)):
+        out = np.empty(5)
+        lib.oracle_dist_to_all(lk, X.ctypes.data_as(P), 60, 3, label.ctypes.data_as(P), 5, q,
+                               out.ctypes.data_as(P))
+        Q = X[label == q]
+        for c in range(5):
+            if c == q:
+                continue
+            C = X[label == c]
+            M = cdist(Q, C)
+            want = [M.max(), M.mean(), math.sqrt(2 * (sse(np.vstack([Q, C])) - sse(Q) - sse(C))),
+                    (M ** 2).mean()][lk]
+            if not abs(out[c] - want) <= 1e-11 * abs(want):
+                caught = True
+    assert caught, mut
