@@ -75,9 +75,10 @@ typedef struct {
 typedef struct {
   int precision;      /* hac_precision; default HAC_PREC_F64 */
   int cache_slots;    /* per-cluster pair-distance cache slots (Section 5), complete and
-                         average only (at most 256); 0 = off.  The first run with a larger
-                         value allocates the tables (n * slots * 20 bytes) in the handle.
-                         hac_run_static ignores it. */
+                         average only (at most 256); 0 = off.  The first run with a value
+                         larger than any before allocates the tables (n * slots * 24
+                         bytes) in the handle, releasing the smaller ones; a smaller value
+                         reuses them.  hac_run_static ignores it. */
   int64_t max_rounds; /* 0 = unlimited; else HAC_ETIMEOUT after this many rounds */
   double timeout_s;   /* 0 = none; else HAC_ETIMEOUT once exceeded (checked per round) */
   void *stream;       /* cudaStream_t to run on; NULL = the handle's own stream */
@@ -235,8 +236,8 @@ typedef struct {
 /* Create a server on the current CUDA device.  `points_per_engine` (2 ..
  * 2^29) sizes every engine, and bounds the n of a request.  An engine holds
  * about 0.35 KB (d <= 2) to 1.4 KB (d > 8) of device memory per point; with
- * opts->cache_slots > 0, complete and average engines add 80 bytes plus 20
- * bytes per slot per point and 128 MiB of big-pair buffers.  An engine is
+ * opts->cache_slots > 0, complete and average engines add about 88 bytes
+ * plus 24 bytes per slot per point and about 280 MiB of big-pair buffers.  An engine is
  * allocated when the first request of its kind arrives.  opts (may be NULL) gives precision
  * and cache_slots for every request; its stream, max_rounds and timeout_s
  * are ignored.  HAC_EINVAL for bad arguments, HAC_ENOMEM, HAC_EDEVICE. */
