@@ -274,6 +274,26 @@ def test_start_independence(lk):
         assert c["same_tree"], (st, c)
 
 
+@pytest.mark.parametrize("lk", LKS)
+def test_unit_square_exact_ties(lk):
+    """Four corners of the unit square, every singleton nearest-neighbour
+    distance tied at 1 (hand-derived).  Round 0: 0 -> {1, 2} picks 1 (smaller
+    cid), 1 -> {0, 3} picks 0, 2 -> {0, 3} picks 0, 3 -> {1, 2} picks 1; only
+    {0, 1} is reciprocal.  Round 1: the pair {2, 3} at 1 is closer than either
+    to {0, 1}.  Round 2: the two sides.  Breaking ties toward the larger cid
+    would instead merge {0, 2} and {1, 3} in round 0."""
+    X = np.array([[0.0, 0.0], [1.0, 0.0], [0.0, 1.0], [1.0, 1.0]])
+    r2 = math.sqrt(2.0)
+    top = {"complete": r2, "average": (1 + r2) / 2, "ward": r2, "average_sq": 1.5}[lk]
+    got = oracle.rounds(X, lk)
+    rec = sorted(zip(got["round"].tolist(), got["a"].tolist(), got["b"].tolist(),
+                     got["size"].tolist(), got["h"].tolist()))
+    want = [(0, 0, 1, 2, 1.0), (1, 2, 3, 2, 1.0), (2, 0, 2, 4, top)]
+    assert [r[:4] for r in rec] == [w[:4] for w in want]
+    for r, w in zip(rec, want):
+        assert r[4] == pytest.approx(w[4], rel=1e-15)
+
+
 def test_lattice_complete_exact_ties():
     """On a coarse lattice every complete-linkage value is sqrt of an exact
     FP64 integer multiple of the step^2, so ties are exact and the Lance-
