@@ -8,8 +8,9 @@ multiply-adds) against FP64 on random and adversarial inputs:
     float64 coordinates (|x| <= M after recentring) are rounded to float32,
     times sqrt(2|A||B|/(|A|+|B|)) for Ward's centroid form; u = 2^-24.
 
-Square roots are perturbed by the documented relative error of the
-hardware approximation the GPU-wide kernels use (2^-23 here, beyond it)."""
+Square roots are also perturbed by a relative 2^-23 in either direction,
+beyond the rounding of a correctly rounded root, as a margin for the
+approximate root the GPU-wide kernels take."""
 import numpy as np
 import pytest
 
