@@ -230,6 +230,30 @@ def test_centroid_lower_bound():
         assert c <= avg * (1 + 1e-12) and avg <= comp * (1 + 1e-12)
 
 
+def test_summary_upper_bounds():
+    """The summary upper bounds the search offers before evaluating a pair
+    (no point pairs needed): D_avg(A,B) <= sqrt(||c_A - c_B||^2 + var A +
+    var B) with per-point variances (Jensen: the mean of ||x - y|| is at most
+    the root of the mean of ||x - y||^2, which is that sum), and D_comp(A,B)
+    at most the distance between the farthest corners of the two bounding
+    boxes; both reach equality for singletons."""
+    rng = np.random.default_rng(10)
+    for _ in range(200):
+        d = int(rng.integers(1, 6))
+        A = rng.normal(size=(rng.integers(1, 12), d)) * rng.uniform(0.1, 3)
+        B = rng.normal(size=(rng.integers(1, 12), d)) * rng.uniform(0.1, 3) + rng.normal(size=d) * 3
+        pv = lambda P: ((P - P.mean(0)) ** 2).sum(1).mean()
+        ub_avg = math.sqrt(((A.mean(0) - B.mean(0)) ** 2).sum() + pv(A) + pv(B))
+        far = np.maximum(np.abs(A.max(0) - B.min(0)), np.abs(B.max(0) - A.min(0)))
+        ub_comp = math.sqrt((far ** 2).sum())
+        assert oracle.cluster_dist("average", A, B) <= ub_avg * (1 + 1e-12)
+        assert oracle.cluster_dist("complete", A, B) <= ub_comp * (1 + 1e-12)
+    x, y = rng.normal(size=(1, 3)), rng.normal(size=(1, 3))
+    assert oracle.cluster_dist("average", x, y) == pytest.approx(np.linalg.norm(x - y), rel=1e-14)
+    far = np.abs(x - y)
+    assert oracle.cluster_dist("complete", x, y) == pytest.approx(np.linalg.norm(far), rel=1e-14)
+
+
 def test_ward_radius_soundness():
     """Section 4.1: if Ward(Ci, B) <= beta then ||c_i - c_B|| <= beta *
     sqrt((|Ci| + n_min) / (2 n_min |Ci|)) for any |B| >= n_min."""
