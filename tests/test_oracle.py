@@ -254,6 +254,22 @@ def test_summary_upper_bounds():
     assert oracle.cluster_dist("complete", x, y) == pytest.approx(np.linalg.norm(far), rel=1e-14)
 
 
+def test_complete_linkage_necessary_conditions():
+    """Section 4.3 reading: the search keeps a candidate B for complete
+    linkage only if ||c_i - c_B|| <= beta and, on every axis,
+    max(hi_B - lo_A, hi_A - lo_B) <= beta; both are implied by
+    D_comp(A, B) <= beta (every point pair is within D_comp, on every axis)."""
+    rng = np.random.default_rng(12)
+    for _ in range(300):
+        d = int(rng.integers(1, 5))
+        A = rng.normal(size=(rng.integers(1, 10), d))
+        B = rng.normal(size=(rng.integers(1, 10), d)) + rng.normal(size=d)
+        beta = oracle.cluster_dist("complete", A, B) * rng.uniform(1.0, 1.3)
+        assert np.linalg.norm(A.mean(0) - B.mean(0)) <= beta * (1 + 1e-12)
+        ext = np.maximum(B.max(0) - A.min(0), A.max(0) - B.min(0))
+        assert np.all(ext <= beta * (1 + 1e-12))
+
+
 def test_ward_radius_soundness():
     """Section 4.1: if Ward(Ci, B) <= beta then ||c_i - c_B|| <= beta *
     sqrt((|Ci| + n_min) / (2 n_min |Ci|)) for any |B| >= n_min."""
