@@ -1650,17 +1650,17 @@ void hac_default_opts(hac_opts *o) {
 }
 
 int hac_create(const void *points, int64_t n, int d, hac_dtype dt, hac_linkage lk, hac_t *out) {
-  return create_common(points, false, n, d, dt, lk, out);
+  return abi_guard([&] { return create_common(points, false, n, d, dt, lk, out); });
 }
 
 int hac_create_device(const void *dev_points, int64_t n, int d, hac_dtype dt, hac_linkage lk,
                       hac_t *out) {
-  return create_common(dev_points, true, n, d, dt, lk, out);
+  return abi_guard([&] { return create_common(dev_points, true, n, d, dt, lk, out); });
 }
 
 int hac_run(hac_t h, const hac_opts *opts) {
   if (!h) return HAC_EINVAL;
-  int rc = run_impl(h, opts);
+  int rc = abi_guard([&] { return run_impl(h, opts); });
   if (rc == HAC_EDEVICE) cudaGetLastError();
   return rc;
 }
@@ -2015,7 +2015,7 @@ extern "C" int hac_run_static(const void *dev_points, int64_t n, int d, hac_dtyp
   Carver cv{arena, 0, kStaticArenaBytes, true};
   if (!carve_state(h, cv)) return HAC_EINVAL;
   const cudaStream_t st = (cudaStream_t)opt.stream;
-  rc = static_run(h, opt, st, dev_out);
+  rc = abi_guard([&] { return static_run(h, opt, st, dev_out); });
   if (rc == HAC_EDEVICE) cudaGetLastError();
   return rc;
 }

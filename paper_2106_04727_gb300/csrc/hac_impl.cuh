@@ -9,6 +9,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <new>
 #include <vector>
 
 namespace hacg {
@@ -160,10 +161,28 @@ int dalloc(hac_ctx *h, T **p, size_t count) {
     cudaGetLastError();
     return HAC_ENOMEM;
   }
-  h->allocs.push_back(q);
+  try {
+    h->allocs.push_back(q);
+  } catch (...) {
+    cudaFree(q);
+    return HAC_ENOMEM;
+  }
   h->bytes += (int64_t)(count * sizeof(T));
   *p = (T *)q;
   return HAC_OK;
+}
+
+// Runs f() and turns a C++ exception (a failed host allocation, a thread
+// that could not start) into a status code, so that none crosses the C ABI.
+template <typename F>
+int abi_guard(F &&f) noexcept {
+  try {
+    return f();
+  } catch (const std::bad_alloc &) {
+    return HAC_ENOMEM;
+  } catch (...) {
+    return HAC_EINTERNAL;
+  }
 }
 
 void free_all(hac_ctx *h);

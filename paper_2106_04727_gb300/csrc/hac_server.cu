@@ -542,7 +542,7 @@ void engine_fail(hac_server *srv, Engine &e, int rc) {
   srv->done_cv.notify_all();
 }
 
-void engine_loop(hac_server *srv, Engine *ep) {
+void engine_loop_body(hac_server *srv, Engine *ep) {
   Engine &e = *ep;
   if (cudaSetDevice(srv->device) != cudaSuccess) {
     cudaGetLastError();
@@ -652,9 +652,21 @@ void engine_loop(hac_server *srv, Engine *ep) {
   }
 }
 
+// The engine thread: an exception (a failed host allocation) fails the
+// engine's requests with a status instead of ending the process.
+void engine_loop(hac_server *srv, Engine *ep) {
+  try {
+    engine_loop_body(srv, ep);
+  } catch (const std::bad_alloc &) {
+    engine_fail(srv, *ep, HAC_ENOMEM);
+  } catch (...) {
+    engine_fail(srv, *ep, HAC_EINTERNAL);
+  }
+}
+
 }  // namespace
 
-extern "C" int hac_server_create(int64_t points_per_engine, const hac_opts *opts,
+static int hac_server_create_body(int64_t points_per_engine, const hac_opts *opts,
                                  hac_server_t *out) {
   if (!out) return HAC_EINVAL;
   *out = nullptr;
@@ -682,7 +694,7 @@ int submit_impl(hac_server_t srv, const void *points, int64_t n, int d, hac_dtyp
                 hac_linkage lk, double timeout_s, bool want_rounds, uint64_t *ticket);
 }
 
-extern "C" int hac_submit(hac_server_t srv, const void *points, int64_t n, int d, hac_dtype dt,
+static int hac_submit_body(hac_server_t srv, const void *points, int64_t n, int d, hac_dtype dt,
                           hac_linkage lk, double timeout_s, uint64_t *ticket) {
   return submit_impl(srv, points, n, d, dt, lk, timeout_s, false, ticket);
 }
@@ -767,7 +779,7 @@ int submit_impl(hac_server_t srv, const void *points, int64_t n, int d, hac_dtyp
 }
 }  // namespace
 
-extern "C" int hac_cancel(hac_server_t srv, uint64_t ticket) {
+static int hac_cancel_body(hac_server_t srv, uint64_t ticket) {
   if (!srv) return HAC_EINVAL;
   std::unique_lock<std::mutex> g(srv->mu);
   auto it = srv->reqs.find(ticket);
@@ -789,7 +801,7 @@ extern "C" int hac_cancel(hac_server_t srv, uint64_t ticket) {
   return HAC_OK;
 }
 
-extern "C" int hac_poll(hac_server_t srv, uint64_t ticket, hac_merge *out, int64_t cap,
+static int hac_poll_body(hac_server_t srv, uint64_t ticket, hac_merge *out, int64_t cap,
                         int64_t *n_written, double *latency_ms) {
   if (!srv || !n_written) return HAC_EINVAL;
   std::lock_guard<std::mutex> g(srv->mu);
@@ -809,7 +821,7 @@ extern "C" int hac_poll(hac_server_t srv, uint64_t ticket, hac_merge *out, int64
   return rc;
 }
 
-extern "C" int hac_server_wait(hac_server_t srv, uint64_t ticket, double timeout_s) {
+static int hac_server_wait_body(hac_server_t srv, uint64_t ticket, double timeout_s) {
   if (!srv || !(timeout_s >= 0)) return HAC_EINVAL;
   std::unique_lock<std::mutex> g(srv->mu);
   auto ready = [&] {
@@ -826,7 +838,7 @@ extern "C" int hac_server_wait(hac_server_t srv, uint64_t ticket, double timeout
   return HAC_OK;
 }
 
-extern "C" int hac_server_stats(hac_server_t srv, hac_server_stats_t *out) {
+static int hac_server_stats_body(hac_server_t srv, hac_server_stats_t *out) {
   if (!srv || !out) return HAC_EINVAL;
   std::lock_guard<std::mutex> g(srv->mu);
   hac_server_stats_t st{};
@@ -849,7 +861,7 @@ extern "C" int hac_server_stats(hac_server_t srv, hac_server_stats_t *out) {
   return srv->err;
 }
 
-extern "C" void hac_server_destroy(hac_server_t srv) {
+static void hac_server_destroy_body(hac_server_t srv) {
   if (!srv) return;
   {
     std::lock_guard<std::mutex> g(srv->mu);
@@ -869,7 +881,7 @@ extern "C" void hac_server_destroy(hac_server_t srv) {
 // Several handles clustered together: a private server with one engine per
 // kind, every handle submitted at once, results written back into the handles
 // as hac_run would leave them.
-extern "C" int hac_run_batch(hac_t *hs, int count, const hac_opts *opts) {
+static int hac_run_batch_body(hac_t *hs, int count, const hac_opts *opts) {
   if (count < 0 || (count > 0 && !hs)) return HAC_EINVAL;
   hac_opts o;
   hac_default_opts(&o);
@@ -941,4 +953,47 @@ extern "C" int hac_run_batch(hac_t *hs, int count, const hac_opts *opts) {
   for (int i = 0; i < count; ++i)
     if (st[i] != HAC_OK) return st[i];
   return HAC_OK;
+}
+
+// ---------------------------------------------------------------------------
+// C ABI: each entry point runs its body under abi_guard, so that a failed host
+// allocation or thread start returns a status instead of ending the process.
+// ---------------------------------------------------------------------------
+
+extern "C" int hac_server_create(int64_t points_per_engine, const hac_opts *opts,
+                                 hac_server_t *out) {
+  return abi_guard([&] { return hac_server_create_body(points_per_engine, opts, out); });
+}
+
+extern "C" int hac_submit(hac_server_t srv, const void *points, int64_t n, int d, hac_dtype dt,
+                          hac_linkage lk, double timeout_s, uint64_t *ticket) {
+  return abi_guard([&] { return hac_submit_body(srv, points, n, d, dt, lk, timeout_s, ticket); });
+}
+
+extern "C" int hac_cancel(hac_server_t srv, uint64_t ticket) {
+  return abi_guard([&] { return hac_cancel_body(srv, ticket); });
+}
+
+extern "C" int hac_poll(hac_server_t srv, uint64_t ticket, hac_merge *out, int64_t cap,
+                        int64_t *n_written, double *latency_ms) {
+  return abi_guard([&] { return hac_poll_body(srv, ticket, out, cap, n_written, latency_ms); });
+}
+
+extern "C" int hac_server_wait(hac_server_t srv, uint64_t ticket, double timeout_s) {
+  return abi_guard([&] { return hac_server_wait_body(srv, ticket, timeout_s); });
+}
+
+extern "C" int hac_server_stats(hac_server_t srv, hac_server_stats_t *out) {
+  return abi_guard([&] { return hac_server_stats_body(srv, out); });
+}
+
+extern "C" int hac_run_batch(hac_t *hs, int count, const hac_opts *opts) {
+  return abi_guard([&] { return hac_run_batch_body(hs, count, opts); });
+}
+
+extern "C" void hac_server_destroy(hac_server_t srv) {
+  try {
+    hac_server_destroy_body(srv);
+  } catch (...) {
+  }
 }
