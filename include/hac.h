@@ -125,46 +125,61 @@ typedef struct {
                                 over rounds */
 } hac_stats_t;
 
-/* Default options (FP64, no cache, no limits, own stream). */
+/* Default options (FP64, no cache, no limits, own stream).  No counterpart in
+ * the paper (the library's own run options). */
 void hac_default_opts(hac_opts *opts);
 
-/* Create an instance from HOST points: `points` is row-major n x d of type
+/* Create an instance from HOST points (paper: Algorithm 1's input, Section 3;
+ * every point starts as a singleton cluster whose cid is its input index,
+ * Section 1 footnote): `points` is row-major n x d of type
  * `dt` (float or double), read during the call and not retained.  Allocates
  * all device memory the instance needs; the points are copied to the device.
  * HAC_EINVAL: points/out NULL, n < 1, d < 1 or d > 16, unknown dt/lk, or a
  * non-finite coordinate.  HAC_ENOMEM: device allocation failed. */
 int hac_create(const void *points, int64_t n, int d, hac_dtype dt, hac_linkage lk, hac_t *out);
 
-/* As hac_create, but `dev_points` is a DEVICE pointer (row-major n x d of
+/* (Paper: as hac_create, Algorithm 1's input.)  As hac_create, but
+ * `dev_points` is a DEVICE pointer (row-major n x d of
  * `dt`, on the current device) that the caller keeps owning; it is copied
  * device-to-device during the call.  Non-finite coordinates are reported by
  * hac_run as HAC_EINVAL. */
 int hac_create_device(const void *dev_points, int64_t n, int d, hac_dtype dt, hac_linkage lk,
                       hac_t *out);
 
-/* Run the whole clustering (initial layout, then rounds until one cluster is
- * left).  opts may be NULL (defaults).  Blocks until done.  May be called
+/* Run the whole clustering (paper: Algorithm 1 -- initialisation, then rounds
+ * of nearest-neighbour search (Algorithms 2-4, Section 4), chain update,
+ * reciprocal-pair filter, merges and the Section 5 cache update (Algorithm 5)
+ * until one cluster is left).  opts may be NULL (defaults).  Blocks until done.  May be called
  * again on the same handle: each call recomputes from the stored points.
  * HAC_ETIMEOUT if a limit in opts is hit (the handle stays usable). */
 int hac_run(hac_t h, const hac_opts *opts);
 
-/* Copy the n-1 merges of the last completed hac_run to host array `out`
+/* Copy the n-1 merges of the last completed hac_run (paper: the merges of
+ * Algorithm 1's merge step; heights are the Table 1 linkage values, cids as
+ * in the Section 1 footnote; the sort order is this library's own, the paper
+ * fixes none) to host array `out`
  * (capacity `cap` records), sorted by (height, size, cid_a).  *n_written
  * receives the count.  HAC_EPENDING before a completed run, HAC_ECAP if
  * cap < n - 1. */
 int hac_dendrogram(hac_t h, hac_merge *out, int64_t cap, int64_t *n_written);
 
-/* The round (0-based) in which each merge of hac_dendrogram's output was
- * made, in the same order.  Same errors as hac_dendrogram. */
+/* The round (0-based) of Algorithm 1 (paper: Section 3, one iteration of its
+ * main loop) in which each merge of hac_dendrogram's output was made, in the
+ * same order.  Same errors as hac_dendrogram. */
 int hac_merge_rounds(hac_t h, int32_t *out, int64_t cap, int64_t *n_written);
 
-/* Counters and phase times of the last hac_run. */
+/* Counters and phase times of the last hac_run (paper: Section 6, analysis of
+ * the framework -- point_pairs is the count of distance computations the
+ * paper calls D, cluster_pairs and the search counters its range-query
+ * statistics).  HAC_EINVAL for a NULL handle or out. */
 int hac_stats(hac_t h, hac_stats_t *out);
 
-/* Free the instance and all its device memory.  NULL is a no-op. */
+/* Free the instance and all its device memory.  NULL is a no-op.  No
+ * counterpart in the paper. */
 void hac_destroy(hac_t h);
 
-/* Static description of a status code. */
+/* Static description of a status code (never NULL; unknown codes get a
+ * generic text).  No counterpart in the paper. */
 const char *hac_strerror(int code);
 
 /* Largest n accepted by hac_run_static. */
@@ -176,11 +191,15 @@ const char *hac_strerror(int code);
  * byte of the GPU, or latency-sensitive code that must not risk the device
  * synchronisation that cudaMalloc/cudaFree can cause).
  *
- * Same result as hac_create + hac_run + hac_dendrogram on the same points and
- * options, computed by the same kernels, but all working memory comes from a
- * fixed 6 MiB device array inside the library, which every GPU that loads the
- * library holds until the process exits.  No cudaMalloc, cudaFree or other
- * allocating call is made.
+ * Same dendrogram as hac_create + hac_run + hac_dendrogram on the same points
+ * and options, computed by the same kernels, but all working memory comes
+ * from a fixed 6 MiB device array inside the library, which every GPU that
+ * loads the library holds until the process exits.  No cudaMalloc, cudaFree
+ * or other allocating call is made.  The pair-distance cache needs memory, so
+ * opts->cache_slots is ignored (no cache, hence no GPU-wide big-pair
+ * evaluation), and the HAC_* environment overrides that hac_create reads
+ * (HAC_BIG_PAIRS, HAC_BIG_PAIRS_F64, HAC_WARP_BUDGET, HAC_BRUTE) do not apply;
+ * these change speed only, never the result.  HAC_FLAG_NO_PRUNE is honoured.
  *   dev_points  DEVICE pointer, row-major n x d of `dt`, on the current device;
  *               read only, owned by the caller.
  *   opts        may be NULL (defaults); opts->stream selects the stream
@@ -190,11 +209,11 @@ const char *hac_strerror(int code);
  * Errors: HAC_EINVAL for n > HAC_STATIC_MAX_N (or the usual bad arguments,
  * including non-finite coordinates), HAC_ECAP if cap < n - 1, HAC_EDEVICE if
  * the array's device address cannot be obtained or a CUDA call fails.
- * The first call on each device looks up the array's device address (once per
- * device, with that device current); make that first call before any stream
- * capture.  Every call shares the one array and overwrites it, so calls that
- * overlap on the GPU (other host threads, other streams) race and must be
- * serialised by the caller. */
+ * Every call looks up the array's device address on the current device
+ * (cudaGetSymbolAddress, which allocates nothing once the library's device
+ * code is loaded).  Every call shares the one array and overwrites it, so
+ * calls that overlap on the GPU (other host threads, other streams) race and
+ * must be serialised by the caller. */
 int hac_run_static(const void *dev_points, int64_t n, int d, hac_dtype dt, hac_linkage lk,
                    const hac_opts *opts, hac_merge *dev_out, int64_t cap);
 
@@ -233,7 +252,8 @@ typedef struct {
   double ms_harvest;       /* ... handing out finished requests */
 } hac_server_stats_t;
 
-/* Create a server on the current CUDA device.  `points_per_engine` (2 ..
+/* (No counterpart in the paper, like every serving call below; each request
+ * is one run of Algorithm 1.)  Create a server on the current CUDA device.  `points_per_engine` (2 ..
  * 2^29) sizes every engine, and bounds the n of a request.  An engine holds
  * about 0.35 KB (d <= 2) to 1.4 KB (d > 8) of device memory per point; with
  * opts->cache_slots > 0, complete and average engines add about 88 bytes
@@ -243,7 +263,8 @@ typedef struct {
  * are ignored.  HAC_EINVAL for bad arguments, HAC_ENOMEM, HAC_EDEVICE. */
 int hac_server_create(int64_t points_per_engine, const hac_opts *opts, hac_server_t *out);
 
-/* Queue a request: HOST points, row-major n x d of `dt`, copied during the
+/* (No counterpart in the paper.)  Queue a request (Algorithm 1's input, as
+ * hac_create): HOST points, row-major n x d of `dt`, copied during the
  * call.  timeout_s > 0 sets a deadline from now: a request not finished by
  * then leaves at the next round boundary with HAC_ETIMEOUT.  *ticket names
  * it for hac_poll / hac_server_wait / hac_cancel.  Never blocks on the GPU,
@@ -253,12 +274,13 @@ int hac_server_create(int64_t points_per_engine, const hac_opts *opts, hac_serve
 int hac_submit(hac_server_t srv, const void *points, int64_t n, int d, hac_dtype dt,
                hac_linkage lk, double timeout_s, uint64_t *ticket);
 
-/* Cancel a request: a queued one leaves at once, a resident one at the next
+/* (No counterpart in the paper.)  Cancel a request: a queued one leaves at once, a resident one at the next
  * round boundary; either then completes with HAC_ECANCELED.  HAC_OK also if
  * it had already finished (its result stays).  HAC_EINVAL: unknown ticket. */
 int hac_cancel(hac_server_t srv, uint64_t ticket);
 
-/* Non-blocking result of a request.  HAC_EPENDING while it runs.  Once it
+/* (No counterpart in the paper; the result is Algorithm 1's merges as in
+ * hac_dendrogram.)  Non-blocking result of a request.  HAC_EPENDING while it runs.  Once it
  * has finished, the n-1 merges go to host array `out` (capacity `cap`;
  * HAC_ECAP if too small, ticket kept), *n_written receives their count,
  * *latency_ms (may be NULL) the time from hac_submit to completion, and the
@@ -268,21 +290,22 @@ int hac_cancel(hac_server_t srv, uint64_t ticket);
 int hac_poll(hac_server_t srv, uint64_t ticket, hac_merge *out, int64_t cap, int64_t *n_written,
              double *latency_ms);
 
-/* Block until the request has finished (hac_poll will not return
+/* (No counterpart in the paper.)  Block until the request has finished (hac_poll will not return
  * HAC_EPENDING) or timeout_s seconds passed (HAC_ETIMEOUT); timeout_s = 0
  * waits without limit.  HAC_EINVAL: unknown ticket. */
 int hac_server_wait(hac_server_t srv, uint64_t ticket, double timeout_s);
 
-/* Counters of the server; returns the sticky error of a failed engine
+/* (No counterpart in the paper.)  Counters of the server; returns the sticky error of a failed engine
  * (HAC_OK if none). */
 int hac_server_stats(hac_server_t srv, hac_server_stats_t *out);
 
-/* Stop every engine after its current round, free all device memory and
+/* (No counterpart in the paper.)  Stop every engine after its current round, free all device memory and
  * every unreleased request.  NULL is a no-op. */
 void hac_server_destroy(hac_server_t srv);
 
 /* Cluster the points of `count` distinct handles together (the batched form
- * of hac_run; the paper has no counterpart).  Handles of the same linkage,
+ * of hac_run, i.e. of Algorithm 1 per handle; the paper has no counterpart
+ * for the batching).  Handles of the same linkage,
  * dimension and input type share one engine of a private server, so each
  * round is one launch per kernel for all of them; different kinds run
  * concurrently.  Afterwards each handle holds what hac_run(h, opts) would

@@ -358,32 +358,46 @@ __global__ void __launch_bounds__(BIG_TPB) k_big_eval32(State s, int r0) {
   }
 }
 
-// CTAs that stay resident together: one wave, tiles handed out dynamically
+// CTAs that stay resident together: one wave (occupancy x SMs CTAs), tiles
+// handed out dynamically; computed once per device and kernel (the cache is
+// the caller's, one per instantiation)
+struct GridCache {
+  std::atomic<int> g[64];
+};
+
 template <typename F>
-int resident_grid(F kernel) {
-  int dev = 0, sms = 0, per = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess ||
-      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kernel, BIG_TPB, 0) != cudaSuccess) {
+int resident_grid(F kernel, GridCache &c) {
+  int dev = 0, per = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
     cudaGetLastError();
-    return 152 * 4;
+    return 1;
   }
-  return std::max(1, sms) * std::max(1, per);
+  const bool cached = dev >= 0 && dev < 64;
+  if (cached) {
+    const int v = c.g[dev].load(std::memory_order_relaxed);
+    if (v > 0) return v;
+  }
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kernel, BIG_TPB, 0) != cudaSuccess) {
+    cudaGetLastError();
+    per = 1;
+  }
+  const int g = device_sms() * std::max(1, per);
+  if (cached) c.g[dev].store(g, std::memory_order_relaxed);
+  return g;
 }
 
 template <int LK, int D>
 void launch_big32(const State &s, int r0, cudaStream_t st) {
   constexpr int DP = D <= 2 ? 2 : D <= 4 ? 4 : D <= 8 ? 8 : 16;
-  static const int g0 = resident_grid(k_big_eval32<LK, D, DP, 0>);
-  static const int g1 = resident_grid(k_big_eval32<LK, D, DP, 1>);
-  k_big_eval32<LK, D, DP, 0><<<g0, BIG_TPB, 0, st>>>(s, r0);
-  k_big_eval32<LK, D, DP, 1><<<g1, BIG_TPB, 0, st>>>(s, r0);
+  static GridCache c0, c1;
+  k_big_eval32<LK, D, DP, 0><<<resident_grid(k_big_eval32<LK, D, DP, 0>, c0), BIG_TPB, 0, st>>>(s, r0);
+  k_big_eval32<LK, D, DP, 1><<<resident_grid(k_big_eval32<LK, D, DP, 1>, c1), BIG_TPB, 0, st>>>(s, r0);
 }
 
 template <int LK, int DP>
 void launch_big64(const State &s, int r0, cudaStream_t st) {
-  static const int g = resident_grid(k_big_eval64<LK, DP>);
-  k_big_eval64<LK, DP><<<g, BIG_TPB, 0, st>>>(s, r0);
+  static GridCache c;
+  k_big_eval64<LK, DP><<<resident_grid(k_big_eval64<LK, DP>, c), BIG_TPB, 0, st>>>(s, r0);
 }
 
 template <int LK>

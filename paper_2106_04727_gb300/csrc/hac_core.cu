@@ -14,7 +14,6 @@
 #include "hac_impl.cuh"
 
 #include <algorithm>
-#include <atomic>
 #include <type_traits>
 #include <chrono>
 #include <cstdio>
@@ -876,6 +875,27 @@ __global__ void k_rec_gather(const State s, int m, const int32_t *perm, hac_merg
 
 namespace hacg {
 
+int device_sms() {
+  constexpr int kMaxDev = 64;
+  static std::atomic<int> cache[kMaxDev];
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    cudaGetLastError();
+    return 1;
+  }
+  if (dev >= 0 && dev < kMaxDev) {
+    const int v = cache[dev].load(std::memory_order_relaxed);
+    if (v > 0) return v;
+  }
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+      sms < 1) {
+    cudaGetLastError();
+    return 1;
+  }
+  if (dev >= 0 && dev < kMaxDev) cache[dev].store(sms, std::memory_order_relaxed);
+  return sms;
+}
+
 void free_all(hac_ctx *h) {
   for (void *p : h->allocs) cudaFree(p);
   h->allocs.clear();
@@ -1030,27 +1050,28 @@ int bits_for(int64_t maxval) {
   return b;
 }
 
+// Initial layout (Algorithm 1 initialisation): bounding box, recentring,
+// Morton keys, radix sort, permuted points and per-cluster state, the tree.
+// Host buffers are stack arrays, so hac_run_static can use it unchanged.
 template <typename T>
 int init_layout(hac_ctx *h, cudaStream_t st) {
   State &s = h->s;
   const T *X = (const T *)h->raw;
   const int64_t n = h->n;
   const int d = h->d;
-  std::vector<unsigned long long> init(2 * MAXD);
+  unsigned long long bb[2 * MAXD];
   for (int k = 0; k < MAXD; ++k) {
-    init[k] = ~0ull;
-    init[MAXD + k] = 0ull;
+    bb[k] = ~0ull;
+    bb[MAXD + k] = 0ull;
   }
-  CK(cudaMemcpyAsync(h->bb, init.data(), 2 * MAXD * sizeof(unsigned long long),
-                     cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(h->bb, bb, sizeof(bb), cudaMemcpyHostToDevice, st));
+  // counters start from zero (the allocation-free arena keeps the last call's)
   CK(cudaMemsetAsync(s.ctr, 0, sizeof(Counters), st));
   k_bbox<T><<<grid_for(n, TPB), TPB, 0, st>>>(X, n, d, h->bb, h->bb + MAXD, s.ctr);
   h->launches += 3;  // bbox, morton, layout
   CK(cudaGetLastError());
-  std::vector<unsigned long long> bb(2 * MAXD);
   Counters c0;
-  CK(cudaMemcpyAsync(bb.data(), h->bb, 2 * MAXD * sizeof(unsigned long long),
-                     cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(bb, h->bb, sizeof(bb), cudaMemcpyDeviceToHost, st));
   CK(cudaMemcpyAsync(&c0, s.ctr, sizeof(Counters), cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
   if (c0.err & ERR_NONFINITE) return HAC_EINVAL;
@@ -1088,6 +1109,31 @@ int init_layout(hac_ctx *h, cudaStream_t st) {
   c.nactive = (int)n;
   CK(cudaMemcpyAsync(s.ctr, &c, sizeof(Counters), cudaMemcpyHostToDevice, st));
   return build_tree(h, s.order[0], (int)n, st);
+}
+
+// Canonical order of the merge records on the device, (height, size, cid_a)
+// by three stable radix passes ((cid_a, size) already identifies a merge, so
+// the order is total), gathered into `out` / `out_round`.
+int sort_records(hac_ctx *h, cudaStream_t st, hac_merge *out, int32_t *out_round) {
+  State &s = h->s;
+  const int64_t m = h->n - 1;
+  if (m <= 0) return HAC_OK;
+  const int mm = (int)m;
+  const int g = grid_for(mm, TPB);
+  int32_t *perm = nullptr;
+  const int fbits[3] = {bits_for(h->n), bits_for(h->n), 64};
+  for (int f = 0; f < 3; ++f) {
+    k_rec_key<<<g, TPB, 0, st>>>(s, mm, f, perm, h->keys[0], h->vals[0]);
+    const int r = radix_sort(h, mm, fbits[f], st);
+    if (r < 0) return r;
+    if (r == 1)
+      CK(cudaMemcpyAsync(h->vals[0], h->vals[1], (size_t)mm * 4, cudaMemcpyDeviceToDevice, st));
+    perm = h->vals[0];
+  }
+  k_rec_gather<<<g, TPB, 0, st>>>(s, mm, perm, out, out_round);
+  h->launches += 4;
+  CK(cudaGetLastError());
+  return HAC_OK;
 }
 
 int create_common(const void *pts, bool dev, int64_t n, int d, hac_dtype dt, hac_linkage lk,
@@ -1285,7 +1331,7 @@ int round_step(hac_ctx *h, cudaStream_t st, int round, int K, int nterm, RoundCt
   ctl.searches += nterm;
   h->launches += 1;
   if (s.cache_slots > 0) {
-    k_cache_insert<<<grid_for((int64_t)152 * 8 * TPB, TPB), TPB, 0, st>>>(s);
+    k_cache_insert<<<grid_for((int64_t)device_sms() * 8 * TPB, TPB), TPB, 0, st>>>(s);
     CK(cudaMemsetAsync(&s.ctr->nins, 0, sizeof(int32_t), st));
     h->launches += 1;
   }
@@ -1336,7 +1382,7 @@ int round_step(hac_ctx *h, cudaStream_t st, int round, int K, int nterm, RoundCt
     CK(launch_query(qa, s.dp, s.prec, st));
     EVREC(ctl.eq1);
     ++ctl.qlaunch;
-    k_cache_insert<<<grid_for((int64_t)152 * 8 * TPB, TPB), TPB, 0, st>>>(s);
+    k_cache_insert<<<grid_for((int64_t)device_sms() * 8 * TPB, TPB), TPB, 0, st>>>(s);
     CK(cudaMemsetAsync(&s.ctr->nins, 0, sizeof(int32_t), st));
     h->launches += 2;
   }
@@ -1356,7 +1402,7 @@ int round_step(hac_ctx *h, cudaStream_t st, int round, int K, int nterm, RoundCt
   if (s.cache_slots > 0) {
     const int S = s.cache_slots;
     const size_t smem = (size_t)CM_WARPS * 5 * S * sizeof(CEntry);
-    const int blocks = std::max(1, std::min(cdiv(npairs, CM_WARPS), 152 * 32));
+    const int blocks = std::max(1, std::min(cdiv(npairs, CM_WARPS), device_sms() * 32));
     // more than the default 48 KB of shared memory per block for large tables
     if (s.linkage == LK_COMPLETE) {
       CK(cudaFuncSetAttribute(k_cache_merge<0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -1401,6 +1447,87 @@ static void dfree(hac_ctx *h, T *&p, size_t count) {
       break;
     }
   p = nullptr;
+}
+
+// Phase timing and per-round trace of run_rounds (hac_run only).
+struct RoundTimes {
+  cudaEvent_t e0 = nullptr, e3 = nullptr;
+  double ms_nn = 0, ms_merge = 0, ms_update = 0;
+  bool trace = false;
+};
+
+// Algorithm 1's rounds from the initial layout until one cluster is left:
+// round_step, tree rebuild, then the round's counters are read and checked.
+// HAC_ETIMEOUT once a limit of `opt` is reached (checked between rounds).
+// `tm` may be null (no timing; ctl's events must be null too).
+int run_rounds(hac_ctx *h, const hac_opts &opt, cudaStream_t st, RoundCtl &ctl, RoundTimes *tm,
+               std::chrono::steady_clock::time_point t0, int *rounds_out) {
+  State &s = h->s;
+  int K = (int)h->n, nterm = (int)h->n, round = 0, rc = 0;
+  Counters c{}, cprev{};
+  const bool trace = tm && tm->trace;
+  *rounds_out = 0;
+  while (K > 1) {
+    if (opt.max_rounds && round >= opt.max_rounds) return HAC_ETIMEOUT;
+    if (opt.timeout_s > 0 &&
+        std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count() >
+            opt.timeout_s)
+      return HAC_ETIMEOUT;
+    if (tm) cudaEventRecord(tm->e0, st);
+    const int big_iters0 = ctl.big_iters, big_reqs0 = ctl.big_reqs;
+    ctl.naive += (int64_t)nterm * (K - 1);
+    int npairs = 0;
+    rc = round_step(h, st, round, K, nterm, ctl, &npairs);
+    if (rc == HAC_EINTERNAL && npairs <= 0 && trace) {
+      CK(cudaMemcpyAsync(&c, s.ctr, sizeof(Counters), cudaMemcpyDeviceToHost, st));
+      CK(cudaStreamSynchronize(st));
+      fprintf(stderr, "hac round %d: no reciprocal pair (err %d)\n", round, c.err);
+    }
+    if (rc) return rc;
+    K -= npairs;
+    if (K > 1) {
+      rc = build_tree(h, s.order[h->ocur], K, st);
+      if (rc) return rc;
+    }
+    if (tm) cudaEventRecord(tm->e3, st);
+    CK(cudaMemcpyAsync(&c, s.ctr, sizeof(Counters), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    // the last merge finishes the instance: its single cluster leaves the order
+    if ((c.err & ~ERR_NONFINITE) || (c.nactive != K && !(K == 1 && c.nactive == 0))) {
+      if (trace)
+        fprintf(stderr, "hac round %d: consistency (err %d, active %d, expected %d)\n", round,
+                c.err, c.nactive, K);
+      return HAC_EINTERNAL;
+    }
+    if (tm) {
+      float a, b, d3, q;
+      cudaEventElapsedTime(&a, tm->e0, ctl.e1);
+      cudaEventElapsedTime(&b, ctl.e1, ctl.e2);
+      cudaEventElapsedTime(&d3, ctl.e2, tm->e3);
+      cudaEventElapsedTime(&q, ctl.eq0, ctl.eq1);
+      ctl.ms_query += q;
+      tm->ms_nn += a;
+      tm->ms_merge += b;
+      tm->ms_update += d3;
+      if (trace) {
+        fprintf(stderr,
+                "hac round %d K %d terms %d pairs %d query_ms %.3f leaf_tests %llu nodes %llu "
+                "cpairs %llu ppairs %llu rechecks %llu nn_ms %.3f merge_ms %.3f update_ms %.3f "
+                "big_iters %d big_reqs %d hits %llu big_pp %llu big_exact %llu\n",
+                round, K + npairs, nterm, npairs, q, c.ltests - cprev.ltests,
+                c.nodes - cprev.nodes, c.cluster_pairs - cprev.cluster_pairs,
+                c.point_pairs - cprev.point_pairs, c.rechecks - cprev.rechecks, a, b, d3,
+                ctl.big_iters - big_iters0, ctl.big_reqs - big_reqs0,
+                c.cache_hits - cprev.cache_hits, c.big_pp - cprev.big_pp,
+                c.big_exact - cprev.big_exact);
+        cprev = c;
+      }
+    }
+    nterm = c.nterm;
+    ++round;
+    *rounds_out = round;
+  }
+  return HAC_OK;
 }
 
 int run_impl(hac_ctx *h, const hac_opts *o) {
@@ -1478,11 +1605,6 @@ int run_impl(hac_ctx *h, const hac_opts *o) {
     cudaEventElapsedTime(&ms, e0.e, e1.e);
     ms_init = ms;
   }
-  int K = (int)h->n, nterm = (int)h->n, round = 0;
-  int64_t naive = 0;  // cluster pairs a search without range queries would test
-  Counters c{}, cprev{};
-  const char *tr = getenv("HAC_TRACE");
-  const bool trace = tr && tr[0] && tr[0] != '0';
   RoundCtl ctl;
   ctl.e1 = e1.e;
   ctl.e2 = e2.e;
@@ -1490,71 +1612,19 @@ int run_impl(hac_ctx *h, const hac_opts *o) {
   ctl.eq1 = eq1.e;
   ctl.eb0 = eb0.e;
   ctl.eb1 = eb1.e;
-  while (K > 1) {
-    if (opt.max_rounds && round >= opt.max_rounds) return HAC_ETIMEOUT;
-    if (opt.timeout_s > 0 &&
-        std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count() >
-            opt.timeout_s)
-      return HAC_ETIMEOUT;
-    cudaEventRecord(e0.e, st);
-    const int big_iters0 = ctl.big_iters, big_reqs0 = ctl.big_reqs;
-    naive += (int64_t)nterm * (K - 1);
-    int npairs = 0;
-    rc = round_step(h, st, round, K, nterm, ctl, &npairs);
-    if (rc == HAC_EINTERNAL && npairs <= 0) {
-      CK(cudaMemcpyAsync(&c, s.ctr, sizeof(Counters), cudaMemcpyDeviceToHost, st));
-      CK(cudaStreamSynchronize(st));
-      if (trace) fprintf(stderr, "hac round %d: no reciprocal pair (err %d)\n", round, c.err);
-    }
-    if (rc) return rc;
-    K -= npairs;
-    if (K > 1) {
-      rc = build_tree(h, s.order[h->ocur], K, st);
-      if (rc) return rc;
-    }
-    cudaEventRecord(e3.e, st);
-    CK(cudaMemcpyAsync(&c, s.ctr, sizeof(Counters), cudaMemcpyDeviceToHost, st));
-    CK(cudaStreamSynchronize(st));
-    // the last merge finishes the instance: its single cluster leaves the order
-    if ((c.err & ~ERR_NONFINITE) || (c.nactive != K && !(K == 1 && c.nactive == 0))) {
-      if (trace)
-        fprintf(stderr, "hac round %d: consistency (err %d, active %d, expected %d)\n", round,
-                c.err, c.nactive, K);
-      return HAC_EINTERNAL;
-    }
-    if (trace) {
-      float qms, nms, mms, ums;
-      cudaEventElapsedTime(&qms, eq0.e, eq1.e);
-      cudaEventElapsedTime(&nms, e0.e, e1.e);
-      cudaEventElapsedTime(&mms, e1.e, e2.e);
-      cudaEventElapsedTime(&ums, e2.e, e3.e);
-      fprintf(stderr,
-              "hac round %d K %d terms %d pairs %d query_ms %.3f leaf_tests %llu nodes %llu "
-              "cpairs %llu ppairs %llu rechecks %llu nn_ms %.3f merge_ms %.3f update_ms %.3f "
-              "big_iters %d big_reqs %d hits %llu big_pp %llu big_exact %llu\n",
-              round, K + npairs, nterm, npairs, qms, c.ltests - cprev.ltests,
-              c.nodes - cprev.nodes, c.cluster_pairs - cprev.cluster_pairs,
-              c.point_pairs - cprev.point_pairs, c.rechecks - cprev.rechecks, nms, mms, ums,
-              ctl.big_iters - big_iters0, ctl.big_reqs - big_reqs0,
-              c.cache_hits - cprev.cache_hits, c.big_pp - cprev.big_pp,
-              c.big_exact - cprev.big_exact);
-      cprev = c;
-    }
-    nterm = c.nterm;
-    {
-      float a, b, d3;
-      cudaEventElapsedTime(&a, e0.e, e1.e);
-      cudaEventElapsedTime(&b, e1.e, e2.e);
-      cudaEventElapsedTime(&d3, e2.e, e3.e);
-      float q;
-      cudaEventElapsedTime(&q, eq0.e, eq1.e);
-      ctl.ms_query += q;
-      ms_nn += a;
-      ms_merge += b;
-      ms_update += d3;
-    }
-    ++round;
-  }
+  RoundTimes tm;
+  tm.e0 = e0.e;
+  tm.e3 = e3.e;
+  const char *tr = getenv("HAC_TRACE");
+  tm.trace = tr && tr[0] && tr[0] != '0';
+  int round = 0;
+  rc = run_rounds(h, opt, st, ctl, &tm, t0, &round);
+  if (rc) return rc;
+  ms_nn = tm.ms_nn;
+  ms_merge = tm.ms_merge;
+  ms_update = tm.ms_update;
+  const int64_t naive = ctl.naive;
+  Counters c{};
   ms_query = ctl.ms_query;
   ms_big = ctl.ms_big;
   qlaunch = ctl.qlaunch;
@@ -1565,27 +1635,9 @@ int run_impl(hac_ctx *h, const hac_opts *o) {
   CK(cudaStreamSynchronize(st));
   const int64_t m = h->n - 1;
   if (c.nmerges != m) return HAC_EINTERNAL;
-  // canonical order on the device: (height, size, cid_a); (cid_a, size)
-  // already identifies a merge, so the order is total
-  if (m > 0) {
-    const int mm = (int)m;
-    const int g = grid_for(mm, TPB);
-    int32_t *perm = nullptr;
-    const int fbits[3] = {bits_for(h->n), bits_for(h->n), 64};
-    for (int f = 0; f < 3; ++f) {
-      k_rec_key<<<g, TPB, 0, st>>>(s, mm, f, perm, h->keys[0], h->vals[0]);
-      const int r = radix_sort(h, mm, fbits[f], st);
-      if (r < 0) return r;
-      if (r == 1) {
-        CK(cudaMemcpyAsync(h->vals[0], h->vals[1], (size_t)mm * 4, cudaMemcpyDeviceToDevice, st));
-      }
-      perm = h->vals[0];
-    }
-    k_rec_gather<<<g, TPB, 0, st>>>(s, mm, perm, h->dout, h->dout_round);
-    h->launches += 4;
-    CK(cudaGetLastError());
-    CK(cudaStreamSynchronize(st));
-  }
+  rc = sort_records(h, st, h->dout, h->dout_round);
+  if (rc) return rc;
+  CK(cudaStreamSynchronize(st));
   h->n_merges = m;
   h->st.rounds = round;
   h->st.merges = c.nmerges;
@@ -1739,29 +1791,18 @@ namespace {
 constexpr size_t kStaticArenaBytes = (size_t)6 << 20;  // 6 MiB: room for n <= HAC_STATIC_MAX_N
 static __device__ __align__(256) unsigned char g_static_arena[kStaticArenaBytes];
 
-constexpr int kStaticMaxDevices = 64;
-std::atomic<unsigned char *> g_static_ptr[kStaticMaxDevices];  // per device, set on first use
-
-// Device address of the arena on the current device.  Host code must not
-// use the symbol g_static_arena itself: on the host it only names a stand-in.
+// Device address of the arena on the current device, looked up on every
+// call (after the module is loaded this allocates nothing; a cached address
+// could outlive a device reset that reloads the module elsewhere).  Host code
+// must not use the symbol g_static_arena itself: on the host it only names a
+// stand-in.
 int static_arena(unsigned char **out) {
-  int dev = -1;
-  if (cudaGetDevice(&dev) != cudaSuccess) {
+  void *q = nullptr;
+  if (cudaGetSymbolAddress(&q, g_static_arena) != cudaSuccess || q == nullptr) {
     cudaGetLastError();
     return HAC_EDEVICE;
   }
-  if (dev < 0 || dev >= kStaticMaxDevices) return HAC_EDEVICE;
-  unsigned char *p = g_static_ptr[dev].load(std::memory_order_acquire);
-  if (!p) {
-    void *q = nullptr;
-    if (cudaGetSymbolAddress(&q, g_static_arena) != cudaSuccess || q == nullptr) {
-      cudaGetLastError();
-      return HAC_EDEVICE;
-    }
-    p = (unsigned char *)q;
-    g_static_ptr[dev].store(p, std::memory_order_release);
-  }
-  *out = p;
+  *out = (unsigned char *)q;
   return HAC_OK;
 }
 
@@ -1869,114 +1910,24 @@ bool carve_state(hac_ctx &h, Carver &cv) {
   return cv.ok;
 }
 
-// initial layout with stack buffers only (no host or device allocation)
-template <typename T>
-int static_layout(hac_ctx &h, cudaStream_t st) {
-  State &s = h.s;
-  const T *X = (const T *)h.raw;
-  const int64_t n = h.n;
-  const int d = h.d;
-  unsigned long long bb[2 * MAXD];
-  for (int k = 0; k < MAXD; ++k) {
-    bb[k] = ~0ull;
-    bb[MAXD + k] = 0ull;
-  }
-  CK(cudaMemcpyAsync(h.bb, bb, sizeof(bb), cudaMemcpyHostToDevice, st));
-  // the arena keeps the previous call's contents: counters start from zero
-  CK(cudaMemsetAsync(s.ctr, 0, sizeof(Counters), st));
-  k_bbox<T><<<grid_for(n, TPB), TPB, 0, st>>>(X, n, d, h.bb, h.bb + MAXD, s.ctr);
-  CK(cudaGetLastError());
-  Counters c0;
-  CK(cudaMemcpyAsync(bb, h.bb, sizeof(bb), cudaMemcpyDeviceToHost, st));
-  CK(cudaMemcpyAsync(&c0, s.ctr, sizeof(Counters), cudaMemcpyDeviceToHost, st));
-  CK(cudaStreamSynchronize(st));
-  if (c0.err & ERR_NONFINITE) return HAC_EINVAL;
-  MortonParams mp{}, ctrp{};
-  double scale = 0.0;
-  for (int k = 0; k < d; ++k) {
-    unsigned long long u = bb[k], v = bb[MAXD + k];
-    u = (u >> 63) ? (u & 0x7fffffffffffffffull) : ~u;
-    v = (v >> 63) ? (v & 0x7fffffffffffffffull) : ~v;
-    double lo, hi;
-    memcpy(&lo, &u, 8);
-    memcpy(&hi, &v, 8);
-    mp.lo[k] = lo;
-    mp.inv[k] = hi > lo ? 1.0 / (hi - lo) : 0.0;
-    ctrp.lo[k] = 0.5 * (lo + hi);
-    scale = std::max(scale, std::max(std::fabs(lo - ctrp.lo[k]), std::fabs(hi - ctrp.lo[k])));
-  }
-  mp.bits = std::min(21, 64 / d);
-  s.abs_slack = std::max(scale, 1e-300) * std::ldexp(1.0, -18);
-  s.coord_scale = (float)(scale * (1.0 + 1e-6));
-  s.delta_pts = s.pts32_exact ? 0.f : 2.01f * 5.9604645e-8f * s.coord_scale * std::sqrt((float)d);
-  k_inst_set<<<1, 1, 0, st>>>(s, 0, (float)s.abs_slack, s.coord_scale, s.delta_pts, 0, (int)n, 0);
-  k_morton<T><<<grid_for(n, TPB), TPB, 0, st>>>(X, n, d, mp, h.keys[0], h.vals[0]);
-  CK(cudaGetLastError());
-  const int sc = radix_sort(&h, (int)n, mp.bits * d, st);
-  if (sc < 0) return sc;
-  h.ocur = h.pcur = 0;
-  h.lay_n = n;
-  s.cur = 0;
-  k_layout<T><<<grid_for(n, TPB), TPB, 0, st>>>(s, X, h.vals[sc], ctrp);
-  CK(cudaGetLastError());
-  Counters c{};
-  c.nterm = (int)n;
-  c.nactive = (int)n;
-  CK(cudaMemcpyAsync(s.ctr, &c, sizeof(Counters), cudaMemcpyHostToDevice, st));
-  return build_tree(&h, s.order[0], (int)n, st);
-}
-
-// Algorithm 1 rounds with the state carved from the arena; writes the
-// canonical dendrogram to `dev_out`
+// Algorithm 1 with the state carved from the arena: the same layout, rounds
+// and canonical record sort as hac_run (no events, no host allocation);
+// writes the dendrogram to `dev_out`
 int static_run(hac_ctx &h, const hac_opts &opt, cudaStream_t st, hac_merge *dev_out) {
   State &s = h.s;
-  int rc = h.dt == HAC_F32 ? static_layout<float>(h, st) : static_layout<double>(h, st);
-  if (rc) return rc;
   const auto t0 = std::chrono::steady_clock::now();
-  int K = (int)h.n, nterm = (int)h.n, round = 0;
-  Counters c{};
+  int rc = h.dt == HAC_F32 ? init_layout<float>(&h, st) : init_layout<double>(&h, st);
+  if (rc) return rc;
   RoundCtl ctl;  // no events: nothing is created here
-  while (K > 1) {
-    if (opt.max_rounds && round >= opt.max_rounds) return HAC_ETIMEOUT;
-    if (opt.timeout_s > 0 &&
-        std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count() >
-            opt.timeout_s)
-      return HAC_ETIMEOUT;
-    int npairs = 0;
-    rc = round_step(&h, st, round, K, nterm, ctl, &npairs);
-    if (rc) return rc;
-    K -= npairs;
-    if (K > 1) {
-      rc = build_tree(&h, s.order[h.ocur], K, st);
-      if (rc) return rc;
-    }
-    CK(cudaMemcpyAsync(&c, s.ctr, sizeof(Counters), cudaMemcpyDeviceToHost, st));
-    CK(cudaStreamSynchronize(st));
-    if ((c.err & ~ERR_NONFINITE) || (c.nactive != K && !(K == 1 && c.nactive == 0)))
-      return HAC_EINTERNAL;
-    nterm = c.nterm;
-    ++round;
-  }
+  int rounds = 0;
+  rc = run_rounds(&h, opt, st, ctl, nullptr, t0, &rounds);
+  if (rc) return rc;
+  Counters c{};
   CK(cudaMemcpyAsync(&c, s.ctr, sizeof(Counters), cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
-  const int64_t m = h.n - 1;
-  if (c.nmerges != m && m > 0) return HAC_EINTERNAL;
-  if (m > 0) {
-    const int mm = (int)m;
-    const int g = grid_for(mm, TPB);
-    int32_t *perm = nullptr;
-    const int fbits[3] = {bits_for(h.n), bits_for(h.n), 64};
-    for (int f = 0; f < 3; ++f) {
-      k_rec_key<<<g, TPB, 0, st>>>(s, mm, f, perm, h.keys[0], h.vals[0]);
-      const int r = radix_sort(&h, mm, fbits[f], st);
-      if (r < 0) return r;
-      if (r == 1)
-        CK(cudaMemcpyAsync(h.vals[0], h.vals[1], (size_t)mm * 4, cudaMemcpyDeviceToDevice, st));
-      perm = h.vals[0];
-    }
-    k_rec_gather<<<g, TPB, 0, st>>>(s, mm, perm, dev_out, h.dout_round);
-    CK(cudaGetLastError());
-  }
+  if (c.nmerges != h.n - 1) return HAC_EINTERNAL;
+  rc = sort_records(&h, st, dev_out, h.dout_round);
+  if (rc) return rc;
   CK(cudaStreamSynchronize(st));
   return HAC_OK;
 }
@@ -2012,6 +1963,7 @@ extern "C" int hac_run_static(const void *dev_points, int64_t n, int d, hac_dtyp
   h.s.linkage = (int)lk;
   h.s.pts32_exact = dt == HAC_F32;
   h.s.prec = opt.precision;
+  h.s.noprune = (opt.flags & HAC_FLAG_NO_PRUNE) ? 1 : 0;
   Carver cv{arena, 0, kStaticArenaBytes, true};
   if (!carve_state(h, cv)) return HAC_EINVAL;
   const cudaStream_t st = (cudaStream_t)opt.stream;

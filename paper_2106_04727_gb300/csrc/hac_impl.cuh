@@ -9,6 +9,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <atomic>
 #include <new>
 #include <vector>
 
@@ -195,10 +196,16 @@ int alloc_state(hac_ctx *h);
     if (e_ != cudaSuccess) return HAC_EDEVICE; \
   } while (0)
 
+// SM count of the current device (looked up once per device)
+int device_sms();
+
+// grid of a grid-stride kernel: one thread per work item, at most 64 blocks
+// per SM
 inline int grid_for(int64_t work, int tpb) {
   int64_t g = (work + tpb - 1) / tpb;
   if (g < 1) g = 1;
-  if (g > 152 * 64) g = 152 * 64;
+  const int64_t cap = (int64_t)device_sms() * 64;
+  if (g > cap) g = cap;
   return (int)g;
 }
 
@@ -215,6 +222,7 @@ struct RoundCtl {
               eb1 = nullptr;
   double ms_query = 0, ms_big = 0;
   int64_t qlaunch = 0, big_launch = 0, searches = 0;
+  int64_t naive = 0;  // terminals x (active clusters - 1), summed over rounds
   int big_iters = 0, big_reqs = 0;
 };
 

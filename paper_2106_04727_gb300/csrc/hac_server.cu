@@ -12,6 +12,7 @@
 #include <cstring>
 #include <deque>
 #include <map>
+#include <memory>
 #include <mutex>
 #include <new>
 #include <thread>
@@ -714,7 +715,8 @@ int submit_impl(hac_server_t srv, const void *points, int64_t n, int d, hac_dtyp
         dt == HAC_F32 ? (double)((const float *)points)[i] : ((const double *)points)[i];
     if (!std::isfinite(x)) return HAC_EINVAL;
   }
-  SrvReq *r = new (std::nothrow) SrvReq();
+  // owned here until published in srv->reqs (a throwing copy or insert frees it)
+  std::unique_ptr<SrvReq> r(new (std::nothrow) SrvReq());
   if (!r) return HAC_ENOMEM;
   r->pts.assign((const unsigned char *)points, (const unsigned char *)points + n * d * esz);
   r->n = n;
@@ -730,49 +732,63 @@ int submit_impl(hac_server_t srv, const void *points, int64_t n, int d, hac_dtyp
   }
   const int key = ((int)lk * 32 + d) * 2 + (dt == HAC_F32 ? 0 : 1);
   std::unique_lock<std::mutex> g(srv->mu);
-  if (srv->err) {
-    const int rc = srv->err;
-    delete r;
-    return rc;
-  }
-  r->ticket = srv->next_ticket++;
+  if (srv->err) return srv->err;
+  const uint64_t tk = srv->next_ticket;
   if (n == 1) {  // nothing to merge
+    r->ticket = tk;
     r->status = HAC_OK;
     r->t_done = r->t_submit;
-    srv->reqs[r->ticket] = r;
-    *ticket = r->ticket;
+    srv->reqs.emplace(tk, r.get());
+    r.release();
+    ++srv->next_ticket;
+    *ticket = tk;
     return HAC_OK;
   }
   auto it = srv->engines.find(key);
   Engine *e = it == srv->engines.end() ? nullptr : it->second;
   if (!e) {
-    // first request of this kind: its engine (device memory for cap points)
+    // first request of this kind: its engine (device memory for cap points);
+    // everything that can throw happens before its thread starts, so a
+    // failure leaves no running engine unreachable from srv
     e = new (std::nothrow) Engine();
-    if (!e) {
-      delete r;
-      return HAC_ENOMEM;
+    if (!e) return HAC_ENOMEM;
+    int rc = engine_init(*e, lk, d, dt, srv->cap, srv->opt);
+    std::map<int, Engine *>::iterator slot;
+    if (!rc) {
+      try {
+        slot = srv->engines.emplace(key, nullptr).first;
+      } catch (...) {
+        rc = HAC_ENOMEM;
+      }
     }
-    const int rc = engine_init(*e, lk, d, dt, srv->cap, srv->opt);
+    if (!rc) {
+      try {
+        e->thr = std::thread(engine_loop, srv, e);
+      } catch (...) {
+        srv->engines.erase(slot);
+        rc = HAC_ENOMEM;
+      }
+    }
     if (rc) {
       engine_free(e);
       delete e;
-      delete r;
       return rc;
     }
-    try {
-      e->thr = std::thread(engine_loop, srv, e);
-    } catch (...) {
-      engine_free(e);
-      delete e;
-      delete r;
-      return HAC_ENOMEM;
-    }
-    srv->engines[key] = e;
+    slot->second = e;
   }
+  // publish: the map insert and the queue append are undone together
+  r->ticket = tk;
   r->eng = e;
-  srv->reqs[r->ticket] = r;
-  e->queue.push_back(r);
-  *ticket = r->ticket;
+  auto ri = srv->reqs.emplace(tk, r.get()).first;
+  try {
+    e->queue.push_back(r.get());
+  } catch (...) {
+    srv->reqs.erase(ri);
+    return HAC_ENOMEM;
+  }
+  r.release();
+  ++srv->next_ticket;
+  *ticket = tk;
   g.unlock();
   srv->cv.notify_all();
   return HAC_OK;

@@ -27,10 +27,11 @@ def test_static_rejects_sizes_beyond_its_maximum():
     assert rc == hac.HAC_ECAP
 
 
-def _static(torch, X, lk, prec):
+def _static(torch, X, lk, prec, bufs):
+    """One hac_run_static call on preallocated device buffers (points, and
+    n - 1 records of 32 bytes)."""
     n, d = X.shape
-    src = torch.from_numpy(X).cuda()
-    out = torch.zeros((n - 1) * 4, dtype=torch.int64, device="cuda")  # 32-byte records
+    src, out = bufs
     rc = hac.hac_run_static(src.data_ptr(), n, d, X.dtype, lk, out.data_ptr(), n - 1,
                             precision=prec)
     assert rc == hac.HAC_OK, hac.hac_strerror(rc)
@@ -41,14 +42,32 @@ def _static(torch, X, lk, prec):
 @pytest.mark.gpu
 @pytest.mark.parametrize("prec", [hac.PREC_F64, hac.PREC_F32_RECHECK], ids=["f64", "f32recheck"])
 def test_static_matches_allocating_path_twice(prec):
+    """Same dendrogram as the allocating path and as the CPU oracle, on
+    consecutive calls that reuse (and overwrite) the fixed array, and no
+    device memory taken by those calls."""
     torch = pytest.importorskip("torch")
     cases = [(inputs.gaussian_mixture(3000, 5, 12, seed=91), "ward"),
              (inputs.uniform_cube(hac.HAC_STATIC_MAX_N, 2, seed=92, dtype=np.float64), "average"),
              (inputs.gaussian_mixture(777, 3, 4, seed=93), "complete")]
-    for X, lk in cases[:2] + cases[2:]:     # consecutive calls reuse the same array
-        got = _static(torch, X, lk, prec)
-        want = hac.cluster(X, lk, precision=prec, with_rounds=False)
-        c = oracle.compare(got, want, rtol=1e-9)
+    # everything that allocates runs before the measured region: the
+    # allocating path, the oracle, and the device buffers of every call
+    wants = [hac.cluster(X, lk, precision=prec, with_rounds=False) for X, lk in cases]
+    refs = [oracle.nnchain(X.astype(np.float64), lk) for X, lk in cases]
+    bufs = [(torch.from_numpy(X).cuda(),
+             torch.zeros((len(X) - 1) * 4, dtype=torch.int64, device="cuda")) for X, _ in cases]
+    torch.cuda.synchronize()
+    _static(torch, *cases[0], prec, bufs[0])   # loads the library's module on this device
+    free0 = torch.cuda.mem_get_info()[0]
+    for i in (0, 1, 2, 0):                     # consecutive calls reuse the same array
+        X, lk = cases[i]
+        got = _static(torch, X, lk, prec, bufs[i])
+        c = oracle.compare(got, wants[i], rtol=1e-9)
         assert c["ok"], (lk, c)
         # same canonical order as hac_dendrogram
-        assert np.array_equal(got["a"], want["a"]) and np.array_equal(got["b"], want["b"])
+        assert np.array_equal(got["a"], wants[i]["a"]) and np.array_equal(got["b"], wants[i]["b"])
+        # FP32 mode: complete / average heights carry the stated FP32 bound
+        rtol = 1e-5 if prec == hac.PREC_F32_RECHECK and lk in ("complete", "average") else 1e-9
+        c = oracle.compare(got, refs[i], rtol=rtol)
+        assert c["ok"], (lk, "oracle", c)
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info()[0] == free0
