@@ -56,7 +56,7 @@ def _load():
             lib.oracle_rounds.restype = i32
             lib.oracle_greedy.argtypes = [P, i64, i32, i32, P, P, P, P]
             lib.oracle_greedy.restype = i32
-            lib.oracle_validate.argtypes = [P, i64, i32, i32, P, P, P, P, i64, f64, f64, P]
+            lib.oracle_validate.argtypes = [P, i64, i32, i32, P, P, P, P, i64, f64, f64, f64, P]
             lib.oracle_validate.restype = i64
             lib.oracle_lw.argtypes = [i32, f64, f64, f64, f64, f64, f64]
             lib.oracle_lw.restype = f64
@@ -144,10 +144,14 @@ def greedy(X, linkage) -> dict:
     return dict(a=a, b=b, h=h, size=s)
 
 
-def validate(X, linkage, dend: dict, rtol: float = 1e-9, atol_scale: float = 1e-300):
-    """Greedy-validity replay of ``dend``.  Returns (first_bad, stats) where
-    first_bad is 0 when valid and stats = (tie-zone merges, max relative
-    excess over the minimum, max relative height error)."""
+def validate(X, linkage, dend: dict, rtol: float = 1e-9, atol_scale: float = 1e-300,
+             htol: float | None = None):
+    """Greedy-validity replay of ``dend``: every merge must join a pair within
+    ``rtol`` (relative) of the smallest active distance, and its height must be
+    within ``htol`` (default: ``rtol``) of that pair's distance.  Returns
+    (first_bad, stats) where first_bad is 0 when valid and stats = (tie-zone
+    merges, max relative excess over the minimum, max relative height error)."""
+    htol = rtol if htol is None else htol
     X = _pts(X)
     n, d = X.shape
     a = np.ascontiguousarray(dend["a"], dtype=np.int64)
@@ -156,7 +160,7 @@ def validate(X, linkage, dend: dict, rtol: float = 1e-9, atol_scale: float = 1e-
     s = np.ascontiguousarray(dend["size"], dtype=np.int64)
     st = np.zeros(3, np.float64)
     rc = _load().oracle_validate(_p(X), n, d, _lk(linkage), _p(a), _p(b), _p(h), _p(s),
-                                 len(a), rtol, atol_scale, _p(st))
+                                 len(a), rtol, htol, atol_scale, _p(st))
     if rc < 0:
         raise ValueError(f"oracle_validate failed ({rc})")
     return int(rc), (int(st[0]), float(st[1]), float(st[2]))

@@ -528,16 +528,17 @@ int oracle_greedy(const double *X, int64_t n, int d, int linkage,
  * (a, b, h, size) is ready when slots a and b are active and their sizes add
  * up to `size`; among ready merges the one of least h goes next.  At each
  * step the merged pair's distance D (from the FP64 Lance-Williams matrix) must
- * satisfy |D - h| <= rtol * max(D, atol_scale) and D <= (1 + rtol) * Dmin +
- * rtol * atol_scale, where Dmin is the smallest distance over all active
- * pairs.  stats[0] = merges whose D exceeded Dmin (tie-zone choices),
+ * satisfy |D - h| <= htol * max(D, atol_scale) (the reported height) and
+ * D <= (1 + rtol) * Dmin + rtol * atol_scale (the merge itself: how far above
+ * the global minimum a tie-zone choice may sit), where Dmin is the smallest
+ * distance over all active pairs.  stats[0] = merges whose D exceeded Dmin (tie-zone choices),
  * stats[1] = largest relative excess of D over Dmin, stats[2] = largest
  * relative height error.  Returns 0 if valid, a positive 1-based merge
  * position of the first violation, or negative on bad input. */
 int64_t oracle_validate(const double *X, int64_t n, int d, int linkage,
                         const int64_t *ma, const int64_t *mb, const double *mh,
-                        const int64_t *msize, int64_t m, double rtol, double atol_scale,
-                        double *stats) {
+                        const int64_t *msize, int64_t m, double rtol, double htol,
+                        double atol_scale, double *stats) {
   if (check_args(X, n, d, linkage)) return -1;
   if (m != n - 1) return -4;
   stats[0] = stats[1] = stats[2] = 0.0;
@@ -577,7 +578,9 @@ int64_t oracle_validate(const double *X, int64_t n, int d, int linkage,
       double ex = (D - Dmin) / fmax(Dmin, atol_scale);
       if (ex > stats[1]) stats[1] = ex;
     }
-    if (herr > rtol || D > (1.0 + rtol) * Dmin + rtol * atol_scale) {
+    /* two separate tolerances: rtol on how far the merged pair may sit above
+     * the global minimum (the tree), htol on the reported height */
+    if (herr > htol || D > (1.0 + rtol) * Dmin + rtol * atol_scale) {
       ret = step + 1;
       break;
     }

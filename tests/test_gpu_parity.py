@@ -128,14 +128,27 @@ def test_lattice_complete_exact_ties(prec):
         _assert_same(got, want, rtol=0.0 if prec == hac.PREC_F64 else RTOL32)
 
 
+def _same_as_fp64(got, X, lk, **kw):
+    """FP32 bulk + FP64 re-score: the tree (and the round of every merge) must
+    be the all-FP64 tree's, merge for merge; heights within the FP32 bound."""
+    ref = hac.cluster(X, lk, precision=hac.PREC_F64, **kw)
+    _assert_same(got, ref, rtol=_rtol(lk, hac.PREC_F32_RECHECK))
+
+
 @pytest.mark.parametrize("prec", PRECS, ids=PREC_IDS)
 @pytest.mark.parametrize("lk", ["average", "ward", "average_sq"])
 def test_lattice_ties_valid(lk, prec):
+    """Exact ties: a valid greedy tree (each merge within 1e-9 of the
+    smallest active distance, heights within the mode's bound), and in the
+    FP32 mode the all-FP64 tree exactly."""
     X = inputs.lattice(300, 4, seed=7, levels=10)
     got = hac.cluster(X, lk, precision=prec)
-    bad, stats = oracle.validate(X.astype(np.float64), lk, got, rtol=_rtol(lk, prec))
+    bad, stats = oracle.validate(X.astype(np.float64), lk, got, rtol=RTOL64,
+                                 htol=_rtol(lk, prec))
     assert bad == 0, stats
     assert oracle.check_tree(got, len(X), rtol=_rtol(lk, prec)) == []
+    if prec == hac.PREC_F32_RECHECK:
+        _same_as_fp64(got, X, lk)
 
 
 @pytest.mark.parametrize("prec", PRECS, ids=PREC_IDS)
@@ -164,8 +177,11 @@ def test_lattice16d_sample(lk, prec):
     greedy-validity replay."""
     X = inputs.workload("lattice16d_1m_f32", n=2000)
     got = hac.cluster(X, lk, precision=prec)
-    bad, stats = oracle.validate(X.astype(np.float64), lk, got, rtol=_rtol(lk, prec))
+    bad, stats = oracle.validate(X.astype(np.float64), lk, got, rtol=RTOL64,
+                                 htol=_rtol(lk, prec))
     assert bad == 0, stats
+    if prec == hac.PREC_F32_RECHECK:
+        _same_as_fp64(got, X, lk)
     want = oracle.rounds(X.astype(np.float64), lk)
     # round-0 merges are between singletons at exactly representable distances
     r0 = lambda d: {(int(a), int(b)) for a, b, r in zip(d["a"], d["b"], d["round"]) if r == 0}
@@ -405,14 +421,19 @@ def test_cache_parity(lk, prec, slots):
     assert got["stats"]["cache_hits"] > 0 and got["stats"]["cache_lw_entries"] > 0
 
 
+@pytest.mark.parametrize("prec", PRECS, ids=PREC_IDS)
 @pytest.mark.parametrize("lk", ["complete", "average"])
-def test_cache_lattice_ties(lk):
+def test_cache_lattice_ties(lk, prec):
     X = inputs.lattice(400, 3, seed=11, levels=16)
-    got = hac.cluster(X, lk, cache_slots=64)
-    bad, stats = oracle.validate(X.astype(np.float64), lk, got, rtol=1e-9)
+    got = hac.cluster(X, lk, precision=prec, cache_slots=64)
+    bad, stats = oracle.validate(X.astype(np.float64), lk, got, rtol=RTOL64,
+                                 htol=_rtol(lk, prec))
     assert bad == 0, stats
     if lk == "complete":  # max of exact values: Lance-Williams is exact too
-        _assert_same(got, oracle.rounds(X.astype(np.float64), lk), rtol=0.0)
+        _assert_same(got, oracle.rounds(X.astype(np.float64), lk),
+                     rtol=0.0 if prec == hac.PREC_F64 else RTOL32)
+    if prec == hac.PREC_F32_RECHECK:
+        _same_as_fp64(got, X, lk, cache_slots=64)
 
 
 @pytest.mark.parametrize("slots", [8, 64])

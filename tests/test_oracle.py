@@ -375,6 +375,31 @@ def test_validate_detects_planted_errors(lk):
 
 
 @pytest.mark.parametrize("lk", LKS)
+def test_validate_tolerances_are_separate(lk):
+    """The replay's two tolerances act on different things: `htol` on the
+    reported heights only, `rtol` on how far a merge may sit above the
+    smallest active distance.  Planted: every height 5e-6 too high (a valid
+    tree), and a tree whose first merge is 1e-7 (relative) above the minimum
+    with exact heights."""
+    X = inputs.uniform_cube(40, 2, seed=5)
+    d = oracle.nnchain(X, lk)
+    hi = dict(d, h=d["h"] * (1 + 5e-6))
+    assert oracle.validate(X, lk, hi, rtol=1e-9, htol=1e-5)[0] == 0
+    assert oracle.validate(X, lk, hi, rtol=1e-9, htol=1e-6)[0] != 0
+    assert oracle.validate(X, lk, hi, rtol=1e-5, htol=1e-6)[0] != 0
+    # 1-D points 0, 1, 2 + 1e-7: merging {1, 2} first is not the minimum
+    P = np.array([[0.0], [1.0], [2.0 + 1e-7]])
+    h1 = oracle.cluster_dist(lk, P[[1]], P[[2]])
+    h2 = oracle.cluster_dist(lk, P[[0]], P[[1, 2]])
+    planted = dict(a=np.array([1, 0]), b=np.array([2, 1]), h=np.array([h1, h2]),
+                   size=np.array([2, 3]))
+    bad, stats = oracle.validate(P, lk, planted, rtol=1e-9, htol=1.0)
+    assert bad == 1 and 1e-8 < stats[1] < 1e-6, stats
+    bad, stats = oracle.validate(P, lk, planted, rtol=1e-6, htol=1e-12)
+    assert bad == 0 and stats[0] == 1, stats
+
+
+@pytest.mark.parametrize("lk", LKS)
 def test_rounds_monotone_and_tree(lk):
     X = inputs.gaussian_mixture(300, 2, 6, seed=21).astype(np.float64)
     r = oracle.rounds(X, lk)
