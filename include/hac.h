@@ -123,6 +123,14 @@ typedef struct {
   int64_t naive_pairs;       /* cluster pairs a search without range queries would
                                 evaluate: terminals x (active clusters - 1), summed
                                 over rounds */
+  int64_t dense_k;           /* average linkage: clusters active when the run switched
+                                to the dense matrix of all their pair distances (0 = it
+                                did not) */
+  int64_t dense_rounds;      /* rounds run on that matrix */
+  int64_t dense_point_pairs; /* point pairs of the all-pairs sweep that filled it (also
+                                in point_pairs) */
+  int64_t dense_rechecks;    /* FP32 mode: matrix entries re-scored in FP64 */
+  double ms_dense;           /* device time of the sweep */
 } hac_stats_t;
 
 /* Default options (FP64, no cache, no limits, own stream).  No counterpart in

@@ -1102,6 +1102,8 @@ int init_layout(hac_ctx *h, cudaStream_t st) {
   h->ocur = h->pcur = 0;
   h->lay_n = n;
   s.cur = 0;
+  s.dense = 0;
+  s.dk = 0;
   k_layout<T><<<grid_for(n, TPB), TPB, 0, st>>>(s, X, h->vals[sc], ctrp);
   CK(cudaGetLastError());
   Counters c{};
@@ -1166,6 +1168,7 @@ int create_common(const void *pts, bool dev, int64_t n, int d, hac_dtype dt, hac
   if (const char *e = getenv("HAC_BIG_PAIRS_F64")) h->big_pairs64 = std::max(1ll, atoll(e));
   if (const char *e = getenv("HAC_WARP_BUDGET")) h->warp_budget = std::max(1ll, atoll(e));
   if (const char *e = getenv("HAC_BRUTE")) h->brute_env = atoi(e) ? 1 : 0;
+  if (const char *e = getenv("HAC_DENSE_K")) h->dense_k = std::max(0ll, atoll(e));
   if (cudaStreamCreateWithFlags(&h->own, cudaStreamNonBlocking) != cudaSuccess) {
     cudaGetLastError();
     delete h;
@@ -1311,26 +1314,36 @@ int round_step(hac_ctx *h, cudaStream_t st, int round, int K, int nterm, RoundCt
   const bool need_points = !closed_form(s.linkage);
   int rc = 0;
   s.cur = h->pcur;
+  // average linkage on the dense matrix once the active clusters fit
+  const int dense = dense_maybe_enter(h, st, K, ctl);
+  if (dense < 0) return dense;
   QueryArgs qa{};
   fill_query_args(h, qa, round, K, nterm);
-  const bool defer = qa.defer != 0;
+  const bool defer = !dense && qa.defer != 0;
   if (defer)
     CK(cudaMemsetAsync(s.side_key, 0xff, (size_t)s.side_cap * sizeof(unsigned long long), st));
-  const bool brute = use_brute(h);
+  const bool brute = !dense && use_brute(h);
   if (brute) {
     CK(cudaMemsetAsync(&s.ctr->npend, 0, sizeof(int32_t), st));
     qa.pend_out = s.blist;
   }
   EVREC(ctl.eq0);
-  if (brute)
+  if (dense) {
+    rc = dense_search(h, st, K, nterm, ctl);
+    if (rc) return rc;
+    ++ctl.dense_rounds;
+  } else if (brute) {
     CK(launch_brute(qa, s.dp, st));
-  else
+  } else {
     CK(launch_query(qa, s.dp, s.prec, st));
+  }
   EVREC(ctl.eq1);
-  ++ctl.qlaunch;
-  ctl.searches += nterm;
-  h->launches += 1;
-  if (s.cache_slots > 0) {
+  if (!dense) {
+    ++ctl.qlaunch;
+    ctl.searches += nterm;
+    h->launches += 1;
+  }
+  if (!dense && s.cache_slots > 0) {
     k_cache_insert<<<grid_for((int64_t)device_sms() * 8 * TPB, TPB), TPB, 0, st>>>(s);
     CK(cudaMemsetAsync(&s.ctr->nins, 0, sizeof(int32_t), st));
     h->launches += 1;
@@ -1399,7 +1412,10 @@ int round_step(hac_ctx *h, cudaStream_t st, int round, int K, int nterm, RoundCt
   if (npairs <= 0) return HAC_EINTERNAL;
   k_merge<<<grid_for(npairs, TPB), TPB, 0, st>>>(s, round, npairs);
   h->launches += 4;  // merge, 3 compaction kernels
-  if (s.cache_slots > 0) {
+  if (dense) {
+    rc = dense_update(h, st, round, K, npairs);
+    if (rc) return rc;
+  } else if (s.cache_slots > 0) {
     const int S = s.cache_slots;
     const size_t smem = (size_t)CM_WARPS * 5 * S * sizeof(CEntry);
     const int blocks = std::max(1, std::min(cdiv(npairs, CM_WARPS), device_sms() * 32));
@@ -1485,7 +1501,7 @@ int run_rounds(hac_ctx *h, const hac_opts &opt, cudaStream_t st, RoundCtl &ctl, 
     }
     if (rc) return rc;
     K -= npairs;
-    if (K > 1) {
+    if (K > 1 && !s.dense) {
       rc = build_tree(h, s.order[h->ocur], K, st);
       if (rc) return rc;
     }
@@ -1655,6 +1671,12 @@ int run_impl(hac_ctx *h, const hac_opts *o) {
   h->st.big_point_pairs = (int64_t)(c.big_pp - c.big_skip);
   h->st.big_launches = big_launch;
   h->st.cache_lw_entries = (int64_t)c.cache_lw;
+  h->st.dense_k = s.dense ? s.dk : 0;
+  h->st.dense_rounds = ctl.dense_rounds;
+  h->st.dense_point_pairs = (int64_t)c.dense_pp;
+  h->st.dense_rechecks = ctl.dense_rechecks;
+  h->st.ms_dense = ctl.ms_dense;
+  h->st.point_pairs += (int64_t)(c.dense_pp + c.dense_rq_pp);
   {
     // algorithmic bytes of the search kernel (true dimension d, not padded):
     // node test = centroid box (+ complete's hi-min / lo-max) + min size;
@@ -1964,6 +1986,7 @@ extern "C" int hac_run_static(const void *dev_points, int64_t n, int d, hac_dtyp
   h.s.pts32_exact = dt == HAC_F32;
   h.s.prec = opt.precision;
   h.s.noprune = (opt.flags & HAC_FLAG_NO_PRUNE) ? 1 : 0;
+  h.dense_k = 0;  // the fixed array has no room for the dense matrix
   Carver cv{arena, 0, kStaticArenaBytes, true};
   if (!carve_state(h, cv)) return HAC_EINVAL;
   const cudaStream_t st = (cudaStream_t)opt.stream;

@@ -1,0 +1,1047 @@
+// Dense phase of average linkage (avg-1): the whole matrix of pair distances
+// once the active clusters fit.
+//
+// Section 5 keeps, per cluster, a table of up to s cached distances that
+// Algorithm 5 updates by Lance-Williams after every merge.  When s reaches
+// the number K of active clusters the table is the full K x K matrix, and no
+// distance ever has to be evaluated twice.  On a GB300 that matrix fits for K
+// in the tens of thousands (8 GiB at K = 32,768), so once K drops to that
+// size this instance switches to it:
+//
+//   * one all-pairs sweep of the points fills it: every pair of points in
+//     different clusters is visited once (the points are laid out in
+//     cluster-contiguous segments in position order, so a tile of 1,024 x
+//     1,024 points covers a handful of cluster pairs), and the sums of point
+//     distances are accumulated per cluster pair.  For average linkage every
+//     such point pair enters exactly one later merge distance, so the sweep
+//     does no work the exact answer does not need;
+//   * every later round finds each terminal's nearest neighbour by a scan of
+//     its row (Algorithm 2 without a range query: the matrix holds every
+//     candidate), and after the merges the rows and columns of the merged
+//     clusters are updated by the average-linkage Lance-Williams formula
+//     (Table 2: D(A u B, C) = (|A| D(A, C) + |B| D(B, C)) / (|A| + |B|));
+//   * the chain update, reciprocal-pair filter, merges and compaction are the
+//     ordinary round's kernels, so the rounds are those of Algorithm 1.
+//
+// Exact sums.  Every entry is kept as the sum of its point distances in
+// 128-bit fixed point (unit 2^e, chosen per instance so that (n/2)^2 times the
+// largest point distance stays below 2^126 units), next to the mean distance
+// that sum gives in FP64.  Integer addition is exact and associative, so:
+//   * tiles can add into a cell with atomics in any order and the run is
+//     deterministic;
+//   * the Lance-Williams update of average linkage is the exact addition of
+//     the sums (S(A u B, C) = S(A, C) + S(B, C)), with no rounding drift;
+//   * in the FP64 mode a cell's sum is the exact sum of the FP64 point
+//     distances of its pairs (each converts exactly), whatever the grouping,
+//     so an FP64 re-score from the points in the FP32 mode reproduces the
+//     FP64 mode's entry bit for bit, and both modes break exact ties alike.
+//
+// Precision.  FP64 mode: point distances in FP64, every entry exact.  FP32
+// mode: the sweep uses the FP32 point copy and the stated error model of an
+// FP32 point distance, |D32 - D| <= delta + rho D with rho = (d + 16) u + 32 u
+// (FP32 partial sums of at most 32 terms), which sums and weighted means
+// preserve; such an entry is an estimate.  A terminal's FP64 nearest
+// neighbour is among the entries whose lower bound is within the least upper
+// bound U; if that window holds estimates they are re-scored in FP64 from the
+// points (GPU-wide) and the search is repeated, so the nearest neighbour,
+// hence the tree, is the FP64 one.  A lone estimate whose bound is within
+// 4e-6 relative keeps its upper bound as the height, as in the tree search.
+#include "hac_impl.cuh"
+
+#include <algorithm>
+#include <cmath>
+#include <cstdlib>
+
+namespace hacg {
+
+namespace {
+
+constexpr unsigned long long KINF_D = 0x7ff0000000000000ull;  // bits of +inf
+constexpr unsigned long long SIGN = 0x8000000000000000ull;
+
+// ---------------------------------------------------------------------------
+// 128-bit fixed-point sums: value = (hi * 2^64 + lo) * 2^e; the top bit of hi
+// marks an estimate (sums stay below 2^126 units, so it never carries)
+// ---------------------------------------------------------------------------
+constexpr unsigned long long TOP = 0x8000000000000000ull;
+
+struct U128 {
+  unsigned long long lo, hi;
+};
+
+// fixed-point value of v >= 0 (exact for v >= 2^(e+52), truncated below 2^e)
+__device__ __forceinline__ U128 fx_of(double v, int e) {
+  U128 r{0ull, 0ull};
+  if (!(v > 0.0)) return r;
+  const unsigned long long bits = (unsigned long long)__double_as_longlong(v);
+  int E = (int)((bits >> 52) & 0x7ff);
+  unsigned long long m = bits & 0xfffffffffffffull;
+  if (E == 0)
+    E = 1;  // subnormal
+  else
+    m |= 1ull << 52;
+  int sh = E - 1075 - e;  // v = m * 2^(sh + e)
+  if (sh > 74) sh = 74;   // cannot happen: every sum stays below 2^126 units
+  if (sh >= 64) {
+    r.hi = m << (sh - 64);
+  } else if (sh > 0) {
+    r.lo = m << sh;
+    r.hi = m >> (64 - sh);
+  } else if (sh == 0) {
+    r.lo = m;
+  } else if (sh > -64) {
+    r.lo = m >> (-sh);
+  }
+  return r;
+}
+
+__device__ __forceinline__ void u128_add(U128 &a, const U128 &b) {
+  const unsigned long long lo = a.lo + b.lo;
+  a.hi += b.hi + (lo < a.lo ? 1ull : 0ull);
+  a.lo = lo;
+}
+
+// atomic a += b on the two words at p (p[0] = lo, p[1] = hi)
+__device__ __forceinline__ void u128_atomic(unsigned long long *p, const U128 &b) {
+  if (!(b.lo | b.hi)) return;
+  const unsigned long long old = atomicAdd(p, b.lo);
+  const unsigned long long carry = old + b.lo < old ? 1ull : 0ull;
+  if (b.hi + carry) atomicAdd(p + 1, b.hi + carry);
+}
+
+__device__ __forceinline__ U128 u128_shfl_down(const U128 &v, int o) {
+  return U128{__shfl_down_sync(0xffffffffu, v.lo, o), __shfl_down_sync(0xffffffffu, v.hi, o)};
+}
+
+__device__ __forceinline__ U128 u128_shfl_xor(const U128 &v, int o) {
+  return U128{__shfl_xor_sync(0xffffffffu, v.lo, o), __shfl_xor_sync(0xffffffffu, v.hi, o)};
+}
+
+// the sum as an FP64 number (the estimate flag ignored)
+__device__ __forceinline__ double fx_value(unsigned long long lo, unsigned long long hi, int e) {
+  return ldexp((double)(hi & ~TOP), 64 + e) + ldexp((double)lo, e);
+}
+
+// mean distance of an entry: its sum / (na nb), the sign bit set for an
+// estimate; one function everywhere, so equal sums give equal means
+__device__ __forceinline__ double entry_mean(unsigned long long lo, unsigned long long hi, int e,
+                                             int na, int nb) {
+  const double v = fx_value(lo, hi, e) / ((double)na * (double)nb);
+  const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+  return __longlong_as_double((long long)((hi & TOP) ? (b | SIGN) : b));
+}
+
+__device__ __forceinline__ bool is_est(double x) {
+  return ((unsigned long long)__double_as_longlong(x) & SIGN) != 0;
+}
+__device__ __forceinline__ double mag(double x) { return fabs(x); }
+
+// ---------------------------------------------------------------------------
+// the all-pairs sweep
+// ---------------------------------------------------------------------------
+constexpr int DS_TPB = 256;  // threads per tile
+constexpr int DS_CH = 256;   // columns per staged chunk
+
+struct SweepArgs {
+  const float *p32;
+  const double *p64;
+  const int32_t *plab;
+  const int32_t *didx;
+  int64_t N;  // points in the layout
+  int dk, e;
+  unsigned long long *sum;  // the sum matrix: cell (i < j) at [i][j] (two words)
+  long long nb;             // blocks of TI points along each axis
+  Counters *ctr;
+};
+
+__device__ __forceinline__ void tile_of(long long t, long long &bi, long long &bj) {
+  long long j = (long long)((sqrt(8.0 * (double)t + 1.0) - 1.0) * 0.5);
+  while (j * (j + 1) / 2 > t) --j;
+  while ((j + 1) * (j + 2) / 2 <= t) ++j;
+  bj = j;
+  bi = t - j * (j + 1) / 2;
+}
+
+// Per chunk: segment starts of equal keys (cluster matrix indices) among the
+// staged columns; returns the count, sstart[count] = cnt.
+__device__ __forceinline__ int chunk_segments(const int *skey, int cnt, int *sstart, int *wtot) {
+  const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+  const bool flag = t < cnt && (t == 0 || skey[t] != skey[t - 1]);
+  const unsigned b = __ballot_sync(0xffffffffu, flag);
+  if (lane == 0) wtot[w] = __popc(b);
+  __syncthreads();
+  int before = 0, total = 0;
+  for (int i = 0; i < DS_TPB / 32; ++i) {
+    before += i < w ? wtot[i] : 0;
+    total += wtot[i];
+  }
+  if (flag) sstart[before + __popc(b & ((1u << lane) - 1u))] = t;
+  if (t == 0) sstart[total] = cnt;
+  __syncthreads();
+  return total;
+}
+
+// Keys of a warp's rows are non-decreasing along the lanes, so equal keys
+// form contiguous runs.  `same` holds, per step o = 1, 2, 4, 8, 16, whether
+// lane + o has this lane's key; after seg_sum the first lane of each run
+// holds the run's total.
+__device__ __forceinline__ unsigned seg_mask(int k, int lane) {
+  unsigned m = 0;
+#pragma unroll
+  for (int i = 0; i < 5; ++i) {
+    const int k2 = __shfl_down_sync(0xffffffffu, k, 1 << i);
+    if (lane + (1 << i) < 32 && k2 == k) m |= 1u << i;
+  }
+  return m;
+}
+
+__device__ __forceinline__ U128 seg_sum(U128 v, unsigned same) {
+#pragma unroll
+  for (int i = 0; i < 5; ++i) {
+    const U128 v2 = u128_shfl_down(v, 1 << i);
+    if ((same >> i) & 1u) u128_add(v, v2);
+  }
+  return v;
+}
+
+// Flush one column segment (key qj) of every row: cell (krow, qj) gets the
+// row's sum when krow < qj (each unordered cluster pair once, its lower
+// matrix index first).  Rows of one warp with the same key are summed first.
+template <int PPT>
+__device__ __forceinline__ void flush(const SweepArgs &a, const U128 (&acc)[PPT],
+                                      const int (&krow)[PPT], const unsigned (&same)[PPT],
+                                      const bool (&lead)[PPT], bool uniform, int qj, int lane) {
+  if (uniform) {  // every row of the warp in one cluster
+    if (!(krow[0] < qj)) return;
+    U128 v = acc[0];
+#pragma unroll
+    for (int r = 1; r < PPT; ++r) u128_add(v, acc[r]);
+#pragma unroll
+    for (int o = 16; o; o >>= 1) u128_add(v, u128_shfl_xor(v, o));
+    if (lane == 0) u128_atomic(&a.sum[2 * ((size_t)krow[0] * a.dk + qj)], v);
+    return;
+  }
+#pragma unroll
+  for (int r = 0; r < PPT; ++r) {
+    const U128 z{0ull, 0ull};
+    const U128 v = seg_sum(krow[r] < qj ? acc[r] : z, same[r]);
+    if (lead[r] && krow[r] < qj) u128_atomic(&a.sum[2 * ((size_t)krow[r] * a.dk + qj)], v);
+  }
+}
+
+// Row setup shared by both sweeps: keys of the PPT rows, run masks and run
+// leaders; returns whether all rows of the warp share one key.
+template <int PPT>
+__device__ __forceinline__ bool row_keys(const SweepArgs &a, long long r0, int lane,
+                                         int (&krow)[PPT], unsigned (&same)[PPT],
+                                         bool (&lead)[PPT], int &kfirst) {
+#pragma unroll
+  for (int r = 0; r < PPT; ++r) {
+    const long long row = r0 + r * 32 + lane;
+    krow[r] = row < a.N ? a.didx[a.plab[row]] : INT_MAX;
+    same[r] = seg_mask(krow[r], lane);
+    const int kp = __shfl_up_sync(0xffffffffu, krow[r], 1);
+    lead[r] = lane == 0 || kp != krow[r];
+  }
+  kfirst = __shfl_sync(0xffffffffu, krow[0], 0);
+  const int klast = __shfl_sync(0xffffffffu, krow[PPT - 1], 31);
+  return kfirst == klast;
+}
+
+// FP32 sweep: H coordinate pairs per point (f32x2 words, rows of stride DP
+// floats), PPT rows per thread; a tile is TI x TI points, TI = 256 * PPT.
+// Per row and column segment: FP32 partial sums of at most 32 terms, added
+// in FP64, then converted to fixed point once.
+template <int H, int DP, int PPT>
+__global__ void __launch_bounds__(DS_TPB) k_dense_sweep32(SweepArgs a) {
+  constexpr int TI = DS_TPB * PPT;
+  __shared__ unsigned long long sy[DS_CH * H];
+  __shared__ int skey[DS_CH];
+  __shared__ int sstart[DS_CH + 1];
+  __shared__ int wtot[DS_TPB / 32];
+  long long bi, bj;
+  tile_of(blockIdx.x + (long long)gridDim.x * blockIdx.y, bi, bj);
+  if (bi >= a.nb || bj >= a.nb) return;  // uniform over the block
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const long long r0 = bi * TI + (long long)w * 32 * PPT;
+  unsigned long long x[PPT][H];
+  int krow[PPT];
+  unsigned same[PPT];
+  bool lead[PPT];
+  int kfirst;
+  const bool uniform = row_keys<PPT>(a, r0, lane, krow, same, lead, kfirst);
+#pragma unroll
+  for (int r = 0; r < PPT; ++r) {
+    const long long row = r0 + r * 32 + lane;
+    const unsigned long long *xr = (const unsigned long long *)(a.p32 + (size_t)row * DP);
+#pragma unroll
+    for (int h = 0; h < H; ++h) x[r][h] = row < a.N ? xr[h] : 0ull;
+  }
+  unsigned long long pairs = 0;
+  for (int ch = 0; ch < PPT; ++ch) {  // TI columns in chunks of DS_CH
+    const long long c0 = bj * TI + (long long)ch * DS_CH;
+    if (c0 >= a.N) break;  // uniform
+    const int cnt = (int)min((long long)DS_CH, a.N - c0);
+    __syncthreads();
+    for (int i = threadIdx.x; i < cnt * H; i += DS_TPB) {
+      const int c = i / H, h = i - c * H;
+      sy[i] = ((const unsigned long long *)(a.p32 + (size_t)(c0 + c) * DP))[h];
+    }
+    if (threadIdx.x < DS_CH)
+      skey[threadIdx.x] = threadIdx.x < cnt ? a.didx[a.plab[c0 + threadIdx.x]] : -1;
+    __syncthreads();
+    const int nseg = chunk_segments(skey, cnt, sstart, wtot);
+    for (int sg = 0; sg < nseg; ++sg) {
+      const int cb = sstart[sg], ce = sstart[sg + 1];
+      const int qj = skey[cb];
+      if (qj <= kfirst) continue;  // no row of this warp pairs with it (uniform)
+      double acc[PPT];
+#pragma unroll
+      for (int r = 0; r < PPT; ++r) acc[r] = 0.0;
+      for (int c1 = cb; c1 < ce; c1 += 32) {
+        const int c2 = min(c1 + 32, ce);
+        float part[PPT];
+#pragma unroll
+        for (int r = 0; r < PPT; ++r) part[r] = 0.f;
+        for (int c = c1; c < c2; ++c) {
+          unsigned long long y[H];
+#pragma unroll
+          for (int h = 0; h < H; ++h) y[h] = sy[c * H + h];
+#pragma unroll
+          for (int r = 0; r < PPT; ++r) {
+            unsigned long long t = f2_sub(x[r][0], y[0]);
+            unsigned long long d2 = f2_mul(t, t);
+#pragma unroll
+            for (int h = 1; h < H; ++h) {
+              t = f2_sub(x[r][h], y[h]);
+              d2 = f2_fma(t, t, d2);
+            }
+            part[r] += sqrt_approx(f2_hsum(d2));
+          }
+        }
+#pragma unroll
+        for (int r = 0; r < PPT; ++r) acc[r] += (double)part[r];
+      }
+      U128 fx[PPT];
+#pragma unroll
+      for (int r = 0; r < PPT; ++r) {
+        fx[r] = fx_of(acc[r], a.e);
+        pairs += (unsigned long long)__popc(__ballot_sync(0xffffffffu, krow[r] < qj)) * (ce - cb);
+      }
+      flush<PPT>(a, fx, krow, same, lead, uniform, qj, lane);
+    }
+  }
+  if (lane == 0 && pairs) atomicAdd(&a.ctr->dense_pp, pairs);
+}
+
+// FP64 sweep: the same tiles, FP64 coordinates; every point distance is
+// added to the row's 128-bit sum exactly.
+template <int DP, int PPT>
+__global__ void __launch_bounds__(DS_TPB) k_dense_sweep64(SweepArgs a) {
+  constexpr int TI = DS_TPB * PPT;
+  __shared__ double sy[DS_CH * DP];
+  __shared__ int skey[DS_CH];
+  __shared__ int sstart[DS_CH + 1];
+  __shared__ int wtot[DS_TPB / 32];
+  long long bi, bj;
+  tile_of(blockIdx.x + (long long)gridDim.x * blockIdx.y, bi, bj);
+  if (bi >= a.nb || bj >= a.nb) return;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const long long r0 = bi * TI + (long long)w * 32 * PPT;
+  double x[PPT][DP];
+  int krow[PPT];
+  unsigned same[PPT];
+  bool lead[PPT];
+  int kfirst;
+  const bool uniform = row_keys<PPT>(a, r0, lane, krow, same, lead, kfirst);
+#pragma unroll
+  for (int r = 0; r < PPT; ++r) {
+    const long long row = r0 + r * 32 + lane;
+#pragma unroll
+    for (int k = 0; k < DP; ++k) x[r][k] = row < a.N ? a.p64[(size_t)row * DP + k] : 0.0;
+  }
+  unsigned long long pairs = 0;
+  for (int ch = 0; ch < PPT; ++ch) {
+    const long long c0 = bj * TI + (long long)ch * DS_CH;
+    if (c0 >= a.N) break;
+    const int cnt = (int)min((long long)DS_CH, a.N - c0);
+    __syncthreads();
+    for (int i = threadIdx.x; i < cnt * DP; i += DS_TPB) sy[i] = a.p64[(size_t)c0 * DP + i];
+    if (threadIdx.x < DS_CH)
+      skey[threadIdx.x] = threadIdx.x < cnt ? a.didx[a.plab[c0 + threadIdx.x]] : -1;
+    __syncthreads();
+    const int nseg = chunk_segments(skey, cnt, sstart, wtot);
+    for (int sg = 0; sg < nseg; ++sg) {
+      const int cb = sstart[sg], ce = sstart[sg + 1];
+      const int qj = skey[cb];
+      if (qj <= kfirst) continue;
+      U128 acc[PPT];
+#pragma unroll
+      for (int r = 0; r < PPT; ++r) acc[r] = U128{0ull, 0ull};
+      for (int c = cb; c < ce; ++c) {
+        const double *y = sy + c * DP;
+#pragma unroll
+        for (int r = 0; r < PPT; ++r) {
+          double d2 = 0.0;
+#pragma unroll
+          for (int k = 0; k < DP; ++k) {
+            const double t = x[r][k] - y[k];
+            d2 = fma(t, t, d2);
+          }
+          u128_add(acc[r], fx_of(sqrt(d2), a.e));
+        }
+      }
+#pragma unroll
+      for (int r = 0; r < PPT; ++r)
+        pairs += (unsigned long long)__popc(__ballot_sync(0xffffffffu, krow[r] < qj)) * (ce - cb);
+      flush<PPT>(a, acc, krow, same, lead, uniform, qj, lane);
+    }
+  }
+  if (lane == 0 && pairs) atomicAdd(&a.ctr->dense_pp, pairs);
+}
+
+// Sums -> means.  32 x 32 tiles of the upper triangle with their mirror
+// tile: the mirror cells get the same sum, both get the mean (+inf and a zero
+// sum on the diagonal); estimates (FP32 mode) carry the flag.  Shared memory
+// keeps every global access a row segment.
+__global__ void k_dense_fin(State s, int dk, bool est) {
+  __shared__ unsigned long long Slo[32][33], Shi[32][33];
+  __shared__ double Mv[32][33];
+  const int nt = (dk + 31) / 32;
+  long long ti, tj;
+  tile_of(blockIdx.x + (long long)gridDim.x * blockIdx.y, ti, tj);
+  if (ti >= nt || tj >= nt) return;
+  const int tx = threadIdx.x, ty = threadIdx.y;  // 32 x 8
+  for (int k = ty; k < 32; k += 8) {
+    const long long i = ti * 32 + k, j = tj * 32 + tx;  // the upper tile
+    unsigned long long lo = 0, hi = 0;
+    double v = 0.0;
+    if (i < dk && j < dk) {
+      if (i == j) {
+        v = __longlong_as_double((long long)KINF_D);
+      } else if (i < j) {
+        const size_t c = 2 * ((size_t)i * dk + j);
+        lo = s.dsum[c];
+        hi = s.dsum[c + 1] | (est ? TOP : 0ull);
+        v = entry_mean(lo, hi, s.dexp, s.qsz[i], s.qsz[j]);
+      }
+    }
+    Slo[k][tx] = lo;
+    Shi[k][tx] = hi;
+    Mv[k][tx] = v;
+  }
+  __syncthreads();
+  if (ti == tj) {
+    // diagonal tile: the lower cells take the upper cells' values
+    for (int k = ty; k < 32; k += 8) {
+      const long long i = ti * 32 + k, j = tj * 32 + tx;
+      if (i >= dk || j >= dk) continue;
+      const bool up = i <= j;
+      const size_t c = 2 * ((size_t)i * dk + j);
+      s.dsum[c] = up ? Slo[k][tx] : Slo[tx][k];
+      s.dsum[c + 1] = up ? Shi[k][tx] : Shi[tx][k];
+      s.dmat[(size_t)i * dk + j] = up ? Mv[k][tx] : Mv[tx][k];
+    }
+    return;
+  }
+  for (int k = ty; k < 32; k += 8) {
+    const long long i = ti * 32 + k, j = tj * 32 + tx;
+    if (i < dk && j < dk) {
+      s.dsum[2 * ((size_t)i * dk + j) + 1] = Shi[k][tx];
+      s.dmat[(size_t)i * dk + j] = Mv[k][tx];
+    }
+    const long long i2 = tj * 32 + k, j2 = ti * 32 + tx;  // mirror: upper cell (tx, k)
+    if (i2 < dk && j2 < dk) {
+      const size_t c = 2 * ((size_t)i2 * dk + j2);
+      s.dsum[c] = Slo[tx][k];
+      s.dsum[c + 1] = Shi[tx][k];
+      s.dmat[(size_t)i2 * dk + j2] = Mv[tx][k];
+    }
+  }
+}
+
+__global__ void k_dense_init(State s, const int32_t *order, int K) {
+  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < K; p += gridDim.x * blockDim.x) {
+    const int c = order[p];
+    s.didx[c] = p;
+    s.dcid[p] = c;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// nearest neighbours on the matrix: one warp per terminal, a scan of its row
+// ---------------------------------------------------------------------------
+struct NNArgs {
+  const double *dmat;
+  int dk, K, nlist;
+  const int32_t *order, *didx, *list;
+  double delta, rho;  // FP32 mode: error model of an estimate
+  double *Ekey;
+  int32_t *Ecid;
+  int32_t *drq_a, *drq_b;
+  int drq_cap;
+  int32_t *pend_out;
+  Counters *ctr;
+};
+
+__device__ __forceinline__ bool kless_d(unsigned long long k1, int c1, unsigned long long k2,
+                                        int c2) {
+  return k1 < k2 || (k1 == k2 && c1 < c2);
+}
+
+__device__ __forceinline__ void warp_argmin_kc(unsigned long long &k, int &c) {
+#pragma unroll
+  for (int o = 16; o; o >>= 1) {
+    const unsigned long long k2 = __shfl_xor_sync(0xffffffffu, k, o);
+    const int c2 = __shfl_xor_sync(0xffffffffu, c, o);
+    if (kless_d(k2, c2, k, c)) {
+      k = k2;
+      c = c2;
+    }
+  }
+}
+
+__device__ __forceinline__ double warp_min_d(double v) {
+#pragma unroll
+  for (int o = 16; o; o >>= 1) v = fmin(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+
+template <int F32>
+__global__ void k_dense_nn(NNArgs a) {
+  const int lane = threadIdx.x & 31;
+  const int nw = (gridDim.x * blockDim.x) >> 5;
+  unsigned long long tests = 0;
+  for (int t = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; t < a.nlist; t += nw) {
+    const int ci = a.list[t];
+    const int qi = a.didx[ci];
+    const double *row = a.dmat + (size_t)qi * a.dk;
+    tests += (unsigned long long)(a.K - 1);
+    if (!F32) {
+      unsigned long long bk = KINF_D;
+      int bc = INT_MAX;
+      for (int p = lane; p < a.K; p += 32) {
+        const int c = a.order[p];
+        if (c == ci) continue;
+        const unsigned long long k = (unsigned long long)__double_as_longlong(row[a.didx[c]]);
+        if (kless_d(k, c, bk, bc)) {
+          bk = k;
+          bc = c;
+        }
+      }
+      warp_argmin_kc(bk, bc);
+      if (lane == 0) {
+        a.Ekey[ci] = __longlong_as_double((long long)bk);
+        a.Ecid[ci] = bc == INT_MAX ? -1 : bc;
+        if (bc == INT_MAX) atomicOr(&a.ctr->err, ERR_NO_NN);
+      }
+      continue;
+    }
+    // FP32 mode.  Bounds of an estimate x on the FP64 value D:
+    // (x - delta) / (1 + rho) <= D <= (x + delta) / (1 - rho), widened by
+    // 1e-12 for the rounding of these FP64 operations.
+    const double lo_f = (1.0 - 1e-12) / (1.0 + a.rho), up_f = (1.0 + 1e-12) / (1.0 - a.rho);
+    double U = INFINITY;
+    for (int p = lane; p < a.K; p += 32) {
+      const int c = a.order[p];
+      if (c == ci) continue;
+      const double x = row[a.didx[c]];
+      const double m = mag(x);
+      const bool exact = !is_est(x) || (m == 0.0 && a.delta == 0.0);
+      U = fmin(U, exact ? m : (m + a.delta) * up_f);
+    }
+    U = warp_min_d(U);
+    unsigned long long bk = KINF_D;
+    int bc = INT_MAX, nW = 0, nE = 0, ec = INT_MAX;
+    double ev = 0.0;
+    for (int p = lane; p < a.K; p += 32) {
+      const int c = a.order[p];
+      if (c == ci) continue;
+      const double x = row[a.didx[c]];
+      const double m = mag(x);
+      const bool exact = !is_est(x) || (m == 0.0 && a.delta == 0.0);
+      const double lo = exact ? m : fmax(m - a.delta, 0.0) * lo_f;
+      if (!(lo <= U)) continue;
+      ++nW;
+      if (exact) {
+        const unsigned long long k = (unsigned long long)__double_as_longlong(m);
+        if (kless_d(k, c, bk, bc)) {
+          bk = k;
+          bc = c;
+        }
+      } else {
+        ++nE;
+        ec = c;
+        ev = m;
+      }
+    }
+    warp_argmin_kc(bk, bc);
+    const int totW = __reduce_add_sync(0xffffffffu, (unsigned)nW);
+    const int totE = __reduce_add_sync(0xffffffffu, (unsigned)nE);
+    if (totE == 0) {
+      if (lane == 0) {
+        a.Ekey[ci] = __longlong_as_double((long long)bk);
+        a.Ecid[ci] = bc == INT_MAX ? -1 : bc;
+        if (bc == INT_MAX) atomicOr(&a.ctr->err, ERR_NO_NN);
+      }
+      continue;
+    }
+    if (totW == 1) {
+      // the lone candidate is an estimate: its upper bound stands in for
+      // the FP64 value when the stated bound is within 4e-6 relative
+      const unsigned holder = __ballot_sync(0xffffffffu, nE > 0);
+      const int hl = __ffs(holder) - 1;
+      const double v = __shfl_sync(0xffffffffu, ev, hl);
+      const int c = __shfl_sync(0xffffffffu, ec, hl);
+      if (a.delta + a.rho * v <= 4e-6 * v) {
+        if (lane == 0) {
+          a.Ekey[ci] = (v + a.delta) * up_f;
+          a.Ecid[ci] = c;
+        }
+        continue;
+      }
+      if (lane == hl) {
+        const int r = atomicAdd(&a.ctr->nrq, 1);
+        if (r < a.drq_cap) {
+          const int q = a.didx[c];
+          a.drq_a[r] = min(qi, q);
+          a.drq_b[r] = max(qi, q);
+        }
+      }
+    } else {
+      // several candidates in the window: re-score its estimates in FP64
+      for (int p = lane; p < a.K; p += 32) {
+        const int c = a.order[p];
+        if (c == ci) continue;
+        const int q = a.didx[c];
+        const double x = row[q];
+        const double m = mag(x);
+        const bool exact = !is_est(x) || (m == 0.0 && a.delta == 0.0);
+        if (exact || !(fmax(m - a.delta, 0.0) * lo_f <= U)) continue;
+        const int r = atomicAdd(&a.ctr->nrq, 1);
+        if (r < a.drq_cap) {
+          a.drq_a[r] = min(qi, q);
+          a.drq_b[r] = max(qi, q);
+        }
+      }
+    }
+    if (lane == 0) a.pend_out[atomicAdd(&a.ctr->npend, 1)] = ci;
+  }
+  for (int o = 16; o; o >>= 1) tests += __shfl_xor_sync(0xffffffffu, tests, o);
+  if (lane == 0 && tests) atomicAdd(&a.ctr->ltests, tests);
+}
+
+// ---------------------------------------------------------------------------
+// FP64 re-score of listed pairs from the points (GPU-wide)
+// ---------------------------------------------------------------------------
+constexpr int RQ_TPB = 256;   // rows (points of the first cluster) per tile
+constexpr int RQ_COLS = 1024; // points of the second cluster per tile
+constexpr int RQ_CH = 128;    // staged per chunk
+
+__global__ void k_drq_count(State s, int m) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gridDim.x * blockDim.x) {
+    const int A = s.dcid[s.drq_a[i]], B = s.dcid[s.drq_b[i]];
+    const long long na = s.csize[A], nb = s.csize[B];
+    s.drq_pre[i] = (int32_t)(((na + RQ_TPB - 1) / RQ_TPB) * ((nb + RQ_COLS - 1) / RQ_COLS));
+  }
+}
+
+// exclusive scan of m tile counts into drq_pre (one block; total at [m])
+__global__ void k_drq_scan(State s, int m) {
+  __shared__ long long part[1024];
+  const int t = threadIdx.x, T = blockDim.x;
+  const int per = (m + T - 1) / T, b0 = t * per;
+  long long sum = 0;
+  for (int i = 0; i < per; ++i)
+    if (b0 + i < m) sum += s.drq_pre[b0 + i];
+  part[t] = sum;
+  __syncthreads();
+  if (t == 0) {
+    long long run = 0;
+    for (int i = 0; i < T; ++i) {
+      const long long v = part[i];
+      part[i] = run;
+      run += v;
+    }
+    s.drq_pre[m] = (int32_t)min(run, (long long)INT_MAX);
+    if (run > INT_MAX) atomicOr(&s.ctr->err, ERR_WINDOW);  // far beyond any real queue
+  }
+  __syncthreads();
+  long long run = part[t];
+  for (int i = 0; i < per; ++i)
+    if (b0 + i < m) {
+      const long long v = s.drq_pre[b0 + i];
+      s.drq_pre[b0 + i] = (int32_t)run;
+      run += v;
+    }
+}
+
+template <int DP>
+__global__ void __launch_bounds__(RQ_TPB) k_drq_eval(State s, int m, int cur) {
+  __shared__ double sy[RQ_CH * DP];
+  __shared__ unsigned long long rlo[RQ_TPB / 32], rhi[RQ_TPB / 32];
+  const int total = s.drq_pre[m];
+  const double *P = s.p64[cur];
+  const int32_t *seg = s.seg[cur];
+  for (int t = blockIdx.x; t < total; t += gridDim.x) {
+    int lo = 0, hi = m - 1;  // last i with pre[i] <= t
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (s.drq_pre[mid] <= t) lo = mid; else hi = mid - 1;
+    }
+    const int i = lo;
+    const int A = s.dcid[s.drq_a[i]], B = s.dcid[s.drq_b[i]];
+    const int na = s.csize[A], nb = s.csize[B];
+    const int tbn = (nb + RQ_COLS - 1) / RQ_COLS;
+    const int j = t - s.drq_pre[i];
+    const int ta = j / tbn, tb = j - ta * tbn;
+    const int row = ta * RQ_TPB + threadIdx.x;
+    double x[DP];
+    const bool act = row < na;
+#pragma unroll
+    for (int k = 0; k < DP; ++k) x[k] = act ? P[(size_t)(seg[A] + row) * DP + k] : 0.0;
+    U128 acc{0ull, 0ull};
+    const int cbeg = tb * RQ_COLS, cend = min(nb, cbeg + RQ_COLS);
+    for (int c0 = cbeg; c0 < cend; c0 += RQ_CH) {
+      const int cnt = min(RQ_CH, cend - c0);
+      __syncthreads();
+      for (int q = threadIdx.x; q < cnt * DP; q += RQ_TPB)
+        sy[q] = P[(size_t)(seg[B] + c0) * DP + q];
+      __syncthreads();
+      if (act)
+        for (int c = 0; c < cnt; ++c) {
+          double d2 = 0.0;
+#pragma unroll
+          for (int k = 0; k < DP; ++k) {
+            const double u = x[k] - sy[c * DP + k];
+            d2 = fma(u, u, d2);
+          }
+          u128_add(acc, fx_of(sqrt(d2), s.dexp));  // exactly as the FP64 sweep
+        }
+    }
+#pragma unroll
+    for (int o = 16; o; o >>= 1) u128_add(acc, u128_shfl_xor(acc, o));
+    if ((threadIdx.x & 31) == 0) {
+      rlo[threadIdx.x >> 5] = acc.lo;
+      rhi[threadIdx.x >> 5] = acc.hi;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      U128 v{0ull, 0ull};
+      for (int w = 0; w < RQ_TPB / 32; ++w) u128_add(v, U128{rlo[w], rhi[w]});
+      u128_atomic(&s.drq_acc[2 * (size_t)i], v);
+      const long long rows = min(RQ_TPB, na - ta * RQ_TPB);
+      atomicAdd(&s.ctr->dense_rq_pp, (unsigned long long)(rows * (cend - cbeg)));
+    }
+  }
+}
+
+// the re-scored sums replace both entries (exact: no flag)
+__global__ void k_drq_fin(State s, int m) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gridDim.x * blockDim.x) {
+    const int qa = s.drq_a[i], qb = s.drq_b[i];
+    const int A = s.dcid[qa], B = s.dcid[qb];
+    const unsigned long long lo = s.drq_acc[2 * (size_t)i], hi = s.drq_acc[2 * (size_t)i + 1];
+    const double v = entry_mean(lo, hi, s.dexp, s.csize[A], s.csize[B]);
+    const size_t c1 = (size_t)qa * s.dk + qb, c2 = (size_t)qb * s.dk + qa;
+    s.dsum[2 * c1] = lo;
+    s.dsum[2 * c1 + 1] = hi;
+    s.dsum[2 * c2] = lo;
+    s.dsum[2 * c2 + 1] = hi;
+    s.dmat[c1] = v;
+    s.dmat[c2] = v;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Lance-Williams update of the matrix after the round's merges: for average
+// linkage the sum of A u B with C is the sum of A's and B's (exact), the mean
+// follows from the new sizes
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ U128 sum_at(const State &s, size_t cell) {
+  return U128{s.dsum[2 * cell], s.dsum[2 * cell + 1]};
+}
+
+__device__ __forceinline__ U128 sum_add(const U128 &x, const U128 &y) {
+  U128 r{x.lo, x.hi & ~TOP};
+  u128_add(r, U128{y.lo, y.hi & ~TOP});
+  r.hi |= (x.hi | y.hi) & TOP;
+  return r;
+}
+
+__device__ __forceinline__ void sum_put(const State &s, size_t cell, const U128 &v) {
+  s.dsum[2 * cell] = v.lo;
+  s.dsum[2 * cell + 1] = v.hi;
+}
+
+// 1. rows: the survivor's row adds its partner's, over every cluster active
+//    at the start of the round; means for the clusters that did not merge
+__global__ void k_dense_row(State s, const int32_t *order_old, int Kold, int npairs, int round) {
+  const int dk = s.dk;
+  for (int p = blockIdx.y; p < npairs; p += gridDim.y) {
+    const int lo = s.pair_lo[p], hi = s.pair_hi[p];
+    const int qa = s.didx[lo], qb = s.didx[hi];
+    const int nab = s.csize[lo];
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < Kold; j += gridDim.x * blockDim.x) {
+      const int c = order_old[j];
+      const int q = s.didx[c];
+      if (q == qa || q == qb) continue;
+      const size_t cell = (size_t)qa * dk + q;
+      const U128 v = sum_add(sum_at(s, cell), sum_at(s, (size_t)qb * dk + q));
+      sum_put(s, cell, v);
+      if (s.mround[c] != round) s.dmat[cell] = entry_mean(v.lo, v.hi, s.dexp, nab, s.csize[c]);
+    }
+  }
+}
+
+// 2. pairs of clusters that both merged this round: the second partner's
+//    part is added from the first survivor's row, and the lower index writes
+//    both cells
+__global__ void k_dense_fix(State s, int npairs) {
+  const long long tot = (long long)npairs * npairs;
+  const int dk = s.dk;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < tot;
+       t += (long long)gridDim.x * blockDim.x) {
+    const int p1 = (int)(t / npairs), p2 = (int)(t - (long long)p1 * npairs);
+    if (p1 == p2) continue;
+    const int a = s.pair_lo[p1];
+    const int c = s.pair_lo[p2], d = s.pair_hi[p2];
+    const int qa = s.didx[a], qc = s.didx[c], qd = s.didx[d];
+    if (qa > qc) continue;
+    const U128 v = sum_add(sum_at(s, (size_t)qa * dk + qc), sum_at(s, (size_t)qa * dk + qd));
+    const double m = entry_mean(v.lo, v.hi, s.dexp, s.csize[a], s.csize[c]);
+    sum_put(s, (size_t)qa * dk + qc, v);
+    sum_put(s, (size_t)qc * dk + qa, v);
+    s.dmat[(size_t)qa * dk + qc] = m;
+    s.dmat[(size_t)qc * dk + qa] = m;
+  }
+}
+
+// 3. columns: every cluster that did not merge gets the survivor's entry in
+//    its own row (the matrix stays exactly symmetric)
+__global__ void k_dense_col(State s, const int32_t *order_old, int Kold, int npairs, int round) {
+  const int dk = s.dk;
+  for (int p = blockIdx.y; p < npairs; p += gridDim.y) {
+    const int qa = s.didx[s.pair_lo[p]];
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < Kold; j += gridDim.x * blockDim.x) {
+      const int c = order_old[j];
+      if (s.mround[c] == round) continue;  // merged this round: its row is done
+      const int r = s.didx[c];
+      const size_t src = (size_t)qa * dk + r, dst = (size_t)r * dk + qa;
+      sum_put(s, dst, sum_at(s, src));
+      s.dmat[dst] = s.dmat[src];
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------
+template <typename F>
+void launch_2d_tiles(F kernel, long long tiles, int threads_x, cudaStream_t st,
+                     const SweepArgs &a) {
+  const unsigned gx = (unsigned)std::min<long long>(tiles, 65535);
+  const unsigned gy = (unsigned)((tiles + gx - 1) / gx);
+  kernel<<<dim3(gx, gy), threads_x, 0, st>>>(a);
+}
+
+int sweep(hac_ctx *h, cudaStream_t st, const SweepArgs &a) {
+  const State &s = h->s;
+  const bool f32 = s.prec == HAC_PREC_F32_RECHECK;
+  const int ppt = f32 ? 4 : 2;
+  const long long TI = (long long)DS_TPB * ppt;
+  SweepArgs b = a;
+  b.nb = (a.N + TI - 1) / TI;
+  const long long tiles = b.nb * (b.nb + 1) / 2;
+  if (f32) {
+    const int H = (s.d + 1) >> 1;
+    switch (s.dp) {
+      case 2: launch_2d_tiles(k_dense_sweep32<1, 2, 4>, tiles, DS_TPB, st, b); break;
+      case 4: launch_2d_tiles(k_dense_sweep32<2, 4, 4>, tiles, DS_TPB, st, b); break;
+      case 8:
+        if (H <= 3)
+          launch_2d_tiles(k_dense_sweep32<3, 8, 4>, tiles, DS_TPB, st, b);
+        else
+          launch_2d_tiles(k_dense_sweep32<4, 8, 4>, tiles, DS_TPB, st, b);
+        break;
+      default:
+        if (H <= 5)
+          launch_2d_tiles(k_dense_sweep32<5, 16, 4>, tiles, DS_TPB, st, b);
+        else if (H == 6)
+          launch_2d_tiles(k_dense_sweep32<6, 16, 4>, tiles, DS_TPB, st, b);
+        else if (H == 7)
+          launch_2d_tiles(k_dense_sweep32<7, 16, 4>, tiles, DS_TPB, st, b);
+        else
+          launch_2d_tiles(k_dense_sweep32<8, 16, 4>, tiles, DS_TPB, st, b);
+    }
+  } else {
+    switch (s.dp) {
+      case 2: launch_2d_tiles(k_dense_sweep64<2, 2>, tiles, DS_TPB, st, b); break;
+      case 4: launch_2d_tiles(k_dense_sweep64<4, 2>, tiles, DS_TPB, st, b); break;
+      case 8: launch_2d_tiles(k_dense_sweep64<8, 2>, tiles, DS_TPB, st, b); break;
+      default: launch_2d_tiles(k_dense_sweep64<16, 2>, tiles, DS_TPB, st, b);
+    }
+  }
+  CK(cudaGetLastError());
+  return HAC_OK;
+}
+
+int64_t dense_threshold(const hac_ctx *h) {
+  if (h->dense_k >= 0) return h->dense_k;
+  return 32768;
+}
+
+// FP64 re-score of the first m listed pairs (they then hold exact values)
+int recheck(hac_ctx *h, cudaStream_t st, int m) {
+  State &s = h->s;
+  if (m <= 0) return HAC_OK;
+  CK(cudaMemsetAsync(s.drq_acc, 0, (size_t)m * 2 * sizeof(unsigned long long), st));
+  k_drq_count<<<grid_for(m, TPB), TPB, 0, st>>>(s, m);
+  k_drq_scan<<<1, 1024, 0, st>>>(s, m);
+  const int g = device_sms() * 4;
+  switch (s.dp) {
+    case 2: k_drq_eval<2><<<g, RQ_TPB, 0, st>>>(s, m, h->pcur); break;
+    case 4: k_drq_eval<4><<<g, RQ_TPB, 0, st>>>(s, m, h->pcur); break;
+    case 8: k_drq_eval<8><<<g, RQ_TPB, 0, st>>>(s, m, h->pcur); break;
+    default: k_drq_eval<16><<<g, RQ_TPB, 0, st>>>(s, m, h->pcur);
+  }
+  k_drq_fin<<<grid_for(m, TPB), TPB, 0, st>>>(s, m);
+  h->launches += 4;
+  CK(cudaGetLastError());
+  return HAC_OK;
+}
+
+}  // namespace
+
+int dense_maybe_enter(hac_ctx *h, cudaStream_t st, int K, RoundCtl &ctl) {
+  State &s = h->s;
+  if (s.dense) return 1;
+  if (s.linkage != LK_AVERAGE || s.max_inst != 1 || s.noprune || K < 2) return 0;
+  if ((int64_t)K > dense_threshold(h)) return 0;
+  // buffers, sized once per handle for the largest matrix it can need
+  if (h->dense_cap < K) {
+    const int64_t cap = std::min<int64_t>(dense_threshold(h), h->n);
+    const int rqcap = (int)std::min<int64_t>(std::max<int64_t>(4 * cap, 1 << 16), 1 << 22);
+    int rc = 0;
+    if ((rc = dalloc(h, &s.didx, h->n)) || (rc = dalloc(h, &s.dcid, cap)) ||
+        (rc = dalloc(h, &s.drq_a, rqcap)) || (rc = dalloc(h, &s.drq_b, rqcap)) ||
+        (rc = dalloc(h, &s.drq_pre, rqcap + 1)) ||
+        (rc = dalloc(h, &s.drq_acc, 2 * (size_t)rqcap)) || (rc = dalloc(h, &s.dpend[0], cap)) ||
+        (rc = dalloc(h, &s.dpend[1], cap)))
+      return rc;
+    s.drq_cap = rqcap;
+    // the matrices last: without room for them the instance stays on the
+    // range-query search (same result)
+    if (dalloc(h, &s.dmat, (size_t)cap * cap) != HAC_OK ||
+        dalloc(h, &s.dsum, 2 * (size_t)cap * cap) != HAC_OK) {
+      h->dense_k = 0;
+      return 0;
+    }
+    h->dense_cap = cap;
+  }
+  s.dk = K;
+  // unit of the fixed-point sums: (n/2)^2 x the largest point distance < 2^126 units
+  const double dmax = 2.0 * (double)s.coord_scale * std::sqrt((double)s.d) * (1.0 + 1e-5);
+  const double smax = 0.25 * (double)h->lay_n * (double)h->lay_n * dmax;
+  s.dexp = smax > 0.0 ? (int)std::floor(std::log2(smax)) + 1 - 126 : -1000;
+  k_dense_init<<<grid_for(K, TPB), TPB, 0, st>>>(s, s.order[h->ocur], K);
+  CK(cudaMemsetAsync(s.dsum, 0, (size_t)K * K * 2 * sizeof(unsigned long long), st));
+  SweepArgs a{};
+  a.p32 = s.p32[h->pcur];
+  a.p64 = s.p64[h->pcur];
+  a.plab = s.plab[h->pcur];
+  a.didx = s.didx;
+  a.N = h->lay_n;
+  a.dk = K;
+  a.e = s.dexp;
+  a.sum = s.dsum;
+  a.ctr = s.ctr;
+  if (ctl.eb0) cudaEventRecord(ctl.eb0, st);
+  int rc = sweep(h, st, a);
+  if (rc) return rc;
+  if (ctl.eb1) cudaEventRecord(ctl.eb1, st);
+  const long long nt = (K + 31) / 32, tiles = nt * (nt + 1) / 2;
+  const unsigned gx = (unsigned)std::min<long long>(tiles, 65535);
+  const unsigned gy = (unsigned)((tiles + gx - 1) / gx);
+  k_dense_fin<<<dim3(gx, gy), dim3(32, 8), 0, st>>>(s, K, s.prec == HAC_PREC_F32_RECHECK);
+  CK(cudaGetLastError());
+  if (ctl.eb0) {
+    CK(cudaEventSynchronize(ctl.eb1));
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, ctl.eb0, ctl.eb1);
+    ctl.ms_dense += ms;
+  }
+  h->launches += 3;
+  ctl.dense_launches += 3;
+  s.dense = 1;
+  return 1;
+}
+
+int dense_search(hac_ctx *h, cudaStream_t st, int K, int nterm, RoundCtl &ctl) {
+  State &s = h->s;
+  NNArgs a{};
+  a.dmat = s.dmat;
+  a.dk = s.dk;
+  a.K = K;
+  a.order = s.order[h->ocur];
+  a.didx = s.didx;
+  a.list = s.term;
+  a.nlist = nterm;
+  a.delta = (double)s.delta_pts;
+  a.rho = ((double)s.d + 48.0) * 5.9604644775390625e-8;
+  a.Ekey = s.Ekey;
+  a.Ecid = s.Ecid;
+  a.drq_a = s.drq_a;
+  a.drq_b = s.drq_b;
+  a.drq_cap = s.drq_cap;
+  a.ctr = s.ctr;
+  const bool f32 = s.prec == HAC_PREC_F32_RECHECK;
+  for (int it = 0;; ++it) {
+    if (it >= 64) return HAC_EINTERNAL;
+    CK(cudaMemsetAsync(&s.ctr->npend, 0, sizeof(int32_t), st));
+    CK(cudaMemsetAsync(&s.ctr->nrq, 0, sizeof(int32_t), st));
+    a.pend_out = s.dpend[it & 1];
+    const int blocks = std::max(1, std::min(cdiv(a.nlist, 8), device_sms() * 16));
+    if (f32)
+      k_dense_nn<1><<<blocks, 256, 0, st>>>(a);
+    else
+      k_dense_nn<0><<<blocks, 256, 0, st>>>(a);
+    CK(cudaGetLastError());
+    h->launches += 1;
+    ctl.searches += a.nlist;
+    if (!f32) break;
+    int cnt[2];  // npend, nrq are not adjacent: two reads
+    CK(cudaMemcpyAsync(&cnt[0], &s.ctr->npend, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(&cnt[1], &s.ctr->nrq, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    if (cnt[0] == 0) break;
+    const int m = std::min(cnt[1], s.drq_cap);
+    ctl.dense_launches += 4;
+    int rc = recheck(h, st, m);
+    if (rc) return rc;
+    ctl.dense_rechecks += m;
+    a.list = s.dpend[it & 1];
+    a.nlist = cnt[0];
+  }
+  return HAC_OK;
+}
+
+int dense_update(hac_ctx *h, cudaStream_t st, int round, int K, int npairs) {
+  State &s = h->s;
+  if (npairs <= 0) return HAC_OK;
+  const int32_t *order_old = s.order[h->ocur];  // active at the start of the round
+  const int gx = std::max(1, std::min(cdiv(K, TPB), 64));
+  const int gy = std::min(npairs, 65535);
+  k_dense_row<<<dim3(gx, gy), TPB, 0, st>>>(s, order_old, K, npairs, round);
+  if (npairs > 1) {
+    const long long tot = (long long)npairs * npairs;
+    k_dense_fix<<<grid_for(tot, TPB), TPB, 0, st>>>(s, npairs);
+    h->launches += 1;
+  }
+  k_dense_col<<<dim3(gx, gy), TPB, 0, st>>>(s, order_old, K, npairs, round);
+  h->launches += 2;
+  CK(cudaGetLastError());
+  return HAC_OK;
+}
+
+}  // namespace hacg

@@ -143,6 +143,10 @@ struct hac_ctx {
   long long big_pairs = hacg::BIG_PAIRS, big_pairs64 = hacg::BIG_PAIRS_F64;
   long long warp_budget = hacg::WARP_BUDGET;  // HAC_WARP_BUDGET overrides it
   int brute_env = -1;   // HAC_BRUTE: -1 unset, 0 never, 1 whenever allowed
+  // average linkage switches to the dense matrix once at most this many
+  // clusters are active (HAC_DENSE_K overrides it; 0 = never)
+  int64_t dense_k = -1;  // -1: the default for the instance
+  int64_t dense_cap = 0; // matrix dimension the buffers were allocated for
   int64_t launches = 0;  // kernels launched in the current run
   int ocur = 0, pcur = 0;
   bool done = false;
@@ -224,6 +228,10 @@ struct RoundCtl {
   int64_t qlaunch = 0, big_launch = 0, searches = 0;
   int64_t naive = 0;  // terminals x (active clusters - 1), summed over rounds
   int big_iters = 0, big_reqs = 0;
+  double ms_dense = 0;         // device time of the dense sweep
+  int64_t dense_launches = 0;  // launches of the dense phase's kernels
+  int64_t dense_rounds = 0;    // rounds run on the dense matrix
+  int64_t dense_rechecks = 0;  // matrix entries re-scored in FP64
 };
 
 int round_step(hac_ctx *h, cudaStream_t st, int round, int K, int nterm, RoundCtl &ctl,
@@ -237,5 +245,14 @@ int launch_big(const State &s, int r0, cudaStream_t st);
 int big_finish(const State &s, int r0, int m, cudaStream_t st);
 int launch_big_complete(const State &s, int r0, cudaStream_t st);
 int launch_big_average(const State &s, int r0, cudaStream_t st);
+
+// dense phase (hac_dense.cu): whether this round should run on the matrix
+// (entering it if needed: allocation, the all-pairs sweep); the
+// nearest-neighbour search of the round's terminals on the matrix (with the
+// FP64 re-score of near ties in the FP32 mode); the Lance-Williams update of
+// the matrix after the round's merges (before the compaction)
+int dense_maybe_enter(hac_ctx *h, cudaStream_t st, int K, RoundCtl &ctl);
+int dense_search(hac_ctx *h, cudaStream_t st, int K, int nterm, RoundCtl &ctl);
+int dense_update(hac_ctx *h, cudaStream_t st, int round, int K, int npairs);
 
 }  // namespace hacg

@@ -31,6 +31,8 @@ struct Counters {
   unsigned long long cache_hits, cache_lw;
   unsigned long long big_pp, big_exact;  // point pairs / FP64 requests of the GPU-wide evaluation
   unsigned long long big_skip;  // of those, pairs complete linkage skipped by box bounds
+  int32_t nrq;       // dense phase: pairs listed for an FP64 re-score this pass
+  unsigned long long dense_pp, dense_rq_pp;  // dense phase: sweep / re-score point pairs
 };
 
 enum : int32_t { ERR_NONFINITE = 1, ERR_NO_NN = 2, ERR_STACK = 4, ERR_WINDOW = 8 };
@@ -156,6 +158,26 @@ struct State {
   float *nhmin, *nlmax; // min over children of box hi / max of box lo, nodes x dp
   int32_t *nnmin;       // min child cluster size
   int32_t lvl_base[MAXLEV + 1];
+  // dense phase (average linkage, one instance): once the active clusters
+  // fit, the whole matrix of their pair distances (the Section 5 cache with
+  // room for every pair), filled by one all-pairs sweep of the points and
+  // updated by Lance-Williams after every round.  Each entry is kept as the
+  // exact sum of its point distances (128-bit fixed point, so a merge adds
+  // sums exactly) and as the mean distance that sum gives (FP64); in the FP32
+  // mode an FP32-derived estimate carries the sign bit of the mean (its
+  // magnitude is the estimate) and the top bit of the sum.
+  int dense;            // 1 once the instance runs on the matrix
+  int dk;               // matrix dimension: active clusters at the switch
+  int dexp;             // exponent of the fixed-point unit of the sweep sums
+  double *dmat;         // dk x dk, row-major; diagonal +inf
+  unsigned long long *dsum;  // dk x dk 128-bit fixed-point sums of point distances
+                             // (two words per entry; the top bit marks an estimate)
+  int32_t *didx;        // cid -> matrix index (the cid's position at the switch)
+  int32_t *dcid;        // matrix index -> cid
+  int drq_cap;          // FP64 re-score queue (pairs, lower index first)
+  int32_t *drq_a, *drq_b, *drq_pre;
+  unsigned long long *drq_acc;  // fixed-point sums, two words per pair
+  int32_t *dpend[2];    // terminals whose search waits for re-scored pairs
   // scan scratch
   int32_t *bsum;        // 3 x nblocks block partial sums
   Counters *ctr;

@@ -46,7 +46,9 @@ class hac_stats_t(ctypes.Structure):
                                               "kernel_launches", "cache_hits",
                                               "cache_lw_entries")] + \
                [("ms_big", ctypes.c_double), ("big_point_pairs", ctypes.c_int64),
-                ("big_launches", ctypes.c_int64), ("naive_pairs", ctypes.c_int64)]
+                ("big_launches", ctypes.c_int64), ("naive_pairs", ctypes.c_int64)] + \
+               [(k, ctypes.c_int64) for k in ("dense_k", "dense_rounds", "dense_point_pairs",
+                                              "dense_rechecks")] + [("ms_dense", ctypes.c_double)]
 
 
 class hac_server_stats_t(ctypes.Structure):

@@ -27,6 +27,13 @@ RTOL32 = 1e-5   # FP32 mode: complete/average heights carry the stated FP32 boun
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
 
 
+@pytest.fixture
+def tree_path(monkeypatch):
+    """Average linkage on the range-query search with the Section 5 cache and
+    the GPU-wide big-pair kernels: the dense matrix is off (HAC_DENSE_K=0)."""
+    monkeypatch.setenv("HAC_DENSE_K", "0")
+
+
 def _round_sets(d):
     out = {}
     for a, b, r in zip(d["a"], d["b"], d["round"]):
@@ -160,13 +167,22 @@ def test_multilevel_tree(lk, prec):
                  rtol=_rtol(lk, prec))
 
 
+@pytest.mark.parametrize("dense", ["tree", "dense"])
 @pytest.mark.parametrize("prec", PRECS, ids=PREC_IDS)
 @pytest.mark.parametrize("lk", LKS)
-def test_gmm5d_sample(lk, prec):
-    """The 5-D Gaussian-mixture workload's recipe at a size the oracle runs."""
+def test_gmm5d_sample(lk, prec, dense, monkeypatch):
+    """The 5-D Gaussian-mixture workload's recipe at a size the oracle runs
+    (average linkage: on the range-query search, and on the dense matrix from
+    the first round)."""
+    if dense == "tree":
+        monkeypatch.setenv("HAC_DENSE_K", "0")
+    elif lk != "average":
+        pytest.skip("the dense matrix is for average linkage")
     X = inputs.workload("gmm5d_1m_f32", n=5000)
-    _assert_same(hac.cluster(X, lk, precision=prec), oracle.rounds(X.astype(np.float64), lk),
-                 rtol=_rtol(lk, prec))
+    got = hac.cluster(X, lk, precision=prec)
+    _assert_same(got, oracle.rounds(X.astype(np.float64), lk), rtol=_rtol(lk, prec))
+    if lk == "average":
+        assert (got["stats"]["dense_k"] > 0) == (dense == "dense")
 
 
 @pytest.mark.parametrize("prec", PRECS, ids=PREC_IDS)
@@ -246,7 +262,7 @@ def test_round_limit_and_rerun():
         hac.hac_destroy(h)
 
 
-def test_cache_resize_between_runs():
+def test_cache_resize_between_runs(tree_path):
     """Reruns of one handle with another cache size give the same tree; a
     larger table replaces the old one (its memory is released) and a smaller
     request reuses it."""
@@ -411,7 +427,7 @@ def test_full_size_16d_lattice(lk):
 @pytest.mark.parametrize("slots", [8, 64])
 @pytest.mark.parametrize("prec", PRECS, ids=PREC_IDS)
 @pytest.mark.parametrize("lk", ["complete", "average"])
-def test_cache_parity(lk, prec, slots):
+def test_cache_parity(lk, prec, slots, tree_path):
     """Section 5 cache with the Lance-Williams update after merges: the tree
     is unchanged, heights stay within 1e-9 of the oracle, and the cache is
     actually used (hits and Lance-Williams-derived entries)."""
@@ -423,7 +439,7 @@ def test_cache_parity(lk, prec, slots):
 
 @pytest.mark.parametrize("prec", PRECS, ids=PREC_IDS)
 @pytest.mark.parametrize("lk", ["complete", "average"])
-def test_cache_lattice_ties(lk, prec):
+def test_cache_lattice_ties(lk, prec, tree_path):
     X = inputs.lattice(400, 3, seed=11, levels=16)
     got = hac.cluster(X, lk, precision=prec, cache_slots=64)
     bad, stats = oracle.validate(X.astype(np.float64), lk, got, rtol=RTOL64,
@@ -439,7 +455,7 @@ def test_cache_lattice_ties(lk, prec):
 @pytest.mark.parametrize("slots", [8, 64])
 @pytest.mark.parametrize("prec", PRECS, ids=PREC_IDS)
 @pytest.mark.parametrize("lk", ["complete", "average"])
-def test_big_pair_deferral(lk, prec, slots, monkeypatch):
+def test_big_pair_deferral(lk, prec, slots, monkeypatch, tree_path):
     """Force nearly every cached pair through the GPU-wide evaluation and
     the re-run search (tiny thresholds): the tree must not change."""
     monkeypatch.setenv("HAC_BIG_PAIRS", "256")
@@ -452,7 +468,7 @@ def test_big_pair_deferral(lk, prec, slots, monkeypatch):
 
 @pytest.mark.parametrize("lk", ["complete", "average"])
 @pytest.mark.parametrize("d", list(range(1, 17)))
-def test_big_pairs_every_dimension(lk, d, monkeypatch):
+def test_big_pairs_every_dimension(lk, d, monkeypatch, tree_path):
     """The GPU-wide FP32 kernels are specialised on the true dimension and
     the FP64 ones on the padded width: with tiny thresholds nearly every
     evaluated pair of >= 256 point pairs goes through them, at every d from 1
