@@ -28,9 +28,8 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
-METRIC = "HAC wall time & distance evals/s vs HBM roofline at n=1M"
+METRIC = "HAC wall time & distance evals/s vs HBM roofline at n=1M; serving p50/p99 ms"
 UNIT = "points/s"
-SMS, FP32_LANES = 152, 128   # GB300: SMs and FP32 lanes per SM
 
 # DRAM bytes (read + write) per launch, from one ncu capture of this bench's
 # command (profiles/launches_gmm5d_1m_ward_average.md); valid for the kernels
@@ -47,9 +46,52 @@ def _peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
             p = json.load(f)
-        return float(p["hbm_gbs"]), float(p.get("sm_max_mhz", 2070.0)), "measured"
+        return float(p["hbm_gbs"]), "measured"
     except Exception:
-        return 6800.0, 2070.0, "fallback"
+        return 6800.0, "fallback"
+
+
+def fp32_peak(local: int):
+    """FP32 multiply-add throughput measured on this GPU (the library's FMA
+    probe: scalar and packed f32x2 loops, CUDA events), with the SM clock
+    sampled during it.  Returns (TFLOP/s, description)."""
+    import ctypes
+
+    from paper_2106_04727_gb300 import build as libbuild
+
+    lib = ctypes.CDLL(libbuild.build_probe())
+    lib.hac_probe_fma.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
+                                  ctypes.POINTER(ctypes.c_float)]
+    best = {}
+    with Clocks(local) as clk:
+        for packed in (0, 1):
+            tf, ms = ctypes.c_double(), ctypes.c_float()
+            rc = lib.hac_probe_fma(packed, 5, ctypes.byref(tf), ctypes.byref(ms))
+            if rc != 0:
+                raise RuntimeError(f"FMA probe failed ({rc})")
+            best["f32x2" if packed else "scalar"] = tf.value
+    c = clk.summary() or {}
+    peak = max(best.values())
+    return peak, (f"measured: FMA-loop probe, {best['scalar']:.1f} TFLOP/s scalar, "
+                  f"{best['f32x2']:.1f} TFLOP/s packed f32x2, median SM clock "
+                  f"{c.get('sm_mhz')} MHz during the probe")
+
+
+def same_tree(a, b, rtol):
+    """Two dendrograms (dicts of arrays a, b, h, size) have the same merges
+    (cid_a, cid_b, size) and heights within rtol; returns (same, largest
+    relative height difference)."""
+    import numpy as np
+
+    ka = np.lexsort((a["b"], a["a"]))
+    kb = np.lexsort((b["b"], b["a"]))
+    same = len(ka) == len(kb) and all(np.array_equal(np.asarray(a[f])[ka], np.asarray(b[f])[kb])
+                                      for f in ("a", "b", "size"))
+    if not same:
+        return False, float("inf")
+    ha, hb = np.asarray(a["h"])[ka], np.asarray(b["h"])[kb]
+    err = float(np.max(np.abs(ha - hb) / np.maximum(np.abs(hb), 1e-300))) if len(ha) else 0.0
+    return err <= rtol, err
 
 
 class Clocks:
@@ -214,20 +256,19 @@ def _per_instance(hac, reqs, pts, prec, slots):
             "p50_ms": _pct(lat, 50), "p99_ms": _pct(lat, 99), "max_ms": max(lat)}, res
 
 
-def run_serving(args):
+def serving_measure(args, steps, warmup, local):
     """The serving stream: requests of uneven n, d and linkage, continuous
-    batching in the library's server (FP32 bulk + FP64 re-score) against the
-    per-instance FP64 path and the same requests run one after the other."""
+    batching in the library's server (FP32 bulk + FP64 re-score): saturated
+    (every request at t = 0) jobs/s and latencies, Poisson arrivals at 0.7 x
+    that rate, and on a sample of the stream the batched server against the
+    plain per-instance FP64 GPU path (hac_create + hac_run + hac_dendrogram
+    per request), the same requests one after the other in FP32 + re-score,
+    and a batched FP64 server, with the trees compared to the FP64 ones."""
     import numpy as np
     import torch
 
-    import oracle
     from paper_2106_04727_gb300 import hac, inputs
 
-    ws, rank, local = dist_env()
-    torch.cuda.set_device(local)
-    if rank != 0:
-        return
     slots = args.serving_cache_slots
     reqs = inputs.serving_requests(args.requests, seed=4)
     pts = [inputs.request_points(r) for r in reqs]
@@ -243,13 +284,13 @@ def run_serving(args):
                 t = hac.hac_submit(srv, inputs.gaussian_mixture(100, d, 4, seed=d), lk)
                 hac.hac_server_wait(srv, t, 600.0)
                 hac.hac_poll(srv, t, 100)
-        for _ in range(args.warmup):
+        for _ in range(warmup):
             _serve(hac, srv, warm, wpts)
         flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
         st0 = hac.hac_server_stats(srv)
         sat = []
         with Clocks(local) as clk:
-            for i in range(args.steps):
+            for i in range(steps):
                 flush.fill_(float(i))
                 torch.cuda.synchronize()
                 sat.append(_serve(hac, srv, reqs, pts)[0])
@@ -268,9 +309,9 @@ def run_serving(args):
         seq32, _ = _per_instance(hac, sreq, spts, hac.PREC_F32_RECHECK, slots)
         same, err = 0, 0.0
         for a, b in zip(res_b, res_64):
-            c = oracle.compare(hac.result_dict(a), b, rtol=1e-5)
-            same += int(c["same_tree"])
-            err = max(err, c["max_rel_err"])
+            ok, e = same_tree(hac.result_dict(a), b, 1e-5)
+            same += int(ok)
+            err = max(err, e)
         srv64 = hac.hac_server_create(cap, precision=hac.PREC_F64, cache_slots=slots)
         for lk in range(3):
             for d in (2, 3, 5, 10):
@@ -281,6 +322,32 @@ def run_serving(args):
     finally:
         hac.hac_server_destroy(srv)
         hac.hac_server_destroy(srv64)
+    out = {"saturated": sat, "poisson": poisson,
+           "sample": {"requests": k, "batched_f32_recheck": batched_s,
+                      "batched_f64": batched64_s,
+                      "per_instance_f64": per64, "sequential_f32_recheck": seq32,
+                      "speedup_batched_vs_per_instance_f64":
+                          batched_s["jobs_per_s"] / per64["jobs_per_s"],
+                      "same_trees_as_f64": f"{same}/{k}",
+                      "max_rel_height_err_vs_f64": err}}
+    return out, reqs, pts, st0, st1, clk.summary()
+
+
+def run_serving(args):
+    """The serving stream as its own benchmark line."""
+    import numpy as np
+    import torch
+
+    import oracle
+    from paper_2106_04727_gb300 import hac  # noqa: F401
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    if rank != 0:
+        return
+    res, reqs, pts, st0, st1, clocks = serving_measure(args, args.steps, args.warmup, local)
+    sat = res["saturated"]
+    best = max(sat, key=lambda x: x["jobs_per_s"])
     cpu = None
     if not args.no_cpu_baseline:
         # the oracle on the stream's requests of n <= 4096 (O(n^2) memory), first 24
@@ -305,24 +372,17 @@ def run_serving(args):
                    "points": int(sum(r["n"] for r in reqs)),
                    "n": "log-uniform [64, 65536]", "d": "{2,3,5,10}",
                    "linkages": "complete+average+ward", "precision": "f32",
-                   "cache_slots": slots, "engine_points": cap,
+                   "cache_slots": args.serving_cache_slots, "engine_points": args.engine_points,
                    "step": "the whole stream submitted at t=0, every result read back",
                    "l2": "flushed before each timed step (256 MB write); inputs are new "
                          "host data each step"},
-        "serving": {"saturated": sat, "poisson": poisson,
-                    "sample": {"requests": k, "batched_f32_recheck": batched_s,
-                               "batched_f64": batched64_s,
-                               "per_instance_f64": per64, "sequential_f32_recheck": seq32,
-                               "speedup_batched_vs_per_instance_f64":
-                                   batched_s["jobs_per_s"] / per64["jobs_per_s"],
-                               "same_trees_as_f64": f"{same}/{k}",
-                               "max_rel_height_err_vs_f64": err}},
+        "serving": res,
         "server": {k2: st1[k2] - st0.get(k2, 0) if isinstance(st1[k2], (int, float)) and
                    k2 not in ("engines", "max_resident", "device_bytes", "status") else st1[k2]
                    for k2 in st1},
         "roofline": None,
         "gpu_launches": int(st1["kernel_launches"] - st0["kernel_launches"]),
-        "clocks": clk.summary(),
+        "clocks": clocks,
         "e2e": {"value": best["jobs_per_s"], "unit": "jobs/s",
                 "h2d_bytes_per_step": pts_bytes, "d2h_bytes_per_step": rec_bytes,
                 "note": "the server API takes host points and returns host records: "
@@ -470,6 +530,10 @@ def main():
     ap.add_argument("--ref-sample", type=int, default=20000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-f64", action="store_true",
+                    help="skip the all-FP64 run of the workload after the timed steps")
+    ap.add_argument("--no-serving", action="store_true",
+                    help="skip the serving-stream summary of the default line")
     ap.add_argument("--requests", type=int, default=4096, help="serving: stream length")
     ap.add_argument("--sample", type=int, default=256,
                     help="serving: requests timed on the per-instance paths")
@@ -548,11 +612,13 @@ def main():
     def agg(key, lk=None):
         return sum(s[l][key] for s in stats for l in s if lk is None or l == lk)
 
-    hbm, sm_mhz, peak_kind = _peaks()
-    fp32_tflops = SMS * FP32_LANES * 2 * sm_mhz * 1e6 / 1e12
+    hbm, peak_kind = _peaks()
+    fp32_tflops, fp32_src = fp32_peak(local)
     # kernels, measured by the library with CUDA events on the launching stream
     q_ms, q_bytes, q_launch = agg("ms_query"), agg("query_bytes"), agg("query_launches")
     b_ms, b_pairs, b_launch = agg("ms_big"), agg("big_point_pairs"), agg("big_launches")
+    s_ms, s_pairs = agg("ms_dense"), agg("dense_point_pairs")
+    s_launch = sum(1 for st in stats for l in st if st[l]["dense_k"] > 0)
     flops_per_pair = 3 * d + 2   # d subtractions, d multiply-adds (2 flops), sqrt, add
     kern = {
         "k_query": {"bound": "hbm", "ms": q_ms / args.steps, "launches": q_launch // args.steps,
@@ -563,14 +629,19 @@ def main():
                          "achieved": b_pairs * flops_per_pair / (b_ms / 1e3) / 1e12 if b_ms else 0.0,
                          "peak": fp32_tflops, "unit": "TFLOP/s",
                          "traffic": TRAFFIC.get(("k_big_eval32", args.workload))},
+        "k_dense_sweep32": {"bound": "alu", "ms": s_ms / args.steps,
+                            "launches": s_launch // args.steps,
+                            "achieved": s_pairs * flops_per_pair / (s_ms / 1e3) / 1e12
+                            if s_ms else 0.0,
+                            "peak": fp32_tflops, "unit": "TFLOP/s",
+                            "traffic": TRAFFIC.get(("k_dense_sweep32", args.workload))},
     }
     for k in kern.values():
         k["frac"] = k["achieved"] / k["peak"] if k["peak"] else 0.0
     dom = max(kern, key=lambda k: kern[k]["ms"])
     roof = dict(kern[dom])
     roof["kernel"] = dom
-    roof["peak_source"] = peak_kind + (" (FP32: 152 SMs x 128 lanes x 2 flops x max SM clock)"
-                                       if roof["bound"] == "alu" else " (HBM copy)")
+    roof["peak_source"] = fp32_src if roof["bound"] == "alu" else peak_kind + " (HBM copy)"
     per_lk = {}
     for lk in args.linkages:
         ms = agg("ms_total", lk) / args.steps
@@ -580,7 +651,30 @@ def main():
                       "cluster_pair_evals_per_s": s0["cluster_pairs"] / (ms / 1e3),
                       "point_pair_evals_per_s": s0["point_pairs"] / (ms / 1e3),
                       "cache_hits": s0["cache_hits"], "ms_search": s0["ms_query"],
-                      "ms_big_pairs": s0["ms_big"]}
+                      "ms_big_pairs": s0["ms_big"], "ms_dense_sweep": s0["ms_dense"],
+                      "dense_k": s0["dense_k"], "dense_rounds": s0["dense_rounds"],
+                      "point_pairs_over_minimum": s0["point_pairs"] / (n * (n - 1) / 2)}
+    # the plain all-FP64 GPU path on the same workload (untimed by the steps):
+    # its wall time per linkage and whether its tree is the FP32 + re-score one
+    c2 = None
+    if rank == 0 and not args.no_f64 and prec != hac.PREC_F64:
+        c2 = {}
+        for lk, h in handles.items():
+            m32 = hac.hac_dendrogram(h, n)
+            d32 = {"a": m32["cid_a"].copy(), "b": m32["cid_b"].copy(), "h": m32["height"].copy(),
+                   "size": m32["size"].copy()}
+            rc = hac.hac_run(h, precision=hac.PREC_F64, cache_slots=args.cache_slots,
+                             stream=stream.cuda_stream)
+            if rc != 0:
+                raise hac.HacError(rc, "hac_run (FP64)")
+            st64 = hac.hac_stats(h)
+            m64 = hac.hac_dendrogram(h, n)
+            d64 = {"a": m64["cid_a"], "b": m64["cid_b"], "h": m64["height"], "size": m64["size"]}
+            ok, err = same_tree(d32, d64, 1e-5)
+            c2[lk] = {"ms_f64": st64["ms_total"], "ms_f32_recheck": per_lk[lk]["ms_per_run"],
+                      "speedup_f32_recheck": st64["ms_total"] / per_lk[lk]["ms_per_run"],
+                      "same_tree": ok, "max_rel_height_err": err,
+                      "ms_dense_sweep_f64": st64["ms_dense"]}
     e2e = None
     cpu = None
     if rank == 0 and not args.no_e2e:
@@ -602,6 +696,27 @@ def main():
         cpu, _ = cpu_baseline(args.workload, args.linkages, args.ref_sample)
     for h in handles.values():
         hac.hac_destroy(h)
+    del Xd, flush
+    torch.cuda.empty_cache()
+    serving = None
+    if rank == 0 and not args.no_serving:
+        res, _, _, _, _, sclk = serving_measure(args, 1, 1, local)
+        sat = res["saturated"][0]
+        smp = res["sample"]
+        serving = {"metric": SERVING_METRIC, "requests": args.requests,
+                   "saturated_jobs_per_s": sat["jobs_per_s"],
+                   "saturated_p50_ms": sat["p50_ms"], "saturated_p99_ms": sat["p99_ms"],
+                   "poisson_rate_jobs_per_s": res["poisson"]["rate_jobs_per_s"],
+                   "poisson_p50_ms": res["poisson"]["p50_ms"],
+                   "poisson_p99_ms": res["poisson"]["p99_ms"],
+                   "sample_requests": smp["requests"],
+                   "batched_f32_recheck_jobs_per_s": smp["batched_f32_recheck"]["jobs_per_s"],
+                   "per_instance_f64_jobs_per_s": smp["per_instance_f64"]["jobs_per_s"],
+                   "speedup_batched_vs_per_instance_f64":
+                       smp["speedup_batched_vs_per_instance_f64"],
+                   "same_trees_as_f64": smp["same_trees_as_f64"],
+                   "max_rel_height_err_vs_f64": smp["max_rel_height_err_vs_f64"],
+                   "clocks": sclk}
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
@@ -621,6 +736,8 @@ def main():
             "clocks": clk.summary(),
             "e2e": e2e,
             "cpu_baseline": cpu,
+            "c2_f64": c2,
+            "serving": serving,
         }
         print(json.dumps(line), flush=True)
     if dist:

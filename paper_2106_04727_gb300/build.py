@@ -76,5 +76,26 @@ def build(force: bool = False, verbose: bool = False, ptxas_v: bool = False) -> 
     return LIB
 
 
+PROBE_SRC = os.path.join(HERE, "probe", "fma_probe.cu")
+PROBE_LIB = os.path.join(BUILD, "libhacprobe.so")
+
+
+def build_probe(force: bool = False) -> str:
+    """The FP32 multiply-add throughput probe the benchmark uses as its
+    arithmetic peak (a separate library; not part of the clustering ABI)."""
+    if not force and os.path.exists(PROBE_LIB) and \
+            os.path.getmtime(PROBE_LIB) >= os.path.getmtime(PROBE_SRC):
+        return PROBE_LIB
+    os.makedirs(BUILD, exist_ok=True)
+    tmp = PROBE_LIB + f".{os.getpid()}.tmp"
+    r = subprocess.run([nvcc(), *_flags(), "-shared", "-o", tmp, PROBE_SRC],
+                       capture_output=True, text=True)
+    if r.returncode != 0:
+        raise RuntimeError(f"nvcc failed for {PROBE_SRC}:\n{r.stdout}\n{r.stderr}")
+    os.replace(tmp, PROBE_LIB)
+    return PROBE_LIB
+
+
 if __name__ == "__main__":
     print(build(force="--force" in sys.argv, verbose=True, ptxas_v="-v" in sys.argv))
+    print(build_probe(force="--force" in sys.argv))

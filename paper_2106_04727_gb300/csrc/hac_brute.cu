@@ -226,6 +226,144 @@ __global__ void __launch_bounds__(BR_T) k_brute_recheck(QueryArgs a) {
   atomicAdd(&a.ctr->rechecks, rechecks);
 }
 
+// ---------------------------------------------------------------------------
+// Candidate lists for average linkage (Euclidean) in high dimension.
+//
+// Average linkage needs point pairs, so the exhaustive scan cannot score
+// candidates itself; it replaces only the tree traversal.  Each terminal (one
+// thread) streams every active cluster's FP32 record through shared memory,
+// as above, and keeps:
+//   U  = the least upper bound on D(C_i, B) over all B: the predecessor bound
+//        beta (Algorithm 2) and the Jensen bound of each record,
+//        mean ||x - y|| <= sqrt(||c_A - c_B||^2 + var A + var B), with the
+//        FP32 centroid distance widened by its error bound;
+//   the positions of the clusters whose centroid lower bound
+//        ||c_A - c_B|| <= D(A, B) (Section 4.2) is within U (times 1 + 1e-5,
+//        plus the search's absolute slack): the only clusters that can be the
+//        nearest neighbour.
+// The list (sorted by lower bound) and U go to the warp search, which
+// evaluates those candidates as it would evaluate a tree leaf.  Tiles start at
+// the CTA's own region of the spatial order, so U drops early and the list
+// stays short; a list longer than BL_CAP is dropped (count -1) and that
+// terminal searches the tree.
+// ---------------------------------------------------------------------------
+template <int DP>
+__global__ void __launch_bounds__(BR_T) k_cand_avg(QueryArgs a, int32_t *lpos, float *llb,
+                                                   int32_t *lcnt, float *lub) {
+  constexpr int H = DP / 2;
+  __shared__ __align__(16) float sq[BR_C * DP];
+  __shared__ float sv[BR_C];
+  const int t = blockIdx.x * BR_T + threadIdx.x;
+  const bool act = t < a.nterm;
+  int ci = -1, mypos = -1;
+  unsigned long long x[H];
+  float vA = 0.f, U = INFINITY, delta0 = 0.f, rho = 0.f, slack = 0.f;
+  if (act) {
+    ci = a.term[t];
+    mypos = a.pos[ci];
+    vA = a.qvar[mypos];
+#pragma unroll
+    for (int h = 0; h < H; ++h)
+      x[h] = ((const unsigned long long *)(a.cent32 + (size_t)ci * DP))[h];
+    const unsigned long long pv = a.pred[ci];
+    if (pv != PRED_EMPTY) U = __uint_as_float((unsigned)(pv >> 32));
+    const int ins = a.inst[ci];
+    delta0 = 2.01f * U32 * a.iscale[ins] * sqrtf((float)a.d);
+    rho = ((float)a.d + 16.f) * U32 + 32.f * U32;
+    slack = a.islack[ins] * 2.f;
+  }
+  // candidate threshold on the squared centroid distance for the current U
+  auto thr2 = [&](float u) {
+    if (!(u < INFINITY)) return INFINITY;
+    const float tt = u * (1.f + EPS) + slack;
+    return tt * tt * (1.f + 1e-6f);
+  };
+  float T2 = thr2(U);
+  int32_t *L = act ? lpos + (size_t)mypos * BL_CAP : nullptr;
+  float *LB = act ? llb + (size_t)mypos * BL_CAP : nullptr;
+  int cnt = 0;
+  bool over = false;
+  const int nt = (a.K + BR_C - 1) / BR_C;
+  const int k0 = a.pos[a.term[blockIdx.x * BR_T]] / BR_C;  // the CTA's own region first
+  unsigned long long scanned = 0;
+  for (int it = 0; it < nt; ++it) {
+    const int p0 = ((k0 + it) % nt) * BR_C;
+    const int n_here = min(BR_C, a.K - p0);
+    __syncthreads();
+    for (int i = threadIdx.x; i < n_here * DP; i += BR_T) sq[i] = a.q32[(size_t)p0 * DP + i];
+    for (int j = threadIdx.x; j < n_here; j += BR_T) sv[j] = a.qvar[p0 + j];
+    __syncthreads();
+    if (!act || over) continue;
+    scanned += n_here;
+    for (int j = 0; j < n_here; ++j) {
+      if (p0 + j == mypos) continue;
+      const unsigned long long *y = (const unsigned long long *)(sq + j * DP);
+      unsigned long long tt = f2_sub(x[0], y[0]);
+      unsigned long long d2 = f2_mul(tt, tt);
+#pragma unroll
+      for (int h = 1; h < H; ++h) {
+        tt = f2_sub(x[h], y[h]);
+        d2 = f2_fma(tt, tt, d2);
+      }
+      const float dc2 = f2_hsum(d2);
+      if (dc2 <= T2) {
+        if (cnt == BL_CAP) {  // full: keep only what the current U still admits
+          const float tl = sqrtf(T2);
+          int k = 0;
+          for (int q = 0; q < cnt; ++q)
+            if (LB[q] <= tl) {
+              L[k] = L[q];
+              LB[k] = LB[q];
+              ++k;
+            }
+          cnt = k;
+        }
+        if (cnt < BL_CAP) {
+          L[cnt] = p0 + j;
+          LB[cnt] = sqrtf(dc2);
+          ++cnt;
+        } else {
+          over = true;
+          break;
+        }
+      }
+      // Jensen upper bound (rounded up), only when it can lower U
+      const float vB = sv[j];
+      if (dc2 + vA + vB < U * U) {
+        const float r = __fadd_ru(__fmul_ru(__fsqrt_ru(dc2), 1.f + rho), delta0);
+        const float ub = __fsqrt_ru(__fadd_ru(__fadd_ru(__fmul_ru(r, r), vA), vB));
+        if (ub < U) {
+          U = ub;
+          T2 = thr2(U);
+        }
+      }
+    }
+  }
+  if (!act) return;
+  if (!over) {
+    // final filter, then insertion sort by lower bound
+    const float tl = sqrtf(T2);
+    int k = 0;
+    for (int q = 0; q < cnt; ++q)
+      if (LB[q] <= tl) {
+        const int pq = L[q];
+        const float lq = LB[q];
+        int w = k++;
+        while (w > 0 && LB[w - 1] > lq) {
+          L[w] = L[w - 1];
+          LB[w] = LB[w - 1];
+          --w;
+        }
+        L[w] = pq;
+        LB[w] = lq;
+      }
+    cnt = k;
+  }
+  lcnt[mypos] = over ? -1 : cnt;
+  lub[mypos] = U;
+  atomicAdd(&a.ctr->ltests, scanned);
+}
+
 template <int LK>
 cudaError_t launch_brute_lk(const QueryArgs &a, int dp, cudaStream_t s) {
   const int blocks = (a.nterm + BR_T - 1) / BR_T;
@@ -245,6 +383,18 @@ cudaError_t launch_brute_lk(const QueryArgs &a, int dp, cudaStream_t s) {
 }
 
 }  // namespace
+
+cudaError_t launch_cand_avg(const QueryArgs &a, int32_t *lpos, float *llb, int32_t *lcnt,
+                            float *lub, int dp, cudaStream_t s) {
+  if (a.nterm <= 0) return cudaSuccess;
+  const int blocks = (a.nterm + BR_T - 1) / BR_T;
+  switch (dp) {
+    case 8: k_cand_avg<8><<<blocks, BR_T, 0, s>>>(a, lpos, llb, lcnt, lub); break;
+    case 16: k_cand_avg<16><<<blocks, BR_T, 0, s>>>(a, lpos, llb, lcnt, lub); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
 
 // The exhaustive search of every terminal (closed-form linkages, FP32 bulk
 // with FP64 re-score, one instance); pend_out must hold nterm entries and

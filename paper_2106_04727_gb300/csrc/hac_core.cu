@@ -1303,6 +1303,16 @@ bool use_brute(const hac_ctx *h) {
   return s.dp == 16;
 }
 
+// Candidate lists from the exhaustive scan instead of the tree for average
+// linkage in d > 8 (one instance); HAC_BRUTE=0 / 1 turns them off / on for any
+// row stride of 8 or 16.
+bool use_cand_avg(const hac_ctx *h) {
+  const State &s = h->s;
+  if (s.linkage != LK_AVERAGE || s.max_inst != 1 || s.noprune || s.dense) return false;
+  if (h->brute_env >= 0) return h->brute_env == 1 && (s.dp == 8 || s.dp == 16);
+  return s.dp == 16;
+}
+
 // One round of Algorithm 1 over the current terminal list: the searches (with
 // big pairs handed to the whole GPU and the deferring searches re-run), the
 // chain update, the R-NN filter, the merges, the cache update, the compaction
@@ -1326,6 +1336,20 @@ int round_step(hac_ctx *h, cudaStream_t st, int round, int K, int nterm, RoundCt
   if (brute) {
     CK(cudaMemsetAsync(&s.ctr->npend, 0, sizeof(int32_t), st));
     qa.pend_out = s.blist;
+  }
+  if (!dense && use_cand_avg(h)) {
+    if (!s.lpos) {  // sized once per handle: BL_CAP positions per cluster
+      if ((rc = dalloc(h, &s.lpos, (size_t)h->n * BL_CAP)) ||
+          (rc = dalloc(h, &s.llb, (size_t)h->n * BL_CAP)) || (rc = dalloc(h, &s.lcnt, h->n)) ||
+          (rc = dalloc(h, &s.lub, h->n)))
+        return rc;
+    }
+    CK(launch_cand_avg(qa, s.lpos, s.llb, s.lcnt, s.lub, s.dp, st));
+    h->launches += 1;
+    qa.lcap = BL_CAP;
+    qa.lpos = s.lpos;
+    qa.lcnt = s.lcnt;
+    qa.lub = s.lub;
   }
   EVREC(ctl.eq0);
   if (dense) {

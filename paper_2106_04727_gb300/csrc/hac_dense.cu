@@ -25,8 +25,9 @@
 //
 // Exact sums.  Every entry is kept as the sum of its point distances in
 // 128-bit fixed point (unit 2^e, chosen per instance so that (n/2)^2 times the
-// largest point distance stays below 2^126 units), next to the mean distance
-// that sum gives in FP64.  Integer addition is exact and associative, so:
+// largest point distance stays below 2^126 units; stored as four 32-bit limbs
+// in 64-bit words, so atomic additions need no carry), next to the mean
+// distance that sum gives in FP64.  Integer addition is exact and associative, so:
 //   * tiles can add into a cell with atomics in any order and the run is
 //     deterministic;
 //   * the Lance-Williams update of average linkage is the exact addition of
@@ -101,12 +102,57 @@ __device__ __forceinline__ void u128_add(U128 &a, const U128 &b) {
   a.lo = lo;
 }
 
-// atomic a += b on the two words at p (p[0] = lo, p[1] = hi)
-__device__ __forceinline__ void u128_atomic(unsigned long long *p, const U128 &b) {
+// A stored sum is four 64-bit words, each the sum of one 32-bit limb of
+// every addend (w0 + w1 2^32 + w2 2^64 + w3 2^96), so additions need no
+// carries and go out as fire-and-forget atomics; 2^32 additions per word
+// cannot overflow.  The estimate flag is the top bit of w3 (sums stay below
+// 2^126 units, so w3 < 2^30).
+constexpr int LIMBS = 4;
+
+__device__ __forceinline__ void limbs_atomic(unsigned long long *w, const U128 &b) {
   if (!(b.lo | b.hi)) return;
-  const unsigned long long old = atomicAdd(p, b.lo);
-  const unsigned long long carry = old + b.lo < old ? 1ull : 0ull;
-  if (b.hi + carry) atomicAdd(p + 1, b.hi + carry);
+  const unsigned long long l0 = b.lo & 0xffffffffull, l1 = b.lo >> 32;
+  const unsigned long long l2 = b.hi & 0xffffffffull, l3 = b.hi >> 32;
+  if (l0) atomicAdd(w, l0);
+  if (l1) atomicAdd(w + 1, l1);
+  if (l2) atomicAdd(w + 2, l2);
+  if (l3) atomicAdd(w + 3, l3);
+}
+
+// the 128-bit value of four limb words (flag bit dropped) and the flag
+__device__ __forceinline__ U128 limbs_value(const unsigned long long *w) {
+  const unsigned long long w0 = w[0], w1 = w[1], w2 = w[2], w3 = w[3] & ~TOP;
+  U128 r;
+  r.lo = w0 + (w1 << 32);
+  const unsigned long long c = r.lo < w0 ? 1ull : 0ull;
+  r.hi = (w1 >> 32) + w2 + (w3 << 32) + c;
+  return r;
+}
+
+// fixed-point value of a non-negative float (exact above 2^(e+23))
+__device__ __forceinline__ U128 fx_of_f(float v, int e) {
+  U128 r{0ull, 0ull};
+  if (!(v > 0.f)) return r;
+  const unsigned bits = __float_as_uint(v);
+  int E = (int)((bits >> 23) & 0xff);
+  unsigned long long m = bits & 0x7fffffu;
+  if (E == 0)
+    E = 1;
+  else
+    m |= 1ull << 23;
+  int sh = E - 150 - e;  // v = m * 2^(sh + e)
+  if (sh > 102) sh = 102;
+  if (sh >= 64) {
+    r.hi = m << (sh - 64);
+  } else if (sh > 0) {
+    r.lo = m << sh;
+    r.hi = sh > 40 ? m >> (64 - sh) : 0ull;
+  } else if (sh == 0) {
+    r.lo = m;
+  } else if (sh > -64) {
+    r.lo = m >> (-sh);
+  }
+  return r;
 }
 
 __device__ __forceinline__ U128 u128_shfl_down(const U128 &v, int o) {
@@ -124,11 +170,11 @@ __device__ __forceinline__ double fx_value(unsigned long long lo, unsigned long 
 
 // mean distance of an entry: its sum / (na nb), the sign bit set for an
 // estimate; one function everywhere, so equal sums give equal means
-__device__ __forceinline__ double entry_mean(unsigned long long lo, unsigned long long hi, int e,
-                                             int na, int nb) {
-  const double v = fx_value(lo, hi, e) / ((double)na * (double)nb);
-  const unsigned long long b = (unsigned long long)__double_as_longlong(v);
-  return __longlong_as_double((long long)((hi & TOP) ? (b | SIGN) : b));
+__device__ __forceinline__ double entry_mean(const unsigned long long *w, int e, int na, int nb) {
+  const U128 v = limbs_value(w);
+  const double m = fx_value(v.lo, v.hi, e) / ((double)na * (double)nb);
+  const unsigned long long b = (unsigned long long)__double_as_longlong(m);
+  return __longlong_as_double((long long)((w[3] & TOP) ? (b | SIGN) : b));
 }
 
 __device__ __forceinline__ bool is_est(double x) {
@@ -149,7 +195,7 @@ struct SweepArgs {
   const int32_t *didx;
   int64_t N;  // points in the layout
   int dk, e;
-  unsigned long long *sum;  // the sum matrix: cell (i < j) at [i][j] (two words)
+  unsigned long long *sum;  // the sum matrix: cell (i < j) at [i][j] (LIMBS words)
   long long nb;             // blocks of TI points along each axis
   Counters *ctr;
 };
@@ -218,14 +264,14 @@ __device__ __forceinline__ void flush(const SweepArgs &a, const U128 (&acc)[PPT]
     for (int r = 1; r < PPT; ++r) u128_add(v, acc[r]);
 #pragma unroll
     for (int o = 16; o; o >>= 1) u128_add(v, u128_shfl_xor(v, o));
-    if (lane == 0) u128_atomic(&a.sum[2 * ((size_t)krow[0] * a.dk + qj)], v);
+    if (lane == 0) limbs_atomic(&a.sum[LIMBS * ((size_t)krow[0] * a.dk + qj)], v);
     return;
   }
 #pragma unroll
   for (int r = 0; r < PPT; ++r) {
     const U128 z{0ull, 0ull};
     const U128 v = seg_sum(krow[r] < qj ? acc[r] : z, same[r]);
-    if (lead[r] && krow[r] < qj) u128_atomic(&a.sum[2 * ((size_t)krow[r] * a.dk + qj)], v);
+    if (lead[r] && krow[r] < qj) limbs_atomic(&a.sum[LIMBS * ((size_t)krow[r] * a.dk + qj)], v);
   }
 }
 
@@ -250,8 +296,8 @@ __device__ __forceinline__ bool row_keys(const SweepArgs &a, long long r0, int l
 
 // FP32 sweep: H coordinate pairs per point (f32x2 words, rows of stride DP
 // floats), PPT rows per thread; a tile is TI x TI points, TI = 256 * PPT.
-// Per row and column segment: FP32 partial sums of at most 32 terms, added
-// in FP64, then converted to fixed point once.
+// Per row and column segment: FP32 partial sums of at most 32 terms, each
+// converted to fixed point exactly and added as integers (no FP64 work).
 template <int H, int DP, int PPT>
 __global__ void __launch_bounds__(DS_TPB) k_dense_sweep32(SweepArgs a) {
   constexpr int TI = DS_TPB * PPT;
@@ -295,9 +341,9 @@ __global__ void __launch_bounds__(DS_TPB) k_dense_sweep32(SweepArgs a) {
       const int cb = sstart[sg], ce = sstart[sg + 1];
       const int qj = skey[cb];
       if (qj <= kfirst) continue;  // no row of this warp pairs with it (uniform)
-      double acc[PPT];
+      U128 acc[PPT];
 #pragma unroll
-      for (int r = 0; r < PPT; ++r) acc[r] = 0.0;
+      for (int r = 0; r < PPT; ++r) acc[r] = U128{0ull, 0ull};
       for (int c1 = cb; c1 < ce; c1 += 32) {
         const int c2 = min(c1 + 32, ce);
         float part[PPT];
@@ -320,15 +366,12 @@ __global__ void __launch_bounds__(DS_TPB) k_dense_sweep32(SweepArgs a) {
           }
         }
 #pragma unroll
-        for (int r = 0; r < PPT; ++r) acc[r] += (double)part[r];
+        for (int r = 0; r < PPT; ++r) u128_add(acc[r], fx_of_f(part[r], a.e));
       }
-      U128 fx[PPT];
 #pragma unroll
-      for (int r = 0; r < PPT; ++r) {
-        fx[r] = fx_of(acc[r], a.e);
+      for (int r = 0; r < PPT; ++r)
         pairs += (unsigned long long)__popc(__ballot_sync(0xffffffffu, krow[r] < qj)) * (ce - cb);
-      }
-      flush<PPT>(a, fx, krow, same, lead, uniform, qj, lane);
+      flush<PPT>(a, acc, krow, same, lead, uniform, qj, lane);
     }
   }
   if (lane == 0 && pairs) atomicAdd(&a.ctr->dense_pp, pairs);
@@ -405,7 +448,7 @@ __global__ void __launch_bounds__(DS_TPB) k_dense_sweep64(SweepArgs a) {
 // sum on the diagonal); estimates (FP32 mode) carry the flag.  Shared memory
 // keeps every global access a row segment.
 __global__ void k_dense_fin(State s, int dk, bool est) {
-  __shared__ unsigned long long Slo[32][33], Shi[32][33];
+  __shared__ unsigned long long W[LIMBS][32][33];
   __shared__ double Mv[32][33];
   const int nt = (dk + 31) / 32;
   long long ti, tj;
@@ -414,48 +457,42 @@ __global__ void k_dense_fin(State s, int dk, bool est) {
   const int tx = threadIdx.x, ty = threadIdx.y;  // 32 x 8
   for (int k = ty; k < 32; k += 8) {
     const long long i = ti * 32 + k, j = tj * 32 + tx;  // the upper tile
-    unsigned long long lo = 0, hi = 0;
+    unsigned long long w[LIMBS] = {0ull, 0ull, 0ull, 0ull};
     double v = 0.0;
     if (i < dk && j < dk) {
       if (i == j) {
         v = __longlong_as_double((long long)KINF_D);
       } else if (i < j) {
-        const size_t c = 2 * ((size_t)i * dk + j);
-        lo = s.dsum[c];
-        hi = s.dsum[c + 1] | (est ? TOP : 0ull);
-        v = entry_mean(lo, hi, s.dexp, s.qsz[i], s.qsz[j]);
+        const unsigned long long *c = s.dsum + LIMBS * ((size_t)i * dk + j);
+#pragma unroll
+        for (int l = 0; l < LIMBS; ++l) w[l] = c[l];
+        if (est) w[3] |= TOP;
+        v = entry_mean(w, s.dexp, s.qsz[i], s.qsz[j]);
       }
     }
-    Slo[k][tx] = lo;
-    Shi[k][tx] = hi;
+#pragma unroll
+    for (int l = 0; l < LIMBS; ++l) W[l][k][tx] = w[l];
     Mv[k][tx] = v;
   }
   __syncthreads();
-  if (ti == tj) {
-    // diagonal tile: the lower cells take the upper cells' values
-    for (int k = ty; k < 32; k += 8) {
-      const long long i = ti * 32 + k, j = tj * 32 + tx;
-      if (i >= dk || j >= dk) continue;
-      const bool up = i <= j;
-      const size_t c = 2 * ((size_t)i * dk + j);
-      s.dsum[c] = up ? Slo[k][tx] : Slo[tx][k];
-      s.dsum[c + 1] = up ? Shi[k][tx] : Shi[tx][k];
-      s.dmat[(size_t)i * dk + j] = up ? Mv[k][tx] : Mv[tx][k];
-    }
-    return;
-  }
   for (int k = ty; k < 32; k += 8) {
     const long long i = ti * 32 + k, j = tj * 32 + tx;
     if (i < dk && j < dk) {
-      s.dsum[2 * ((size_t)i * dk + j) + 1] = Shi[k][tx];
-      s.dmat[(size_t)i * dk + j] = Mv[k][tx];
+      // diagonal tile: the lower cells take the upper cells' values
+      const bool mir = ti == tj && i > j;
+      unsigned long long *c = s.dsum + LIMBS * ((size_t)i * dk + j);
+#pragma unroll
+      for (int l = 0; l < LIMBS; ++l) c[l] = mir ? W[l][tx][k] : W[l][k][tx];
+      s.dmat[(size_t)i * dk + j] = mir ? Mv[tx][k] : Mv[k][tx];
     }
-    const long long i2 = tj * 32 + k, j2 = ti * 32 + tx;  // mirror: upper cell (tx, k)
-    if (i2 < dk && j2 < dk) {
-      const size_t c = 2 * ((size_t)i2 * dk + j2);
-      s.dsum[c] = Slo[tx][k];
-      s.dsum[c + 1] = Shi[tx][k];
-      s.dmat[(size_t)i2 * dk + j2] = Mv[tx][k];
+    if (ti != tj) {  // mirror tile: row tj*32+k, column ti*32+tx = upper cell (tx, k)
+      const long long i2 = tj * 32 + k, j2 = ti * 32 + tx;
+      if (i2 < dk && j2 < dk) {
+        unsigned long long *c = s.dsum + LIMBS * ((size_t)i2 * dk + j2);
+#pragma unroll
+        for (int l = 0; l < LIMBS; ++l) c[l] = W[l][tx][k];
+        s.dmat[(size_t)i2 * dk + j2] = Mv[tx][k];
+      }
     }
   }
 }
@@ -729,7 +766,7 @@ __global__ void __launch_bounds__(RQ_TPB) k_drq_eval(State s, int m, int cur) {
     if (threadIdx.x == 0) {
       U128 v{0ull, 0ull};
       for (int w = 0; w < RQ_TPB / 32; ++w) u128_add(v, U128{rlo[w], rhi[w]});
-      u128_atomic(&s.drq_acc[2 * (size_t)i], v);
+      limbs_atomic(&s.drq_acc[LIMBS * (size_t)i], v);
       const long long rows = min(RQ_TPB, na - ta * RQ_TPB);
       atomicAdd(&s.ctr->dense_rq_pp, (unsigned long long)(rows * (cend - cbeg)));
     }
@@ -741,13 +778,14 @@ __global__ void k_drq_fin(State s, int m) {
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gridDim.x * blockDim.x) {
     const int qa = s.drq_a[i], qb = s.drq_b[i];
     const int A = s.dcid[qa], B = s.dcid[qb];
-    const unsigned long long lo = s.drq_acc[2 * (size_t)i], hi = s.drq_acc[2 * (size_t)i + 1];
-    const double v = entry_mean(lo, hi, s.dexp, s.csize[A], s.csize[B]);
+    const unsigned long long *w = s.drq_acc + LIMBS * (size_t)i;
+    const double v = entry_mean(w, s.dexp, s.csize[A], s.csize[B]);
     const size_t c1 = (size_t)qa * s.dk + qb, c2 = (size_t)qb * s.dk + qa;
-    s.dsum[2 * c1] = lo;
-    s.dsum[2 * c1 + 1] = hi;
-    s.dsum[2 * c2] = lo;
-    s.dsum[2 * c2 + 1] = hi;
+#pragma unroll
+    for (int l = 0; l < LIMBS; ++l) {
+      s.dsum[LIMBS * c1 + l] = w[l];
+      s.dsum[LIMBS * c2 + l] = w[l];
+    }
     s.dmat[c1] = v;
     s.dmat[c2] = v;
   }
@@ -758,20 +796,29 @@ __global__ void k_drq_fin(State s, int m) {
 // linkage the sum of A u B with C is the sum of A's and B's (exact), the mean
 // follows from the new sizes
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ U128 sum_at(const State &s, size_t cell) {
-  return U128{s.dsum[2 * cell], s.dsum[2 * cell + 1]};
-}
+struct Limbs {
+  unsigned long long w[LIMBS];
+};
 
-__device__ __forceinline__ U128 sum_add(const U128 &x, const U128 &y) {
-  U128 r{x.lo, x.hi & ~TOP};
-  u128_add(r, U128{y.lo, y.hi & ~TOP});
-  r.hi |= (x.hi | y.hi) & TOP;
+__device__ __forceinline__ Limbs sum_at(const State &s, size_t cell) {
+  Limbs r;
+#pragma unroll
+  for (int l = 0; l < LIMBS; ++l) r.w[l] = s.dsum[LIMBS * cell + l];
   return r;
 }
 
-__device__ __forceinline__ void sum_put(const State &s, size_t cell, const U128 &v) {
-  s.dsum[2 * cell] = v.lo;
-  s.dsum[2 * cell + 1] = v.hi;
+// limb-wise sum (the flags OR)
+__device__ __forceinline__ Limbs sum_add(const Limbs &x, const Limbs &y) {
+  Limbs r;
+#pragma unroll
+  for (int l = 0; l < LIMBS - 1; ++l) r.w[l] = x.w[l] + y.w[l];
+  r.w[3] = ((x.w[3] & ~TOP) + (y.w[3] & ~TOP)) | ((x.w[3] | y.w[3]) & TOP);
+  return r;
+}
+
+__device__ __forceinline__ void sum_put(const State &s, size_t cell, const Limbs &v) {
+#pragma unroll
+  for (int l = 0; l < LIMBS; ++l) s.dsum[LIMBS * cell + l] = v.w[l];
 }
 
 // 1. rows: the survivor's row adds its partner's, over every cluster active
@@ -787,9 +834,9 @@ __global__ void k_dense_row(State s, const int32_t *order_old, int Kold, int npa
       const int q = s.didx[c];
       if (q == qa || q == qb) continue;
       const size_t cell = (size_t)qa * dk + q;
-      const U128 v = sum_add(sum_at(s, cell), sum_at(s, (size_t)qb * dk + q));
+      const Limbs v = sum_add(sum_at(s, cell), sum_at(s, (size_t)qb * dk + q));
       sum_put(s, cell, v);
-      if (s.mround[c] != round) s.dmat[cell] = entry_mean(v.lo, v.hi, s.dexp, nab, s.csize[c]);
+      if (s.mround[c] != round) s.dmat[cell] = entry_mean(v.w, s.dexp, nab, s.csize[c]);
     }
   }
 }
@@ -808,8 +855,8 @@ __global__ void k_dense_fix(State s, int npairs) {
     const int c = s.pair_lo[p2], d = s.pair_hi[p2];
     const int qa = s.didx[a], qc = s.didx[c], qd = s.didx[d];
     if (qa > qc) continue;
-    const U128 v = sum_add(sum_at(s, (size_t)qa * dk + qc), sum_at(s, (size_t)qa * dk + qd));
-    const double m = entry_mean(v.lo, v.hi, s.dexp, s.csize[a], s.csize[c]);
+    const Limbs v = sum_add(sum_at(s, (size_t)qa * dk + qc), sum_at(s, (size_t)qa * dk + qd));
+    const double m = entry_mean(v.w, s.dexp, s.csize[a], s.csize[c]);
     sum_put(s, (size_t)qa * dk + qc, v);
     sum_put(s, (size_t)qc * dk + qa, v);
     s.dmat[(size_t)qa * dk + qc] = m;
@@ -848,7 +895,9 @@ void launch_2d_tiles(F kernel, long long tiles, int threads_x, cudaStream_t st,
 int sweep(hac_ctx *h, cudaStream_t st, const SweepArgs &a) {
   const State &s = h->s;
   const bool f32 = s.prec == HAC_PREC_F32_RECHECK;
-  const int ppt = f32 ? 4 : 2;
+  // rows per thread: 4 (2 for 16-wide FP32 rows and for FP64), for 2-3
+  // resident tiles per SM
+  const int ppt = f32 && s.dp <= 8 ? 4 : 2;
   const long long TI = (long long)DS_TPB * ppt;
   SweepArgs b = a;
   b.nb = (a.N + TI - 1) / TI;
@@ -866,13 +915,13 @@ int sweep(hac_ctx *h, cudaStream_t st, const SweepArgs &a) {
         break;
       default:
         if (H <= 5)
-          launch_2d_tiles(k_dense_sweep32<5, 16, 4>, tiles, DS_TPB, st, b);
+          launch_2d_tiles(k_dense_sweep32<5, 16, 2>, tiles, DS_TPB, st, b);
         else if (H == 6)
-          launch_2d_tiles(k_dense_sweep32<6, 16, 4>, tiles, DS_TPB, st, b);
+          launch_2d_tiles(k_dense_sweep32<6, 16, 2>, tiles, DS_TPB, st, b);
         else if (H == 7)
-          launch_2d_tiles(k_dense_sweep32<7, 16, 4>, tiles, DS_TPB, st, b);
+          launch_2d_tiles(k_dense_sweep32<7, 16, 2>, tiles, DS_TPB, st, b);
         else
-          launch_2d_tiles(k_dense_sweep32<8, 16, 4>, tiles, DS_TPB, st, b);
+          launch_2d_tiles(k_dense_sweep32<8, 16, 2>, tiles, DS_TPB, st, b);
     }
   } else {
     switch (s.dp) {
@@ -895,7 +944,7 @@ int64_t dense_threshold(const hac_ctx *h) {
 int recheck(hac_ctx *h, cudaStream_t st, int m) {
   State &s = h->s;
   if (m <= 0) return HAC_OK;
-  CK(cudaMemsetAsync(s.drq_acc, 0, (size_t)m * 2 * sizeof(unsigned long long), st));
+  CK(cudaMemsetAsync(s.drq_acc, 0, (size_t)m * LIMBS * sizeof(unsigned long long), st));
   k_drq_count<<<grid_for(m, TPB), TPB, 0, st>>>(s, m);
   k_drq_scan<<<1, 1024, 0, st>>>(s, m);
   const int g = device_sms() * 4;
@@ -926,14 +975,14 @@ int dense_maybe_enter(hac_ctx *h, cudaStream_t st, int K, RoundCtl &ctl) {
     if ((rc = dalloc(h, &s.didx, h->n)) || (rc = dalloc(h, &s.dcid, cap)) ||
         (rc = dalloc(h, &s.drq_a, rqcap)) || (rc = dalloc(h, &s.drq_b, rqcap)) ||
         (rc = dalloc(h, &s.drq_pre, rqcap + 1)) ||
-        (rc = dalloc(h, &s.drq_acc, 2 * (size_t)rqcap)) || (rc = dalloc(h, &s.dpend[0], cap)) ||
+        (rc = dalloc(h, &s.drq_acc, LIMBS * (size_t)rqcap)) || (rc = dalloc(h, &s.dpend[0], cap)) ||
         (rc = dalloc(h, &s.dpend[1], cap)))
       return rc;
     s.drq_cap = rqcap;
     // the matrices last: without room for them the instance stays on the
     // range-query search (same result)
     if (dalloc(h, &s.dmat, (size_t)cap * cap) != HAC_OK ||
-        dalloc(h, &s.dsum, 2 * (size_t)cap * cap) != HAC_OK) {
+        dalloc(h, &s.dsum, LIMBS * (size_t)cap * cap) != HAC_OK) {
       h->dense_k = 0;
       return 0;
     }
@@ -945,7 +994,7 @@ int dense_maybe_enter(hac_ctx *h, cudaStream_t st, int K, RoundCtl &ctl) {
   const double smax = 0.25 * (double)h->lay_n * (double)h->lay_n * dmax;
   s.dexp = smax > 0.0 ? (int)std::floor(std::log2(smax)) + 1 - 126 : -1000;
   k_dense_init<<<grid_for(K, TPB), TPB, 0, st>>>(s, s.order[h->ocur], K);
-  CK(cudaMemsetAsync(s.dsum, 0, (size_t)K * K * 2 * sizeof(unsigned long long), st));
+  CK(cudaMemsetAsync(s.dsum, 0, (size_t)K * K * LIMBS * sizeof(unsigned long long), st));
   SweepArgs a{};
   a.p32 = s.p32[h->pcur];
   a.p64 = s.p64[h->pcur];

@@ -148,6 +148,9 @@ struct State {
   int32_t *order[2];    // active cids in spatial order
   int32_t *term;        // terminal cids
   int32_t *blist;       // terminals left to the FP64 re-score of the exhaustive search
+  // candidate lists of the exhaustive scan for average linkage (by position)
+  int32_t *lpos, *lcnt;
+  float *llb, *lub;
   int32_t *pair_lo, *pair_hi;
   double *pair_key;
   // dendrogram records
@@ -171,7 +174,8 @@ struct State {
   int dexp;             // exponent of the fixed-point unit of the sweep sums
   double *dmat;         // dk x dk, row-major; diagonal +inf
   unsigned long long *dsum;  // dk x dk 128-bit fixed-point sums of point distances
-                             // (two words per entry; the top bit marks an estimate)
+                             // (four limb words per entry; the top bit of the last
+                             // marks an estimate)
   int32_t *didx;        // cid -> matrix index (the cid's position at the switch)
   int32_t *dcid;        // matrix index -> cid
   int drq_cap;          // FP64 re-score queue (pairs, lower index first)
@@ -233,6 +237,11 @@ struct QueryArgs {
   int32_t *breq_cov;
   float *breq_berr;
   int32_t *pend_out;
+  // candidate lists of the exhaustive scan (average linkage, high dimension),
+  // indexed by the terminal's position: lcnt < 0 (or lcnt null) = use the tree
+  int lcap;
+  const int32_t *lpos, *lcnt;
+  const float *lub;
 };
 
 // pairs of at least this many point pairs are evaluated by the whole GPU
@@ -278,5 +287,12 @@ cudaError_t launch_query(const QueryArgs &a, int dp, int prec, cudaStream_t s);
 // shared memory (hac_brute.cu): closed-form linkages, FP32 + FP64 re-score,
 // one instance; uses pend_out (nterm entries) and ctr->npend (zeroed first)
 cudaError_t launch_brute(const QueryArgs &a, int dp, cudaStream_t s);
+// candidate lists for average linkage: every terminal scans every active
+// cluster's record (tiles in shared memory) and lists, by position, those
+// whose centroid lower bound is within its least Jensen upper bound
+// (at most lcap; lcnt = -1 if more, and the terminal searches the tree)
+constexpr int BL_CAP = 64;
+cudaError_t launch_cand_avg(const QueryArgs &a, int32_t *lpos, float *llb, int32_t *lcnt,
+                            float *lub, int dp, cudaStream_t s);
 
 }  // namespace hacg

@@ -618,9 +618,11 @@ struct Searcher {
     return kbits(ward_key<DP>(cA, cB, na, nb));
   }
 
-  __device__ void leaf(int j, bool seed) {
-    const int idx = j * FAN + lane;
-    const bool in = idx < a.K;
+  __device__ void leaf(int j, bool seed) { leaf_at(j * FAN + lane, j * FAN + lane < a.K, seed); }
+
+  // the candidate at position idx of this lane (in: the lane has one); the
+  // 32 lanes' candidates are tested, scored and offered together
+  __device__ void leaf_at(int idx, bool in, bool seed) {
     const int cb = in ? a.order[idx] : -1;
     const bool valid = in && cb != ci && a.qinst[idx] == myseq;
     const int nb = valid ? a.qsz[idx] : 1;
@@ -1027,6 +1029,21 @@ __device__ void traverse(const QueryArgs &a, Searcher<LK, DP, MODE> &S, uint32_t
   }
 }
 
+// The same search over an explicit candidate list (positions, by increasing
+// lower bound) written by the exhaustive candidate scan of hac_brute.cu: every
+// cluster whose centroid lower bound is within the least summary upper bound
+// of the terminal (that bound is offered first).
+template <int LK, int DP, int MODE>
+__device__ void traverse_list(const QueryArgs &a, Searcher<LK, DP, MODE> &S, int p, int cnt,
+                              int lane) {
+  S.offer_ub(lane == 0 ? a.lub[p] : INFINITY);
+  const int32_t *L = a.lpos + (size_t)p * a.lcap;
+  for (int b = 0; b < cnt; b += 32) {
+    const int i = b + lane;
+    S.leaf_at(i < cnt ? L[i] : 0, i < cnt, false);
+  }
+}
+
 template <int LK, int DP, int MODE>
 __device__ void tally(const Searcher<LK, DP, MODE> &S, unsigned long long *c) {
   c[0] += S.cpairs;  // warp-uniform counts
@@ -1051,19 +1068,27 @@ __global__ void __launch_bounds__(QWARPS * 32) k_query(QueryArgs a) {
   for (int t = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; t < a.nterm; t += nw) {
     const int ci = a.term[t];
     const int own = a.pos[ci] / FAN;
+    // a candidate list from the exhaustive scan replaces the tree traversal
+    const int lc = a.lcnt ? a.lcnt[a.pos[ci]] : -1;
     unsigned long long bk;
     int bc;
     bool deferred = false;
     if (PREC == 0) {
       Searcher<LK, DP, M_F64> S(a, lane, ci, INFINITY);
-      traverse(a, S, sn, sl, own, lane);
+      if (lc >= 0)
+        traverse_list(a, S, a.pos[ci], lc, lane);
+      else
+        traverse(a, S, sn, sl, own, lane);
       bk = S.bk;
       bc = S.bc;
       deferred = S.deferred;
       tally(S, c);
     } else {
       Searcher<LK, DP, M_F32> S(a, lane, ci, INFINITY);
-      traverse(a, S, sn, sl, own, lane);
+      if (lc >= 0)
+        traverse_list(a, S, a.pos[ci], lc, lane);
+      else
+        traverse(a, S, sn, sl, own, lane);
       if (S.deferred) {
         // incomplete: some candidates still wait for their values
         deferred = true;
@@ -1080,7 +1105,10 @@ __global__ void __launch_bounds__(QWARPS * 32) k_query(QueryArgs a) {
       } else {
         tally(S, c);
         Searcher<LK, DP, M_RECHECK> R(a, lane, ci, S.U);
-        traverse(a, R, sn, sl, own, lane);
+        if (lc >= 0)
+          traverse_list(a, R, a.pos[ci], lc, lane);
+        else
+          traverse(a, R, sn, sl, own, lane);
         bk = R.bk;
         bc = R.bc;
         deferred = R.deferred;

@@ -111,3 +111,20 @@ def test_dense_deterministic(prec, monkeypatch):
         assert np.array_equal(a[k], b[k])
     assert np.array_equal(a["h"].view(np.int64), b["h"].view(np.int64))
     assert a["stats"]["dense_k"] > 0
+
+
+@pytest.mark.parametrize("prec", PRECS, ids=PREC_IDS)
+@pytest.mark.parametrize("shape", [(4000, 16), (3000, 10), (2500, 8)], ids=lambda s: f"n{s[0]}d{s[1]}")
+def test_candidate_lists_match(shape, prec, monkeypatch):
+    """Average linkage with the exhaustive candidate scan in place of the tree
+    (the default for d > 8, forced here for d = 8 too) and no dense matrix:
+    the oracle's tree, round for round; every search scanned every cluster
+    (a terminal whose list overflows searches the tree as well)."""
+    monkeypatch.setenv("HAC_DENSE_K", "0")
+    monkeypatch.setenv("HAC_BRUTE", "1")
+    n, d = shape
+    X = inputs.gaussian_mixture(n, d, 7, seed=n + d)
+    got = hac.cluster(X, "average", precision=prec, cache_slots=32)
+    _same(got, oracle.rounds(X.astype(np.float64), "average"), _rtol(prec))
+    st = got["stats"]
+    assert st["leaf_tests"] >= st["naive_pairs"]
