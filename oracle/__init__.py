@@ -28,8 +28,11 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "hac_oracle.c")
 _BUILD = os.path.join(_HERE, "_build")
 _SO = os.path.join(_BUILD, "liboracle.so")
+_PC_SRC = os.path.join(_HERE, "hac_parchain_cpu.c")
+_PC_SO = os.path.join(_BUILD, "libparchain_cpu.so")
 _lock = threading.Lock()
 _lib = None
+_pclib = None
 
 
 def build(force: bool = False) -> str:
@@ -41,6 +44,49 @@ def build(force: bool = False) -> str:
                                "-shared", "-fPIC", "-o", tmp, _SRC, "-lm"])
         os.replace(tmp, _SO)
     return _SO
+
+
+def build_parchain_cpu(force: bool = False) -> str:
+    """Compile the multithreaded CPU NN-chain (gcc, pthreads, plain FP64)."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if force or not os.path.exists(_PC_SO) or os.path.getmtime(_PC_SO) < os.path.getmtime(_PC_SRC):
+        tmp = _PC_SO + f".{os.getpid()}.tmp"
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math",
+                               "-shared", "-fPIC", "-pthread", "-o", tmp, _PC_SRC, "-lm"])
+        os.replace(tmp, _PC_SO)
+    return _PC_SO
+
+
+def parchain_cpu(X, linkage, threads: int = 0, timeout_s: float = 0.0) -> dict:
+    """Algorithm 1 on the host cores (hac_parchain_cpu.c): FP64, linear memory,
+    kd-tree range queries.  threads = 0: every core.  Returns the oracle's
+    dict layout (a, b, h, size, round) in merge order, plus n_rounds,
+    point_pairs, seconds, threads and complete (False when timeout_s stopped
+    it between rounds; then only the merges made are returned)."""
+    global _pclib
+    X = _pts(X)
+    n, d = X.shape
+    with _lock:
+        if _pclib is None:
+            lib = ctypes.CDLL(build_parchain_cpu())
+            P = ctypes.c_void_p
+            lib.parchain_cpu.argtypes = [P, ctypes.c_int64, ctypes.c_int, ctypes.c_int,
+                                         ctypes.c_int, ctypes.c_double, P, P, P, P, P, P]
+            lib.parchain_cpu.restype = ctypes.c_int64
+            _pclib = lib
+    if threads <= 0:
+        threads = os.cpu_count() or 1
+    m = max(n - 1, 0)
+    a, b, h, s = _outs(m)
+    r = np.zeros(m, np.int64)
+    st = np.zeros(3, np.float64)
+    got = _pclib.parchain_cpu(_p(X), n, d, _lk(linkage), threads, float(timeout_s), _p(a), _p(b),
+                              _p(h), _p(s), _p(r), _p(st))
+    if got < 0:
+        raise ValueError(f"parchain_cpu failed ({got})")
+    return dict(a=a[:got], b=b[:got], h=h[:got], size=s[:got], round=r[:got],
+                n_rounds=int(st[0]), point_pairs=int(st[1]), seconds=float(st[2]),
+                threads=threads, complete=bool(got == m))
 
 
 def _load():

@@ -187,7 +187,14 @@ __device__ __forceinline__ double mag(double x) { return fabs(x); }
 // ---------------------------------------------------------------------------
 constexpr int DS_TPB = 256;  // threads per tile
 constexpr int DS_CH = 256;   // columns per staged chunk
-
+// FP32 sweep shape: rows per thread for d <= 8 (2 above), and the resident
+// tiles per SM the register budget is cut for (measured best: 4 and 3)
+#ifndef HAC_DS_PPT8
+#define HAC_DS_PPT8 4
+#endif
+#ifndef HAC_DS_MINB
+#define HAC_DS_MINB 3
+#endif
 struct SweepArgs {
   const float *p32;
   const double *p64;
@@ -294,14 +301,17 @@ __device__ __forceinline__ bool row_keys(const SweepArgs &a, long long r0, int l
   return kfirst == klast;
 }
 
-// FP32 sweep: H coordinate pairs per point (f32x2 words, rows of stride DP
+// FP32 sweep, specialised on the true dimension D (rows of stride DP
 // floats), PPT rows per thread; a tile is TI x TI points, TI = 256 * PPT.
-// Per row and column segment: FP32 partial sums of at most 32 terms, each
+// Two of a thread's rows share each f32x2 word (one coordinate of each) and
+// every staged column is duplicated into both halves, so one packed subtract
+// and one packed multiply-add advance two point pairs by one coordinate.  Per
+// row and column segment: FP32 partial sums of at most 32 terms, each
 // converted to fixed point exactly and added as integers (no FP64 work).
-template <int H, int DP, int PPT>
-__global__ void __launch_bounds__(DS_TPB) k_dense_sweep32(SweepArgs a) {
-  constexpr int TI = DS_TPB * PPT;
-  __shared__ unsigned long long sy[DS_CH * H];
+template <int D, int DP, int PPT>
+__global__ void __launch_bounds__(DS_TPB, HAC_DS_MINB) k_dense_sweep32(SweepArgs a) {
+  constexpr int TI = DS_TPB * PPT, NP = PPT / 2;
+  __shared__ unsigned long long sy[DS_CH * D];
   __shared__ int skey[DS_CH];
   __shared__ int sstart[DS_CH + 1];
   __shared__ int wtot[DS_TPB / 32];
@@ -310,18 +320,19 @@ __global__ void __launch_bounds__(DS_TPB) k_dense_sweep32(SweepArgs a) {
   if (bi >= a.nb || bj >= a.nb) return;  // uniform over the block
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const long long r0 = bi * TI + (long long)w * 32 * PPT;
-  unsigned long long x[PPT][H];
+  unsigned long long x[NP][D];
   int krow[PPT];
   unsigned same[PPT];
   bool lead[PPT];
   int kfirst;
   const bool uniform = row_keys<PPT>(a, r0, lane, krow, same, lead, kfirst);
 #pragma unroll
-  for (int r = 0; r < PPT; ++r) {
-    const long long row = r0 + r * 32 + lane;
-    const unsigned long long *xr = (const unsigned long long *)(a.p32 + (size_t)row * DP);
+  for (int h = 0; h < NP; ++h) {
+    const long long ra = r0 + (2 * h) * 32 + lane, rb = ra + 32;
 #pragma unroll
-    for (int h = 0; h < H; ++h) x[r][h] = row < a.N ? xr[h] : 0ull;
+    for (int k = 0; k < D; ++k)
+      x[h][k] = f2_pack(ra < a.N ? a.p32[(size_t)ra * DP + k] : 0.f,
+                        rb < a.N ? a.p32[(size_t)rb * DP + k] : 0.f);
   }
   unsigned long long pairs = 0;
   for (int ch = 0; ch < PPT; ++ch) {  // TI columns in chunks of DS_CH
@@ -329,9 +340,10 @@ __global__ void __launch_bounds__(DS_TPB) k_dense_sweep32(SweepArgs a) {
     if (c0 >= a.N) break;  // uniform
     const int cnt = (int)min((long long)DS_CH, a.N - c0);
     __syncthreads();
-    for (int i = threadIdx.x; i < cnt * H; i += DS_TPB) {
-      const int c = i / H, h = i - c * H;
-      sy[i] = ((const unsigned long long *)(a.p32 + (size_t)(c0 + c) * DP))[h];
+    for (int i = threadIdx.x; i < cnt * D; i += DS_TPB) {
+      const int c = i / D, k = i - c * D;
+      const float y = a.p32[(size_t)(c0 + c) * DP + k];
+      sy[i] = f2_pack(y, y);
     }
     if (threadIdx.x < DS_CH)
       skey[threadIdx.x] = threadIdx.x < cnt ? a.didx[a.plab[c0 + threadIdx.x]] : -1;
@@ -350,19 +362,22 @@ __global__ void __launch_bounds__(DS_TPB) k_dense_sweep32(SweepArgs a) {
 #pragma unroll
         for (int r = 0; r < PPT; ++r) part[r] = 0.f;
         for (int c = c1; c < c2; ++c) {
-          unsigned long long y[H];
+          unsigned long long y[D];
 #pragma unroll
-          for (int h = 0; h < H; ++h) y[h] = sy[c * H + h];
+          for (int k = 0; k < D; ++k) y[k] = sy[c * D + k];
 #pragma unroll
-          for (int r = 0; r < PPT; ++r) {
-            unsigned long long t = f2_sub(x[r][0], y[0]);
+          for (int h = 0; h < NP; ++h) {
+            unsigned long long t = f2_sub(x[h][0], y[0]);
             unsigned long long d2 = f2_mul(t, t);
 #pragma unroll
-            for (int h = 1; h < H; ++h) {
-              t = f2_sub(x[r][h], y[h]);
+            for (int k = 1; k < D; ++k) {
+              t = f2_sub(x[h][k], y[k]);
               d2 = f2_fma(t, t, d2);
             }
-            part[r] += sqrt_approx(f2_hsum(d2));
+            float s0, s1;
+            f2_unpack(d2, s0, s1);
+            part[2 * h] += sqrt_approx(s0);
+            part[2 * h + 1] += sqrt_approx(s1);
           }
         }
 #pragma unroll
@@ -897,31 +912,30 @@ int sweep(hac_ctx *h, cudaStream_t st, const SweepArgs &a) {
   const bool f32 = s.prec == HAC_PREC_F32_RECHECK;
   // rows per thread: 4 (2 for 16-wide FP32 rows and for FP64), for 2-3
   // resident tiles per SM
-  const int ppt = f32 && s.dp <= 8 ? 4 : 2;
+  const int ppt = f32 && s.dp <= 8 ? HAC_DS_PPT8 : 2;
   const long long TI = (long long)DS_TPB * ppt;
   SweepArgs b = a;
   b.nb = (a.N + TI - 1) / TI;
   const long long tiles = b.nb * (b.nb + 1) / 2;
   if (f32) {
-    const int H = (s.d + 1) >> 1;
-    switch (s.dp) {
-      case 2: launch_2d_tiles(k_dense_sweep32<1, 2, 4>, tiles, DS_TPB, st, b); break;
-      case 4: launch_2d_tiles(k_dense_sweep32<2, 4, 4>, tiles, DS_TPB, st, b); break;
-      case 8:
-        if (H <= 3)
-          launch_2d_tiles(k_dense_sweep32<3, 8, 4>, tiles, DS_TPB, st, b);
-        else
-          launch_2d_tiles(k_dense_sweep32<4, 8, 4>, tiles, DS_TPB, st, b);
-        break;
-      default:
-        if (H <= 5)
-          launch_2d_tiles(k_dense_sweep32<5, 16, 2>, tiles, DS_TPB, st, b);
-        else if (H == 6)
-          launch_2d_tiles(k_dense_sweep32<6, 16, 2>, tiles, DS_TPB, st, b);
-        else if (H == 7)
-          launch_2d_tiles(k_dense_sweep32<7, 16, 2>, tiles, DS_TPB, st, b);
-        else
-          launch_2d_tiles(k_dense_sweep32<8, 16, 2>, tiles, DS_TPB, st, b);
+    constexpr int P8 = HAC_DS_PPT8;
+    switch (s.d) {  // specialised on the true dimension
+      case 1: launch_2d_tiles(k_dense_sweep32<1, 2, P8>, tiles, DS_TPB, st, b); break;
+      case 2: launch_2d_tiles(k_dense_sweep32<2, 2, P8>, tiles, DS_TPB, st, b); break;
+      case 3: launch_2d_tiles(k_dense_sweep32<3, 4, P8>, tiles, DS_TPB, st, b); break;
+      case 4: launch_2d_tiles(k_dense_sweep32<4, 4, P8>, tiles, DS_TPB, st, b); break;
+      case 5: launch_2d_tiles(k_dense_sweep32<5, 8, P8>, tiles, DS_TPB, st, b); break;
+      case 6: launch_2d_tiles(k_dense_sweep32<6, 8, P8>, tiles, DS_TPB, st, b); break;
+      case 7: launch_2d_tiles(k_dense_sweep32<7, 8, P8>, tiles, DS_TPB, st, b); break;
+      case 8: launch_2d_tiles(k_dense_sweep32<8, 8, P8>, tiles, DS_TPB, st, b); break;
+      case 9: launch_2d_tiles(k_dense_sweep32<9, 16, 2>, tiles, DS_TPB, st, b); break;
+      case 10: launch_2d_tiles(k_dense_sweep32<10, 16, 2>, tiles, DS_TPB, st, b); break;
+      case 11: launch_2d_tiles(k_dense_sweep32<11, 16, 2>, tiles, DS_TPB, st, b); break;
+      case 12: launch_2d_tiles(k_dense_sweep32<12, 16, 2>, tiles, DS_TPB, st, b); break;
+      case 13: launch_2d_tiles(k_dense_sweep32<13, 16, 2>, tiles, DS_TPB, st, b); break;
+      case 14: launch_2d_tiles(k_dense_sweep32<14, 16, 2>, tiles, DS_TPB, st, b); break;
+      case 15: launch_2d_tiles(k_dense_sweep32<15, 16, 2>, tiles, DS_TPB, st, b); break;
+      default: launch_2d_tiles(k_dense_sweep32<16, 16, 2>, tiles, DS_TPB, st, b);
     }
   } else {
     switch (s.dp) {

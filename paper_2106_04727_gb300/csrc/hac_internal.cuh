@@ -291,7 +291,7 @@ cudaError_t launch_brute(const QueryArgs &a, int dp, cudaStream_t s);
 // cluster's record (tiles in shared memory) and lists, by position, those
 // whose centroid lower bound is within its least Jensen upper bound
 // (at most lcap; lcnt = -1 if more, and the terminal searches the tree)
-constexpr int BL_CAP = 64;
+constexpr int BL_CAP = 256;
 cudaError_t launch_cand_avg(const QueryArgs &a, int32_t *lpos, float *llb, int32_t *lcnt,
                             float *lub, int dp, cudaStream_t s);
 
