@@ -407,21 +407,28 @@ def test_full_size_10m_spreaders(lk):
         _check_rnn(got, X, lk, 6, side_cap=32)
 
 
-@pytest.mark.parametrize("lk", ["ward", "average_sq"])
+@pytest.mark.parametrize("lk", ["ward", "average", "average_sq"])
 def test_full_size_16d_lattice(lk):
     """The 10^6-point 16-D lattice (exact ties everywhere) with the FP32 bulk
-    and the exhaustive search: a valid tree and sampled heights equal to the
-    oracle's value of the merged point sets.  (Average linkage on Euclidean
-    distances does not finish at this size: its centroid bound prunes almost
-    nothing in 16-D.)"""
+    and the exhaustive scans of d > 8 (average linkage: candidate lists, then
+    the dense matrix; 128 cache slots): a valid tree, sampled heights equal
+    to the oracle's value of the merged point sets, sampled merges of
+    reciprocal nearest neighbours, and for Ward and average the all-FP64
+    GPU tree merge for merge and round for round (runs stop at 10 minutes
+    rather than hold the GPU)."""
     X = _workload("lattice16d_1m_f32")
-    got = hac.cluster(X, lk, precision=hac.PREC_F32_RECHECK)
-    assert dendro.check(got, len(X), rtol=1e-12) == []
-    _check_sampled(got, X, lk, RTOL64)
+    slots = 128 if lk == "average" else 0
+    got = hac.cluster(X, lk, precision=hac.PREC_F32_RECHECK, cache_slots=slots, timeout_s=600.0)
+    rtol = _rtol(lk, hac.PREC_F32_RECHECK)
+    assert dendro.check(got, len(X), rtol=2 * rtol) == []
+    _check_sampled(got, X, lk, rtol)
     if lk == "ward":
         _check_rnn(got, X, lk, 20, k_big=2, every_size=True)
     else:
         _check_rnn(got, X, lk, 8, side_cap=32)
+    if lk != "average_sq":
+        ref = hac.cluster(X, lk, precision=hac.PREC_F64, cache_slots=slots, timeout_s=600.0)
+        _assert_same(got, ref, rtol=rtol)
 
 
 @pytest.mark.parametrize("slots", [8, 64])
@@ -506,9 +513,10 @@ def test_paper_shapes_sample(name, prec):
 
 
 @pytest.mark.parametrize("lk", LKS)
-def test_no_prune_ablation_same_tree(lk):
+def test_no_prune_ablation_same_tree(lk, tree_path):
     """HAC_FLAG_NO_PRUNE makes every cluster a candidate: the same tree, and
-    the range query is what keeps the evaluations far below the naive count."""
+    the range query is what keeps the evaluations far below the naive count
+    (average linkage on the range-query search, not the dense matrix)."""
     X = inputs.workload("gaussiandisc2d_1m_f32", n=2500)
     slots = 64 if lk in ("complete", "average") else 0
     a = hac.cluster(X, lk, precision=hac.PREC_F32_RECHECK, cache_slots=slots)
