@@ -157,7 +157,12 @@ int hac_create_device(const void *dev_points, int64_t n, int d, hac_dtype dt, ha
 /* Run the whole clustering (paper: Algorithm 1 -- initialisation, then rounds
  * of nearest-neighbour search (Algorithms 2-4, Section 4), chain update,
  * reciprocal-pair filter, merges and the Section 5 cache update (Algorithm 5)
- * until one cluster is left).  opts may be NULL (defaults).  Blocks until done.  May be called
+ * until one cluster is left).  Average linkage switches, once at most 32,768
+ * clusters are active, to the full matrix of their pair distances (the
+ * Section 5 cache with room for every pair: 24 bytes per pair of active
+ * clusters, allocated once per handle; without room for it the run stays on
+ * the range-query search); the environment variable HAC_DENSE_K, read at
+ * hac_create, sets that threshold (0 = never).  opts may be NULL (defaults).  Blocks until done.  May be called
  * again on the same handle: each call recomputes from the stored points.
  * HAC_ETIMEOUT if a limit in opts is hit (the handle stays usable). */
 int hac_run(hac_t h, const hac_opts *opts);
@@ -200,13 +205,16 @@ const char *hac_strerror(int code);
  * synchronisation that cudaMalloc/cudaFree can cause).
  *
  * Same dendrogram as hac_create + hac_run + hac_dendrogram on the same points
- * and options, computed by the same kernels, but all working memory comes
+ * and options (with the dense matrix of average linkage off, HAC_DENSE_K=0;
+ * with it on, the same tree and heights within the precision mode's stated
+ * bound), computed by the same kernels, but all working memory comes
  * from a fixed 6 MiB device array inside the library, which every GPU that
  * loads the library holds until the process exits.  No cudaMalloc, cudaFree
  * or other allocating call is made.  The pair-distance cache needs memory, so
  * opts->cache_slots is ignored (no cache, hence no GPU-wide big-pair
  * evaluation), and the HAC_* environment overrides that hac_create reads
- * (HAC_BIG_PAIRS, HAC_BIG_PAIRS_F64, HAC_WARP_BUDGET, HAC_BRUTE) do not apply;
+ * (HAC_BIG_PAIRS, HAC_BIG_PAIRS_F64, HAC_WARP_BUDGET, HAC_BRUTE, HAC_DENSE_K) do
+ * not apply;
  * these change speed only, never the result.  HAC_FLAG_NO_PRUNE is honoured.
  *   dev_points  DEVICE pointer, row-major n x d of `dt`, on the current device;
  *               read only, owned by the caller.

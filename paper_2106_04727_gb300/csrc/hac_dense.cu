@@ -109,6 +109,11 @@ __device__ __forceinline__ void u128_add(U128 &a, const U128 &b) {
 // 2^126 units, so w3 < 2^30).
 constexpr int LIMBS = 4;
 
+// the pair i < j of a k x k matrix in the packed upper triangle
+__host__ __device__ __forceinline__ size_t tri(long long i, long long j, long long k) {
+  return (size_t)(i * k - i * (i + 1) / 2 + (j - i - 1));
+}
+
 __device__ __forceinline__ void limbs_atomic(unsigned long long *w, const U128 &b) {
   if (!(b.lo | b.hi)) return;
   const unsigned long long l0 = b.lo & 0xffffffffull, l1 = b.lo >> 32;
@@ -163,16 +168,16 @@ __device__ __forceinline__ U128 u128_shfl_xor(const U128 &v, int o) {
   return U128{__shfl_xor_sync(0xffffffffu, v.lo, o), __shfl_xor_sync(0xffffffffu, v.hi, o)};
 }
 
-// the sum as an FP64 number (the estimate flag ignored)
-__device__ __forceinline__ double fx_value(unsigned long long lo, unsigned long long hi, int e) {
-  return ldexp((double)(hi & ~TOP), 64 + e) + ldexp((double)lo, e);
-}
-
-// mean distance of an entry: its sum / (na nb), the sign bit set for an
-// estimate; one function everywhere, so equal sums give equal means
-__device__ __forceinline__ double entry_mean(const unsigned long long *w, int e, int na, int nb) {
+// The mean distance of an entry, one function everywhere so that equal sums
+// and sizes give equal means: the 128-bit sum as an FP64 number (the words
+// scaled by 2^e and 2^(64+e)), times 1 / size of the cluster with the lower
+// matrix index, times 1 / size of the other (reciprocals kept per matrix
+// index: no FP64 division); the sign bit set for an estimate.
+__device__ __forceinline__ double entry_mean(const unsigned long long *w, double sl, double sh,
+                                             double inv_lo, double inv_hi) {
   const U128 v = limbs_value(w);
-  const double m = fx_value(v.lo, v.hi, e) / ((double)na * (double)nb);
+  const double S = fma((double)v.hi, sh, (double)v.lo * sl);
+  const double m = S * inv_lo * inv_hi;
   const unsigned long long b = (unsigned long long)__double_as_longlong(m);
   return __longlong_as_double((long long)((w[3] & TOP) ? (b | SIGN) : b));
 }
@@ -202,7 +207,7 @@ struct SweepArgs {
   const int32_t *didx;
   int64_t N;  // points in the layout
   int dk, e;
-  unsigned long long *sum;  // the sum matrix: cell (i < j) at [i][j] (LIMBS words)
+  unsigned long long *sum;  // the packed upper triangle of sums (LIMBS words per pair)
   long long nb;             // blocks of TI points along each axis
   Counters *ctr;
 };
@@ -271,14 +276,14 @@ __device__ __forceinline__ void flush(const SweepArgs &a, const U128 (&acc)[PPT]
     for (int r = 1; r < PPT; ++r) u128_add(v, acc[r]);
 #pragma unroll
     for (int o = 16; o; o >>= 1) u128_add(v, u128_shfl_xor(v, o));
-    if (lane == 0) limbs_atomic(&a.sum[LIMBS * ((size_t)krow[0] * a.dk + qj)], v);
+    if (lane == 0) limbs_atomic(&a.sum[LIMBS * tri(krow[0], qj, a.dk)], v);
     return;
   }
 #pragma unroll
   for (int r = 0; r < PPT; ++r) {
     const U128 z{0ull, 0ull};
     const U128 v = seg_sum(krow[r] < qj ? acc[r] : z, same[r]);
-    if (lead[r] && krow[r] < qj) limbs_atomic(&a.sum[LIMBS * ((size_t)krow[r] * a.dk + qj)], v);
+    if (lead[r] && krow[r] < qj) limbs_atomic(&a.sum[LIMBS * tri(krow[r], qj, a.dk)], v);
   }
 }
 
@@ -458,12 +463,11 @@ __global__ void __launch_bounds__(DS_TPB) k_dense_sweep64(SweepArgs a) {
   if (lane == 0 && pairs) atomicAdd(&a.ctr->dense_pp, pairs);
 }
 
-// Sums -> means.  32 x 32 tiles of the upper triangle with their mirror
-// tile: the mirror cells get the same sum, both get the mean (+inf and a zero
-// sum on the diagonal); estimates (FP32 mode) carry the flag.  Shared memory
-// keeps every global access a row segment.
+// Sums -> means: both triangles of the mean matrix (+inf on the diagonal);
+// an estimate (FP32 mode) gets its flag in the sum.  32 x 32 tiles of the
+// upper triangle with their mirror tile, written through shared memory so
+// every global access is a row segment.
 __global__ void k_dense_fin(State s, int dk, bool est) {
-  __shared__ unsigned long long W[LIMBS][32][33];
   __shared__ double Mv[32][33];
   const int nt = (dk + 31) / 32;
   long long ti, tj;
@@ -472,42 +476,26 @@ __global__ void k_dense_fin(State s, int dk, bool est) {
   const int tx = threadIdx.x, ty = threadIdx.y;  // 32 x 8
   for (int k = ty; k < 32; k += 8) {
     const long long i = ti * 32 + k, j = tj * 32 + tx;  // the upper tile
-    unsigned long long w[LIMBS] = {0ull, 0ull, 0ull, 0ull};
     double v = 0.0;
     if (i < dk && j < dk) {
       if (i == j) {
         v = __longlong_as_double((long long)KINF_D);
       } else if (i < j) {
-        const unsigned long long *c = s.dsum + LIMBS * ((size_t)i * dk + j);
-#pragma unroll
-        for (int l = 0; l < LIMBS; ++l) w[l] = c[l];
-        if (est) w[3] |= TOP;
-        v = entry_mean(w, s.dexp, s.qsz[i], s.qsz[j]);
+        unsigned long long *c = s.dsum + LIMBS * tri(i, j, dk);
+        if (est) c[3] |= TOP;
+        v = entry_mean(c, s.dsl, s.dsh, s.dinv[i], s.dinv[j]);
       }
     }
-#pragma unroll
-    for (int l = 0; l < LIMBS; ++l) W[l][k][tx] = w[l];
     Mv[k][tx] = v;
   }
   __syncthreads();
   for (int k = ty; k < 32; k += 8) {
     const long long i = ti * 32 + k, j = tj * 32 + tx;
-    if (i < dk && j < dk) {
-      // diagonal tile: the lower cells take the upper cells' values
-      const bool mir = ti == tj && i > j;
-      unsigned long long *c = s.dsum + LIMBS * ((size_t)i * dk + j);
-#pragma unroll
-      for (int l = 0; l < LIMBS; ++l) c[l] = mir ? W[l][tx][k] : W[l][k][tx];
-      s.dmat[(size_t)i * dk + j] = mir ? Mv[tx][k] : Mv[k][tx];
-    }
+    if (i < dk && j < dk)  // diagonal tile: the lower cells take the upper cells' means
+      s.dmat[(size_t)i * dk + j] = ti == tj && i > j ? Mv[tx][k] : Mv[k][tx];
     if (ti != tj) {  // mirror tile: row tj*32+k, column ti*32+tx = upper cell (tx, k)
       const long long i2 = tj * 32 + k, j2 = ti * 32 + tx;
-      if (i2 < dk && j2 < dk) {
-        unsigned long long *c = s.dsum + LIMBS * ((size_t)i2 * dk + j2);
-#pragma unroll
-        for (int l = 0; l < LIMBS; ++l) c[l] = W[l][tx][k];
-        s.dmat[(size_t)i2 * dk + j2] = Mv[tx][k];
-      }
+      if (i2 < dk && j2 < dk) s.dmat[(size_t)i2 * dk + j2] = Mv[tx][k];
     }
   }
 }
@@ -517,6 +505,7 @@ __global__ void k_dense_init(State s, const int32_t *order, int K) {
     const int c = order[p];
     s.didx[c] = p;
     s.dcid[p] = c;
+    s.dinv[p] = 1.0 / (double)s.qsz[p];
   }
 }
 
@@ -526,8 +515,13 @@ __global__ void k_dense_init(State s, const int32_t *order, int K) {
 struct NNArgs {
   const double *dmat;
   int dk, K, nlist;
-  const int32_t *order, *didx, *list;
+  const int32_t *order, *didx, *list, *dq;
   double delta, rho;  // FP32 mode: error model of an estimate
+  // FP32 mode with delta = 0: the bounds as steps of the FP64 bit pattern
+  // (adding N ulps to a non-negative double multiplies it by at least
+  // 1 + N 2^-53): up = x + nu ulps >= x / (1 - rho), lo = x - nl ulps <=
+  // x / (1 + rho) (nl doubled for a step down across a power of two)
+  unsigned long long nu, nl;
   double *Ekey;
   int32_t *Ecid;
   int32_t *drq_a, *drq_b;
@@ -559,6 +553,9 @@ __device__ __forceinline__ double warp_min_d(double v) {
   return v;
 }
 
+// One warp per terminal; each lane has NN_U loads of the row in flight.
+constexpr int NN_U = 4;
+
 template <int F32>
 __global__ void k_dense_nn(NNArgs a) {
   const int lane = threadIdx.x & 31;
@@ -572,14 +569,21 @@ __global__ void k_dense_nn(NNArgs a) {
     if (!F32) {
       unsigned long long bk = KINF_D;
       int bc = INT_MAX;
-      for (int p = lane; p < a.K; p += 32) {
-        const int c = a.order[p];
-        if (c == ci) continue;
-        const unsigned long long k = (unsigned long long)__double_as_longlong(row[a.didx[c]]);
-        if (kless_d(k, c, bk, bc)) {
-          bk = k;
-          bc = c;
+      for (int p0 = 0; p0 < a.K; p0 += 32 * NN_U) {
+        unsigned long long k[NN_U];
+        int c[NN_U];
+#pragma unroll
+        for (int u = 0; u < NN_U; ++u) {
+          const int p = p0 + u * 32 + lane;
+          c[u] = p < a.K ? a.order[p] : ci;
+          k[u] = p < a.K ? (unsigned long long)__double_as_longlong(row[a.dq[p]]) : KINF_D;
         }
+#pragma unroll
+        for (int u = 0; u < NN_U; ++u)
+          if (c[u] != ci && kless_d(k[u], c[u], bk, bc)) {
+            bk = k[u];
+            bc = c[u];
+          }
       }
       warp_argmin_kc(bk, bc);
       if (lane == 0) {
@@ -589,42 +593,157 @@ __global__ void k_dense_nn(NNArgs a) {
       }
       continue;
     }
+    if (F32 == 2) {
+      // FP32 mode, integer bounds (no FP64 arithmetic in the scan)
+      unsigned long long U = ~0ull;
+      for (int p0 = 0; p0 < a.K; p0 += 32 * NN_U) {
+        unsigned long long x[NN_U];
+        int c[NN_U];
+#pragma unroll
+        for (int u = 0; u < NN_U; ++u) {
+          const int p = p0 + u * 32 + lane;
+          c[u] = p < a.K ? a.order[p] : ci;
+          x[u] = p < a.K ? (unsigned long long)__double_as_longlong(row[a.dq[p]]) : KINF_D;
+        }
+#pragma unroll
+        for (int u = 0; u < NN_U; ++u) {
+          if (c[u] == ci) continue;
+          const unsigned long long m = x[u] & ~SIGN;
+          const unsigned long long up = (x[u] & SIGN) && m ? m + a.nu : m;
+          U = up < U ? up : U;
+        }
+      }
+#pragma unroll
+      for (int o = 16; o; o >>= 1) {
+        const unsigned long long u2 = __shfl_xor_sync(0xffffffffu, U, o);
+        U = u2 < U ? u2 : U;
+      }
+      unsigned long long bk = KINF_D, ev = 0;
+      int bc = INT_MAX, nW = 0, nE = 0, ec = INT_MAX;
+      for (int p0 = 0; p0 < a.K; p0 += 32 * NN_U) {
+        unsigned long long x[NN_U];
+        int c[NN_U];
+#pragma unroll
+        for (int u = 0; u < NN_U; ++u) {
+          const int p = p0 + u * 32 + lane;
+          c[u] = p < a.K ? a.order[p] : ci;
+          x[u] = p < a.K ? (unsigned long long)__double_as_longlong(row[a.dq[p]]) : KINF_D;
+        }
+#pragma unroll
+        for (int u = 0; u < NN_U; ++u) {
+          if (c[u] == ci) continue;
+          const unsigned long long m = x[u] & ~SIGN;
+          const bool exact = !(x[u] & SIGN) || m == 0;  // an estimate of 0 is exact (delta = 0)
+          const unsigned long long lo = exact ? m : (m > a.nl ? m - a.nl : 0ull);
+          if (lo > U) continue;
+          ++nW;
+          if (exact) {
+            if (kless_d(m, c[u], bk, bc)) {
+              bk = m;
+              bc = c[u];
+            }
+          } else {
+            ++nE;
+            ec = c[u];
+            ev = m;
+          }
+        }
+      }
+      warp_argmin_kc(bk, bc);
+      const int totW = __reduce_add_sync(0xffffffffu, (unsigned)nW);
+      const int totE = __reduce_add_sync(0xffffffffu, (unsigned)nE);
+      if (totE == 0) {
+        if (lane == 0) {
+          a.Ekey[ci] = __longlong_as_double((long long)bk);
+          a.Ecid[ci] = bc == INT_MAX ? -1 : bc;
+          if (bc == INT_MAX) atomicOr(&a.ctr->err, ERR_NO_NN);
+        }
+        continue;
+      }
+      if (totW == 1) {
+        // the lone candidate is an estimate; rho <= 4e-6 here (checked by the
+        // host), so its upper bound stands in for the FP64 value
+        const unsigned holder = __ballot_sync(0xffffffffu, nE > 0);
+        const int hl = __ffs(holder) - 1;
+        const unsigned long long v = __shfl_sync(0xffffffffu, ev, hl);
+        const int c = __shfl_sync(0xffffffffu, ec, hl);
+        if (lane == 0) {
+          a.Ekey[ci] = __longlong_as_double((long long)(v + a.nu));
+          a.Ecid[ci] = c;
+        }
+        continue;
+      }
+      // several candidates in the window: re-score its estimates in FP64
+      for (int p = lane; p < a.K; p += 32) {
+        const int c = a.order[p];
+        if (c == ci) continue;
+        const int q = a.dq[p];
+        const unsigned long long xb = (unsigned long long)__double_as_longlong(row[q]);
+        const unsigned long long m = xb & ~SIGN;
+        if (!(xb & SIGN) || m == 0 || (m > a.nl ? m - a.nl : 0ull) > U) continue;
+        const int r = atomicAdd(&a.ctr->nrq, 1);
+        if (r < a.drq_cap) {
+          a.drq_a[r] = min(qi, q);
+          a.drq_b[r] = max(qi, q);
+        }
+      }
+      if (lane == 0) a.pend_out[atomicAdd(&a.ctr->npend, 1)] = ci;
+      continue;
+    }
     // FP32 mode.  Bounds of an estimate x on the FP64 value D:
     // (x - delta) / (1 + rho) <= D <= (x + delta) / (1 - rho), widened by
     // 1e-12 for the rounding of these FP64 operations.
     const double lo_f = (1.0 - 1e-12) / (1.0 + a.rho), up_f = (1.0 + 1e-12) / (1.0 - a.rho);
     double U = INFINITY;
-    for (int p = lane; p < a.K; p += 32) {
-      const int c = a.order[p];
-      if (c == ci) continue;
-      const double x = row[a.didx[c]];
-      const double m = mag(x);
-      const bool exact = !is_est(x) || (m == 0.0 && a.delta == 0.0);
-      U = fmin(U, exact ? m : (m + a.delta) * up_f);
+    for (int p0 = 0; p0 < a.K; p0 += 32 * NN_U) {
+      double x[NN_U];
+      int c[NN_U];
+#pragma unroll
+      for (int u = 0; u < NN_U; ++u) {
+        const int p = p0 + u * 32 + lane;
+        c[u] = p < a.K ? a.order[p] : ci;
+        x[u] = p < a.K ? row[a.dq[p]] : INFINITY;
+      }
+#pragma unroll
+      for (int u = 0; u < NN_U; ++u) {
+        if (c[u] == ci) continue;
+        const double m = mag(x[u]);
+        const bool exact = !is_est(x[u]) || (m == 0.0 && a.delta == 0.0);
+        U = fmin(U, exact ? m : (m + a.delta) * up_f);
+      }
     }
     U = warp_min_d(U);
     unsigned long long bk = KINF_D;
     int bc = INT_MAX, nW = 0, nE = 0, ec = INT_MAX;
     double ev = 0.0;
-    for (int p = lane; p < a.K; p += 32) {
-      const int c = a.order[p];
-      if (c == ci) continue;
-      const double x = row[a.didx[c]];
-      const double m = mag(x);
-      const bool exact = !is_est(x) || (m == 0.0 && a.delta == 0.0);
-      const double lo = exact ? m : fmax(m - a.delta, 0.0) * lo_f;
-      if (!(lo <= U)) continue;
-      ++nW;
-      if (exact) {
-        const unsigned long long k = (unsigned long long)__double_as_longlong(m);
-        if (kless_d(k, c, bk, bc)) {
-          bk = k;
-          bc = c;
+    for (int p0 = 0; p0 < a.K; p0 += 32 * NN_U) {
+      double x[NN_U];
+      int c[NN_U];
+#pragma unroll
+      for (int u = 0; u < NN_U; ++u) {
+        const int p = p0 + u * 32 + lane;
+        c[u] = p < a.K ? a.order[p] : ci;
+        x[u] = p < a.K ? row[a.dq[p]] : INFINITY;
+      }
+#pragma unroll
+      for (int u = 0; u < NN_U; ++u) {
+        if (c[u] == ci) continue;
+        const double m = mag(x[u]);
+        const bool exact = !is_est(x[u]) || (m == 0.0 && a.delta == 0.0);
+        const double lo = exact ? m : fmax(m - a.delta, 0.0) * lo_f;
+        if (!(lo <= U)) continue;
+        ++nW;
+        if (exact) {
+          const unsigned long long k = (unsigned long long)__double_as_longlong(m);
+          if (kless_d(k, c[u], bk, bc)) {
+            bk = k;
+            bc = c[u];
+          }
+        } else {
+          ++nE;
+          ec = c[u];
+          ev = m;
         }
-      } else {
-        ++nE;
-        ec = c;
-        ev = m;
       }
     }
     warp_argmin_kc(bk, bc);
@@ -665,7 +784,7 @@ __global__ void k_dense_nn(NNArgs a) {
       for (int p = lane; p < a.K; p += 32) {
         const int c = a.order[p];
         if (c == ci) continue;
-        const int q = a.didx[c];
+        const int q = a.dq[p];
         const double x = row[q];
         const double m = mag(x);
         const bool exact = !is_est(x) || (m == 0.0 && a.delta == 0.0);
@@ -792,17 +911,13 @@ __global__ void __launch_bounds__(RQ_TPB) k_drq_eval(State s, int m, int cur) {
 __global__ void k_drq_fin(State s, int m) {
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gridDim.x * blockDim.x) {
     const int qa = s.drq_a[i], qb = s.drq_b[i];
-    const int A = s.dcid[qa], B = s.dcid[qb];
     const unsigned long long *w = s.drq_acc + LIMBS * (size_t)i;
-    const double v = entry_mean(w, s.dexp, s.csize[A], s.csize[B]);
-    const size_t c1 = (size_t)qa * s.dk + qb, c2 = (size_t)qb * s.dk + qa;
+    const double v = entry_mean(w, s.dsl, s.dsh, s.dinv[qa], s.dinv[qb]);  // qa < qb
+    unsigned long long *c = s.dsum + LIMBS * tri(qa, qb, s.dk);  // qa < qb
 #pragma unroll
-    for (int l = 0; l < LIMBS; ++l) {
-      s.dsum[LIMBS * c1 + l] = w[l];
-      s.dsum[LIMBS * c2 + l] = w[l];
-    }
-    s.dmat[c1] = v;
-    s.dmat[c2] = v;
+    for (int l = 0; l < LIMBS; ++l) c[l] = w[l];
+    s.dmat[(size_t)qa * s.dk + qb] = v;
+    s.dmat[(size_t)qb * s.dk + qa] = v;
   }
 }
 
@@ -815,10 +930,11 @@ struct Limbs {
   unsigned long long w[LIMBS];
 };
 
-__device__ __forceinline__ Limbs sum_at(const State &s, size_t cell) {
+__device__ __forceinline__ Limbs sum_at(const State &s, int i, int j) {  // the pair {i, j}
+  const unsigned long long *c = s.dsum + LIMBS * (i < j ? tri(i, j, s.dk) : tri(j, i, s.dk));
   Limbs r;
 #pragma unroll
-  for (int l = 0; l < LIMBS; ++l) r.w[l] = s.dsum[LIMBS * cell + l];
+  for (int l = 0; l < LIMBS; ++l) r.w[l] = c[l];
   return r;
 }
 
@@ -831,34 +947,45 @@ __device__ __forceinline__ Limbs sum_add(const Limbs &x, const Limbs &y) {
   return r;
 }
 
-__device__ __forceinline__ void sum_put(const State &s, size_t cell, const Limbs &v) {
+__device__ __forceinline__ void sum_put(const State &s, int i, int j, const Limbs &v) {
+  unsigned long long *c = s.dsum + LIMBS * (i < j ? tri(i, j, s.dk) : tri(j, i, s.dk));
 #pragma unroll
-  for (int l = 0; l < LIMBS; ++l) s.dsum[LIMBS * cell + l] = v.w[l];
+  for (int l = 0; l < LIMBS; ++l) c[l] = v.w[l];
 }
 
-// 1. rows: the survivor's row adds its partner's, over every cluster active
-//    at the start of the round; means for the clusters that did not merge
-__global__ void k_dense_row(State s, const int32_t *order_old, int Kold, int npairs, int round) {
+// the round's positions after the merges: size of each cluster and whether
+// it merged (the order is the one of the start of the round)
+__global__ void k_dense_cols(State s, const int32_t *order_old, int Kold, int round, int npairs) {
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < Kold; j += gridDim.x * blockDim.x)
+    s.dqm[j] = s.mround[order_old[j]] == round ? 1 : 0;
+  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < npairs; p += gridDim.x * blockDim.x) {
+    const int lo = s.pair_lo[p];
+    s.dinv[s.didx[lo]] = 1.0 / (double)s.csize[lo];  // the merged cluster's size
+  }
+}
+
+// 1. rows: the survivor's sum with every cluster that did not merge this
+//    round adds its partner's; means in the survivor's row
+__global__ void k_dense_row(State s, int Kold, int npairs) {
   const int dk = s.dk;
   for (int p = blockIdx.y; p < npairs; p += gridDim.y) {
     const int lo = s.pair_lo[p], hi = s.pair_hi[p];
     const int qa = s.didx[lo], qb = s.didx[hi];
-    const int nab = s.csize[lo];
+    const double ia = s.dinv[qa];  // already the merged cluster's
     for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < Kold; j += gridDim.x * blockDim.x) {
-      const int c = order_old[j];
-      const int q = s.didx[c];
-      if (q == qa || q == qb) continue;
-      const size_t cell = (size_t)qa * dk + q;
-      const Limbs v = sum_add(sum_at(s, cell), sum_at(s, (size_t)qb * dk + q));
-      sum_put(s, cell, v);
-      if (s.mround[c] != round) s.dmat[cell] = entry_mean(v.w, s.dexp, nab, s.csize[c]);
+      if (s.dqm[j]) continue;  // pairs of two merged clusters: k_dense_fix
+      const int q = s.dq[j];
+      const Limbs v = sum_add(sum_at(s, qa, q), sum_at(s, qb, q));
+      sum_put(s, qa, q, v);
+      const double iq = s.dinv[q];
+      s.dmat[(size_t)qa * dk + q] = qa < q ? entry_mean(v.w, s.dsl, s.dsh, ia, iq)
+                                           : entry_mean(v.w, s.dsl, s.dsh, iq, ia);
     }
   }
 }
 
-// 2. pairs of clusters that both merged this round: the second partner's
-//    part is added from the first survivor's row, and the lower index writes
-//    both cells
+// 2. pairs of clusters that both merged this round: the four old sums, once
+//    per unordered pair (the lower index writes both means)
 __global__ void k_dense_fix(State s, int npairs) {
   const long long tot = (long long)npairs * npairs;
   const int dk = s.dk;
@@ -866,34 +993,38 @@ __global__ void k_dense_fix(State s, int npairs) {
        t += (long long)gridDim.x * blockDim.x) {
     const int p1 = (int)(t / npairs), p2 = (int)(t - (long long)p1 * npairs);
     if (p1 == p2) continue;
-    const int a = s.pair_lo[p1];
+    const int a = s.pair_lo[p1], b = s.pair_hi[p1];
     const int c = s.pair_lo[p2], d = s.pair_hi[p2];
-    const int qa = s.didx[a], qc = s.didx[c], qd = s.didx[d];
+    const int qa = s.didx[a], qb = s.didx[b], qc = s.didx[c], qd = s.didx[d];
     if (qa > qc) continue;
-    const Limbs v = sum_add(sum_at(s, (size_t)qa * dk + qc), sum_at(s, (size_t)qa * dk + qd));
-    const double m = entry_mean(v.w, s.dexp, s.csize[a], s.csize[c]);
-    sum_put(s, (size_t)qa * dk + qc, v);
-    sum_put(s, (size_t)qc * dk + qa, v);
+    const Limbs v = sum_add(sum_add(sum_at(s, qa, qc), sum_at(s, qa, qd)),
+                            sum_add(sum_at(s, qb, qc), sum_at(s, qb, qd)));
+    sum_put(s, qa, qc, v);
+    const double m = entry_mean(v.w, s.dsl, s.dsh, s.dinv[qa], s.dinv[qc]);  // qa < qc
     s.dmat[(size_t)qa * dk + qc] = m;
     s.dmat[(size_t)qc * dk + qa] = m;
   }
 }
 
-// 3. columns: every cluster that did not merge gets the survivor's entry in
-//    its own row (the matrix stays exactly symmetric)
-__global__ void k_dense_col(State s, const int32_t *order_old, int Kold, int npairs, int round) {
+// 3. columns: every cluster that did not merge gets the survivor's mean in
+//    its own row (the mean matrix stays exactly symmetric)
+__global__ void k_dense_col(State s, int Kold, int npairs) {
   const int dk = s.dk;
   for (int p = blockIdx.y; p < npairs; p += gridDim.y) {
     const int qa = s.didx[s.pair_lo[p]];
+    const double *ra = s.dmat + (size_t)qa * dk;
     for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < Kold; j += gridDim.x * blockDim.x) {
-      const int c = order_old[j];
-      if (s.mround[c] == round) continue;  // merged this round: its row is done
-      const int r = s.didx[c];
-      const size_t src = (size_t)qa * dk + r, dst = (size_t)r * dk + qa;
-      sum_put(s, dst, sum_at(s, src));
-      s.dmat[dst] = s.dmat[src];
+      if (s.dqm[j]) continue;
+      const int r = s.dq[j];
+      s.dmat[(size_t)r * dk + qa] = ra[r];
     }
   }
+}
+
+// matrix index of every active position (the search's column list)
+__global__ void k_dense_q(State s, const int32_t *order, int K) {
+  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < K; p += gridDim.x * blockDim.x)
+    s.dq[p] = s.didx[order[p]];
 }
 
 // ---------------------------------------------------------------------------
@@ -987,6 +1118,8 @@ int dense_maybe_enter(hac_ctx *h, cudaStream_t st, int K, RoundCtl &ctl) {
     const int rqcap = (int)std::min<int64_t>(std::max<int64_t>(4 * cap, 1 << 16), 1 << 22);
     int rc = 0;
     if ((rc = dalloc(h, &s.didx, h->n)) || (rc = dalloc(h, &s.dcid, cap)) ||
+        (rc = dalloc(h, &s.dq, cap)) || (rc = dalloc(h, &s.dinv, cap)) ||
+        (rc = dalloc(h, &s.dqm, cap)) ||
         (rc = dalloc(h, &s.drq_a, rqcap)) || (rc = dalloc(h, &s.drq_b, rqcap)) ||
         (rc = dalloc(h, &s.drq_pre, rqcap + 1)) ||
         (rc = dalloc(h, &s.drq_acc, LIMBS * (size_t)rqcap)) || (rc = dalloc(h, &s.dpend[0], cap)) ||
@@ -996,7 +1129,7 @@ int dense_maybe_enter(hac_ctx *h, cudaStream_t st, int K, RoundCtl &ctl) {
     // the matrices last: without room for them the instance stays on the
     // range-query search (same result)
     if (dalloc(h, &s.dmat, (size_t)cap * cap) != HAC_OK ||
-        dalloc(h, &s.dsum, LIMBS * (size_t)cap * cap) != HAC_OK) {
+        dalloc(h, &s.dsum, LIMBS * (size_t)cap * (cap - 1) / 2 + 1) != HAC_OK) {
       h->dense_k = 0;
       return 0;
     }
@@ -1007,8 +1140,11 @@ int dense_maybe_enter(hac_ctx *h, cudaStream_t st, int K, RoundCtl &ctl) {
   const double dmax = 2.0 * (double)s.coord_scale * std::sqrt((double)s.d) * (1.0 + 1e-5);
   const double smax = 0.25 * (double)h->lay_n * (double)h->lay_n * dmax;
   s.dexp = smax > 0.0 ? (int)std::floor(std::log2(smax)) + 1 - 126 : -1000;
+  s.dsl = std::ldexp(1.0, s.dexp);
+  s.dsh = std::ldexp(1.0, 64 + s.dexp);
   k_dense_init<<<grid_for(K, TPB), TPB, 0, st>>>(s, s.order[h->ocur], K);
-  CK(cudaMemsetAsync(s.dsum, 0, (size_t)K * K * LIMBS * sizeof(unsigned long long), st));
+  CK(cudaMemsetAsync(s.dsum, 0, (size_t)K * (K - 1) / 2 * LIMBS * sizeof(unsigned long long),
+                     st));
   SweepArgs a{};
   a.p32 = s.p32[h->pcur];
   a.p64 = s.p64[h->pcur];
@@ -1048,7 +1184,10 @@ int dense_search(hac_ctx *h, cudaStream_t st, int K, int nterm, RoundCtl &ctl) {
   a.K = K;
   a.order = s.order[h->ocur];
   a.didx = s.didx;
+  a.dq = s.dq;
   a.list = s.term;
+  k_dense_q<<<grid_for(K, TPB), TPB, 0, st>>>(s, a.order, K);
+  h->launches += 1;
   a.nlist = nterm;
   a.delta = (double)s.delta_pts;
   a.rho = ((double)s.d + 48.0) * 5.9604644775390625e-8;
@@ -1059,13 +1198,20 @@ int dense_search(hac_ctx *h, cudaStream_t st, int K, int nterm, RoundCtl &ctl) {
   a.drq_cap = s.drq_cap;
   a.ctr = s.ctr;
   const bool f32 = s.prec == HAC_PREC_F32_RECHECK;
+  // integer bounds when the estimates carry no absolute term and the lone
+  // estimate's bound is within the 4e-6 the height convention allows
+  const bool intb = f32 && a.delta == 0.0 && a.rho <= 4e-6;
+  a.nu = (unsigned long long)std::ceil(std::ldexp(a.rho / (1.0 - a.rho), 53) * (1.0 + 1e-6)) + 2;
+  a.nl = 2 * ((unsigned long long)std::ceil(std::ldexp(a.rho, 53) * (1.0 + 1e-6)) + 2);
   for (int it = 0;; ++it) {
     if (it >= 64) return HAC_EINTERNAL;
     CK(cudaMemsetAsync(&s.ctr->npend, 0, sizeof(int32_t), st));
     CK(cudaMemsetAsync(&s.ctr->nrq, 0, sizeof(int32_t), st));
     a.pend_out = s.dpend[it & 1];
     const int blocks = std::max(1, std::min(cdiv(a.nlist, 8), device_sms() * 16));
-    if (f32)
+    if (intb)
+      k_dense_nn<2><<<blocks, 256, 0, st>>>(a);
+    else if (f32)
       k_dense_nn<1><<<blocks, 256, 0, st>>>(a);
     else
       k_dense_nn<0><<<blocks, 256, 0, st>>>(a);
@@ -1092,17 +1238,18 @@ int dense_search(hac_ctx *h, cudaStream_t st, int K, int nterm, RoundCtl &ctl) {
 int dense_update(hac_ctx *h, cudaStream_t st, int round, int K, int npairs) {
   State &s = h->s;
   if (npairs <= 0) return HAC_OK;
-  const int32_t *order_old = s.order[h->ocur];  // active at the start of the round
+  // s.dq holds this round's positions (the order before the compaction)
+  k_dense_cols<<<grid_for(K, TPB), TPB, 0, st>>>(s, s.order[h->ocur], K, round, npairs);
   const int gx = std::max(1, std::min(cdiv(K, TPB), 64));
   const int gy = std::min(npairs, 65535);
-  k_dense_row<<<dim3(gx, gy), TPB, 0, st>>>(s, order_old, K, npairs, round);
+  k_dense_row<<<dim3(gx, gy), TPB, 0, st>>>(s, K, npairs);
   if (npairs > 1) {
     const long long tot = (long long)npairs * npairs;
     k_dense_fix<<<grid_for(tot, TPB), TPB, 0, st>>>(s, npairs);
     h->launches += 1;
   }
-  k_dense_col<<<dim3(gx, gy), TPB, 0, st>>>(s, order_old, K, npairs, round);
-  h->launches += 2;
+  k_dense_col<<<dim3(gx, gy), TPB, 0, st>>>(s, K, npairs);
+  h->launches += 3;
   CK(cudaGetLastError());
   return HAC_OK;
 }

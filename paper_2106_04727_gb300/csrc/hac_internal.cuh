@@ -172,10 +172,14 @@ struct State {
   int dense;            // 1 once the instance runs on the matrix
   int dk;               // matrix dimension: active clusters at the switch
   int dexp;             // exponent of the fixed-point unit of the sweep sums
+  double dsl, dsh;      // 2^dexp and 2^(64 + dexp): a sum's low and high word scales
+  double *dinv;         // 1 / size of the cluster at each matrix index
   double *dmat;         // dk x dk, row-major; diagonal +inf
-  unsigned long long *dsum;  // dk x dk 128-bit fixed-point sums of point distances
-                             // (four limb words per entry; the top bit of the last
-                             // marks an estimate)
+  unsigned long long *dsum;  // 128-bit fixed-point sums of point distances of the
+                             // pairs i < j, packed upper triangle (four limb words
+                             // per pair; the top bit of the last marks an estimate)
+  int32_t *dq;          // this round: matrix index of each active position
+  uint8_t *dqm;         // after the merges: 1 if that cluster merged this round
   int32_t *didx;        // cid -> matrix index (the cid's position at the switch)
   int32_t *dcid;        // matrix index -> cid
   int drq_cap;          // FP64 re-score queue (pairs, lower index first)

@@ -41,11 +41,13 @@ def _static(torch, X, lk, prec, bufs):
 
 @pytest.mark.gpu
 @pytest.mark.parametrize("prec", [hac.PREC_F64, hac.PREC_F32_RECHECK], ids=["f64", "f32recheck"])
-def test_static_matches_allocating_path_twice(prec):
-    """Same dendrogram as the allocating path and as the CPU oracle, on
-    consecutive calls that reuse (and overwrite) the fixed array, and no
-    device memory taken by those calls."""
+def test_static_matches_allocating_path_twice(prec, monkeypatch):
+    """Same dendrogram as the allocating path (which, like this entry point,
+    stays on the range-query search here: no dense matrix) and as the CPU
+    oracle, on consecutive calls that reuse (and overwrite) the fixed array,
+    and no device memory taken by those calls."""
     torch = pytest.importorskip("torch")
+    monkeypatch.setenv("HAC_DENSE_K", "0")
     cases = [(inputs.gaussian_mixture(3000, 5, 12, seed=91), "ward"),
              (inputs.uniform_cube(hac.HAC_STATIC_MAX_N, 2, seed=92, dtype=np.float64), "average"),
              (inputs.gaussian_mixture(777, 3, 4, seed=93), "complete")]
