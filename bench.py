@@ -203,12 +203,13 @@ def run_reference(args):
     ws, rank, _ = dist_env()
     if rank != 0:
         return
+    n_ref = getattr(args, "ref_n", None)
     for _ in range(args.warmup):
-        cpu_baseline(args.workload, args.linkages, args.cpu_cap, n=20000)
+        cpu_baseline(args.workload, args.linkages, args.cpu_cap, n=min(20000, n_ref or 20000))
     ts = []
     cb = None
     for _ in range(args.steps):
-        cb, dt = cpu_baseline(args.workload, args.linkages, args.cpu_cap)
+        cb, dt = cpu_baseline(args.workload, args.linkages, args.cpu_cap, n=n_ref)
         ts.append(dt)
     tot = sum(ts)
     n = cb["n"]
@@ -550,6 +551,8 @@ def main():
                     help="Section 5 cache slots per cluster for complete/average")
     ap.add_argument("--cpu-cap", type=float, default=30.0,
                     help="CPU baseline: seconds per linkage before it stops between rounds")
+    ap.add_argument("--ref-n", type=int, default=None,
+                    help="reference arm: points of the workload (default: all of it)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-f64", action="store_true",

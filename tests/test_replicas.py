@@ -60,7 +60,7 @@ def test_single_rank_needs_no_collective():
 
 def test_reference_arm_runs_on_rank_zero_only(monkeypatch):
     args = SimpleNamespace(gpus=2, steps=1, warmup=0, workload="gmm5d_1m_f32",
-                           linkages=["ward"], ref_sample=300)
+                           linkages=["ward"], cpu_cap=5.0, ref_n=300)
     monkeypatch.setenv("WORLD_SIZE", "2")
     monkeypatch.setenv("RANK", "1")
     out = io.StringIO()
