@@ -262,13 +262,49 @@ __device__ __forceinline__ U128 seg_sum(U128 v, unsigned same) {
   return v;
 }
 
-// Flush one column segment (key qj) of every row: cell (krow, qj) gets the
-// row's sum when krow < qj (each unordered cluster pair once, its lower
-// matrix index first).  Rows of one warp with the same key are summed first.
+// Row layout of a warp: lane l holds PPT consecutive rows, r0 + l * PPT + r,
+// so a lane's rows mostly share one key (cluster), and keys are
+// non-decreasing along (lane, r).  Per lane: its head run (key of row 0), its
+// tail run (key of row PPT - 1), and any runs wholly inside the lane.
+struct RowKeys {
+  int head, tail;
+  unsigned same;  // seg_mask of the tail keys
+  bool lead;      // first lane of its tail run
+  bool absorbed;  // the head run continues the previous lane's tail run
+  bool split;     // head != tail
+};
+
+// Row setup shared by both sweeps; returns whether all rows of the warp
+// share one key.
+template <int PPT>
+__device__ __forceinline__ bool row_keys(const SweepArgs &a, long long r0, int lane,
+                                         int (&krow)[PPT], RowKeys &rk, int &kfirst) {
+#pragma unroll
+  for (int r = 0; r < PPT; ++r) {
+    const long long row = r0 + (long long)lane * PPT + r;
+    krow[r] = row < a.N ? a.didx[a.plab[row]] : INT_MAX;
+  }
+  rk.head = krow[0];
+  rk.tail = krow[PPT - 1];
+  rk.split = rk.head != rk.tail;
+  rk.same = seg_mask(rk.tail, lane);
+  const int pt = __shfl_up_sync(0xffffffffu, rk.tail, 1);
+  rk.lead = lane == 0 || pt != rk.tail;
+  rk.absorbed = lane > 0 && rk.split && pt == rk.head;
+  kfirst = __shfl_sync(0xffffffffu, rk.head, 0);
+  const int klast = __shfl_sync(0xffffffffu, rk.tail, 31);
+  return kfirst == klast;
+}
+
+// Flush one column segment (key qj) of every row: cell (key, qj) gets the
+// sum of the rows with that key when key < qj (each unordered cluster pair
+// once, its lower matrix index first).  Runs inside a lane are summed there;
+// a head run that continues the previous lane's tail is handed to it; the
+// tails are summed over each run of lanes by one segmented reduction.
 template <int PPT>
 __device__ __forceinline__ void flush(const SweepArgs &a, const U128 (&acc)[PPT],
-                                      const int (&krow)[PPT], const unsigned (&same)[PPT],
-                                      const bool (&lead)[PPT], bool uniform, int qj, int lane) {
+                                      const int (&krow)[PPT], const RowKeys &rk, bool uniform,
+                                      int qj, int lane) {
   if (uniform) {  // every row of the warp in one cluster
     if (!(krow[0] < qj)) return;
     U128 v = acc[0];
@@ -279,31 +315,39 @@ __device__ __forceinline__ void flush(const SweepArgs &a, const U128 (&acc)[PPT]
     if (lane == 0) limbs_atomic(&a.sum[LIMBS * tri(krow[0], qj, a.dk)], v);
     return;
   }
+  U128 vh{0ull, 0ull}, vt{0ull, 0ull};
 #pragma unroll
   for (int r = 0; r < PPT; ++r) {
-    const U128 z{0ull, 0ull};
-    const U128 v = seg_sum(krow[r] < qj ? acc[r] : z, same[r]);
-    if (lead[r] && krow[r] < qj) limbs_atomic(&a.sum[LIMBS * tri(krow[r], qj, a.dk)], v);
+    if (krow[r] == rk.tail)
+      u128_add(vt, acc[r]);
+    else if (krow[r] == rk.head)
+      u128_add(vh, acc[r]);
   }
-}
-
-// Row setup shared by both sweeps: keys of the PPT rows, run masks and run
-// leaders; returns whether all rows of the warp share one key.
-template <int PPT>
-__device__ __forceinline__ bool row_keys(const SweepArgs &a, long long r0, int lane,
-                                         int (&krow)[PPT], unsigned (&same)[PPT],
-                                         bool (&lead)[PPT], int &kfirst) {
+  if (rk.split) {
+    // runs wholly inside this lane (a cluster of fewer than PPT points here)
+    int k = -1;
+    U128 m{0ull, 0ull};
 #pragma unroll
-  for (int r = 0; r < PPT; ++r) {
-    const long long row = r0 + r * 32 + lane;
-    krow[r] = row < a.N ? a.didx[a.plab[row]] : INT_MAX;
-    same[r] = seg_mask(krow[r], lane);
-    const int kp = __shfl_up_sync(0xffffffffu, krow[r], 1);
-    lead[r] = lane == 0 || kp != krow[r];
+    for (int r = 0; r < PPT; ++r) {
+      const int kr = krow[r];
+      if (kr == rk.head || kr == rk.tail) continue;
+      if (kr != k) {
+        if (k >= 0 && k < qj) limbs_atomic(&a.sum[LIMBS * tri(k, qj, a.dk)], m);
+        k = kr;
+        m = U128{0ull, 0ull};
+      }
+      u128_add(m, acc[r]);
+    }
+    if (k >= 0 && k < qj) limbs_atomic(&a.sum[LIMBS * tri(k, qj, a.dk)], m);
   }
-  kfirst = __shfl_sync(0xffffffffu, krow[0], 0);
-  const int klast = __shfl_sync(0xffffffffu, krow[PPT - 1], 31);
-  return kfirst == klast;
+  // the next lane's head joins this tail when it continues the run
+  const U128 nh = u128_shfl_down(vh, 1);
+  const bool nabs = __shfl_down_sync(0xffffffffu, rk.absorbed, 1);
+  if (lane < 31 && nabs) u128_add(vt, nh);
+  if (rk.split && !rk.absorbed && rk.head < qj)
+    limbs_atomic(&a.sum[LIMBS * tri(rk.head, qj, a.dk)], vh);
+  vt = seg_sum(vt, rk.same);
+  if (rk.lead && rk.tail < qj) limbs_atomic(&a.sum[LIMBS * tri(rk.tail, qj, a.dk)], vt);
 }
 
 // FP32 sweep, specialised on the true dimension D (rows of stride DP
@@ -327,13 +371,12 @@ __global__ void __launch_bounds__(DS_TPB, HAC_DS_MINB) k_dense_sweep32(SweepArgs
   const long long r0 = bi * TI + (long long)w * 32 * PPT;
   unsigned long long x[NP][D];
   int krow[PPT];
-  unsigned same[PPT];
-  bool lead[PPT];
+  RowKeys rk;
   int kfirst;
-  const bool uniform = row_keys<PPT>(a, r0, lane, krow, same, lead, kfirst);
+  const bool uniform = row_keys<PPT>(a, r0, lane, krow, rk, kfirst);
 #pragma unroll
   for (int h = 0; h < NP; ++h) {
-    const long long ra = r0 + (2 * h) * 32 + lane, rb = ra + 32;
+    const long long ra = r0 + (long long)lane * PPT + 2 * h, rb = ra + 1;
 #pragma unroll
     for (int k = 0; k < D; ++k)
       x[h][k] = f2_pack(ra < a.N ? a.p32[(size_t)ra * DP + k] : 0.f,
@@ -388,10 +431,11 @@ __global__ void __launch_bounds__(DS_TPB, HAC_DS_MINB) k_dense_sweep32(SweepArgs
 #pragma unroll
         for (int r = 0; r < PPT; ++r) u128_add(acc[r], fx_of_f(part[r], a.e));
       }
+      int below = 0;
 #pragma unroll
-      for (int r = 0; r < PPT; ++r)
-        pairs += (unsigned long long)__popc(__ballot_sync(0xffffffffu, krow[r] < qj)) * (ce - cb);
-      flush<PPT>(a, acc, krow, same, lead, uniform, qj, lane);
+      for (int r = 0; r < PPT; ++r) below += krow[r] < qj;
+      pairs += (unsigned long long)__reduce_add_sync(0xffffffffu, (unsigned)below) * (ce - cb);
+      flush<PPT>(a, acc, krow, rk, uniform, qj, lane);
     }
   }
   if (lane == 0 && pairs) atomicAdd(&a.ctr->dense_pp, pairs);
@@ -413,13 +457,12 @@ __global__ void __launch_bounds__(DS_TPB) k_dense_sweep64(SweepArgs a) {
   const long long r0 = bi * TI + (long long)w * 32 * PPT;
   double x[PPT][DP];
   int krow[PPT];
-  unsigned same[PPT];
-  bool lead[PPT];
+  RowKeys rk;
   int kfirst;
-  const bool uniform = row_keys<PPT>(a, r0, lane, krow, same, lead, kfirst);
+  const bool uniform = row_keys<PPT>(a, r0, lane, krow, rk, kfirst);
 #pragma unroll
   for (int r = 0; r < PPT; ++r) {
-    const long long row = r0 + r * 32 + lane;
+    const long long row = r0 + (long long)lane * PPT + r;
 #pragma unroll
     for (int k = 0; k < DP; ++k) x[r][k] = row < a.N ? a.p64[(size_t)row * DP + k] : 0.0;
   }
@@ -454,10 +497,11 @@ __global__ void __launch_bounds__(DS_TPB) k_dense_sweep64(SweepArgs a) {
           u128_add(acc[r], fx_of(sqrt(d2), a.e));
         }
       }
+      int below = 0;
 #pragma unroll
-      for (int r = 0; r < PPT; ++r)
-        pairs += (unsigned long long)__popc(__ballot_sync(0xffffffffu, krow[r] < qj)) * (ce - cb);
-      flush<PPT>(a, acc, krow, same, lead, uniform, qj, lane);
+      for (int r = 0; r < PPT; ++r) below += krow[r] < qj;
+      pairs += (unsigned long long)__reduce_add_sync(0xffffffffu, (unsigned)below) * (ce - cb);
+      flush<PPT>(a, acc, krow, rk, uniform, qj, lane);
     }
   }
   if (lane == 0 && pairs) atomicAdd(&a.ctr->dense_pp, pairs);
