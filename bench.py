@@ -32,15 +32,14 @@ if ROOT not in sys.path:
 METRIC = "HAC wall time & distance evals/s vs HBM roofline at n=1M; serving p50/p99 ms"
 UNIT = "points/s"
 
-# DRAM bytes (read + write) per launch, from one ncu capture of this bench's
-# command (profiles/launches_gmm5d_1m_ward_average.md); valid for the kernels
-# and batching as captured.  Big pairs: one batch launches three evaluation
-# kernels (6.229 + 5.569 + 0.067 MB), the entry is the mean per launch; the
-# search: 628 average + 256 Ward launches.
-TRAFFIC = {
-    ("k_big_eval32", "gmm5d_1m_f32"): 11.865e6 / 3,
-    ("k_query", "gmm5d_1m_f32"): (628 * 30.481e6 + 256 * 27.348e6) / 884,
-}
+# Per-launch DRAM traffic of the kernels other than the sweep is not scaled
+# from small captures (their launches differ too much in size): null.
+TRAFFIC = {}
+# DRAM bytes (read + write) per point pair of the dense sweep, from a
+# small-case ncu capture of the current kernel (profiles/
+# k_dense_sweep32_gmm5d_100k.md: 375.4 MB for 4.99e9 pairs); the bench scales
+# it by the pairs of a full launch
+SWEEP_DRAM_PER_PAIR = 375.4e6 / 4.995e9
 
 
 def _peaks():
@@ -659,7 +658,10 @@ def main():
                             "achieved": s_pairs * flops_per_pair / (s_ms / 1e3) / 1e12
                             if s_ms else 0.0,
                             "peak": fp32_tflops, "unit": "TFLOP/s",
-                            "traffic": TRAFFIC.get(("k_dense_sweep32", args.workload))},
+                            "traffic": SWEEP_DRAM_PER_PAIR * s_pairs / max(s_launch, 1)
+                            if s_launch else None,
+                            "traffic_note": "DRAM bytes per point pair of a small-case ncu "
+                                            "capture, times the pairs of a launch"},
     }
     for k in kern.values():
         k["frac"] = k["achieved"] / k["peak"] if k["peak"] else 0.0
