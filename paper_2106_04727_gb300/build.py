@@ -47,16 +47,33 @@ def _stale() -> bool:
     return any(os.path.getmtime(p) > t for p in deps)
 
 
-def build(force: bool = False, verbose: bool = False, ptxas_v: bool = False) -> str:
-    """Compile and link libhac.so if any source is newer than it."""
-    if not force and not _stale():
+def variant_dir(defines) -> str:
+    """Build folder of a compiled variant (the tuner's tile shapes)."""
+    tag = "_".join(f"{k}-{v}" for k, v in sorted(defines.items()))
+    return os.path.join(BUILD, "variants", tag)
+
+
+def build(force: bool = False, verbose: bool = False, ptxas_v: bool = False,
+          defines=None) -> str:
+    """Compile and link libhac.so if any source is newer than it.  With
+    `defines` (macro -> value: the tile shapes of the tuner), a variant is
+    built in its own folder and its path returned; the default library is
+    untouched."""
+    out_dir = variant_dir(defines) if defines else BUILD
+    lib = os.path.join(out_dir, "libhac.so")
+    if not force and not defines and not _stale():
         return LIB
-    os.makedirs(BUILD, exist_ok=True)
+    if defines and not force and os.path.exists(lib) and \
+            all(os.path.getmtime(p) <= os.path.getmtime(lib)
+                for p in sources() + glob.glob(os.path.join(CSRC, "*.cuh"))):
+        return lib
+    os.makedirs(out_dir, exist_ok=True)
     nv = nvcc()
     extra = ["-Xptxas", "-v"] if ptxas_v else []
+    extra += [f"-D{k}={v}" for k, v in sorted((defines or {}).items())]
 
     def compile_one(src):
-        obj = os.path.join(BUILD, os.path.basename(src)[:-3] + ".o")
+        obj = os.path.join(out_dir, os.path.basename(src)[:-3] + ".o")
         cmd = [nv, *_flags(extra), "-c", src, "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
@@ -67,13 +84,13 @@ def build(force: bool = False, verbose: bool = False, ptxas_v: bool = False) -> 
 
     with ThreadPoolExecutor(max_workers=max(1, min(16, os.cpu_count() or 1, len(sources())))) as ex:
         objs = list(ex.map(compile_one, sources()))
-    tmp = LIB + f".{os.getpid()}.tmp"
+    tmp = lib + f".{os.getpid()}.tmp"
     r = subprocess.run([nv, *ARCH, "-shared", "-o", tmp, *objs],
                        capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 PROBE_SRC = os.path.join(HERE, "probe", "fma_probe.cu")

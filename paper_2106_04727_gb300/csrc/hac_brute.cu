@@ -21,8 +21,15 @@ namespace hacg {
 
 namespace {
 
-constexpr int BR_T = 256;  // terminals per CTA
-constexpr int BR_C = 128;  // candidate records per staged tile
+// tile shape (the tuner's compiled variants override these)
+#ifndef HAC_BR_T
+#define HAC_BR_T 256
+#endif
+#ifndef HAC_BR_C
+#define HAC_BR_C 128
+#endif
+constexpr int BR_T = HAC_BR_T;  // terminals per CTA
+constexpr int BR_C = HAC_BR_C;  // candidate records per staged tile
 
 template <int LK, int DP>
 struct BruteTerm {

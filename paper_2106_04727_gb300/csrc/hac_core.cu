@@ -493,7 +493,10 @@ struct CEntry {
   double val;
 };
 
-constexpr int CM_WARPS = 2;  // warps per block of k_cache_merge (5 * slots entries each)
+#ifndef HAC_CM_WARPS
+#define HAC_CM_WARPS 2
+#endif
+constexpr int CM_WARPS = HAC_CM_WARPS;  // warps per block of k_cache_merge (5 * slots entries each)
 
 // look for neighbour `g` in a warp-local list
 __device__ __forceinline__ int clist_find(const CEntry *L, int n, int g) {

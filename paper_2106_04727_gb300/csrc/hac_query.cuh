@@ -53,7 +53,15 @@ namespace hacg {
 
 namespace {
 
-constexpr int QWARPS = 4;          // warps per block
+// block shape of the search (the tuner's compiled variants override these)
+#ifndef HAC_QWARPS
+#define HAC_QWARPS 4
+#endif
+#ifndef HAC_QMINB
+#define HAC_QMINB 1
+#endif
+constexpr int QWARPS = HAC_QWARPS;  // warps per block
+constexpr int QMINB = HAC_QMINB;    // resident blocks per SM the register budget must allow
 constexpr int STK = 256;           // per-warp stack, >= 1 + 31 * (MAXLEV - 1)
 constexpr float EPS = 1e-5f;       // relative slack of the FP32 bound tests
 constexpr long long SMALLP = 32;   // pairs of at most this many point pairs run per lane
@@ -61,6 +69,18 @@ constexpr float U32 = 5.9604645e-8f;  // 2^-24
 constexpr unsigned long long KINF = 0x7ff0000000000000ull;  // bits of +inf
 
 enum { M_F64 = 0, M_F32 = 1, M_RECHECK = 2 };
+
+// The warp-wide pair evaluations, which a search takes for its larger
+// candidates only, are kept out of line (HAC_Q_OUTLINE=1), so that their
+// registers do not count against the scan of tree nodes and leaves.
+#ifndef HAC_Q_OUTLINE
+#define HAC_Q_OUTLINE 0
+#endif
+#if HAC_Q_OUTLINE
+#define HAC_Q_COLD __noinline__
+#else
+#define HAC_Q_COLD
+#endif
 
 __device__ __forceinline__ unsigned long long kbits(double k) {
   return (unsigned long long)__double_as_longlong(k);
@@ -220,7 +240,7 @@ __device__ double eval64_lane(const double *P, int sa, int na, int sb, int nb) {
 // cluster's points, each lane loops over the smaller one (broadcast loads).
 // Returns +inf once a partial result proves D > bound (D units).
 template <int LK, int DP>
-__device__ double eval64_warp(const double *P, int sa, int na, int sb, int nb, double bound,
+HAC_Q_COLD __device__ double eval64_warp(const double *P, int sa, int na, int sb, int nb, double bound,
                               int lane, unsigned long long &pp) {
   int sL = sa, nL = na, sS = sb, nS = nb;
   if (nb > na) {
@@ -355,7 +375,7 @@ __device__ float eval32_warp_h(const float *P, int sa, int na, int sb, int nb, f
 
 // eval32_warp_h for the instance's true dimension d (rows have stride DP)
 template <int LK, int DP>
-__device__ float eval32_warp(const float *P, int d, int sa, int na, int sb, int nb, float bound,
+HAC_Q_COLD __device__ float eval32_warp(const float *P, int d, int sa, int na, int sb, int nb, float bound,
                              float delta, float rho, int lane, unsigned long long &pp) {
   const int H = (d + 1) >> 1;
   if (DP == 2) return eval32_warp_h<LK, 1, DP>(P, sa, na, sb, nb, bound, delta, rho, lane, pp);
@@ -1056,7 +1076,7 @@ __device__ void tally(const Searcher<LK, DP, MODE> &S, unsigned long long *c) {
 }
 
 template <int LK, int DP, int PREC>
-__global__ void __launch_bounds__(QWARPS * 32) k_query(QueryArgs a) {
+__global__ void __launch_bounds__(QWARPS * 32, QMINB) k_query(QueryArgs a) {
   __shared__ uint32_t s_node[QWARPS][STK];
   __shared__ float s_lb[QWARPS][STK];
   const int lane = threadIdx.x & 31;

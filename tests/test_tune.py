@@ -49,3 +49,38 @@ def test_grid_environment_and_best(monkeypatch, capsys):
     best = lines[-1]["best"]
     assert (best["HAC_BIG_PAIRS"], best["HAC_WARP_BUDGET"]) == (65536, 131072)
     assert best["ms"] == 5.0 and lines[-1]["n"] == 5
+
+
+def test_shape_grid_builds_and_times_each_variant(monkeypatch, capsys):
+    """--shapes: one compiled variant per combination of the macro values,
+    each timed in a child process; the fastest is reported."""
+    import subprocess
+    import sys
+
+    from paper_2106_04727_gb300 import build
+
+    assert tune.shape_grid("HAC_DS_PPT8=2,4;HAC_QWARPS=4") == [
+        {"HAC_DS_PPT8": 2, "HAC_QWARPS": 4}, {"HAC_DS_PPT8": 4, "HAC_QWARPS": 4}]
+    try:
+        tune.shape_grid("HAC_NOT_A_SHAPE=1")
+        raise AssertionError("an unknown macro must be refused")
+    except ValueError:
+        pass
+    built, cmds = [], []
+    monkeypatch.setattr(build, "build", lambda defines=None, **k: built.append(defines) or
+                        f"/v/{defines['HAC_DS_MINB']}/libhac.so")
+    ms = {"/v/2/libhac.so": 8.0, "/v/3/libhac.so": 6.5}
+
+    def run(cmd, capture_output, text):
+        cmds.append(cmd)
+        lib = cmd[cmd.index("--lib") + 1]
+        out = json.dumps({"best": {"ms": ms[lib], "ms_search": 1.0}})
+        return subprocess.CompletedProcess(cmd, 0, stdout=out + "\n", stderr="")
+
+    monkeypatch.setattr(subprocess, "run", run)
+    tune.main(["--shapes", "HAC_DS_MINB=2,3", "--workload", "gmm5d_1m_f32", "--n", "9"])
+    lines = [json.loads(x) for x in capsys.readouterr().out.splitlines()]
+    assert built == [{"HAC_DS_MINB": 2}, {"HAC_DS_MINB": 3}]
+    assert all(c[0] == sys.executable and "--lib" in c and c[c.index("--n") + 1] == "9"
+               for c in cmds)
+    assert lines[-1]["best"] == {"HAC_DS_MINB": 3, "ms": 6.5, "ms_search": 1.0}
