@@ -60,7 +60,10 @@ typedef enum {
   HAC_PREC_F32_RECHECK = 1  /* bulk distances in FP32; candidates within the
                                stated FP32 error bound of the minimum are
                                re-scored in FP64, so nearest neighbours (and
-                               hence the tree) are the FP64 ones */
+                               hence the tree) are the FP64 ones.  Ward and
+                               avg-2 tree searches (O(d) closed forms) run in
+                               FP64 in both modes; their exhaustive scans
+                               (d > 8) use the FP32 bulk */
 } hac_precision;
 
 /* One dendrogram node: clusters cid_a < cid_b merged at `height` into a

@@ -10,7 +10,7 @@
 //                               active order, new terminal list, new segment
 //                               offsets; k_relayout moves points so every
 //                               cluster stays one contiguous segment;
-//                               k_tree_*: rebuild the range-query tree
+//                               k_tg_*: rebuild the range-query tree
 #include "hac_impl.cuh"
 
 #include <algorithm>
@@ -231,7 +231,8 @@ __global__ void k_morton(const T *X, int64_t n, int d, MortonParams mp, uint64_t
 }
 
 template <typename T>
-__global__ void k_layout(State s, const T *X, const int32_t *perm, MortonParams ctr_) {
+__global__ void k_layout(State s, const T *X, const int32_t *perm, const uint64_t *skey,
+                         MortonParams ctr_) {
   // ctr_.lo holds the recentring offset
   const int64_t n = s.n;
   const int d = s.d, dp = s.dp;
@@ -279,6 +280,7 @@ __global__ void k_layout(State s, const T *X, const int32_t *perm, MortonParams 
     s.qinst[p] = 0;
     s.order[0][p] = i;
     s.pos[i] = (int32_t)p;
+    s.mkey[i] = skey[p];
     s.term[p] = i;
   }
 }
@@ -299,61 +301,172 @@ __global__ void k_inst_set(State s, int slot, float slack, float scale, float dp
 // ---------------------------------------------------------------------------
 // range-query tree
 // ---------------------------------------------------------------------------
-template <int DP>
-__global__ void k_tree_leaf(State s, const int32_t *order, int K) {
-  const int lane = threadIdx.x & 31;
-  const int cnt = level_count(K, 0);
-  for (int j = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; j < cnt;
-       j += (gridDim.x * blockDim.x) >> 5) {
-    const int idx = j * FAN + lane;
-    const bool v = idx < K;
-    const size_t c = v ? (size_t)idx : 0;  // position-ordered records
-    int nm = v ? s.qsz[c] : INT_MAX;
-    int il = v ? s.qinst[c] : INT_MAX, ih = v ? s.qinst[c] : INT_MIN;
-    for (int o = 16; o; o >>= 1) {
-      nm = min(nm, __shfl_xor_sync(0xffffffffu, nm, o));
-      il = min(il, __shfl_xor_sync(0xffffffffu, il, o));
-      ih = max(ih, __shfl_xor_sync(0xffffffffu, ih, o));
+// Level L cuts the m elements below it (positions for L = 0, level-(L-1)
+// nodes above) into runs of at most 32 consecutive elements.  An element's
+// key is 96 bits: its instance's admission number, then the Morton key of its
+// (first) position at layout; keys never decrease along the order.  A run is
+// the largest cell of that key hierarchy (the elements sharing a key prefix)
+// holding at most 32 elements, so sibling boxes are those of disjoint Morton
+// cells instead of fixed slices that straddle cell boundaries.  Element i's
+// cell has prefix length l* = 1 + c, c being the 32nd largest common-prefix
+// length between i and its 64 neighbours i - 32 .. i + 32 (a cell of more
+// than 32 elements has at least 32 of them in that window); i starts a run
+// iff it shares at most c leading bits with i - 1.  Cells nest, so the runs
+// partition the elements.  More than 32 equal keys are also cut every 32
+// positions.  A level whose runs would exceed its capacity (tree_caps), or
+// whose keys are out of order, is cut into fixed runs of 32 instead.
+constexpr int TG_H = 32;              // window half-width
+constexpr int TG_W = TPB + 2 * TG_H;  // keys staged per block
+
+// keys of elements [b0 - 32, b0 + TPB + 32) into shared memory (instance -1:
+// no element); level 0 reads them through the order
+__device__ void tg_stage(uint64_t *sk, int32_t *sq, const uint64_t *ekey, const int32_t *eorder,
+                         const int32_t *einst, int m, int b0) {
+  for (int t = threadIdx.x; t < TG_W; t += TPB) {
+    const int i = b0 - TG_H + t;
+    const bool v = i >= 0 && i < m;
+    sk[t] = v ? ekey[eorder ? eorder[i] : i] : 0ull;
+    sq[t] = v ? einst[i] : -1;
+  }
+  __syncthreads();
+}
+
+// common-prefix length of the 96-bit keys at staged slots u and w (-1: none)
+__device__ __forceinline__ int tg_cpl(const uint64_t *sk, const int32_t *sq, int u, int w) {
+  if (sq[w] < 0) return -1;
+  if (sq[u] != sq[w]) return __clz(sq[u] ^ sq[w]);
+  const uint64_t x = sk[u] ^ sk[w];
+  return x ? 32 + __clzll((long long)x) : 96;
+}
+
+// does element i (staged at slot t + 32) start a run?
+__device__ bool tg_start(const uint64_t *sk, const int32_t *sq, int i, int t) {
+  if (i == 0) return true;
+  const int u = t + TG_H;
+  const int left1 = tg_cpl(sk, sq, u, u - 1);
+  // the 32nd largest of the 64 neighbour lengths: both sides fall off
+  // monotonically, so merge them from the nearest outwards
+  int a = 1, b = 1, lv = left1, rv = tg_cpl(sk, sq, u, u + 1), c = -1;
+  for (int k = 0; k < TG_H; ++k) {
+    if (lv >= rv) {
+      c = lv;
+      ++a;
+      lv = a <= TG_H ? tg_cpl(sk, sq, u, u - a) : -2;
+    } else {
+      c = rv;
+      ++b;
+      rv = b <= TG_H ? tg_cpl(sk, sq, u, u + b) : -2;
     }
-    const int node = s.lvl_base[0] + j;
-    if (lane == 0) {
-      s.ninlo[node] = il;
-      s.ninhi[node] = ih;
+  }
+  if (c >= 96) return left1 < 96 || (i % FAN) == 0;  // more than 32 equal keys
+  return left1 <= c;
+}
+
+// elements of level L and whether the build stopped below it (a lower level
+// already has at most 32 nodes)
+__device__ __forceinline__ bool tg_idle(const State &s, int L) {
+  const int top = s.tinfo[TI_TOP];
+  return top != 0 && top - 1 < L;
+}
+
+// per-block counts of run starts; flags the level if its keys are out of order
+__global__ void k_tg_count(State s, int L, const uint64_t *ekey, const int32_t *eorder,
+                           const int32_t *einst, int K) {
+  __shared__ uint64_t sk[TG_W];
+  __shared__ int32_t sq[TG_W];
+  if (tg_idle(s, L)) return;
+  const int m = L ? s.tinfo[L - 1] : K;
+  if ((int)blockIdx.x >= cdiv(m, TPB)) return;
+  const int b0 = blockIdx.x * TPB;
+  tg_stage(sk, sq, ekey, eorder, einst, m, b0);
+  const int i = b0 + threadIdx.x;
+  int f = 0;
+  if (i < m) {
+    f = tg_start(sk, sq, i, threadIdx.x);
+    const int u = threadIdx.x + TG_H;
+    if (i > 0 && (sq[u - 1] > sq[u] || (sq[u - 1] == sq[u] && sk[u - 1] > sk[u])))
+      atomicOr(&s.tinfo[TI_FIXED], 1 << L);
+  }
+  f = block_sum(f);
+  if (threadIdx.x == 0) s.bsum[blockIdx.x] = f;
+}
+
+// one block: scan of the block counts; the level's node count, its end
+// entry, and the choice between the Morton runs and fixed runs of 32
+__global__ void k_tg_top(State s, int L, int K, int cap) {
+  if (tg_idle(s, L)) return;
+  const int m = L ? s.tinfo[L - 1] : K;
+  const int nb = cdiv(m, TPB);
+  const int per = cdiv(nb, TPB);
+  const int b0 = threadIdx.x * per;
+  int sum = 0;
+  for (int i = 0; i < per; ++i)
+    if (b0 + i < nb) sum += s.bsum[b0 + i];
+  int tot;
+  int pre = block_excl_scan(sum, &tot);
+  for (int i = 0; i < per; ++i)
+    if (b0 + i < nb) {
+      const int v = s.bsum[b0 + i];
+      s.bsum[b0 + i] = pre;
+      pre += v;
     }
-#pragma unroll
-    for (int k = 0; k < DP; ++k) {
-      float lo = v ? s.q32[c * DP + k] : INFINITY;
-      float hi = v ? s.q32[c * DP + k] : -INFINITY;
-      float hm = v ? s.qbhi[c * DP + k] : INFINITY;
-      float lm = v ? s.qblo[c * DP + k] : -INFINITY;
-      for (int o = 16; o; o >>= 1) {
-        lo = fminf(lo, __shfl_xor_sync(0xffffffffu, lo, o));
-        hi = fmaxf(hi, __shfl_xor_sync(0xffffffffu, hi, o));
-        hm = fminf(hm, __shfl_xor_sync(0xffffffffu, hm, o));
-        lm = fmaxf(lm, __shfl_xor_sync(0xffffffffu, lm, o));
-      }
-      if (lane == k) {
-        s.nclo[(size_t)node * DP + k] = lo;
-        s.nchi[(size_t)node * DP + k] = hi;
-        s.nhmin[(size_t)node * DP + k] = hm;
-        s.nlmax[(size_t)node * DP + k] = lm;
-      }
-    }
-    if (lane == 0) s.nnmin[node] = nm;
+  if (threadIdx.x == 0) {
+    const bool fixed = ((s.tinfo[TI_FIXED] >> L) & 1) || tot > cap;
+    const int mL = fixed ? cdiv(m, FAN) : tot;
+    s.tinfo[L] = mL;
+    if (fixed) s.tinfo[TI_FIXED] |= 1 << L;
+    s.nch[s.chb[L] + mL] = m;
+    if (mL <= FAN) s.tinfo[TI_TOP] = L + 1;
   }
 }
 
+// first child of every node of level L, the node's key (its first child's),
+// and for L = 0 the bucket of every position
+__global__ void k_tg_write(State s, int L, const uint64_t *ekey, const int32_t *eorder,
+                           const int32_t *einst, uint64_t *okey, int32_t *oinst, int K) {
+  __shared__ uint64_t sk[TG_W];
+  __shared__ int32_t sq[TG_W];
+  if (tg_idle(s, L)) return;
+  const int m = L ? s.tinfo[L - 1] : K;
+  if ((int)blockIdx.x >= cdiv(m, TPB)) return;
+  const bool fixed = (s.tinfo[TI_FIXED] >> L) & 1;
+  const int b0 = blockIdx.x * TPB;
+  tg_stage(sk, sq, ekey, eorder, einst, m, b0);
+  const int i = b0 + threadIdx.x;
+  const int f = i < m && (fixed ? (i % FAN) == 0 : tg_start(sk, sq, i, threadIdx.x));
+  int tot;
+  const int idx = block_excl_scan(f, &tot) + (fixed ? b0 / FAN : s.bsum[blockIdx.x]);
+  if (f) {
+    s.nch[s.chb[L] + idx] = i;
+    okey[idx] = sk[threadIdx.x + TG_H];
+    oinst[idx] = sq[threadIdx.x + TG_H];
+  }
+  if (L == 0 && i < m) s.pbkt[i] = idx + f - 1;
+}
+
+// boxes, least cluster size and instance range of every node of level L
+// (one warp per node, one lane per child)
 template <int DP>
-__global__ void k_tree_up(State s, int K, int L) {
+__global__ void k_tg_box(State s, int L, int K) {
+  if (tg_idle(s, L)) return;
   const int lane = threadIdx.x & 31;
-  const int cnt = level_count(K, L), ccnt = level_count(K, L - 1);
+  const int cnt = s.tinfo[L];
+  const int mb = L ? s.tinfo[L - 1] : K;  // children of this level
+  const int *nch = s.nch + s.chb[L];
   for (int j = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; j < cnt;
        j += (gridDim.x * blockDim.x) >> 5) {
-    const int ch = j * FAN + lane;
-    const bool v = ch < ccnt;
-    const int cn = s.lvl_base[L - 1] + (v ? ch : 0);
-    int nm = v ? s.nnmin[cn] : INT_MAX;
-    int il = v ? s.ninlo[cn] : INT_MAX, ih = v ? s.ninhi[cn] : INT_MIN;
+    const int c0 = nch[j];
+    int nc = nch[j + 1] - c0;
+    if (nc < 1 || nc > FAN) {
+      if (lane == 0) atomicOr(&s.ctr->err, ERR_TREE);
+      nc = max(1, min(nc, FAN));
+    }
+    const bool v = lane < nc && c0 + lane < mb;
+    // a child: a position-ordered record (L = 0) or a node of level L - 1
+    const size_t c = (size_t)(L ? s.lvl_base[L - 1] : 0) + (size_t)(v ? c0 + lane : c0);
+    int nm = v ? (L ? s.nnmin[c] : s.qsz[c]) : INT_MAX;
+    int il = v ? (L ? s.ninlo[c] : s.qinst[c]) : INT_MAX;
+    int ih = v ? (L ? s.ninhi[c] : s.qinst[c]) : INT_MIN;
     for (int o = 16; o; o >>= 1) {
       nm = min(nm, __shfl_xor_sync(0xffffffffu, nm, o));
       il = min(il, __shfl_xor_sync(0xffffffffu, il, o));
@@ -363,13 +476,22 @@ __global__ void k_tree_up(State s, int K, int L) {
     if (lane == 0) {
       s.ninlo[node] = il;
       s.ninhi[node] = ih;
+      s.nnmin[node] = nm;
     }
 #pragma unroll
     for (int k = 0; k < DP; ++k) {
-      float lo = v ? s.nclo[(size_t)cn * DP + k] : INFINITY;
-      float hi = v ? s.nchi[(size_t)cn * DP + k] : -INFINITY;
-      float hm = v ? s.nhmin[(size_t)cn * DP + k] : INFINITY;
-      float lm = v ? s.nlmax[(size_t)cn * DP + k] : -INFINITY;
+      float lo, hi, hm, lm;
+      if (L) {
+        lo = v ? s.nclo[c * DP + k] : INFINITY;
+        hi = v ? s.nchi[c * DP + k] : -INFINITY;
+        hm = v ? s.nhmin[c * DP + k] : INFINITY;
+        lm = v ? s.nlmax[c * DP + k] : -INFINITY;
+      } else {
+        lo = v ? s.q32[c * DP + k] : INFINITY;
+        hi = v ? s.q32[c * DP + k] : -INFINITY;
+        hm = v ? s.qbhi[c * DP + k] : INFINITY;
+        lm = v ? s.qblo[c * DP + k] : -INFINITY;
+      }
       for (int o = 16; o; o >>= 1) {
         lo = fminf(lo, __shfl_xor_sync(0xffffffffu, lo, o));
         hi = fmaxf(hi, __shfl_xor_sync(0xffffffffu, hi, o));
@@ -383,7 +505,6 @@ __global__ void k_tree_up(State s, int K, int L) {
         s.nlmax[(size_t)node * DP + k] = lm;
       }
     }
-    if (lane == 0) s.nnmin[node] = nm;
   }
 }
 
@@ -908,6 +1029,24 @@ void free_all(hac_ctx *h) {
 
 int pad_dim(int d) { return d <= 2 ? 2 : d <= 4 ? 4 : d <= 8 ? 8 : 16; }
 
+// Offsets of every tree level in the node arrays (lvl_base) and in the
+// first-child array (chb, one end entry per level), for up to n clusters.
+void tree_layout(State &s, int n, int *nodes, int *chs) {
+  int cap[MAXLEV + 1];
+  const int nl = tree_caps(n, cap);
+  int base = 0, cb = 0;
+  for (int L = 0; L <= MAXLEV; ++L) {
+    s.lvl_base[L] = base;
+    s.chb[L] = cb;
+    if (L < nl) {
+      base += cap[L];
+      cb += cap[L] + 1;
+    }
+  }
+  *nodes = base;
+  *chs = cb;
+}
+
 int alloc_state(hac_ctx *h) {
   State &s = h->s;
   const int64_t n = h->n;
@@ -975,13 +1114,8 @@ int alloc_state(hac_ctx *h) {
   A(s.m_round, n);
   A(s.m_h, n);
   // tree levels sized for K = n
-  int base = 0;
-  const int nlev = tree_levels((int)n);
-  for (int L = 0; L <= MAXLEV; ++L) {
-    s.lvl_base[L] = base;
-    if (L < nlev) base += level_count((int)n, L);
-  }
-  h->nlev_max = nlev;
+  int base = 0, chbase = 0;
+  tree_layout(s, (int)n, &base, &chbase);
   A(s.nclo, (int64_t)base * dp);
   A(s.nchi, (int64_t)base * dp);
   A(s.nhmin, (int64_t)base * dp);
@@ -989,6 +1123,10 @@ int alloc_state(hac_ctx *h) {
   A(s.nnmin, base);
   A(s.ninlo, base);
   A(s.ninhi, base);
+  A(s.nch, chbase);
+  A(s.pbkt, n);
+  A(s.mkey, n);
+  A(s.tinfo, TI_SIZE);
   A(s.bsum, 3 * (int64_t)cdiv(n, TPB) + 3);
   A(s.ctr, 1);
   for (int b = 0; b < 2; ++b) {
@@ -1007,11 +1145,22 @@ int alloc_state(hac_ctx *h) {
 
 template <int DP>
 int build_tree_dp(hac_ctx *h, const int32_t *order, int K, cudaStream_t st) {
-  const int nlev = tree_levels(K);
-  h->launches += nlev;
-  k_tree_leaf<DP><<<grid_for((int64_t)level_count(K, 0) * 32, TPB), TPB, 0, st>>>(h->s, order, K);
-  for (int L = 1; L < nlev; ++L)
-    k_tree_up<DP><<<grid_for((int64_t)level_count(K, L) * 32, TPB), TPB, 0, st>>>(h->s, K, L);
+  State &s = h->s;
+  int cap[MAXLEV + 1];
+  const int nl = tree_caps(K, cap);
+  CK(cudaMemsetAsync(s.tinfo, 0, TI_SIZE * sizeof(int32_t), st));
+  // levels above the first one of at most 32 nodes return at once
+  for (int L = 0; L < nl; ++L) {
+    const int nb = cdiv(L ? cap[L - 1] : K, TPB);  // blocks for the most elements possible
+    const uint64_t *ek = L ? h->keys[(L - 1) & 1] : s.mkey;
+    const int32_t *eo = L ? nullptr : order;
+    const int32_t *ei = L ? h->vals[(L - 1) & 1] : s.qinst;
+    k_tg_count<<<nb, TPB, 0, st>>>(s, L, ek, eo, ei, K);
+    k_tg_top<<<1, TPB, 0, st>>>(s, L, K, cap[L]);
+    k_tg_write<<<nb, TPB, 0, st>>>(s, L, ek, eo, ei, h->keys[L & 1], h->vals[L & 1], K);
+    k_tg_box<DP><<<grid_for((int64_t)cap[L] * 32, TPB), TPB, 0, st>>>(s, L, K);
+  }
+  h->launches += 4 * nl + 1;
   CK(cudaGetLastError());
   return HAC_OK;
 }
@@ -1107,7 +1256,7 @@ int init_layout(hac_ctx *h, cudaStream_t st) {
   s.cur = 0;
   s.dense = 0;
   s.dk = 0;
-  k_layout<T><<<grid_for(n, TPB), TPB, 0, st>>>(s, X, h->vals[sc], ctrp);
+  k_layout<T><<<grid_for(n, TPB), TPB, 0, st>>>(s, X, h->vals[sc], h->keys[sc], ctrp);
   CK(cudaGetLastError());
   Counters c{};
   c.nterm = (int)n;
@@ -1253,7 +1402,13 @@ void fill_query_args(hac_ctx *h, QueryArgs &qa, int round, int K, int nterm) {
   qa.islack = s.islack;
   qa.iscale = s.iscale;
   qa.idpts = s.idpts;
-  for (int L = 0; L <= MAXLEV; ++L) qa.lvl_base[L] = s.lvl_base[L];
+  qa.nch = s.nch;
+  qa.pbkt = s.pbkt;
+  qa.tinfo = s.tinfo;
+  for (int L = 0; L <= MAXLEV; ++L) {
+    qa.lvl_base[L] = s.lvl_base[L];
+    qa.chb[L] = s.chb[L];
+  }
   qa.Ekey = s.Ekey;
   qa.Ecid = s.Ecid;
   qa.ctr = s.ctr;
@@ -1316,6 +1471,15 @@ bool use_cand_avg(const hac_ctx *h) {
   return s.dp == 16;
 }
 
+// Precision of the tree search.  Ward and avg-2 distances are O(d) closed
+// forms of the cluster records, so an FP64 evaluation costs no more than the
+// FP32 bound test and needs no re-score pass: their tree searches run in FP64
+// in both modes (measured faster on every workload tried); the FP32 mode
+// keeps its FP32 bulk for the exhaustive scans and for complete / average.
+int query_prec(const State &s) {
+  return closed_form(s.linkage) ? (int)HAC_PREC_F64 : s.prec;
+}
+
 // One round of Algorithm 1 over the current terminal list: the searches (with
 // big pairs handed to the whole GPU and the deferring searches re-run), the
 // chain update, the R-NN filter, the merges, the cache update, the compaction
@@ -1362,7 +1526,7 @@ int round_step(hac_ctx *h, cudaStream_t st, int round, int K, int nterm, RoundCt
   } else if (brute) {
     CK(launch_brute(qa, s.dp, st));
   } else {
-    CK(launch_query(qa, s.dp, s.prec, st));
+    CK(launch_query(qa, s.dp, query_prec(s), st));
   }
   EVREC(ctl.eq1);
   if (!dense) {
@@ -1419,7 +1583,7 @@ int round_step(hac_ctx *h, cudaStream_t st, int round, int K, int nterm, RoundCt
     qa.pend_out = s.pend[(it & 1) ^ 1];
     qa.defer = it < 4 ? 1 : 0;
     EVREC(ctl.eq0);
-    CK(launch_query(qa, s.dp, s.prec, st));
+    CK(launch_query(qa, s.dp, query_prec(s), st));
     EVREC(ctl.eq1);
     ++ctl.qlaunch;
     k_cache_insert<<<grid_for((int64_t)device_sms() * 8 * TPB, TPB), TPB, 0, st>>>(s);
@@ -1931,13 +2095,8 @@ bool carve_state(hac_ctx &h, Carver &cv) {
   cv.take(&s.m_size, n);
   cv.take(&s.m_round, n);
   cv.take(&s.m_h, n);
-  int base = 0;
-  const int nlev = tree_levels((int)n);
-  for (int L = 0; L <= MAXLEV; ++L) {
-    s.lvl_base[L] = base;
-    if (L < nlev) base += level_count((int)n, L);
-  }
-  h.nlev_max = nlev;
+  int base = 0, chbase = 0;
+  tree_layout(s, (int)n, &base, &chbase);
   cv.take(&s.nclo, (size_t)base * dp);
   cv.take(&s.nchi, (size_t)base * dp);
   cv.take(&s.nhmin, (size_t)base * dp);
@@ -1945,6 +2104,10 @@ bool carve_state(hac_ctx &h, Carver &cv) {
   cv.take(&s.nnmin, (size_t)base);
   cv.take(&s.ninlo, (size_t)base);
   cv.take(&s.ninhi, (size_t)base);
+  cv.take(&s.nch, (size_t)chbase);
+  cv.take(&s.pbkt, n);
+  cv.take(&s.mkey, n);
+  cv.take(&s.tinfo, TI_SIZE);
   cv.take(&s.bsum, 3 * (size_t)cdiv(n, TPB) + 3);
   cv.take(&s.ctr, 1);
   for (int b = 0; b < 2; ++b) {

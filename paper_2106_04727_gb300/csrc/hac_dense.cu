@@ -193,12 +193,13 @@ __device__ __forceinline__ double mag(double x) { return fabs(x); }
 constexpr int DS_TPB = 256;  // threads per tile
 constexpr int DS_CH = 256;   // columns per staged chunk
 // FP32 sweep shape: rows per thread for d <= 8 (2 above), and the resident
-// tiles per SM the register budget is cut for (measured best: 4 and 3)
+// tiles per SM the register budget is cut for (the shape tuner's best at
+// 10^6 points, 5-D: 4 and 4)
 #ifndef HAC_DS_PPT8
 #define HAC_DS_PPT8 4
 #endif
 #ifndef HAC_DS_MINB
-#define HAC_DS_MINB 3
+#define HAC_DS_MINB 4
 #endif
 struct SweepArgs {
   const float *p32;

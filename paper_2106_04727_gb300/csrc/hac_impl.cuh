@@ -135,7 +135,6 @@ struct hac_ctx {
   int32_t *vals[2] = {nullptr, nullptr};
   int32_t *hist = nullptr, *hbs = nullptr;
   unsigned long long *bb = nullptr;  // 2 x MAXD bbox words
-  int nlev_max = 1;
   int cache_alloc_slots = 0;  // slots per cluster the cache tables were allocated for
   int64_t lay_n = 0;          // points in the current layout (all n for one instance)
   // pairs of at least this many point pairs go to the GPU-wide evaluation

@@ -12,8 +12,8 @@
 namespace hacg {
 
 constexpr int MAXD = 16;     // largest supported dimension
-constexpr int FAN = 32;      // range-query tree fan-out (one warp lane per child)
-constexpr int MAXLEV = 8;    // 32^8 > 2^31 > any n
+constexpr int FAN = 32;      // range-query tree: at most this many children per node
+constexpr int MAXLEV = 10;   // tree levels of any n < 2^31 (tree_caps)
 constexpr unsigned long long PRED_EMPTY = ~0ull;
 
 // Device-side counters of one instance.
@@ -35,7 +35,7 @@ struct Counters {
   unsigned long long dense_pp, dense_rq_pp;  // dense phase: sweep / re-score point pairs
 };
 
-enum : int32_t { ERR_NONFINITE = 1, ERR_NO_NN = 2, ERR_STACK = 4, ERR_WINDOW = 8 };
+enum : int32_t { ERR_NONFINITE = 1, ERR_NO_NN = 2, ERR_STACK = 4, ERR_WINDOW = 8, ERR_TREE = 16 };
 
 constexpr unsigned long long CKEY_EMPTY = ~0ull;
 constexpr long long CACHE_MIN_PAIRS = 64;  // smaller pairs are cheaper to recompute
@@ -156,11 +156,21 @@ struct State {
   // dendrogram records
   int32_t *m_a, *m_b, *m_size, *m_round;
   double *m_h;
-  // range-query tree: level L node j lives at index lvl_base[L] + j
+  // range-query tree, rebuilt every round over the active clusters in
+  // position order: a level-0 node (a bucket) is a run of at most 32
+  // positions, a level-L node a run of at most 32 level-(L-1) nodes, each run
+  // one cell of the Morton-key hierarchy where the data allow (tree_caps,
+  // build_tree).  Level L node j lives at index lvl_base[L] + j; its children
+  // are [nch[chb[L] + j], nch[chb[L] + j + 1]) (positions for L = 0).
   float *nclo, *nchi;   // box of the children's FP32 centroids, nodes x dp
   float *nhmin, *nlmax; // min over children of box hi / max of box lo, nodes x dp
   int32_t *nnmin;       // min child cluster size
+  int32_t *nch;         // first child of every node, plus one end entry per level
+  int32_t *pbkt;        // bucket (level-0 node) of every position
+  uint64_t *mkey;       // Morton key of each cluster's position at layout (cid)
+  int32_t *tinfo;       // node count of every level, then TI_TOP, TI_FIXED
   int32_t lvl_base[MAXLEV + 1];
+  int32_t chb[MAXLEV + 1];
   // dense phase (average linkage, one instance): once the active clusters
   // fit, the whole matrix of their pair distances (the Section 5 cache with
   // room for every pair), filled by one all-pairs sweep of the points and
@@ -207,8 +217,9 @@ struct QueryArgs {
   const float *qvar;
   const double *sse;
   const float *nclo, *nchi, *nhmin, *nlmax;
-  const int32_t *nnmin;
+  const int32_t *nnmin, *nch, *pbkt, *tinfo;
   int32_t lvl_base[MAXLEV + 1];
+  int32_t chb[MAXLEV + 1];
   double *Ekey;
   int32_t *Ecid;
   Counters *ctr;
@@ -269,21 +280,27 @@ constexpr float EST_MARK = 1e-30f;
 // sizes (Ward, avg-2): no point pairs, no cache, no point re-layout
 __host__ __device__ inline bool closed_form(int linkage) { return linkage >= 2; }
 
-// number of tree levels for K active clusters (>= 1)
-__host__ __device__ inline int tree_levels(int K) {
-  int lev = 1, c = (K + FAN - 1) / FAN;
-  while (c > 1) {
-    c = (c + FAN - 1) / FAN;
-    ++lev;
+// Node capacities of the range-query tree for K active clusters: level 0
+// holds at most ceil(K / 8) + 1 buckets and level L at most
+// ceil(cap[L-1] / 8) + 1 nodes; a level whose Morton-cell grouping would
+// exceed its capacity (or whose keys are out of order) is cut into fixed runs
+// of 32 instead, which always fit.  The last level has at most 32 nodes.
+// Returns the number of levels (<= MAXLEV + 1).
+__host__ __device__ inline int tree_caps(int K, int *cap) {
+  int c = (K + 7) / 8 + 1, L = 0;
+  if (cap) cap[0] = c;
+  while (c > FAN) {
+    c = (c + 7) / 8 + 1;
+    ++L;
+    if (cap) cap[L] = c;
   }
-  return lev;
+  return L + 1;
 }
 
-__host__ __device__ inline int level_count(int K, int L) {
-  int c = (K + FAN - 1) / FAN;
-  for (int l = 0; l < L; ++l) c = (c + FAN - 1) / FAN;
-  return c < 1 ? 1 : c;
-}
+// tinfo entries after the per-level node counts
+constexpr int TI_TOP = MAXLEV + 1;    // lowest level with at most 32 nodes (the root's children)
+constexpr int TI_FIXED = MAXLEV + 2;  // bit L: level L was cut into fixed runs of 32
+constexpr int TI_SIZE = MAXLEV + 3;
 
 // launches the nearest-neighbour query of every terminal (hac_query.cu)
 cudaError_t launch_query(const QueryArgs &a, int dp, int prec, cudaStream_t s);

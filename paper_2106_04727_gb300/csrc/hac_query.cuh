@@ -58,11 +58,14 @@ namespace {
 #define HAC_QWARPS 4
 #endif
 #ifndef HAC_QMINB
-#define HAC_QMINB 1
+#define HAC_QMINB 4
 #endif
 constexpr int QWARPS = HAC_QWARPS;  // warps per block
-constexpr int QMINB = HAC_QMINB;    // resident blocks per SM the register budget must allow
-constexpr int STK = 256;           // per-warp stack, >= 1 + 31 * (MAXLEV - 1)
+// resident blocks per SM the register budget must allow: the complete and
+// average searches are latency-bound, and more resident warps beat their
+// register spills (measured); Ward and avg-2 need fewer registers anyway
+constexpr int QMINB = HAC_QMINB;
+constexpr int STK = 288;           // per-warp stack: >= 32 + 31 * (levels - 1), 9 levels for n < 2^31
 constexpr float EPS = 1e-5f;       // relative slack of the FP32 bound tests
 constexpr long long SMALLP = 32;   // pairs of at most this many point pairs run per lane
 constexpr float U32 = 5.9604645e-8f;  // 2^-24
@@ -589,32 +592,49 @@ struct Searcher {
     }
   }
 
-  // FP32 candidates: every lane offers its own estimate (has = false if none)
+  // FP32 candidates: every lane offers its own estimate (has = false if none).
+  // U (which sets the pruning threshold) is reduced over the warp at once; the
+  // two least lower bounds and the candidate of the least are kept per lane
+  // and combined once, by finish_f32, after the traversal.
   __device__ void offer_f32(bool has, float d32, float dlt, int c) {
     const float lo = has ? lower(d32, dlt) : INFINITY;
     const float up = has ? (d32 + dlt) * (1.f + rho) : INFINITY;
-    const int cc = has ? c : INT_MAX;
-    const float umin = warp_minf(up);
-    float m1 = lo;
-    int ml = lane;
-    warp_argmin_f(m1, ml);
-    const float m2 = warp_minf(lane == ml ? INFINITY : lo);
-    const int cmin = __shfl_sync(0xffffffffu, cc, ml);
-    const float dsel = __shfl_sync(0xffffffffu, d32, ml);
-    const float esel = __shfl_sync(0xffffffffu, dlt, ml);
-    if (m1 < L1 || (m1 == L1 && cmin < c1)) {
-      L2 = fminf(L1, m2);
-      L1 = m1;
-      c1 = cmin;
-      d1 = dsel;
-      e1 = esel;
-    } else {
-      L2 = fminf(L2, m1);
+    if (has) {
+      if (lo < L1 || (lo == L1 && c < c1)) {
+        L2 = L1;
+        L1 = lo;
+        c1 = c;
+        d1 = d32;
+        e1 = dlt;
+      } else {
+        L2 = fminf(L2, lo);
+      }
     }
+    const float umin = warp_minf(up);
     if (umin < U) {
       U = umin;
       refresh();
     }
+  }
+
+  // The warp's two least FP32 lower bounds (L1, L2) over every candidate
+  // offered, with the candidate, value and error term of the least (ties on
+  // L1 to the smaller cid); warp-uniform afterwards.
+  __device__ void finish_f32() {
+    // lower bounds are >= +0, so their bits order like their values
+    unsigned long long k = ((unsigned long long)__float_as_uint(L1) << 32) | (unsigned)c1;
+    int who = lane;
+    int cw = c1;
+    warp_argmin_u(k, cw);
+    const unsigned m = __ballot_sync(0xffffffffu, L1 == __uint_as_float((unsigned)(k >> 32)) &&
+                                                      c1 == cw);
+    who = __ffs(m) - 1;
+    const float l2 = warp_minf(fminf(L2, lane == who ? INFINITY : L1));
+    L1 = __uint_as_float((unsigned)(k >> 32));
+    L2 = l2;
+    c1 = cw;
+    d1 = __shfl_sync(0xffffffffu, d1, who);
+    e1 = __shfl_sync(0xffffffffu, e1, who);
   }
 
   // exact (FP64) key of a closed-form linkage: Ward from the centroids and
@@ -638,7 +658,11 @@ struct Searcher {
     return kbits(ward_key<DP>(cA, cB, na, nb));
   }
 
-  __device__ void leaf(int j, bool seed) { leaf_at(j * FAN + lane, j * FAN + lane < a.K, seed); }
+  // the records of bucket j, one per lane
+  __device__ void leaf(int j, bool seed) {
+    const int b = a.nch[a.chb[0] + j];
+    leaf_at(b + lane, lane < a.nch[a.chb[0] + j + 1] - b && b + lane < a.K, seed);
+  }
 
   // the candidate at position idx of this lane (in: the lane has one); the
   // 32 lanes' candidates are tested, scored and offered together
@@ -987,65 +1011,80 @@ struct Searcher {
   }
 };
 
-// Branch-and-bound traversal of the tree for one Searcher.
+// Branch-and-bound traversal of the tree for one Searcher: the terminal's
+// own bucket first (it usually settles a tight bound), then depth first from
+// the nodes of the top level, nearest child first, pruning every node whose
+// lower bound exceeds the threshold.
+template <int LK, int DP, int MODE>
+__device__ int push_children(const QueryArgs &a, Searcher<LK, DP, MODE> &S, uint32_t *sn,
+                             float *sl, int top, int Lc, int c0, int cnt, int lane) {
+  const int child = c0 + lane;
+  float lbc = INFINITY;
+  bool ok = false;
+  // (the bound on the level's node count only guards a malformed tree,
+  // which the build flags as ERR_TREE)
+  if (lane < cnt && child < a.tinfo[Lc]) {
+    const int node = a.lvl_base[Lc] + child;
+    if (a.ninlo[node] <= S.myseq && S.myseq <= a.ninhi[node]) {
+      lbc = node_lb<LK, DP>(a, node, S.ci32, S.alo, S.ahi, S.fna, S.vA);
+      ok = S.pass(lbc);
+    }
+    S.nodes += 1;
+  }
+  unsigned m = __ballot_sync(0xffffffffu, ok);
+  if (top + __popc(m) > STK) {  // cannot happen for the level counts of tree_caps
+    if (lane == 0) atomicOr(&a.ctr->err, ERR_STACK);
+    m = 0;
+  }
+  if (m) {
+    const int rank = __popc(m & ((1u << lane) - 1u));
+    if (ok) {
+      sn[top + rank] = ((uint32_t)Lc << 28) | (uint32_t)child;
+      sl[top + rank] = lbc;
+    }
+    float mv = ok ? lbc : INFINITY;
+    int ml = lane;
+    warp_argmin_f(mv, ml);
+    __syncwarp();
+    if (lane == 0) {  // nearest child popped first
+      const int mp = top + __popc(m & ((1u << ml) - 1u));
+      const int last = top + __popc(m) - 1;
+      const uint32_t tn = sn[mp];
+      const float tl = sl[mp];
+      sn[mp] = sn[last];
+      sl[mp] = sl[last];
+      sn[last] = tn;
+      sl[last] = tl;
+    }
+    top += __popc(m);
+    __syncwarp();
+  }
+  return top;
+}
+
 template <int LK, int DP, int MODE>
 __device__ void traverse(const QueryArgs &a, Searcher<LK, DP, MODE> &S, uint32_t *sn, float *sl,
                          int own, int lane) {
-  const int nlev = tree_levels(a.K);
   S.leaf(own, true);
-  if (lane == 0) {
-    sn[0] = (uint32_t)(nlev - 1) << 27;
-    sl[0] = 0.f;
+  const int tl = a.tinfo[TI_TOP] - 1;  // top level: at most 32 nodes
+  if (tl < 0 || tl > MAXLEV) {          // never for a finished build
+    if (lane == 0) atomicOr(&a.ctr->err, ERR_TREE);
+    return;
   }
-  int top = 1;
-  __syncwarp();
+  int top = push_children(a, S, sn, sl, 0, tl, 0, min(a.tinfo[tl], FAN), lane);
   while (top > 0) {
     --top;
     const uint32_t e = sn[top];
     const float lb = sl[top];
     __syncwarp();
     if (!S.pass(lb)) continue;
-    const int L = (int)(e >> 27), j = (int)(e & ((1u << 27) - 1));
+    const int L = (int)(e >> 28), j = (int)(e & ((1u << 28) - 1));
     if (L == 0) {
       if (j != own) S.leaf(j, false);
       continue;
     }
-    const int cnt = level_count(a.K, L - 1);
-    const int child = j * FAN + lane;
-    float lbc = INFINITY;
-    bool ok = false;
-    if (child < cnt) {
-      const int node = a.lvl_base[L - 1] + child;
-      if (a.ninlo[node] <= S.myseq && S.myseq <= a.ninhi[node]) {
-        lbc = node_lb<LK, DP>(a, node, S.ci32, S.alo, S.ahi, S.fna, S.vA);
-        ok = S.pass(lbc);
-      }
-      S.nodes += 1;
-    }
-    const unsigned m = __ballot_sync(0xffffffffu, ok);
-    if (m) {
-      const int rank = __popc(m & ((1u << lane) - 1u));
-      if (ok) {
-        sn[top + rank] = ((uint32_t)(L - 1) << 27) | (uint32_t)child;
-        sl[top + rank] = lbc;
-      }
-      float mv = ok ? lbc : INFINITY;
-      int ml = lane;
-      warp_argmin_f(mv, ml);
-      __syncwarp();
-      if (lane == 0) {  // nearest child popped first
-        const int mp = top + __popc(m & ((1u << ml) - 1u));
-        const int last = top + __popc(m) - 1;
-        const uint32_t tn = sn[mp];
-        const float tl = sl[mp];
-        sn[mp] = sn[last];
-        sl[mp] = sl[last];
-        sn[last] = tn;
-        sl[last] = tl;
-      }
-      top += __popc(m);
-      __syncwarp();
-    }
+    const int c0 = a.nch[a.chb[L] + j];
+    top = push_children(a, S, sn, sl, top, L - 1, c0, a.nch[a.chb[L] + j + 1] - c0, lane);
   }
 }
 
@@ -1087,7 +1126,7 @@ __global__ void __launch_bounds__(QWARPS * 32, QMINB) k_query(QueryArgs a) {
   unsigned long long c[7] = {0, 0, 0, 0, 0, 0, 0};
   for (int t = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; t < a.nterm; t += nw) {
     const int ci = a.term[t];
-    const int own = a.pos[ci] / FAN;
+    const int own = a.pbkt[a.pos[ci]];
     // a candidate list from the exhaustive scan replaces the tree traversal
     const int lc = a.lcnt ? a.lcnt[a.pos[ci]] : -1;
     unsigned long long bk;
@@ -1109,6 +1148,7 @@ __global__ void __launch_bounds__(QWARPS * 32, QMINB) k_query(QueryArgs a) {
         traverse_list(a, S, a.pos[ci], lc, lane);
       else
         traverse(a, S, sn, sl, own, lane);
+      S.finish_f32();
       if (S.deferred) {
         // incomplete: some candidates still wait for their values
         deferred = true;

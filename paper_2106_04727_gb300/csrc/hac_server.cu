@@ -120,7 +120,8 @@ __global__ void k_admit_keys(const T *stage, int m, int d, const AdmitInst *ai, 
 // point sits at its cid's slot instead (pts_at_cid).
 template <typename T>
 __global__ void k_admit_layout(State s, const T *stage, int m, const AdmitInst *ai, int na,
-                               const int32_t *sorted, int32_t *order, int K, int nterm,
+                               const int32_t *sorted, const uint64_t *skey, int32_t *order,
+                               int K, int nterm,
                                int64_t P, int pc, int round, int pts_at_cid) {
   const int d = s.d, dp = s.dp;
   for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < m; p += gridDim.x * blockDim.x) {
@@ -166,6 +167,7 @@ __global__ void k_admit_layout(State s, const T *stage, int m, const AdmitInst *
     s.inst[c] = a.slot;
     order[op] = c;
     s.pos[c] = op;
+    s.mkey[c] = skey[p] & ((1ull << 40) - 1);  // the Morton key below the batch rank
     s.term[nterm + p] = c;
     s.qsz[op] = 1;
     s.qseg[op] = (int32_t)pp;
@@ -413,12 +415,12 @@ int engine_admit(Engine &e, const std::vector<SrvReq *> &batch) {
   int32_t *ord = s.order[h.ocur];
   if (f32)
     k_admit_layout<float><<<grid_for(m, TPB), TPB, 0, st>>>(
-        s, (const float *)e.stage, m, e.d_ai, na, h.vals[sc], ord, e.K, e.nterm, e.P, h.pcur,
-        e.round, ward);
+        s, (const float *)e.stage, m, e.d_ai, na, h.vals[sc], h.keys[sc], ord, e.K, e.nterm, e.P,
+        h.pcur, e.round, ward);
   else
     k_admit_layout<double><<<grid_for(m, TPB), TPB, 0, st>>>(
-        s, (const double *)e.stage, m, e.d_ai, na, h.vals[sc], ord, e.K, e.nterm, e.P, h.pcur,
-        e.round, ward);
+        s, (const double *)e.stage, m, e.d_ai, na, h.vals[sc], h.keys[sc], ord, e.K, e.nterm, e.P,
+        h.pcur, e.round, ward);
   CK(cudaGetLastError());
   h.launches += 3;
   e.K += m;
