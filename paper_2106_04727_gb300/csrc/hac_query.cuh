@@ -61,9 +61,13 @@ namespace {
 #define HAC_QMINB 4
 #endif
 constexpr int QWARPS = HAC_QWARPS;  // warps per block
-// resident blocks per SM the register budget must allow: the complete and
-// average searches are latency-bound, and more resident warps beat their
-// register spills (measured); Ward and avg-2 need fewer registers anyway
+// resident blocks per SM the register budget must allow.  The complete and
+// average searches are latency-bound, and more resident warps beat the
+// register spills they cost: the shape tuner's average-linkage runs at
+// 10^6 points take 523 / 515 / 514 / 507 ms at 3 / 4 / 5 / 6 blocks (168 /
+// 128 / 96 / 80 registers, 20 / 156 / 472 / 580 B of spill stores).  4 is
+// kept: 6 gains 1.5 %, about the run-to-run spread, for 4x the spills.
+// Ward and avg-2 (about 110 registers, no spills) are bounded the same way.
 constexpr int QMINB = HAC_QMINB;
 constexpr int STK = 288;           // per-warp stack: >= 32 + 31 * (levels - 1), 9 levels for n < 2^31
 constexpr float EPS = 1e-5f;       // relative slack of the FP32 bound tests
@@ -72,6 +76,8 @@ constexpr float U32 = 5.9604645e-8f;  // 2^-24
 constexpr unsigned long long KINF = 0x7ff0000000000000ull;  // bits of +inf
 
 enum { M_F64 = 0, M_F32 = 1, M_RECHECK = 2 };
+// per-warp search counters (shared memory), added to the instance's at the end
+enum { C_CPAIRS, C_PPAIRS, C_NODES, C_LTESTS, C_PROWS, C_RECHECKS, C_HITS, C_N };
 
 // The warp-wide pair evaluations, which a search takes for its larger
 // candidates only, are kept out of line (HAC_Q_OUTLINE=1), so that their
@@ -424,10 +430,12 @@ struct Searcher {
   bool pown_ci;   //   and whether C_i owns it
   bool deferred;  // a big pair was handed to the GPU-wide evaluation
   float delta0, rho;
-  unsigned long long cpairs, ppairs, nodes, ltests, prows, rechecks, hits;
+  unsigned long long ppairs;  // point pairs this search evaluated (its budget)
+  unsigned long long *sc;     // this warp's counters in shared memory (C_*)
 
-  __device__ Searcher(const QueryArgs &args, int lane_, int ci_, float Ufix)
-      : a(args), lane(lane_), ci(ci_) {
+  __device__ Searcher(const QueryArgs &args, int lane_, int ci_, float Ufix,
+                       unsigned long long *sc_)
+      : a(args), lane(lane_), ci(ci_), sc(sc_) {
     na = a.csize[ci];
     fna = (float)na;
     myinst = a.inst[ci];
@@ -459,8 +467,13 @@ struct Searcher {
     c1 = INT_MAX;
     d1 = e1 = INFINITY;
     deferred = false;
-    cpairs = ppairs = nodes = ltests = prows = rechecks = hits = 0;
+    ppairs = 0;
     refresh();
+  }
+
+  // add a warp-uniform amount to counter k (lane 0 keeps the warp's counts)
+  __device__ void count(int k, unsigned long long v) const {
+    if (lane == 0) sc[k] += v;
   }
 
   // Section 5 cache: look for the entry of `nbr` in the table of `owner`
@@ -519,18 +532,18 @@ struct Searcher {
     if (h1 && p1 == 0) {
       v = v1;
       e = f1;
-      hits += 1;
+      count(C_HITS, 1);
       return 1;
     }
     const bool h2 = cache_find(cw, ci, v2, f2, p2);
     if (h2 && p2 == 0) {
       v = v2;
       e = f2;
-      hits += 1;
+      count(C_HITS, 1);
       return 1;
     }
     if ((long long)na * nw >= BIG_MIN_PAIRS && side_find(cw, v, e)) {
-      hits += 1;
+      count(C_HITS, 1);
       return 1;
     }
     if (h1 || h2) {
@@ -682,8 +695,8 @@ struct Searcher {
           bx = fmaxf(bx, ahi[k] - a.qblo[(size_t)idx * DP + k]);
         }
       }
-      ltests += 1;
     }
+    count(C_LTESTS, __popc(__ballot_sync(0xffffffffu, valid)));
     if (LK == LK_WARD || LK == LK_AVG2) {
       float d32, dlt;  // FP32 distance (D units) and its absolute error term
       if (LK == LK_WARD) {
@@ -697,7 +710,7 @@ struct Searcher {
       if (MODE == M_F32) {
         const bool has = valid && (lower(d32, dlt) <= T || a.noprune);
         if (__any_sync(0xffffffffu, has)) {
-          cpairs += __popc(__ballot_sync(0xffffffffu, has));
+          count(C_CPAIRS, __popc(__ballot_sync(0xffffffffu, has)));
           offer_f32(has, d32, dlt, cb);
         }
         return;
@@ -717,8 +730,8 @@ struct Searcher {
           k = ward64(idx, nb, cb);
           c = cb;
         }
-        cpairs += 1;
-        if (MODE == M_RECHECK) rechecks += 1;
+        count(C_CPAIRS, 1);
+        if (MODE == M_RECHECK) count(C_RECHECKS, 1);
         offer_exact(k, c);
         ok = ok && lane != who && pass(d32);
         m = __ballot_sync(0xffffffffu, ok);
@@ -730,8 +743,8 @@ struct Searcher {
         k = ward64(idx, nb, cb);
         c = cb;
       }
-      cpairs += __popc(m);
-      if (MODE == M_RECHECK) rechecks += __popc(m);
+      count(C_CPAIRS, __popc(m));
+      if (MODE == M_RECHECK) count(C_RECHECKS, __popc(m));
       offer_exact(k, c);
       return;
     }
@@ -782,12 +795,12 @@ struct Searcher {
         c = cb;
       }
       ppairs += __reduce_add_sync(0xffffffffu, small ? (unsigned)(na * nb) : 0u);
-      prows += __reduce_add_sync(0xffffffffu, small ? (unsigned)(na + nb) : 0u);
-      cpairs += __popc(sm);
+      count(C_PROWS, __reduce_add_sync(0xffffffffu, small ? (unsigned)(na + nb) : 0u));
+      count(C_CPAIRS, __popc(sm));
       if (MODE == M_F32) {
         offer_f32(small, d32, dlt, cb);
       } else {
-        if (MODE == M_RECHECK) rechecks += __popc(__ballot_sync(0xffffffffu, rec));
+        if (MODE == M_RECHECK) count(C_RECHECKS, __popc(__ballot_sync(0xffffffffu, rec)));
         offer_exact(k, c);
       }
     }
@@ -802,8 +815,8 @@ struct Searcher {
       const int nw = __shfl_sync(0xffffffffu, nb, who);
       const int sw = __shfl_sync(0xffffffffu, sb, who);
       unsigned long long pp = 0;
-      cpairs += 1;
-      prows += (unsigned long long)(na + nw);
+      count(C_CPAIRS, 1);
+      count(C_PROWS, (unsigned long long)(na + nw));
       double cv = 0.0;
       float ce = 0.f;
       const int hit = cache_get(cw, nw, cv, ce);
@@ -881,7 +894,7 @@ struct Searcher {
             unsigned long long pp2 = 0;
             key = eval64_warp<LK, DP>(a.p64, sa, na, sw, nw, INFINITY, lane, pp2);
             ppairs += pp2;
-            rechecks += 1;
+            count(C_RECHECKS, 1);
             cache_put(cw, nw, key, 0.f);
           }
         }
@@ -1023,14 +1036,15 @@ __device__ int push_children(const QueryArgs &a, Searcher<LK, DP, MODE> &S, uint
   bool ok = false;
   // (the bound on the level's node count only guards a malformed tree,
   // which the build flags as ERR_TREE)
-  if (lane < cnt && child < a.tinfo[Lc]) {
+  const bool in = lane < cnt && child < a.tinfo[Lc];
+  if (in) {
     const int node = a.lvl_base[Lc] + child;
     if (a.ninlo[node] <= S.myseq && S.myseq <= a.ninhi[node]) {
       lbc = node_lb<LK, DP>(a, node, S.ci32, S.alo, S.ahi, S.fna, S.vA);
       ok = S.pass(lbc);
     }
-    S.nodes += 1;
   }
+  S.count(C_NODES, __popc(__ballot_sync(0xffffffffu, in)));
   unsigned m = __ballot_sync(0xffffffffu, ok);
   if (top + __popc(m) > STK) {  // cannot happen for the level counts of tree_caps
     if (lane == 0) atomicOr(&a.ctr->err, ERR_STACK);
@@ -1103,27 +1117,20 @@ __device__ void traverse_list(const QueryArgs &a, Searcher<LK, DP, MODE> &S, int
   }
 }
 
-template <int LK, int DP, int MODE>
-__device__ void tally(const Searcher<LK, DP, MODE> &S, unsigned long long *c) {
-  c[0] += S.cpairs;  // warp-uniform counts
-  c[1] += S.ppairs;
-  c[2] += S.nodes;   // per-lane counts below
-  c[3] += S.ltests;
-  c[4] += S.prows;
-  c[5] += S.rechecks;
-  c[6] += S.hits;
-}
 
 template <int LK, int DP, int PREC>
 __global__ void __launch_bounds__(QWARPS * 32, QMINB) k_query(QueryArgs a) {
   __shared__ uint32_t s_node[QWARPS][STK];
   __shared__ float s_lb[QWARPS][STK];
+  __shared__ unsigned long long s_cnt[QWARPS][C_N];
   const int lane = threadIdx.x & 31;
   const int wib = threadIdx.x >> 5;
   const int nw = (gridDim.x * blockDim.x) >> 5;
   uint32_t *sn = s_node[wib];
   float *sl = s_lb[wib];
-  unsigned long long c[7] = {0, 0, 0, 0, 0, 0, 0};
+  unsigned long long *sc = s_cnt[wib];
+  if (lane < C_N) sc[lane] = 0;
+  __syncwarp();
   for (int t = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; t < a.nterm; t += nw) {
     const int ci = a.term[t];
     const int own = a.pbkt[a.pos[ci]];
@@ -1133,7 +1140,7 @@ __global__ void __launch_bounds__(QWARPS * 32, QMINB) k_query(QueryArgs a) {
     int bc;
     bool deferred = false;
     if (PREC == 0) {
-      Searcher<LK, DP, M_F64> S(a, lane, ci, INFINITY);
+      Searcher<LK, DP, M_F64> S(a, lane, ci, INFINITY, sc);
       if (lc >= 0)
         traverse_list(a, S, a.pos[ci], lc, lane);
       else
@@ -1141,9 +1148,9 @@ __global__ void __launch_bounds__(QWARPS * 32, QMINB) k_query(QueryArgs a) {
       bk = S.bk;
       bc = S.bc;
       deferred = S.deferred;
-      tally(S, c);
+      S.count(C_PPAIRS, S.ppairs);
     } else {
-      Searcher<LK, DP, M_F32> S(a, lane, ci, INFINITY);
+      Searcher<LK, DP, M_F32> S(a, lane, ci, INFINITY, sc);
       if (lc >= 0)
         traverse_list(a, S, a.pos[ci], lc, lane);
       else
@@ -1154,17 +1161,17 @@ __global__ void __launch_bounds__(QWARPS * 32, QMINB) k_query(QueryArgs a) {
         deferred = true;
         bk = KINF;
         bc = INT_MAX;
-        tally(S, c);
+        S.count(C_PPAIRS, S.ppairs);
       } else if (S.L2 > S.U && S.c1 != INT_MAX) {
         // exactly one candidate can be the FP64 winner
         bc = S.c1;
         bk = S.exact_of(a.pos[bc], bc);
-        S.rechecks += 1;
+        S.count(C_RECHECKS, 1);
         deferred = S.deferred;
-        tally(S, c);
+        S.count(C_PPAIRS, S.ppairs);
       } else {
-        tally(S, c);
-        Searcher<LK, DP, M_RECHECK> R(a, lane, ci, S.U);
+        S.count(C_PPAIRS, S.ppairs);
+        Searcher<LK, DP, M_RECHECK> R(a, lane, ci, S.U, sc);
         if (lc >= 0)
           traverse_list(a, R, a.pos[ci], lc, lane);
         else
@@ -1172,7 +1179,7 @@ __global__ void __launch_bounds__(QWARPS * 32, QMINB) k_query(QueryArgs a) {
         bk = R.bk;
         bc = R.bc;
         deferred = R.deferred;
-        tally(R, c);
+        R.count(C_PPAIRS, R.ppairs);
       }
     }
     if (deferred) {
@@ -1186,19 +1193,15 @@ __global__ void __launch_bounds__(QWARPS * 32, QMINB) k_query(QueryArgs a) {
       if (bc == INT_MAX) atomicOr(&a.ctr->err, ERR_NO_NN);
     }
   }
-  // node / leaf-slot tests are counted per lane; everything else per warp
-  for (int o = 16; o; o >>= 1) {
-    c[2] += __shfl_xor_sync(0xffffffffu, c[2], o);
-    c[3] += __shfl_xor_sync(0xffffffffu, c[3], o);
-  }
+  __syncwarp();
   if (lane == 0) {
-    atomicAdd(&a.ctr->cluster_pairs, c[0]);
-    atomicAdd(&a.ctr->point_pairs, c[1]);
-    atomicAdd(&a.ctr->nodes, c[2]);
-    atomicAdd(&a.ctr->ltests, c[3]);
-    atomicAdd(&a.ctr->prows, c[4]);
-    atomicAdd(&a.ctr->rechecks, c[5]);
-    atomicAdd(&a.ctr->cache_hits, c[6]);
+    atomicAdd(&a.ctr->cluster_pairs, sc[C_CPAIRS]);
+    atomicAdd(&a.ctr->point_pairs, sc[C_PPAIRS]);
+    atomicAdd(&a.ctr->nodes, sc[C_NODES]);
+    atomicAdd(&a.ctr->ltests, sc[C_LTESTS]);
+    atomicAdd(&a.ctr->prows, sc[C_PROWS]);
+    atomicAdd(&a.ctr->rechecks, sc[C_RECHECKS]);
+    atomicAdd(&a.ctr->cache_hits, sc[C_HITS]);
   }
 }
 

@@ -1,7 +1,8 @@
 """Run one clustering of a named synthetic workload and print its counters.
 
     python -m paper_2106_04727_gb300.run_case --workload gmm5d_1m_f32 --n 100000 \
-        --linkage average --precision f32 --cache-slots 128 [--dense-k 4096] [--runs 1]
+        --linkage average --precision f32 --cache-slots 128 [--dense-k 4096] [--runs 1] \
+        [--lib path/to/libhac.so]
 
 A single process, one GPU, device-resident input: the command the profile
 summaries under profiles/ run under ncu (small cases), and a quick way to time
@@ -24,12 +25,16 @@ def main() -> None:
     ap.add_argument("--dense-k", type=int, default=None,
                     help="average linkage: dense-matrix threshold (HAC_DENSE_K)")
     ap.add_argument("--runs", type=int, default=1)
+    ap.add_argument("--lib", default=None, help="run with this compiled libhac.so")
     args = ap.parse_args()
     if args.dense_k is not None:
         os.environ["HAC_DENSE_K"] = str(args.dense_k)  # read by hac_create
 
-    from . import hac, inputs
+    from . import build, hac, inputs
 
+    if args.lib:
+        build.LIB = args.lib  # a compiled variant: loaded as is, never rebuilt
+        hac.load(build_if_missing=False)
     X = inputs.workload(args.workload, n=args.n)
     prec = hac.PREC_F64 if args.precision == "f64" else hac.PREC_F32_RECHECK
     h = hac.hac_create(X, args.linkage)
