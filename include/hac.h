@@ -63,7 +63,11 @@ typedef enum {
                                hence the tree) are the FP64 ones.  Ward and
                                avg-2 tree searches (O(d) closed forms) run in
                                FP64 in both modes; their exhaustive scans
-                               (d > 8) use the FP32 bulk */
+                               (d > 8) use the FP32 bulk.  hac_run and
+                               hac_run_static run inputs whose FP32 copy has
+                               a coordinate of 2^40 or more (FP32 input: the
+                               input; FP64 input: the recentred points) in
+                               FP64; an FP32 server refuses them (HAC_EINVAL) */
 } hac_precision;
 
 /* One dendrogram node: clusters cid_a < cid_b merged at `height` into a

@@ -1234,14 +1234,17 @@ int init_layout(hac_ctx *h, cudaStream_t st) {
     return x;
   };
   MortonParams mp{}, ctrp{};
-  double scale = 0.0;
+  double scale = 0.0, raw = 0.0;
   for (int k = 0; k < d; ++k) {
     double lo = dec(bb[k]), hi = dec(bb[MAXD + k]);
     mp.lo[k] = lo;
     mp.inv[k] = hi > lo ? 1.0 / (hi - lo) : 0.0;
     ctrp.lo[k] = 0.5 * (lo + hi);
     scale = std::max(scale, std::max(std::fabs(lo - ctrp.lo[k]), std::fabs(hi - ctrp.lo[k])));
+    raw = std::max(raw, std::max(std::fabs(lo), std::fabs(hi)));
   }
+  // the FP32 copy holds the input itself (FP32 input) or the recentred points
+  s.p32_max = s.pts32_exact ? raw : scale * (1.0 + 1e-6);
   mp.bits = std::min(21, 64 / d);
   s.abs_slack = std::max(scale, 1e-300) * std::ldexp(1.0, -18);
   s.coord_scale = (float)(scale * (1.0 + 1e-6));
@@ -1805,6 +1808,7 @@ int run_impl(hac_ctx *h, const hac_opts *o) {
   cudaEventRecord(e0.e, st);
   int rc = h->dt == HAC_F32 ? init_layout<float>(h, st) : init_layout<double>(h, st);
   if (rc) return rc;
+  if (s.p32_max >= FP32_COORD_LIMIT) s.prec = HAC_PREC_F64;  // FP32 would overflow
   cudaEventRecord(e1.e, st);
   CK(cudaEventSynchronize(e1.e));
   {
@@ -2130,6 +2134,7 @@ int static_run(hac_ctx &h, const hac_opts &opt, cudaStream_t st, hac_merge *dev_
   const auto t0 = std::chrono::steady_clock::now();
   int rc = h.dt == HAC_F32 ? init_layout<float>(&h, st) : init_layout<double>(&h, st);
   if (rc) return rc;
+  if (s.p32_max >= FP32_COORD_LIMIT) s.prec = HAC_PREC_F64;  // FP32 would overflow
   RoundCtl ctl;  // no events: nothing is created here
   int rounds = 0;
   rc = run_rounds(&h, opt, st, ctl, nullptr, t0, &rounds);

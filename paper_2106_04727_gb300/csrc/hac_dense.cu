@@ -52,6 +52,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdlib>
+#include <cstring>
 
 namespace hacg {
 
@@ -208,6 +209,12 @@ struct SweepArgs {
   const int32_t *didx;
   int64_t N;  // points in the layout
   int dk, e;
+  // FP32 sweep: coordinates times scl = 2^k (exact), so that squared
+  // distances flushed to zero by the square root (below 2^-126) are below
+  // 2^(-126-2k) unscaled; sums of scaled distances convert with unit 2^es,
+  // es = e + k, to the same fixed-point values
+  float scl;
+  int es;
   unsigned long long *sum;  // the packed upper triangle of sums (LIMBS words per pair)
   long long nb;             // blocks of TI points along each axis
   Counters *ctr;
@@ -380,8 +387,8 @@ __global__ void __launch_bounds__(DS_TPB, HAC_DS_MINB) k_dense_sweep32(SweepArgs
     const long long ra = r0 + (long long)lane * PPT + 2 * h, rb = ra + 1;
 #pragma unroll
     for (int k = 0; k < D; ++k)
-      x[h][k] = f2_pack(ra < a.N ? a.p32[(size_t)ra * DP + k] : 0.f,
-                        rb < a.N ? a.p32[(size_t)rb * DP + k] : 0.f);
+      x[h][k] = f2_pack(ra < a.N ? a.p32[(size_t)ra * DP + k] * a.scl : 0.f,
+                        rb < a.N ? a.p32[(size_t)rb * DP + k] * a.scl : 0.f);
   }
   unsigned long long pairs = 0;
   for (int ch = 0; ch < PPT; ++ch) {  // TI columns in chunks of DS_CH
@@ -391,7 +398,7 @@ __global__ void __launch_bounds__(DS_TPB, HAC_DS_MINB) k_dense_sweep32(SweepArgs
     __syncthreads();
     for (int i = threadIdx.x; i < cnt * D; i += DS_TPB) {
       const int c = i / D, k = i - c * D;
-      const float y = a.p32[(size_t)(c0 + c) * DP + k];
+      const float y = a.p32[(size_t)(c0 + c) * DP + k] * a.scl;
       sy[i] = f2_pack(y, y);
     }
     if (threadIdx.x < DS_CH)
@@ -410,6 +417,7 @@ __global__ void __launch_bounds__(DS_TPB, HAC_DS_MINB) k_dense_sweep32(SweepArgs
         float part[PPT];
 #pragma unroll
         for (int r = 0; r < PPT; ++r) part[r] = 0.f;
+#pragma unroll 2
         for (int c = c1; c < c2; ++c) {
           unsigned long long y[D];
 #pragma unroll
@@ -425,12 +433,12 @@ __global__ void __launch_bounds__(DS_TPB, HAC_DS_MINB) k_dense_sweep32(SweepArgs
             }
             float s0, s1;
             f2_unpack(d2, s0, s1);
-            part[2 * h] += sqrt_approx(s0);
-            part[2 * h + 1] += sqrt_approx(s1);
+            part[2 * h] += sqrt_approx_ftz(s0);
+            part[2 * h + 1] += sqrt_approx_ftz(s1);
           }
         }
 #pragma unroll
-        for (int r = 0; r < PPT; ++r) u128_add(acc[r], fx_of_f(part[r], a.e));
+        for (int r = 0; r < PPT; ++r) u128_add(acc[r], fx_of_f(part[r], a.es));
       }
       int below = 0;
 #pragma unroll
@@ -561,12 +569,18 @@ struct NNArgs {
   const double *dmat;
   int dk, K, nlist;
   const int32_t *order, *didx, *list, *dq;
-  double delta, rho;  // FP32 mode: error model of an estimate
+  // FP32 mode: error model of an estimate x of the FP64 value D,
+  // |x - D| <= delta + rho D + eta; eta (absolute) covers the sums' fixed-
+  // point truncation (below one unit 2^e per partial sum, on both sides)
+  // and the square roots' flush of squared distances below 2^-126 (scaled)
+  double delta, rho, eta;
   // FP32 mode with delta = 0: the bounds as steps of the FP64 bit pattern
   // (adding N ulps to a non-negative double multiplies it by at least
-  // 1 + N 2^-53): up = x + nu ulps >= x / (1 - rho), lo = x - nl ulps <=
-  // x / (1 + rho) (nl doubled for a step down across a power of two)
-  unsigned long long nu, nl;
+  // 1 + N 2^-53): for x >= m0 (so eta <= 2^-30 x) up = x + nu ulps >=
+  // (x + eta) / (1 - rho) and lo = x - nl ulps <= (x - eta) / (1 + rho) (nl
+  // doubled for a step down across a power of two); an estimate below m0
+  // spans [0, m0up] (m0up = 2 m0 >= its upper bound)
+  unsigned long long nu, nl, m0, m0up;
   double *Ekey;
   int32_t *Ecid;
   int32_t *drq_a, *drq_b;
@@ -654,7 +668,7 @@ __global__ void k_dense_nn(NNArgs a) {
         for (int u = 0; u < NN_U; ++u) {
           if (c[u] == ci) continue;
           const unsigned long long m = x[u] & ~SIGN;
-          const unsigned long long up = (x[u] & SIGN) && m ? m + a.nu : m;
+          const unsigned long long up = (x[u] & SIGN) ? (m < a.m0 ? a.m0up : m + a.nu) : m;
           U = up < U ? up : U;
         }
       }
@@ -678,8 +692,8 @@ __global__ void k_dense_nn(NNArgs a) {
         for (int u = 0; u < NN_U; ++u) {
           if (c[u] == ci) continue;
           const unsigned long long m = x[u] & ~SIGN;
-          const bool exact = !(x[u] & SIGN) || m == 0;  // an estimate of 0 is exact (delta = 0)
-          const unsigned long long lo = exact ? m : (m > a.nl ? m - a.nl : 0ull);
+          const bool exact = !(x[u] & SIGN);
+          const unsigned long long lo = exact ? m : (m < a.m0 ? 0ull : m - a.nl);
           if (lo > U) continue;
           ++nW;
           if (exact) {
@@ -707,16 +721,19 @@ __global__ void k_dense_nn(NNArgs a) {
       }
       if (totW == 1) {
         // the lone candidate is an estimate; rho <= 4e-6 here (checked by the
-        // host), so its upper bound stands in for the FP64 value
+        // host), so its upper bound stands in for the FP64 value, unless the
+        // absolute term dominates it (below m0: re-scored)
         const unsigned holder = __ballot_sync(0xffffffffu, nE > 0);
         const int hl = __ffs(holder) - 1;
         const unsigned long long v = __shfl_sync(0xffffffffu, ev, hl);
         const int c = __shfl_sync(0xffffffffu, ec, hl);
-        if (lane == 0) {
-          a.Ekey[ci] = __longlong_as_double((long long)(v + a.nu));
-          a.Ecid[ci] = c;
+        if (v >= a.m0) {
+          if (lane == 0) {
+            a.Ekey[ci] = __longlong_as_double((long long)(v + a.nu));
+            a.Ecid[ci] = c;
+          }
+          continue;
         }
-        continue;
       }
       // several candidates in the window: re-score its estimates in FP64
       for (int p = lane; p < a.K; p += 32) {
@@ -725,7 +742,7 @@ __global__ void k_dense_nn(NNArgs a) {
         const int q = a.dq[p];
         const unsigned long long xb = (unsigned long long)__double_as_longlong(row[q]);
         const unsigned long long m = xb & ~SIGN;
-        if (!(xb & SIGN) || m == 0 || (m > a.nl ? m - a.nl : 0ull) > U) continue;
+        if (!(xb & SIGN) || (m < a.m0 ? 0ull : m - a.nl) > U) continue;
         const int r = atomicAdd(&a.ctr->nrq, 1);
         if (r < a.drq_cap) {
           a.drq_a[r] = min(qi, q);
@@ -736,8 +753,9 @@ __global__ void k_dense_nn(NNArgs a) {
       continue;
     }
     // FP32 mode.  Bounds of an estimate x on the FP64 value D:
-    // (x - delta) / (1 + rho) <= D <= (x + delta) / (1 - rho), widened by
-    // 1e-12 for the rounding of these FP64 operations.
+    // (x - delta - eta) / (1 + rho) <= D <= (x + delta + eta) / (1 - rho),
+    // widened by 1e-12 for the rounding of these FP64 operations.
+    const double dl = a.delta + a.eta;
     const double lo_f = (1.0 - 1e-12) / (1.0 + a.rho), up_f = (1.0 + 1e-12) / (1.0 - a.rho);
     double U = INFINITY;
     for (int p0 = 0; p0 < a.K; p0 += 32 * NN_U) {
@@ -753,8 +771,8 @@ __global__ void k_dense_nn(NNArgs a) {
       for (int u = 0; u < NN_U; ++u) {
         if (c[u] == ci) continue;
         const double m = mag(x[u]);
-        const bool exact = !is_est(x[u]) || (m == 0.0 && a.delta == 0.0);
-        U = fmin(U, exact ? m : (m + a.delta) * up_f);
+        const bool exact = !is_est(x[u]);
+        U = fmin(U, exact ? m : (m + dl) * up_f);
       }
     }
     U = warp_min_d(U);
@@ -774,8 +792,8 @@ __global__ void k_dense_nn(NNArgs a) {
       for (int u = 0; u < NN_U; ++u) {
         if (c[u] == ci) continue;
         const double m = mag(x[u]);
-        const bool exact = !is_est(x[u]) || (m == 0.0 && a.delta == 0.0);
-        const double lo = exact ? m : fmax(m - a.delta, 0.0) * lo_f;
+        const bool exact = !is_est(x[u]);
+        const double lo = exact ? m : fmax(m - dl, 0.0) * lo_f;
         if (!(lo <= U)) continue;
         ++nW;
         if (exact) {
@@ -809,9 +827,9 @@ __global__ void k_dense_nn(NNArgs a) {
       const int hl = __ffs(holder) - 1;
       const double v = __shfl_sync(0xffffffffu, ev, hl);
       const int c = __shfl_sync(0xffffffffu, ec, hl);
-      if (a.delta + a.rho * v <= 4e-6 * v) {
+      if (dl + a.rho * v <= 4e-6 * v) {
         if (lane == 0) {
-          a.Ekey[ci] = (v + a.delta) * up_f;
+          a.Ekey[ci] = (v + dl) * up_f;
           a.Ecid[ci] = c;
         }
         continue;
@@ -832,8 +850,8 @@ __global__ void k_dense_nn(NNArgs a) {
         const int q = a.dq[p];
         const double x = row[q];
         const double m = mag(x);
-        const bool exact = !is_est(x) || (m == 0.0 && a.delta == 0.0);
-        if (exact || !(fmax(m - a.delta, 0.0) * lo_f <= U)) continue;
+        const bool exact = !is_est(x);
+        if (exact || !(fmax(m - dl, 0.0) * lo_f <= U)) continue;
         const int r = atomicAdd(&a.ctr->nrq, 1);
         if (r < a.drq_cap) {
           a.drq_a[r] = min(qi, q);
@@ -1198,6 +1216,16 @@ int dense_maybe_enter(hac_ctx *h, cudaStream_t st, int K, RoundCtl &ctl) {
   a.N = h->lay_n;
   a.dk = K;
   a.e = s.dexp;
+  // the FP32 copy scaled by 2^k toward |coordinate| <= 2^40 (squared
+  // distances stay below 2^86 for d <= 16; k >= 0 keeps the scaling exact)
+  {
+    int k = 0;
+    if (s.p32_max > 0.0)
+      k = std::max(0, std::min(100, 40 - (int)std::ceil(std::log2(s.p32_max))));
+    s.dsk = k;
+    a.scl = std::ldexp(1.0f, k);
+    a.es = s.dexp + k;
+  }
   a.sum = s.dsum;
   a.ctr = s.ctr;
   if (ctl.eb0) cudaEventRecord(ctl.eb0, st);
@@ -1242,12 +1270,25 @@ int dense_search(hac_ctx *h, cudaStream_t st, int K, int nterm, RoundCtl &ctl) {
   a.drq_b = s.drq_b;
   a.drq_cap = s.drq_cap;
   a.ctr = s.ctr;
+  // absolute term: a truncation below one unit 2^dexp on each side (the FP32
+  // partial sums and the FP64 re-score's distances) and the flush of scaled
+  // squared distances below 2^-126 (distances below 2^(-63-dsk))
+  a.eta = (2.0 * std::ldexp(1.0, s.dexp) + std::ldexp(1.0, -63 - s.dsk)) * (1.0 + 1e-9);
   const bool f32 = s.prec == HAC_PREC_F32_RECHECK;
-  // integer bounds when the estimates carry no absolute term and the lone
-  // estimate's bound is within the 4e-6 the height convention allows
-  const bool intb = f32 && a.delta == 0.0 && a.rho <= 4e-6;
-  a.nu = (unsigned long long)std::ceil(std::ldexp(a.rho / (1.0 - a.rho), 53) * (1.0 + 1e-6)) + 2;
-  a.nl = 2 * ((unsigned long long)std::ceil(std::ldexp(a.rho, 53) * (1.0 + 1e-6)) + 2);
+  // integer bounds when the estimates carry no relative-to-scale absolute
+  // term and the lone estimate's bound is within the 4e-6 the height
+  // convention allows; above m0 = 2^30 eta the absolute term is within
+  // 2^-30 of an entry and joins rho
+  const double rho_i = a.rho + std::ldexp(1.0, -30);
+  const bool intb = f32 && a.delta == 0.0 && rho_i <= 4e-6;
+  a.nu = (unsigned long long)std::ceil(std::ldexp(rho_i / (1.0 - rho_i), 53) * (1.0 + 1e-6)) + 2;
+  a.nl = 2 * ((unsigned long long)std::ceil(std::ldexp(rho_i, 53) * (1.0 + 1e-6)) + 2);
+  {
+    const double m0 = std::ldexp(a.eta, 30);
+    memcpy(&a.m0, &m0, 8);
+    const double m0up = 2.0 * m0;
+    memcpy(&a.m0up, &m0up, 8);
+  }
   for (int it = 0;; ++it) {
     if (it >= 64) return HAC_EINTERNAL;
     CK(cudaMemsetAsync(&s.ctr->npend, 0, sizeof(int32_t), st));

@@ -16,6 +16,15 @@ __device__ __forceinline__ float sqrt_approx(float x) {
   return r;
 }
 
+// The same with subnormal inputs flushed to zero (one instruction fewer
+// paths); callers account for the flush: a squared distance below 2^-126
+// yields 0 instead of at most 2^-63.
+__device__ __forceinline__ float sqrt_approx_ftz(float x) {
+  float r;
+  asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+
 // Packed FP32 pairs (f32x2 in a 64-bit word): each half is rounded as the
 // scalar instruction would round it.
 __device__ __forceinline__ unsigned long long f2_pack(float a, float b) {

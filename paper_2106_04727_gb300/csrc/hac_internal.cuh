@@ -54,6 +54,7 @@ struct State {
   int linkage, prec;
   double abs_slack;     // absolute pruning slack (coordinate scale * 2^-18)
   float coord_scale;    // largest |coordinate| after recentring
+  double p32_max;       // largest |coordinate| of the FP32 point copy
   float delta_pts;      // absolute error term of an FP32 point distance (0 for FP32 input)
   int pts32_exact;      // the FP32 point copy is the FP32 input itself
   // points, permuted into cluster-contiguous segments
@@ -182,6 +183,7 @@ struct State {
   int dense;            // 1 once the instance runs on the matrix
   int dk;               // matrix dimension: active clusters at the switch
   int dexp;             // exponent of the fixed-point unit of the sweep sums
+  int dsk;              // the FP32 sweep scales coordinates by 2^dsk
   double dsl, dsh;      // 2^dexp and 2^(64 + dexp): a sum's low and high word scales
   double *dinv;         // 1 / size of the cluster at each matrix index
   double *dmat;         // dk x dk, row-major; diagonal +inf
@@ -296,6 +298,11 @@ __host__ __device__ inline int tree_caps(int K, int *cap) {
   }
   return L + 1;
 }
+
+// The FP32 paths take coordinates (of the FP32 copy) below 2^40: squared
+// differences then stay below 2^86 even for d = 16 and Ward's weights.  Runs
+// over larger coordinates take the FP64 path in either precision mode.
+constexpr double FP32_COORD_LIMIT = 1099511627776.0;  // 2^40
 
 // tinfo entries after the per-level node counts
 constexpr int TI_TOP = MAXLEV + 1;    // lowest level with at most 32 nodes (the root's children)

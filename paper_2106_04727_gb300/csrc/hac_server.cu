@@ -712,10 +712,24 @@ int submit_impl(hac_server_t srv, const void *points, int64_t n, int d, hac_dtyp
     return HAC_EINVAL;
   if (n > srv->cap) return HAC_ENOMEM;
   const size_t esz = dt == HAC_F32 ? 4 : 8;
+  double lo[MAXD], hi[MAXD], amax = 0.0;
+  for (int k = 0; k < d; ++k) {
+    lo[k] = INFINITY;
+    hi[k] = -INFINITY;
+  }
   for (int64_t i = 0; i < n * d; ++i) {
     const double x =
         dt == HAC_F32 ? (double)((const float *)points)[i] : ((const double *)points)[i];
     if (!std::isfinite(x)) return HAC_EINVAL;
+    lo[i % d] = std::min(lo[i % d], x);
+    hi[i % d] = std::max(hi[i % d], x);
+    amax = std::max(amax, std::fabs(x));
+  }
+  // the FP32 copy is the input itself (FP32 input) or the recentred points
+  if (srv->opt.precision == HAC_PREC_F32_RECHECK) {
+    double ext = 0.0;
+    for (int k = 0; k < d; ++k) ext = std::max(ext, 0.5 * (hi[k] - lo[k]));
+    if ((dt == HAC_F32 ? amax : ext) >= FP32_COORD_LIMIT) return HAC_EINVAL;
   }
   // owned here until published in srv->reqs (a throwing copy or insert frees it)
   std::unique_ptr<SrvReq> r(new (std::nothrow) SrvReq());

@@ -115,3 +115,80 @@ def test_ward_centroid_form(d):
     D32 = np.sqrt((w32 * dc2).astype(F)).astype(np.float64)
     delta = 2.01 * U * M * np.sqrt(d) * np.sqrt(w)
     assert np.all(np.abs(D32 - D) <= delta + (d + 16) * U * D)
+
+
+def _dense_estimate(A, B, k, es, sign):
+    """The dense sweep's FP32 estimate of the mean distance of two clusters of
+    float32 points: coordinates times 2^k, every FP32 step rounded, squared
+    distances below 2^-126 flushed to zero before the approximate root,
+    partial sums of at most 32 roots, each truncated to the unit 2^es."""
+    s = F(2.0 ** k)
+    As, Bs = (A * s).astype(F), (B * s).astype(F)
+    total = 0
+    for a in As:
+        acc = np.zeros(len(Bs), F)
+        for kk in range(A.shape[1]):
+            t = (a[kk] - Bs[:, kk]).astype(F)
+            acc = (acc + (t * t).astype(F)).astype(F)
+        acc[acc < F(2.0 ** -126)] = 0
+        roots = (np.sqrt(acc.astype(np.float64)) * (1.0 + sign * 2.0 ** -23)).astype(F)
+        for g in range(0, len(roots), 32):
+            part = F(0)
+            for v in roots[g:g + 32]:
+                part = F(part + v)
+            total += int(np.floor(float(part) / 2.0 ** es))
+    return total * 2.0 ** (es - k) / (len(A) * len(B))
+
+
+def _dense_fp64(A, B, e):
+    """The FP64 entry: every FP64 point distance truncated to the unit 2^e."""
+    d = np.sqrt(((A[:, None, :].astype(np.float64) - B[None, :, :]) ** 2).sum(-1))
+    return float(np.floor(d / 2.0 ** e).sum()) * 2.0 ** e / d.size
+
+
+@pytest.mark.parametrize("scale", [1e-30, 1e-3, 1.0, 1e5, 1e11])
+def test_dense_sweep_absolute_term(scale):
+    """Dense-phase estimates against the FP64 entries they stand in for:
+    |x - D| <= rho D + eta, rho = (d + 48) u, eta = 2 * 2^e + 2^(-63-k),
+    with the sweep's scale 2^k (|coordinate| toward 2^40, 0 <= k <= 100) and
+    unit e of a 10^6-point layout; clusters at every scale below the FP32
+    paths' limit of 2^40, including near-duplicate points whose squared
+    distances underflow unscaled."""
+    rng = np.random.default_rng(int(np.log10(scale)) + 400)
+    d, n = 5, 10 ** 6
+    for trial in range(6):
+        na, nb = rng.integers(1, 70, size=2)
+        ca = rng.normal(size=d) * scale
+        A = (ca + rng.normal(size=(na, d)) * scale * 10.0 ** -rng.integers(0, 9)).astype(F)
+        B = (ca + rng.normal(size=d) * scale * 10.0 ** -rng.integers(0, 9)
+             + rng.normal(size=(nb, d)) * scale * 10.0 ** -rng.integers(0, 9)).astype(F)
+        pmax = float(max(np.abs(A).max(), np.abs(B).max()))
+        k = max(0, min(100, 40 - int(np.ceil(np.log2(pmax))))) if pmax > 0 else 0
+        dmax = 2.0 * pmax * np.sqrt(d) * (1 + 1e-5)
+        e = int(np.floor(np.log2(0.25 * n * n * dmax))) + 1 - 126
+        D = _dense_fp64(A, B, e)
+        eta = (2.0 * 2.0 ** e + 2.0 ** (-63 - k)) * (1 + 1e-9)
+        rho = (d + 48) * U
+        for sign in (1.0, -1.0):
+            x = _dense_estimate(A, B, k, e + k, sign)
+            assert abs(x - D) <= rho * D + eta, (scale, trial, x, D, eta)
+
+
+def test_dense_sweep_flush_near_origin():
+    """Clusters of points within 1e-32 of the origin in a layout whose largest
+    coordinate is 1 (so the sweep's scale is 2^40): their scaled squared
+    distances fall below 2^-126 and flush to zero; the estimate stays within
+    the absolute term 2^(-63-k)."""
+    d, n = 3, 10 ** 6
+    A = np.array([[0, 0, 0], [1e-32, 0, 0], [0, 3e-33, 0]], F)
+    B = np.array([[2e-32, 1e-32, 0], [5e-33, 5e-33, 5e-33]], F)
+    pmax, k = 1.0, 40
+    dmax = 2.0 * pmax * np.sqrt(d) * (1 + 1e-5)
+    e = int(np.floor(np.log2(0.25 * n * n * dmax))) + 1 - 126
+    D = _dense_fp64(A, B, e)
+    eta = (2.0 * 2.0 ** e + 2.0 ** (-63 - k)) * (1 + 1e-9)
+    s = F(2.0 ** k)
+    assert ((A[0] * s - B[1] * s).astype(F) ** 2).sum() < 2.0 ** -126  # the flush occurs
+    for sign in (1.0, -1.0):
+        x = _dense_estimate(A, B, k, e + k, sign)
+        assert abs(x - D) <= (d + 48) * U * D + eta

@@ -111,6 +111,22 @@ def test_duplicates(lk):
 
 
 @pytest.mark.parametrize("lk", LKS)
+def test_huge_coordinates_take_fp64(lk):
+    """FP32 point copies with a coordinate of 2^40 or more would overflow the
+    FP32 paths: hac_run runs them in FP64 in either mode (same tree as the
+    oracle at FP64 tolerance)."""
+    rng = np.random.default_rng(77)
+    X = rng.normal(size=(400, 4)) * 1e13  # extent far above 2^40 after recentring
+    want = oracle.nnchain(X, lk)
+    for prec in PRECS:
+        got = hac.cluster(X, lk, precision=prec)
+        _assert_same(got, want, rtol=RTOL64, rounds=False)
+    got32 = hac.cluster(X.astype(np.float32), lk, precision=hac.PREC_F32_RECHECK)
+    _assert_same(got32, oracle.nnchain(X.astype(np.float32).astype(np.float64), lk),
+                 rtol=RTOL64, rounds=False)
+
+
+@pytest.mark.parametrize("lk", LKS)
 def test_collinear_closed_form(lk):
     m, hsp = 64, 0.25
     X = np.zeros((m, 2))

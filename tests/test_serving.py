@@ -279,3 +279,29 @@ def test_server_rejects_bad_options():
     srv = ctypes.c_void_p()
     assert hac.load().hac_server_create(1024, ctypes.byref(o), ctypes.byref(srv)) == hac.HAC_EINVAL
     assert hac.load().hac_server_create(1, None, ctypes.byref(srv)) == hac.HAC_EINVAL
+
+
+def test_fp32_server_refuses_huge_coordinates():
+    """An FP32 + re-score server takes FP32 copies below 2^40 (FP32 input:
+    the coordinates; FP64 input: the recentred ones); an FP64 server takes
+    anything finite."""
+    X = np.random.default_rng(5).normal(size=(50, 3)) * 1e13
+    srv = hac.hac_server_create(1 << 12, precision=hac.PREC_F32_RECHECK)
+    try:
+        for Y in (X, X.astype(np.float32)):
+            with pytest.raises(hac.HacError) as ex:
+                hac.hac_submit(srv, Y, "ward")
+            assert ex.value.code == hac.HAC_EINVAL
+        # a large offset with a small extent is fine for FP64 input
+        t = hac.hac_submit(srv, X * 1e-13 + 1e15, "ward")
+        assert hac.hac_server_wait(srv, t, 60.0) == hac.HAC_OK
+    finally:
+        hac.hac_server_destroy(srv)
+    srv = hac.hac_server_create(1 << 12, precision=hac.PREC_F64)
+    try:
+        t = hac.hac_submit(srv, X, "ward")
+        assert hac.hac_server_wait(srv, t, 60.0) == hac.HAC_OK
+        rc, m, _ = hac.hac_poll(srv, t, len(X))
+        assert rc == hac.HAC_OK and len(m) == len(X) - 1
+    finally:
+        hac.hac_server_destroy(srv)
