@@ -164,12 +164,14 @@ int hac_create_device(const void *dev_points, int64_t n, int d, hac_dtype dt, ha
 /* Run the whole clustering (paper: Algorithm 1 -- initialisation, then rounds
  * of nearest-neighbour search (Algorithms 2-4, Section 4), chain update,
  * reciprocal-pair filter, merges and the Section 5 cache update (Algorithm 5)
- * until one cluster is left).  Average linkage switches, once at most 32,768
+ * until one cluster is left).  Average linkage switches, once at most K
  * clusters are active, to the full matrix of their pair distances (the
- * Section 5 cache with room for every pair: 24 bytes per pair of active
- * clusters, allocated once per handle; without room for it the run stays on
- * the range-query search); the environment variable HAC_DENSE_K, read at
- * hac_create, sets that threshold (0 = never).  opts may be NULL (defaults).  Blocks until done.  May be called
+ * Section 5 cache with room for every pair: 24 bytes per entry of the K x K
+ * matrix, allocated once per handle; without room for it the run stays on
+ * the range-query search).  K is 8,192 for d <= 3, 16,384 for d <= 8 and
+ * 65,536 above, capped so that the matrix takes at most half of the device
+ * memory free when the run starts; the environment variable HAC_DENSE_K,
+ * read at hac_create, sets it instead (0 = never).  opts may be NULL (defaults).  Blocks until done.  May be called
  * again on the same handle: each call recomputes from the stored points.
  * HAC_ETIMEOUT if a limit in opts is hit (the handle stays usable). */
 int hac_run(hac_t h, const hac_opts *opts);

@@ -1809,6 +1809,7 @@ int run_impl(hac_ctx *h, const hac_opts *o) {
   int rc = h->dt == HAC_F32 ? init_layout<float>(h, st) : init_layout<double>(h, st);
   if (rc) return rc;
   if (s.p32_max >= FP32_COORD_LIMIT) s.prec = HAC_PREC_F64;  // FP32 would overflow
+  if (h->dense_k < 0 && s.linkage == LK_AVERAGE) h->dense_def = dense_default(s.d);
   cudaEventRecord(e1.e, st);
   CK(cudaEventSynchronize(e1.e));
   {

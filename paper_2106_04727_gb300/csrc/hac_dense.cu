@@ -1144,8 +1144,7 @@ int sweep(hac_ctx *h, cudaStream_t st, const SweepArgs &a) {
 }
 
 int64_t dense_threshold(const hac_ctx *h) {
-  if (h->dense_k >= 0) return h->dense_k;
-  return 32768;
+  return h->dense_k >= 0 ? h->dense_k : h->dense_def;
 }
 
 // FP64 re-score of the first m listed pairs (they then hold exact values)
@@ -1169,6 +1168,25 @@ int recheck(hac_ctx *h, cudaStream_t st, int m) {
 }
 
 }  // namespace
+
+// Default switch-over for a run: the tree search prunes well in low
+// dimension and poorly above 8, so the matrix pays off later (smaller K) in
+// 2-D and much earlier in 16-D.  Measured at 10^6 points (whole average run,
+// ms at 8,192 / 16,384 / 32,768): 2-D uniform 171 / 186 / 241, 2-D Gaussian
+// disc 174 / 185 / 250; 5-D mixture 438 / 432 / 472, 5-D uniform
+// 368 (12,288) / 374 / 429, 5-D Gaussian disc 778 / 521 / 518; 16-D lattice
+// 21.4 s / 11.5 s (32,768) / 9.0 s (49,152) / 8.3 s (65,536).  The two
+// matrices (24 B per entry of the K x K matrix) take at most half of the
+// device memory free at the start of the run.
+int64_t dense_default(int d) {
+  int64_t k = d <= 3 ? 8192 : d <= 8 ? 16384 : 65536;
+  size_t fr = 0, tot = 0;
+  if (cudaMemGetInfo(&fr, &tot) == cudaSuccess)
+    k = std::min<int64_t>(k, (int64_t)std::sqrt(0.5 * (double)fr / 24.0));
+  else
+    cudaGetLastError();
+  return k;
+}
 
 int dense_maybe_enter(hac_ctx *h, cudaStream_t st, int K, RoundCtl &ctl) {
   State &s = h->s;

@@ -145,6 +145,7 @@ struct hac_ctx {
   // average linkage switches to the dense matrix once at most this many
   // clusters are active (HAC_DENSE_K overrides it; 0 = never)
   int64_t dense_k = -1;  // -1: the default for the instance
+  int64_t dense_def = 0;  // that default for the current run (dense_default)
   int64_t dense_cap = 0; // matrix dimension the buffers were allocated for
   int64_t launches = 0;  // kernels launched in the current run
   int ocur = 0, pcur = 0;
@@ -250,6 +251,7 @@ int launch_big_average(const State &s, int r0, cudaStream_t st);
 // nearest-neighbour search of the round's terminals on the matrix (with the
 // FP64 re-score of near ties in the FP32 mode); the Lance-Williams update of
 // the matrix after the round's merges (before the compaction)
+int64_t dense_default(int d);
 int dense_maybe_enter(hac_ctx *h, cudaStream_t st, int K, RoundCtl &ctl);
 int dense_search(hac_ctx *h, cudaStream_t st, int K, int nterm, RoundCtl &ctl);
 int dense_update(hac_ctx *h, cudaStream_t st, int round, int K, int npairs);
