@@ -508,6 +508,199 @@ __global__ void k_tg_box(State s, int L, int K) {
   }
 }
 
+// The upper levels in one block.  Once a level has at most TG_TAIL elements
+// (and for the whole tree when K <= TG_TAIL), one block of 1,024 threads
+// builds it and every level above: the elements' keys are staged in shared
+// memory, runs are cut by the same rule as above (tg_start over the whole
+// staged level), the node keys of the next level stay in shared memory, and
+// the boxes are reduced by the block's 32 warps.  This saves four launches
+// per level in the many late rounds of small K.
+constexpr int TG_TAIL = 2048;
+constexpr int TG_TT = 1024;  // threads of the tail block
+struct TgCaps {
+  int cap[MAXLEV + 1];
+};
+
+// exclusive scan of one int per thread over TG_TT threads
+__device__ int tail_scan(int v, int *total, int *ws) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  int x = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) ws[w] = x;
+  __syncthreads();
+  if (w == 0) {
+    int t = ws[lane];
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, t, o);
+      if (lane >= o) t += y;
+    }
+    ws[lane] = t;
+  }
+  __syncthreads();
+  const int pre = w ? ws[w - 1] : 0;
+  *total = ws[31];
+  __syncthreads();
+  return pre + x - v;
+}
+
+// boxes of the nodes of level L (children: positions for L = 0), one warp per
+// node; the same reductions as k_tg_box
+template <int DP>
+__device__ void tail_boxes(State &s, int L, int mL, int mb) {
+  const int lane = threadIdx.x & 31;
+  const int *nch = s.nch + s.chb[L];
+  for (int j = threadIdx.x >> 5; j < mL; j += TG_TT / 32) {
+    const int c0 = nch[j];
+    int nc = nch[j + 1] - c0;
+    if (nc < 1 || nc > FAN) {
+      if (lane == 0) atomicOr(&s.ctr->err, ERR_TREE);
+      nc = max(1, min(nc, FAN));
+    }
+    const bool v = lane < nc && c0 + lane < mb;
+    const size_t c = (size_t)(L ? s.lvl_base[L - 1] : 0) + (size_t)(v ? c0 + lane : c0);
+    int nm = v ? (L ? s.nnmin[c] : s.qsz[c]) : INT_MAX;
+    int il = v ? (L ? s.ninlo[c] : s.qinst[c]) : INT_MAX;
+    int ih = v ? (L ? s.ninhi[c] : s.qinst[c]) : INT_MIN;
+    for (int o = 16; o; o >>= 1) {
+      nm = min(nm, __shfl_xor_sync(0xffffffffu, nm, o));
+      il = min(il, __shfl_xor_sync(0xffffffffu, il, o));
+      ih = max(ih, __shfl_xor_sync(0xffffffffu, ih, o));
+    }
+    const int node = s.lvl_base[L] + j;
+    if (lane == 0) {
+      s.ninlo[node] = il;
+      s.ninhi[node] = ih;
+      s.nnmin[node] = nm;
+    }
+#pragma unroll
+    for (int k = 0; k < DP; ++k) {
+      float lo, hi, hm, lm;
+      if (L) {
+        lo = v ? s.nclo[c * DP + k] : INFINITY;
+        hi = v ? s.nchi[c * DP + k] : -INFINITY;
+        hm = v ? s.nhmin[c * DP + k] : INFINITY;
+        lm = v ? s.nlmax[c * DP + k] : -INFINITY;
+      } else {
+        lo = v ? s.q32[c * DP + k] : INFINITY;
+        hi = v ? s.q32[c * DP + k] : -INFINITY;
+        hm = v ? s.qbhi[c * DP + k] : INFINITY;
+        lm = v ? s.qblo[c * DP + k] : -INFINITY;
+      }
+      for (int o = 16; o; o >>= 1) {
+        lo = fminf(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+        hi = fmaxf(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+        hm = fminf(hm, __shfl_xor_sync(0xffffffffu, hm, o));
+        lm = fmaxf(lm, __shfl_xor_sync(0xffffffffu, lm, o));
+      }
+      if (lane == k) {
+        s.nclo[(size_t)node * DP + k] = lo;
+        s.nchi[(size_t)node * DP + k] = hi;
+        s.nhmin[(size_t)node * DP + k] = hm;
+        s.nlmax[(size_t)node * DP + k] = lm;
+      }
+    }
+  }
+}
+
+// levels L0 .. nl - 1 in one block (L0: the first level the host leaves to
+// it; a lower level may already be the top, then nothing is left to do)
+template <int DP>
+__global__ void __launch_bounds__(TG_TT) k_tg_tail(State s, const int32_t *order,
+                                                   const uint64_t *ekey, const int32_t *einst,
+                                                   int L0, int nl, int K, TgCaps caps) {
+  // the level staged whole, between halos of TG_H empty slots (instance -1),
+  // so that tg_start reads it exactly as the grid-wide kernels read theirs
+  __shared__ uint64_t sk_h[TG_TAIL + 2 * TG_H];
+  __shared__ int32_t sq_h[TG_TAIL + 2 * TG_H];
+  uint64_t *sk = sk_h + TG_H;
+  int32_t *sq = sq_h + TG_H;
+  __shared__ int ws[32];
+  __shared__ int s_fixed;
+  if (L0 > 0 && tg_idle(s, L0)) return;  // uniform
+  int m = L0 ? s.tinfo[L0 - 1] : K;
+  if (m > TG_TAIL) {  // cannot happen: the host hands over levels of at most TG_TAIL
+    if (threadIdx.x == 0) atomicOr(&s.ctr->err, ERR_TREE);
+    return;
+  }
+  for (int i = threadIdx.x; i < m; i += TG_TT) {
+    sk[i] = L0 ? ekey[i] : s.mkey[order[i]];
+    sq[i] = L0 ? einst[i] : s.qinst[i];
+  }
+  for (int L = L0; L < nl; ++L) {
+    // empty slots from m on (the halo below 0 stays empty)
+    for (int i = threadIdx.x; i < TG_TAIL + TG_H; i += TG_TT) {
+      if (i < TG_H) sq_h[i] = -1;
+      if (i >= m) sq[i] = -1;
+    }
+    if (threadIdx.x == 0) s_fixed = 0;
+    __syncthreads();
+    // run starts of this thread's elements (at most TG_TAIL / TG_TT of them)
+    constexpr int PER = TG_TAIL / TG_TT;
+    bool f[PER];
+    uint64_t kk[PER];
+    int32_t qq[PER];
+    int cnt = 0;
+#pragma unroll
+    for (int r = 0; r < PER; ++r) {
+      const int i = threadIdx.x * PER + r;
+      f[r] = false;
+      if (i < m) {
+        f[r] = tg_start(sk_h, sq_h, i, i);
+        kk[r] = sk[i];
+        qq[r] = sq[i];
+        if (i > 0 && (sq[i - 1] > sq[i] || (sq[i - 1] == sq[i] && sk[i - 1] > sk[i])))
+          s_fixed = 1;
+      }
+    }
+    __syncthreads();
+    int tot;
+#pragma unroll
+    for (int r = 0; r < PER; ++r) cnt += f[r];
+    int pre = tail_scan(cnt, &tot, ws);
+    const bool fixed = s_fixed || tot > caps.cap[L];
+    if (fixed) {
+      cnt = 0;
+#pragma unroll
+      for (int r = 0; r < PER; ++r) {
+        const int i = threadIdx.x * PER + r;
+        f[r] = i < m && (i % FAN) == 0;
+        cnt += f[r];
+      }
+      pre = tail_scan(cnt, &tot, ws);
+    }
+    const int mL = tot;
+    // first children, node keys (into shared memory for the next level), buckets
+#pragma unroll
+    for (int r = 0; r < PER; ++r) {
+      const int i = threadIdx.x * PER + r;
+      if (i >= m) continue;
+      if (f[r]) {
+        s.nch[s.chb[L] + pre] = i;
+        sk[pre] = kk[r];
+        sq[pre] = qq[r];
+      }
+      if (L == 0) s.pbkt[i] = pre + (f[r] ? 0 : -1);
+      pre += f[r];
+    }
+    if (threadIdx.x == 0) {
+      s.tinfo[L] = mL;
+      if (fixed) s.tinfo[TI_FIXED] |= 1 << L;
+      s.nch[s.chb[L] + mL] = m;
+      if (mL <= FAN) s.tinfo[TI_TOP] = L + 1;
+    }
+    __syncthreads();
+    tail_boxes<DP>(s, L, mL, m);
+    __syncthreads();
+    if (mL <= FAN) break;
+    m = mL;
+  }
+}
+
 // ---------------------------------------------------------------------------
 // per-round kernels
 // ---------------------------------------------------------------------------
@@ -1149,8 +1342,10 @@ int build_tree_dp(hac_ctx *h, const int32_t *order, int K, cudaStream_t st) {
   int cap[MAXLEV + 1];
   const int nl = tree_caps(K, cap);
   CK(cudaMemsetAsync(s.tinfo, 0, TI_SIZE * sizeof(int32_t), st));
+  // levels whose elements may exceed TG_TAIL: four grid-wide launches each;
   // levels above the first one of at most 32 nodes return at once
-  for (int L = 0; L < nl; ++L) {
+  int L = 0;
+  for (; L < nl && (L ? cap[L - 1] : K) > TG_TAIL; ++L) {
     const int nb = cdiv(L ? cap[L - 1] : K, TPB);  // blocks for the most elements possible
     const uint64_t *ek = L ? h->keys[(L - 1) & 1] : s.mkey;
     const int32_t *eo = L ? nullptr : order;
@@ -1159,8 +1354,17 @@ int build_tree_dp(hac_ctx *h, const int32_t *order, int K, cudaStream_t st) {
     k_tg_top<<<1, TPB, 0, st>>>(s, L, K, cap[L]);
     k_tg_write<<<nb, TPB, 0, st>>>(s, L, ek, eo, ei, h->keys[L & 1], h->vals[L & 1], K);
     k_tg_box<DP><<<grid_for((int64_t)cap[L] * 32, TPB), TPB, 0, st>>>(s, L, K);
+    h->launches += 4;
   }
-  h->launches += 4 * nl + 1;
+  // the rest in one block
+  if (L < nl) {
+    TgCaps c{};
+    for (int l = 0; l < nl; ++l) c.cap[l] = cap[l];
+    k_tg_tail<DP><<<1, TG_TT, 0, st>>>(s, order, L ? h->keys[(L - 1) & 1] : nullptr,
+                                       L ? h->vals[(L - 1) & 1] : nullptr, L, nl, K, c);
+    h->launches += 1;
+  }
+  h->launches += 1;
   CK(cudaGetLastError());
   return HAC_OK;
 }

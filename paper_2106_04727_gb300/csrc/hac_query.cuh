@@ -680,15 +680,27 @@ struct Searcher {
   // the candidate at position idx of this lane (in: the lane has one); the
   // 32 lanes' candidates are tested, scored and offered together
   __device__ void leaf_at(int idx, bool in, bool seed) {
-    const int cb = in ? a.order[idx] : -1;
-    const bool valid = in && cb != ci && a.qinst[idx] == myseq;
-    const int nb = valid ? a.qsz[idx] : 1;
+    // every load of the candidate's record is issued before any test on it,
+    // so a leaf step waits for memory once, not once per dependent test
+    int cb = -1, qi = -1, nbq = 1, sbq = 0;
+    float qc[DP], qv = 0.f;
+    if (in) {
+      cb = a.order[idx];
+      qi = a.qinst[idx];
+      nbq = a.qsz[idx];
+#pragma unroll
+      for (int k = 0; k < DP; ++k) qc[k] = a.q32[(size_t)idx * DP + k];
+      if (LK == LK_AVERAGE || LK == LK_AVG2) qv = a.qvar[idx];
+      if (LK == LK_COMPLETE || LK == LK_AVERAGE) sbq = a.qseg[idx];
+    }
+    const bool valid = in && cb != ci && qi == myseq;
+    const int nb = valid ? nbq : 1;
     float dc2 = INFINITY, bx = 0.f;
     if (valid) {
       dc2 = 0.f;
 #pragma unroll
       for (int k = 0; k < DP; ++k) {
-        const float t = ci32[k] - a.q32[(size_t)idx * DP + k];
+        const float t = ci32[k] - qc[k];
         dc2 = fmaf(t, t, dc2);
         if (LK == LK_COMPLETE) {
           bx = fmaxf(bx, a.qbhi[(size_t)idx * DP + k] - alo[k]);
@@ -704,7 +716,7 @@ struct Searcher {
         d32 = valid ? sqrtf(w * dc2) : INFINITY;
         dlt = delta0 * sqrtf(w);
       } else {
-        d32 = valid ? sqrtf(dc2 + vA + a.qvar[idx]) : INFINITY;
+        d32 = valid ? sqrtf(dc2 + vA + qv) : INFINITY;
         dlt = delta0;
       }
       if (MODE == M_F32) {
@@ -756,7 +768,7 @@ struct Searcher {
           // mean ||x - y|| <= sqrt(mean ||x - y||^2) = sqrt(||c_A - c_B||^2 + var A + var B)
           // (Jensen); the FP32 centroid distance is widened by its error bound
           const float r = __fadd_ru(__fmul_ru(__fsqrt_ru(dc2), 1.f + rho), delta0);
-          ub = __fsqrt_ru(__fadd_ru(__fadd_ru(__fmul_ru(r, r), vA), a.qvar[idx]));
+          ub = __fsqrt_ru(__fadd_ru(__fadd_ru(__fmul_ru(r, r), vA), qv));
         } else {
           // max ||x - y|| <= distance between the farthest corners of the boxes
           float s2 = 0.f;
@@ -773,7 +785,7 @@ struct Searcher {
     }
     const float lb = valid ? fmaxf(sqrtf(dc2), bx) : INFINITY;
     const bool ok = valid && pass(lb);
-    const int sb = valid ? a.qseg[idx] : 0;
+    const int sb = valid ? sbq : 0;
     const float dlt = dpts;
     const bool small = ok && (long long)na * nb <= SMALLP;
     const unsigned sm = __ballot_sync(0xffffffffu, small);
@@ -1029,18 +1041,23 @@ struct Searcher {
 // the nodes of the top level, nearest child first, pruning every node whose
 // lower bound exceeds the threshold.
 template <int LK, int DP, int MODE>
-__device__ int push_children(const QueryArgs &a, Searcher<LK, DP, MODE> &S, uint32_t *sn,
-                             float *sl, int top, int Lc, int c0, int cnt, int lane) {
+__device__ int push_children(const QueryArgs &a, const int *ti, Searcher<LK, DP, MODE> &S,
+                             uint32_t *sn, float *sl, int top, int Lc, int c0, int cnt,
+                             int lane) {
   const int child = c0 + lane;
   float lbc = INFINITY;
   bool ok = false;
   // (the bound on the level's node count only guards a malformed tree,
   // which the build flags as ERR_TREE)
-  const bool in = lane < cnt && child < a.tinfo[Lc];
+  const bool in = lane < cnt && child < ti[Lc];
   if (in) {
+    // the node's bound is computed while its instance range is still in
+    // flight (both loads issued together)
     const int node = a.lvl_base[Lc] + child;
-    if (a.ninlo[node] <= S.myseq && S.myseq <= a.ninhi[node]) {
-      lbc = node_lb<LK, DP>(a, node, S.ci32, S.alo, S.ahi, S.fna, S.vA);
+    const int ilo = a.ninlo[node], ihi = a.ninhi[node];
+    const float lb = node_lb<LK, DP>(a, node, S.ci32, S.alo, S.ahi, S.fna, S.vA);
+    if (ilo <= S.myseq && S.myseq <= ihi) {
+      lbc = lb;
       ok = S.pass(lbc);
     }
   }
@@ -1077,15 +1094,15 @@ __device__ int push_children(const QueryArgs &a, Searcher<LK, DP, MODE> &S, uint
 }
 
 template <int LK, int DP, int MODE>
-__device__ void traverse(const QueryArgs &a, Searcher<LK, DP, MODE> &S, uint32_t *sn, float *sl,
-                         int own, int lane) {
+__device__ void traverse(const QueryArgs &a, const int *ti, Searcher<LK, DP, MODE> &S,
+                         uint32_t *sn, float *sl, int own, int lane) {
   S.leaf(own, true);
-  const int tl = a.tinfo[TI_TOP] - 1;  // top level: at most 32 nodes
-  if (tl < 0 || tl > MAXLEV) {          // never for a finished build
+  const int tl = ti[TI_TOP] - 1;  // top level: at most 32 nodes
+  if (tl < 0 || tl > MAXLEV) {    // never for a finished build
     if (lane == 0) atomicOr(&a.ctr->err, ERR_TREE);
     return;
   }
-  int top = push_children(a, S, sn, sl, 0, tl, 0, min(a.tinfo[tl], FAN), lane);
+  int top = push_children(a, ti, S, sn, sl, 0, tl, 0, min(ti[tl], FAN), lane);
   while (top > 0) {
     --top;
     const uint32_t e = sn[top];
@@ -1098,7 +1115,7 @@ __device__ void traverse(const QueryArgs &a, Searcher<LK, DP, MODE> &S, uint32_t
       continue;
     }
     const int c0 = a.nch[a.chb[L] + j];
-    top = push_children(a, S, sn, sl, top, L - 1, c0, a.nch[a.chb[L] + j + 1] - c0, lane);
+    top = push_children(a, ti, S, sn, sl, top, L - 1, c0, a.nch[a.chb[L] + j + 1] - c0, lane);
   }
 }
 
@@ -1130,7 +1147,10 @@ __global__ void __launch_bounds__(QWARPS * 32, QMINB) k_query(QueryArgs a) {
   float *sl = s_lb[wib];
   unsigned long long *sc = s_cnt[wib];
   if (lane < C_N) sc[lane] = 0;
-  __syncwarp();
+  // the tree's level counts and top level, read once per block
+  __shared__ int s_ti[TI_SIZE];
+  for (int i = threadIdx.x; i < TI_SIZE; i += blockDim.x) s_ti[i] = a.tinfo[i];
+  __syncthreads();
   for (int t = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; t < a.nterm; t += nw) {
     const int ci = a.term[t];
     const int own = a.pbkt[a.pos[ci]];
@@ -1144,7 +1164,7 @@ __global__ void __launch_bounds__(QWARPS * 32, QMINB) k_query(QueryArgs a) {
       if (lc >= 0)
         traverse_list(a, S, a.pos[ci], lc, lane);
       else
-        traverse(a, S, sn, sl, own, lane);
+        traverse(a, s_ti, S, sn, sl, own, lane);
       bk = S.bk;
       bc = S.bc;
       deferred = S.deferred;
@@ -1154,7 +1174,7 @@ __global__ void __launch_bounds__(QWARPS * 32, QMINB) k_query(QueryArgs a) {
       if (lc >= 0)
         traverse_list(a, S, a.pos[ci], lc, lane);
       else
-        traverse(a, S, sn, sl, own, lane);
+        traverse(a, s_ti, S, sn, sl, own, lane);
       S.finish_f32();
       if (S.deferred) {
         // incomplete: some candidates still wait for their values
@@ -1175,7 +1195,7 @@ __global__ void __launch_bounds__(QWARPS * 32, QMINB) k_query(QueryArgs a) {
         if (lc >= 0)
           traverse_list(a, R, a.pos[ci], lc, lane);
         else
-          traverse(a, R, sn, sl, own, lane);
+          traverse(a, s_ti, R, sn, sl, own, lane);
         bk = R.bk;
         bc = R.bc;
         deferred = R.deferred;
