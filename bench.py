@@ -37,9 +37,9 @@ UNIT = "points/s"
 TRAFFIC = {}
 # DRAM bytes (read + write) per point pair of the dense sweep, from a
 # small-case ncu capture of the current kernel (profiles/
-# k_dense_sweep32_gmm5d_100k.md: 383.4 MB for 4.995e9 pairs); the bench
+# k_dense_sweep32_gmm5d_100k.md: 385.1 MB for 4.995e9 pairs); the bench
 # scales it by the pairs of a full launch
-SWEEP_DRAM_PER_PAIR = 383.4e6 / 4.995e9
+SWEEP_DRAM_PER_PAIR = 385.1e6 / 4.995e9
 
 
 def _peaks():
