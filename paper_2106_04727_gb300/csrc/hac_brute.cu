@@ -112,7 +112,7 @@ struct BruteTerm {
       }
       return kbits(g2 + a.sse[ci] / (double)na + a.sse[cb] / (double)nb);
     }
-    return kbits(ward_key<DP>(cA, cB, na, nb));
+    return kbits(ward_key<DP>(cA, cB, na, nb, DP));
   }
 };
 

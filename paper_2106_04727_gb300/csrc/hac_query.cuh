@@ -202,12 +202,15 @@ __device__ __forceinline__ float node_lb(const QueryArgs &a, int node, const flo
 
 // Ward key 2|A||B|/(|A|+|B|) ||c_A - c_B||^2 in FP64 (Table 1).
 template <int DP>
-__device__ __forceinline__ double ward_key(const double *cA, const double *cB, int na, int nb) {
+__device__ __forceinline__ double ward_key(const double *cA, const double *cB, int na, int nb,
+                                           int d) {
   double s = 0.0;
 #pragma unroll
   for (int k = 0; k < DP; ++k) {
-    double t = cA[k] - cB[k];
-    s += t * t;
+    if (k < d) {  // the padding coordinates add +0
+      double t = cA[k] - cB[k];
+      s += t * t;
+    }
   }
   return (2.0 * (double)na * (double)nb) / (double)(na + nb) * s;
 }
@@ -652,23 +655,28 @@ struct Searcher {
 
   // exact (FP64) key of a closed-form linkage: Ward from the centroids and
   // sizes; avg-2 = ||c_A - c_B||^2 + SSE_A/|A| + SSE_B/|B| (Table 1)
+  // (coordinates from d up to the row stride DP are zero on both sides: they
+  // are skipped, which leaves every sum bit for bit unchanged and spares the
+  // small FP64 pipe)
   __device__ unsigned long long ward64(int q, int nb, int cb) const {
     double cA[DP], cB[DP];
 #pragma unroll
     for (int k = 0; k < DP; ++k) {
-      cA[k] = a.cent[(size_t)ci * DP + k];
-      cB[k] = a.q64[(size_t)q * DP + k];
+      cA[k] = k < a.d ? a.cent[(size_t)ci * DP + k] : 0.0;
+      cB[k] = k < a.d ? a.q64[(size_t)q * DP + k] : 0.0;
     }
     if (LK == LK_AVG2) {
       double g2 = 0.0;
 #pragma unroll
       for (int k = 0; k < DP; ++k) {
-        const double t = cA[k] - cB[k];
-        g2 += t * t;
+        if (k < a.d) {
+          const double t = cA[k] - cB[k];
+          g2 += t * t;
+        }
       }
       return kbits(g2 + a.sse[ci] / (double)na + a.sse[cb] / (double)nb);
     }
-    return kbits(ward_key<DP>(cA, cB, na, nb));
+    return kbits(ward_key<DP>(cA, cB, na, nb, a.d));
   }
 
   // the records of bucket j, one per lane
