@@ -58,16 +58,14 @@ namespace {
 #define HAC_QWARPS 4
 #endif
 #ifndef HAC_QMINB
-#define HAC_QMINB 4
+#define HAC_QMINB 6
 #endif
 constexpr int QWARPS = HAC_QWARPS;  // warps per block
-// resident blocks per SM the register budget must allow.  The complete and
-// average searches are latency-bound, and more resident warps beat the
-// register spills they cost: the shape tuner's average-linkage runs at
-// 10^6 points take 523 / 515 / 514 / 507 ms at 3 / 4 / 5 / 6 blocks (168 /
-// 128 / 96 / 80 registers, 20 / 156 / 472 / 580 B of spill stores).  4 is
-// kept: 6 gains 1.5 %, about the run-to-run spread, for 4x the spills.
-// Ward and avg-2 (about 110 registers, no spills) are bounded the same way.
+// resident blocks per SM the register budget must allow.  The searches are
+// latency-bound, and more resident warps beat the register spills they cost:
+// the shape tuner's whole-run times at 10^6 points (5-D mixture), at 4 / 5 / 6
+// blocks (128 / 96 / 80 registers): average 431 / 431 / 423 ms, complete
+// 365 / 374 / 366 ms, Ward 68 / - / 61 ms.
 constexpr int QMINB = HAC_QMINB;
 constexpr int STK = 288;           // per-warp stack: >= 32 + 31 * (levels - 1), 9 levels for n < 2^31
 constexpr float EPS = 1e-5f;       // relative slack of the FP32 bound tests
