@@ -58,15 +58,19 @@ namespace {
 #define HAC_QWARPS 4
 #endif
 #ifndef HAC_QMINB
-#define HAC_QMINB 6
+#define HAC_QMINB 8
+#endif
+#ifndef HAC_QMINB_COMPLETE
+#define HAC_QMINB_COMPLETE 6
 #endif
 constexpr int QWARPS = HAC_QWARPS;  // warps per block
 // resident blocks per SM the register budget must allow.  The searches are
 // latency-bound, and more resident warps beat the register spills they cost:
-// the shape tuner's whole-run times at 10^6 points (5-D mixture), at 4 / 5 / 6
-// blocks (128 / 96 / 80 registers): average 431 / 431 / 423 ms, complete
-// 365 / 374 / 366 ms, Ward 68 / - / 61 ms.
-constexpr int QMINB = HAC_QMINB;
+// the shape tuner's whole-run times at 10^6 points (5-D mixture), at
+// 4 / 5 / 6 / 8 blocks (128 / 96 / 80 / 64 registers): average 431 / 431 /
+// 423 / 415 ms, Ward 68 / - / 61 / 59 ms; complete 365 / 374 / 366 / - ms
+// (its box bounds hold more registers), so complete keeps 6.
+constexpr int qminb(int lk) { return lk == LK_COMPLETE ? HAC_QMINB_COMPLETE : HAC_QMINB; }
 constexpr int STK = 288;           // per-warp stack: >= 32 + 31 * (levels - 1), 9 levels for n < 2^31
 constexpr float EPS = 1e-5f;       // relative slack of the FP32 bound tests
 constexpr long long SMALLP = 32;   // pairs of at most this many point pairs run per lane
@@ -1142,7 +1146,7 @@ __device__ void traverse_list(const QueryArgs &a, Searcher<LK, DP, MODE> &S, int
 
 
 template <int LK, int DP, int PREC>
-__global__ void __launch_bounds__(QWARPS * 32, QMINB) k_query(QueryArgs a) {
+__global__ void __launch_bounds__(QWARPS * 32, qminb(LK)) k_query(QueryArgs a) {
   __shared__ uint32_t s_node[QWARPS][STK];
   __shared__ float s_lb[QWARPS][STK];
   __shared__ unsigned long long s_cnt[QWARPS][C_N];

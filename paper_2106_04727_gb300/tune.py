@@ -27,7 +27,8 @@ thresholds at their defaults); one JSON line per variant, then the fastest.
 
 The macros: HAC_DS_PPT8 / HAC_DS_MINB (rows per thread of the dense sweep for
 d <= 8 / its resident tiles per SM), HAC_QWARPS (warps per block of the
-search), HAC_QMINB (its resident blocks per SM, which bounds its registers),
+search), HAC_QMINB / HAC_QMINB_COMPLETE (its resident blocks per SM, which
+bound its registers; the second for complete linkage),
 HAC_Q_OUTLINE (1: its warp-wide pair evaluations compiled out of line),
 HAC_BR_T / HAC_BR_C (terminals per CTA / records per staged tile of
 the exhaustive scans), HAC_CM_WARPS (warps per block of the cache update).
@@ -41,7 +42,7 @@ import os
 import statistics
 
 
-SHAPES = ("HAC_DS_PPT8", "HAC_DS_MINB", "HAC_QWARPS", "HAC_QMINB", "HAC_Q_OUTLINE", "HAC_BR_T",
+SHAPES = ("HAC_DS_PPT8", "HAC_DS_MINB", "HAC_QWARPS", "HAC_QMINB", "HAC_QMINB_COMPLETE", "HAC_Q_OUTLINE", "HAC_BR_T",
           "HAC_BR_C", "HAC_CM_WARPS")
 
 
