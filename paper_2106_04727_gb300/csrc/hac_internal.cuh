@@ -289,7 +289,7 @@ __host__ __device__ inline bool closed_form(int linkage) { return linkage >= 2; 
 // of 32 instead, which always fit.  The last level has at most 32 nodes.
 // Returns the number of levels (<= MAXLEV + 1).
 __host__ __device__ inline int tree_caps(int K, int *cap) {
-  int c = (K + 7) / 8 + 1, L = 0;
+  int c = (int)(((long long)K + 7) / 8) + 1, L = 0;  // K + 7 may overflow an int
   if (cap) cap[0] = c;
   while (c > FAN) {
     c = (c + 7) / 8 + 1;
