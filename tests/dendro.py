@@ -109,6 +109,26 @@ def sample_small(d, k, cap=64, seed=0):
     return out
 
 
+def sample_big(d, k, max_pairs):
+    """The k merges with the most point pairs |A| x |B| among those with at
+    most max_pairs, with the point sets of their two sides:
+    [(t, side_a, side_b)]."""
+    ca, cb, probs = children(d)
+    assert not probs, probs
+    size = np.asarray(d["size"], np.int64)
+    sa = np.where(ca >= 0, size[np.maximum(ca, 0)], 1)
+    sb = np.where(cb >= 0, size[np.maximum(cb, 0)], 1)
+    pairs = sa * sb
+    ok = np.flatnonzero(pairs <= max_pairs)
+    pick = ok[np.argsort(pairs[ok], kind="stable")][-k:]
+    out = []
+    for t in pick:
+        A = members(d, ca[t], ca, cb) if ca[t] >= 0 else [int(d["a"][t])]
+        B = members(d, cb[t], ca, cb) if cb[t] >= 0 else [int(d["b"][t])]
+        out.append((int(t), A, B))
+    return out
+
+
 def pick_merges(d, k_small, cap=32, k_big=0, big_cap=2048, every_size=False, seed=0):
     """Merges to check: k_small random ones whose cluster has at most cap
     points (any size with every_size), plus the k_big largest whose smaller

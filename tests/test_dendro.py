@@ -129,3 +129,17 @@ def test_rnn_check_catches_a_wrong_partner(lk):
     bad["b"][m] = far
     probs, _, _ = dendro.rnn_check(bad, X, lk, [m], oracle.dist_to_all)
     assert probs and "closer" in probs[0]
+
+
+def test_sample_big_picks_the_most_pairs_within_the_limit():
+    """Merges ((0,1), (2,3), (01,23), (0123,4)) of five points: pair counts
+    1, 1, 4, 4; a limit of 3 leaves the first two; the largest within 4 are
+    the last two, with their point sets."""
+    d = {"a": np.array([0, 2, 0, 0]), "b": np.array([1, 3, 2, 4]),
+         "h": np.array([1.0, 1.0, 2.0, 3.0]), "size": np.array([2, 2, 4, 5]),
+         "round": np.array([0, 0, 1, 2])}
+    got = dendro.sample_big(d, 2, 4)
+    assert [t for t, _, _ in got] == [2, 3]
+    assert sorted(got[0][1]) == [0, 1] and sorted(got[0][2]) == [2, 3]
+    assert sorted(got[1][1]) == [0, 1, 2, 3] and got[1][2] == [4]
+    assert [t for t, _, _ in dendro.sample_big(d, 2, 3)] == [0, 1]

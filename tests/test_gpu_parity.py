@@ -371,6 +371,19 @@ def _check_sampled(got, X, lk, rtol, k=300):
         assert got["h"][t] == pytest.approx(want, rel=rtol, abs=1e-12), (t, len(sa), len(sb))
 
 
+def _check_big(got, X, lk, rtol, k=2, max_pairs=4e8):
+    """The merges with the most point pairs the oracle can afford here
+    (|A| x |B| <= max_pairs): the height equals its Table 1 value of the two
+    merged point sets."""
+    X64 = X.astype(np.float64)
+    picks = dendro.sample_big(got, k, max_pairs)
+    assert len(picks) == k
+    for t, sa, sb in picks:
+        assert len(sa) * len(sb) > 10 ** 5  # big merges, not the small ones again
+        want = oracle.cluster_dist(lk, X64[sa], X64[sb])
+        assert got["h"][t] == pytest.approx(want, rel=rtol, abs=1e-12), (t, len(sa), len(sb))
+
+
 def _check_rnn(got, X, lk, k_small, k_big=0, every_size=False, side_cap=None):
     """Sampled merges were reciprocal nearest neighbours among the clusters
     active in their round, every distance from the points by the oracle (for
@@ -395,6 +408,7 @@ def test_full_size_1m_average(prec):
     rtol = _rtol("average", prec)
     assert dendro.check(got, len(X), rtol=2 * rtol) == []
     _check_sampled(got, X, "average", rtol)
+    _check_big(got, X, "average", rtol)
     _check_rnn(got, X, "average", 12, k_big=1, side_cap=512)
     if prec == hac.PREC_F64:
         _FULL["average"] = got
