@@ -756,6 +756,9 @@ __global__ void k_dense_nn(NNArgs a) {
     // (x - delta - eta) / (1 + rho) <= D <= (x + delta + eta) / (1 - rho),
     // widened by 1e-12 for the rounding of these FP64 operations.
     const double dl = a.delta + a.eta;
+    // x - dl rounds by up to 2^-52 max(x, dl): when x is close to dl that is
+    // not within the relative 1e-12, so the lower bound subtracts a little more
+    const double dlo = dl * (1.0 + 0x1p-50);
     const double lo_f = (1.0 - 1e-12) / (1.0 + a.rho), up_f = (1.0 + 1e-12) / (1.0 - a.rho);
     double U = INFINITY;
     for (int p0 = 0; p0 < a.K; p0 += 32 * NN_U) {
@@ -793,7 +796,7 @@ __global__ void k_dense_nn(NNArgs a) {
         if (c[u] == ci) continue;
         const double m = mag(x[u]);
         const bool exact = !is_est(x[u]);
-        const double lo = exact ? m : fmax(m - dl, 0.0) * lo_f;
+        const double lo = exact ? m : fmax(m - dlo, 0.0) * lo_f;
         if (!(lo <= U)) continue;
         ++nW;
         if (exact) {
@@ -851,7 +854,7 @@ __global__ void k_dense_nn(NNArgs a) {
         const double x = row[q];
         const double m = mag(x);
         const bool exact = !is_est(x);
-        if (exact || !(fmax(m - dl, 0.0) * lo_f <= U)) continue;
+        if (exact || !(fmax(m - dlo, 0.0) * lo_f <= U)) continue;
         const int r = atomicAdd(&a.ctr->nrq, 1);
         if (r < a.drq_cap) {
           a.drq_a[r] = min(qi, q);
