@@ -342,7 +342,9 @@ void hac_server_destroy(hac_server_t srv);
  * are done; allocates the engines for the call (about the size of the
  * handles' own state) and frees them before returning.  Returns HAC_OK, or
  * the first error of any handle (that handle then has no dendrogram;
- * HAC_EINVAL also for a NULL or repeated handle or a non-finite coordinate). */
+ * HAC_EINVAL also for a NULL or repeated handle, a non-finite coordinate, or
+ * in the FP32 + re-score mode a handle whose FP32 copy would hold a
+ * coordinate of 2^40 or more, which hac_run runs in FP64 instead). */
 int hac_run_batch(hac_t *hs, int count, const hac_opts *opts);
 
 #ifdef __cplusplus
