@@ -444,68 +444,73 @@ __global__ void k_tg_write(State s, int L, const uint64_t *ekey, const int32_t *
   if (L == 0 && i < m) s.pbkt[i] = idx + f - 1;
 }
 
+// Box, least cluster size and instance range of node j of level L, one lane
+// per child (children: positions for L = 0, of which there are mb)
+template <int DP>
+__device__ void tg_node_box(const State &s, int L, int j, int mb, int lane) {
+  const int *nch = s.nch + s.chb[L];
+  const int c0 = nch[j];
+  int nc = nch[j + 1] - c0;
+  if (nc < 1 || nc > FAN) {
+    if (lane == 0) atomicOr(&s.ctr->err, ERR_TREE);
+    nc = max(1, min(nc, FAN));
+  }
+  const bool v = lane < nc && c0 + lane < mb;
+  // a child: a position-ordered record (L = 0) or a node of level L - 1
+  const size_t c = (size_t)(L ? s.lvl_base[L - 1] : 0) + (size_t)(v ? c0 + lane : c0);
+  int nm = v ? (L ? s.nnmin[c] : s.qsz[c]) : INT_MAX;
+  int il = v ? (L ? s.ninlo[c] : s.qinst[c]) : INT_MAX;
+  int ih = v ? (L ? s.ninhi[c] : s.qinst[c]) : INT_MIN;
+  for (int o = 16; o; o >>= 1) {
+    nm = min(nm, __shfl_xor_sync(0xffffffffu, nm, o));
+    il = min(il, __shfl_xor_sync(0xffffffffu, il, o));
+    ih = max(ih, __shfl_xor_sync(0xffffffffu, ih, o));
+  }
+  const int node = s.lvl_base[L] + j;
+  if (lane == 0) {
+    s.ninlo[node] = il;
+    s.ninhi[node] = ih;
+    s.nnmin[node] = nm;
+  }
+#pragma unroll
+  for (int k = 0; k < DP; ++k) {
+    float lo, hi, hm, lm;
+    if (L) {
+      lo = v ? s.nclo[c * DP + k] : INFINITY;
+      hi = v ? s.nchi[c * DP + k] : -INFINITY;
+      hm = v ? s.nhmin[c * DP + k] : INFINITY;
+      lm = v ? s.nlmax[c * DP + k] : -INFINITY;
+    } else {
+      lo = v ? s.q32[c * DP + k] : INFINITY;
+      hi = v ? s.q32[c * DP + k] : -INFINITY;
+      hm = v ? s.qbhi[c * DP + k] : INFINITY;
+      lm = v ? s.qblo[c * DP + k] : -INFINITY;
+    }
+    for (int o = 16; o; o >>= 1) {
+      lo = fminf(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+      hi = fmaxf(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+      hm = fminf(hm, __shfl_xor_sync(0xffffffffu, hm, o));
+      lm = fmaxf(lm, __shfl_xor_sync(0xffffffffu, lm, o));
+    }
+    if (lane == k) {
+      s.nclo[(size_t)node * DP + k] = lo;
+      s.nchi[(size_t)node * DP + k] = hi;
+      s.nhmin[(size_t)node * DP + k] = hm;
+      s.nlmax[(size_t)node * DP + k] = lm;
+    }
+  }
+}
+
 // boxes, least cluster size and instance range of every node of level L
-// (one warp per node, one lane per child)
+// (one warp per node)
 template <int DP>
 __global__ void k_tg_box(State s, int L, int K) {
   if (tg_idle(s, L)) return;
-  const int lane = threadIdx.x & 31;
   const int cnt = s.tinfo[L];
   const int mb = L ? s.tinfo[L - 1] : K;  // children of this level
-  const int *nch = s.nch + s.chb[L];
   for (int j = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; j < cnt;
-       j += (gridDim.x * blockDim.x) >> 5) {
-    const int c0 = nch[j];
-    int nc = nch[j + 1] - c0;
-    if (nc < 1 || nc > FAN) {
-      if (lane == 0) atomicOr(&s.ctr->err, ERR_TREE);
-      nc = max(1, min(nc, FAN));
-    }
-    const bool v = lane < nc && c0 + lane < mb;
-    // a child: a position-ordered record (L = 0) or a node of level L - 1
-    const size_t c = (size_t)(L ? s.lvl_base[L - 1] : 0) + (size_t)(v ? c0 + lane : c0);
-    int nm = v ? (L ? s.nnmin[c] : s.qsz[c]) : INT_MAX;
-    int il = v ? (L ? s.ninlo[c] : s.qinst[c]) : INT_MAX;
-    int ih = v ? (L ? s.ninhi[c] : s.qinst[c]) : INT_MIN;
-    for (int o = 16; o; o >>= 1) {
-      nm = min(nm, __shfl_xor_sync(0xffffffffu, nm, o));
-      il = min(il, __shfl_xor_sync(0xffffffffu, il, o));
-      ih = max(ih, __shfl_xor_sync(0xffffffffu, ih, o));
-    }
-    const int node = s.lvl_base[L] + j;
-    if (lane == 0) {
-      s.ninlo[node] = il;
-      s.ninhi[node] = ih;
-      s.nnmin[node] = nm;
-    }
-#pragma unroll
-    for (int k = 0; k < DP; ++k) {
-      float lo, hi, hm, lm;
-      if (L) {
-        lo = v ? s.nclo[c * DP + k] : INFINITY;
-        hi = v ? s.nchi[c * DP + k] : -INFINITY;
-        hm = v ? s.nhmin[c * DP + k] : INFINITY;
-        lm = v ? s.nlmax[c * DP + k] : -INFINITY;
-      } else {
-        lo = v ? s.q32[c * DP + k] : INFINITY;
-        hi = v ? s.q32[c * DP + k] : -INFINITY;
-        hm = v ? s.qbhi[c * DP + k] : INFINITY;
-        lm = v ? s.qblo[c * DP + k] : -INFINITY;
-      }
-      for (int o = 16; o; o >>= 1) {
-        lo = fminf(lo, __shfl_xor_sync(0xffffffffu, lo, o));
-        hi = fmaxf(hi, __shfl_xor_sync(0xffffffffu, hi, o));
-        hm = fminf(hm, __shfl_xor_sync(0xffffffffu, hm, o));
-        lm = fmaxf(lm, __shfl_xor_sync(0xffffffffu, lm, o));
-      }
-      if (lane == k) {
-        s.nclo[(size_t)node * DP + k] = lo;
-        s.nchi[(size_t)node * DP + k] = hi;
-        s.nhmin[(size_t)node * DP + k] = hm;
-        s.nlmax[(size_t)node * DP + k] = lm;
-      }
-    }
-  }
+       j += (gridDim.x * blockDim.x) >> 5)
+    tg_node_box<DP>(s, L, j, mb, threadIdx.x & 31);
 }
 
 // The upper levels in one block.  Once a level has at most TG_TAIL elements
@@ -546,65 +551,6 @@ __device__ int tail_scan(int v, int *total, int *ws) {
   *total = ws[31];
   __syncthreads();
   return pre + x - v;
-}
-
-// boxes of the nodes of level L (children: positions for L = 0), one warp per
-// node; the same reductions as k_tg_box
-template <int DP>
-__device__ void tail_boxes(State &s, int L, int mL, int mb) {
-  const int lane = threadIdx.x & 31;
-  const int *nch = s.nch + s.chb[L];
-  for (int j = threadIdx.x >> 5; j < mL; j += TG_TT / 32) {
-    const int c0 = nch[j];
-    int nc = nch[j + 1] - c0;
-    if (nc < 1 || nc > FAN) {
-      if (lane == 0) atomicOr(&s.ctr->err, ERR_TREE);
-      nc = max(1, min(nc, FAN));
-    }
-    const bool v = lane < nc && c0 + lane < mb;
-    const size_t c = (size_t)(L ? s.lvl_base[L - 1] : 0) + (size_t)(v ? c0 + lane : c0);
-    int nm = v ? (L ? s.nnmin[c] : s.qsz[c]) : INT_MAX;
-    int il = v ? (L ? s.ninlo[c] : s.qinst[c]) : INT_MAX;
-    int ih = v ? (L ? s.ninhi[c] : s.qinst[c]) : INT_MIN;
-    for (int o = 16; o; o >>= 1) {
-      nm = min(nm, __shfl_xor_sync(0xffffffffu, nm, o));
-      il = min(il, __shfl_xor_sync(0xffffffffu, il, o));
-      ih = max(ih, __shfl_xor_sync(0xffffffffu, ih, o));
-    }
-    const int node = s.lvl_base[L] + j;
-    if (lane == 0) {
-      s.ninlo[node] = il;
-      s.ninhi[node] = ih;
-      s.nnmin[node] = nm;
-    }
-#pragma unroll
-    for (int k = 0; k < DP; ++k) {
-      float lo, hi, hm, lm;
-      if (L) {
-        lo = v ? s.nclo[c * DP + k] : INFINITY;
-        hi = v ? s.nchi[c * DP + k] : -INFINITY;
-        hm = v ? s.nhmin[c * DP + k] : INFINITY;
-        lm = v ? s.nlmax[c * DP + k] : -INFINITY;
-      } else {
-        lo = v ? s.q32[c * DP + k] : INFINITY;
-        hi = v ? s.q32[c * DP + k] : -INFINITY;
-        hm = v ? s.qbhi[c * DP + k] : INFINITY;
-        lm = v ? s.qblo[c * DP + k] : -INFINITY;
-      }
-      for (int o = 16; o; o >>= 1) {
-        lo = fminf(lo, __shfl_xor_sync(0xffffffffu, lo, o));
-        hi = fmaxf(hi, __shfl_xor_sync(0xffffffffu, hi, o));
-        hm = fminf(hm, __shfl_xor_sync(0xffffffffu, hm, o));
-        lm = fmaxf(lm, __shfl_xor_sync(0xffffffffu, lm, o));
-      }
-      if (lane == k) {
-        s.nclo[(size_t)node * DP + k] = lo;
-        s.nchi[(size_t)node * DP + k] = hi;
-        s.nhmin[(size_t)node * DP + k] = hm;
-        s.nlmax[(size_t)node * DP + k] = lm;
-      }
-    }
-  }
 }
 
 // levels L0 .. nl - 1 in one block (L0: the first level the host leaves to
@@ -694,7 +640,8 @@ __global__ void __launch_bounds__(TG_TT) k_tg_tail(State s, const int32_t *order
       if (mL <= FAN) s.tinfo[TI_TOP] = L + 1;
     }
     __syncthreads();
-    tail_boxes<DP>(s, L, mL, m);
+    for (int j = threadIdx.x >> 5; j < mL; j += TG_TT / 32)
+      tg_node_box<DP>(s, L, j, m, threadIdx.x & 31);
     __syncthreads();
     if (mL <= FAN) break;
     m = mL;
